@@ -1,0 +1,289 @@
+"""ctypes front end of the FP64 oracle (``bem_oracle.c``) plus the adaptive loop.
+
+TEST INFRASTRUCTURE ONLY.  Each function names the passage of Betcke, Haberl and
+Praetorius (arXiv 1901.08393) it follows; the arithmetic lives in bem_oracle.c
+(plain FP64 C, no FMA contraction) and, for the cross-check solve, in LAPACK via
+numpy (a library primitive).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bem_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "liborc.so")
+_lib = None
+_lock = threading.Lock()
+
+__all__ = [
+    "build", "lib", "gauss_legendre01", "radon7", "geometry", "pair_far", "pair_identical",
+    "pair_edge", "pair_vertex", "pair_type", "entry", "entries", "assemble", "pcg",
+    "solve_cholesky", "capacity", "zz", "dorfler", "canonical", "refine", "num_threads",
+    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA",
+]
+
+
+def build(force: bool = False) -> str:
+    """Compile bem_oracle.c into liborc.so (gcc, OpenMP, no FP contraction)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB_PATH)
+            d, i64, i32, vp = C.c_double, C.c_int64, C.c_int, C.c_void_p
+            L.orc_gauss_legendre01.argtypes = [i32, vp, vp]
+            L.orc_radon7.argtypes = [vp, vp]
+            L.orc_geometry.argtypes = [vp, i64, vp, i64, vp, vp]
+            L.orc_pair_far.argtypes = [vp, vp]
+            L.orc_pair_far.restype = d
+            L.orc_pair_identical.argtypes = [vp, i32]
+            L.orc_pair_identical.restype = d
+            L.orc_pair_edge.argtypes = [vp, vp, i32]
+            L.orc_pair_edge.restype = d
+            L.orc_pair_vertex.argtypes = [vp, vp, i32]
+            L.orc_pair_vertex.restype = d
+            L.orc_pair_type.argtypes = [vp, i64, i64]
+            L.orc_entry.argtypes = [vp, vp, i64, i64, i32]
+            L.orc_entry.restype = d
+            L.orc_entries.argtypes = [vp, vp, vp, vp, i64, i32, vp]
+            L.orc_assemble.argtypes = [vp, i64, vp, i64, i32, vp]
+            L.orc_pcg.argtypes = [vp, i64, vp, vp, vp, d, i32, i32, vp, vp]
+            L.orc_matvec.argtypes = [vp, i64, vp, vp]
+            L.orc_capacity.argtypes = [vp, vp, i64]
+            L.orc_capacity.restype = d
+            L.orc_zz.argtypes = [vp, i64, vp, i64, vp, i32, vp, vp]
+            L.orc_dorfler.argtypes = [vp, i64, d, vp, vp]
+            L.orc_canonical.argtypes = [vp, vp, i64, vp, vp]
+            L.orc_refine.argtypes = [vp, i64, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]
+            L.orc_num_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def num_threads() -> int:
+    return int(lib().orc_num_threads())
+
+
+def gauss_legendre01(n: int):
+    x, w = np.zeros(n), np.zeros(n)
+    lib().orc_gauss_legendre01(n, _p(x), _p(w))
+    return x, w
+
+
+def radon7():
+    """Radon's 7-point degree-5 triangle rule: barycentric points (7,3), weights (7,)."""
+    b, w = np.zeros((7, 3)), np.zeros(7)
+    lib().orc_radon7(_p(b), _p(w))
+    return b, w
+
+
+def geometry(verts, tris):
+    """(area, diam) per triangle, in the exact operation order the GPU also uses."""
+    v, t = _f64(verts), _i32(tris)
+    N = t.shape[0]
+    a, d = np.zeros(N), np.zeros(N)
+    lib().orc_geometry(_p(v), v.shape[0], _p(t), N, _p(a), _p(d))
+    return a, d
+
+
+def pair_far(P, Q):
+    """int_P int_Q 1/(4 pi |x-y|) by the 7x7 Radon product rule."""
+    return float(lib().orc_pair_far(_p(_f64(P)), _p(_f64(Q))))
+
+
+def pair_identical(P, n=4):
+    return float(lib().orc_pair_identical(_p(_f64(P)), n))
+
+
+def pair_edge(P, Q, n=4):
+    """P = (A,B,C), Q = (A,B,D) share the edge AB (same vertex order)."""
+    return float(lib().orc_pair_edge(_p(_f64(P)), _p(_f64(Q)), n))
+
+
+def pair_vertex(P, Q, n=4):
+    """P = (A,B,C), Q = (A,D,E) share the vertex A."""
+    return float(lib().orc_pair_vertex(_p(_f64(P)), _p(_f64(Q)), n))
+
+
+def pair_type(tris, i, j) -> int:
+    t = _i32(tris)
+    return int(lib().orc_pair_type(_p(t), i, j))
+
+
+def entry(verts, tris, i, j, n=4) -> float:
+    v, t = _f64(verts), _i32(tris)
+    return float(lib().orc_entry(_p(v), _p(t), i, j, n))
+
+
+def entries(verts, tris, I, J, n=4):
+    v, t = _f64(verts), _i32(tris)
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    out = np.zeros(I.shape[0])
+    lib().orc_entries(_p(v), _p(t), _p(I), _p(J), I.shape[0], n, _p(out))
+    return out
+
+
+def assemble(verts, tris, n=4):
+    """Dense Galerkin matrix V (Eq. 2.4 on primal P0, App. A Eq. A.1), FP64."""
+    v, t = _f64(verts), _i32(tris)
+    N = t.shape[0]
+    out = np.zeros((N, N))
+    lib().orc_assemble(_p(v), v.shape[0], _p(t), N, n, _p(out))
+    return out
+
+
+def pcg(A, b, x0=None, tol=1e-12, maxit=10000, precond=1):
+    """Jacobi (precond=1) or plain (0) CG on the SPD system A x = b."""
+    A = _f64(A)
+    b = _f64(b)
+    N = b.shape[0]
+    x = np.zeros(N)
+    its = C.c_int(0)
+    rr = C.c_double(0.0)
+    x0a = _f64(x0) if x0 is not None else None
+    rc = lib().orc_pcg(_p(A), N, _p(b), _p(x0a), _p(x), tol, maxit, precond,
+                       C.byref(its), C.byref(rr))
+    return x, int(its.value), float(rr.value), int(rc)
+
+
+def solve_cholesky(A, b):
+    """Cross-check solve through LAPACK's Cholesky (fails if A is not SPD)."""
+    L = np.linalg.cholesky(A)
+    y = np.linalg.solve(L, b)
+    return np.linalg.solve(L.T, y)
+
+
+def capacity(area, x) -> float:
+    """Cap_l = (1/4pi) <Phi_l, 1> = (1/4pi) sum |T_i| x_i   (Eq. 2.8)."""
+    a, xx = _f64(area), _f64(x)
+    return float(lib().orc_capacity(_p(a), _p(xx), a.shape[0]))
+
+
+def zz(verts, tris, x, h_mode=0, with_scale=False):
+    """ZZ-type indicators eta(T)^2 (Eq. 1.6, primal-P0 reading); with_scale also
+    returns sum_T h_T |T| x_T^2 / 12."""
+    v, t, xx = _f64(verts), _i32(tris), _f64(x)
+    N = t.shape[0]
+    out = np.zeros(N)
+    sc = C.c_double(0.0)
+    lib().orc_zz(_p(v), v.shape[0], _p(t), N, _p(xx), h_mode, _p(out), C.byref(sc))
+    return (out, float(sc.value)) if with_scale else out
+
+
+# An estimator whose total is below this fraction of sum h|T|x^2/12 is rounding
+# noise of a solution that is constant up to rounding (a fully symmetric mesh).
+VANISHING_ETA = 1e-20
+
+
+def mark(eta2, scale, theta=0.5):
+    """Alg. 1 (iii): Doerfler marking; when the estimator vanishes up to rounding
+    the empty set satisfies Eq. 2.6 and the step refines uniformly instead."""
+    if not np.sum(eta2) > VANISHING_ETA * scale:
+        return np.ones(eta2.shape[0], dtype=np.uint8)
+    return dorfler(eta2, theta)
+
+
+def dorfler(eta2, theta=0.5):
+    """Doerfler marking (Eq. 2.6); returns a uint8 flag per element."""
+    e = _f64(eta2)
+    N = e.shape[0]
+    m = np.zeros(N, dtype=np.uint8)
+    nm = C.c_int64(0)
+    lib().orc_dorfler(_p(e), N, theta, _p(m), C.byref(nm))
+    return m
+
+
+def canonical(verts, tris, ref_edge=None):
+    """Rotate triangles so that the reference edge is local edge 0 (Fig. 3)."""
+    v, t = _f64(verts), _i32(tris)
+    out = np.zeros_like(t)
+    re = np.ascontiguousarray(ref_edge, dtype=np.uint8) if ref_edge is not None else None
+    lib().orc_canonical(_p(v), _p(t), t.shape[0], _p(re), _p(out))
+    return out
+
+
+def refine(verts, tris, marked, bisec3=False):
+    """NVB refinement with closure (Fig. 3).  Returns (verts, tris, parent, kept)."""
+    v, t = _f64(verts), _i32(tris)
+    M, N = v.shape[0], t.shape[0]
+    mk = np.ascontiguousarray(marked, dtype=np.uint8)
+    vo = np.zeros((M + 3 * N, 3))
+    to = np.zeros((4 * N, 3), dtype=np.int32)
+    par = np.zeros(4 * N, dtype=np.int32)
+    kept = np.zeros(4 * N, dtype=np.uint8)
+    Mo, No = C.c_int64(0), C.c_int64(0)
+    lib().orc_refine(_p(v), M, _p(t), N, _p(mk), int(bisec3), _p(vo), _p(to), _p(par),
+                     _p(kept), C.byref(Mo), C.byref(No))
+    Mo, No = Mo.value, No.value
+    return vo[:Mo].copy(), to[:No].copy(), par[:No].copy(), kept[:No].copy()
+
+
+def solve_capacity(verts, tris, n_ss=4, tol=1e-12, maxit=20000, precond=1, x0=None):
+    """Assemble V, solve V x = |T| by PCG, return (cap, x, its, V)."""
+    V = assemble(verts, tris, n_ss)
+    area, _ = geometry(verts, tris)
+    x, its, rr, rc = pcg(V, area, x0=x0, tol=tol, maxit=maxit, precond=precond)
+    return capacity(area, x), x, its, V
+
+
+def adaptive_run(verts, tris, theta=0.5, max_N=2000, n_ss=4, tol=1e-12, h_mode=0,
+                 max_levels=100, callback=None):
+    """Algorithm 1 on the primal P0 space: solve -> estimate -> mark -> refine
+    until the mesh has at least max_N triangles; the previous level's solution,
+    copied to the children, starts the next solve.  Returns one record per level."""
+    t = canonical(verts, tris)
+    v = _f64(verts)
+    hist = []
+    x_prev = None
+    for lvl in range(max_levels):
+        cap, x, its, _ = solve_capacity(v, t, n_ss=n_ss, tol=tol, x0=x_prev)
+        eta2, scale = zz(v, t, x, h_mode, with_scale=True)
+        rec = {"level": lvl, "N": t.shape[0], "M": v.shape[0], "cap": cap, "its": its,
+               "eta2_total": float(np.sum(eta2)), "x": x, "eta2": eta2,
+               "verts": v, "tris": t}
+        if t.shape[0] >= max_N:
+            hist.append(rec)
+            if callback:
+                callback(rec)
+            break
+        m = mark(eta2, scale, theta)
+        rec["marked"] = m
+        hist.append(rec)
+        if callback:
+            callback(rec)
+        v, t, parent, kept = refine(v, t, m)
+        x_prev = x[parent]
+    return hist
+
+
+FOUR_PI = 4.0 * math.pi

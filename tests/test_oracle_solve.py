@@ -1,0 +1,103 @@
+"""Pins of the oracle's Galerkin matrix, solve and capacity (Eq. 2.4-2.8, Prop. 1,
+Corollary of App. A) against invariants and values the paper prints."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1901_08393_gb300 import inputs
+from tests._golden import capacity_reference
+
+REF = capacity_reference()
+
+
+def _cap(m, **kw):
+    t = O.canonical(m.verts, m.tris)
+    return O.solve_capacity(m.verts, t, **kw)
+
+
+def test_V_symmetric_positive_definite():
+    m = inputs.cube_mesh(2)
+    cap, x, its, V = _cap(m)
+    assert np.array_equal(V, V.T)
+    assert np.all(V > 0)
+    np.linalg.cholesky(V)  # raises if not SPD
+    assert np.all(np.diag(V) >= V.max(axis=1) * (1 - 1e-15))
+
+
+def test_pcg_matches_cholesky():
+    m = inputs.workload_polycube_adaptive()
+    t = O.canonical(m.verts, m.tris)
+    V = O.assemble(m.verts, t)
+    area, _ = O.geometry(m.verts, t)
+    x, its, rr, rc = O.pcg(V, area, tol=1e-13)
+    assert rc == 0 and rr <= 1e-13
+    xc = O.solve_cholesky(V, area)
+    assert np.max(np.abs(x - xc)) / np.max(np.abs(xc)) < 1e-10
+    x0, its0, _, rc0 = O.pcg(V, area, tol=1e-13, precond=0)
+    assert rc0 == 0 and np.max(np.abs(x0 - xc)) / np.max(np.abs(xc)) < 1e-10
+
+
+def test_cube_sequence_increases_below_reference():
+    """Nested uniform cube meshes: Cap_l increases (Corollary, App. A) and stays
+    below the reference value of Sec. 3.1 (Prop. 1) and inside Polya's bounds."""
+    caps = [_cap(inputs.cube_mesh(n))[0] for n in (1, 2, 4, 8)]
+    assert all(b > a for a, b in zip(caps, caps[1:]))
+    assert caps[-1] < REF["unit_cube_capacity"]
+    assert REF["polya_lower"] < caps[2] < REF["polya_upper"]
+    # O(N^{-2/3}) uniform rate (Sec. 3.1): error shrinks by about 4^{2/3} per level
+    err = [REF["unit_cube_capacity"] - c for c in caps]
+    ratios = [err[i] / err[i + 1] for i in range(1, 3)]
+    assert all(2.0 < r < 3.5 for r in ratios), ratios
+
+
+def test_sphere_limit():
+    """Inscribed polyhedra of the unit sphere: 0 < Cap_h < 1 and Cap_h -> 1 (Sec. 1.2)."""
+    caps = [_cap(inputs.icosphere_mesh(k, 1.0))[0] for k in (2, 4, 8)]
+    assert all(0 < c < REF["sphere_capacity_over_radius"] for c in caps)
+    assert all(b > a for a, b in zip(caps, caps[1:]))
+    assert 1 - caps[-1] < 0.01
+    c2 = _cap(inputs.icosphere_mesh(4, 2.5))[0]
+    assert abs(c2 / (2.5 * caps[1]) - 1) < 1e-12
+
+
+def test_scaling_and_rigid_motion():
+    m = inputs.workload_polycube_adaptive()
+    c1 = _cap(m)[0]
+    c2 = _cap(inputs.Mesh(m.verts * 2.0, m.tris))[0]
+    assert abs(c2 / (2 * c1) - 1) < 1e-14
+    R = inputs.random_rotation(inputs.SplitMix64(7))
+    c3 = _cap(inputs.transformed(m, R, 1.0, (0.3, -1.0, 2.0)))[0]
+    assert abs(c3 / c1 - 1) < 1e-10
+
+
+def test_prolongation_pythagoras():
+    """Corollary (App. A): with nested P0 spaces and the coarse Galerkin matrix
+    P^T V_f P, 4 pi (Cap_f - Cap_c) = |||Phi_f - Phi_c|||^2."""
+    m = inputs.cube_mesh(2)
+    t = O.canonical(m.verts, m.tris)
+    rng = np.random.default_rng(0)
+    marked = (rng.random(m.N) < 0.3).astype(np.uint8)
+    vf, tf, parent, kept = O.refine(m.verts, t, marked)
+    Vf = O.assemble(vf, tf)
+    af, _ = O.geometry(vf, tf)
+    P = np.zeros((tf.shape[0], m.N))
+    P[np.arange(tf.shape[0]), parent] = 1.0
+    Vc = P.T @ Vf @ P
+    ac = P.T @ af
+    xf = O.solve_cholesky(Vf, af)
+    xc = O.solve_cholesky(Vc, ac)
+    capf = O.capacity(af, xf)
+    capc = float(ac @ xc) / (4 * math.pi)
+    e = xf - P @ xc
+    assert capf > capc > 0
+    assert abs(4 * math.pi * (capf - capc) - e @ Vf @ e) < 1e-10 * (capf - capc)
+
+
+def test_capacity_positive_and_rhs():
+    m = inputs.tetra_mesh(3)
+    cap, x, its, V = _cap(m)
+    assert cap > 0 and np.all(x > 0)  # equilibrium charge density is positive
+    area, _ = O.geometry(m.verts, O.canonical(m.verts, m.tris))
+    assert abs(O.capacity(area, x) - cap) == 0.0
