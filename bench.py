@@ -1,0 +1,315 @@
+#!/usr/bin/env python
+"""Benchmark of the adaptive BEM capacity hot path on GB300.
+
+Workload (one "step" = one complete adaptive capacity computation, Alg. 1):
+seeded random polycube (occupied voxels of a 6x6x6 grid, p = 0.5, seed 1,
+largest face-connected component, cavities filled), boundary quads split into 2
+triangles; ZZ estimate + Doerfler marking (theta = 0.5) + newest-vertex bisection
+until N >= 20,000 triangles; every level assembles V (7x7 Radon far field,
+Sauter-Schwab order 4 near field, entries of unrefined pairs reused), solves
+V x = |T| by Jacobi-PCG to 1e-10 and reduces Cap, all in FP64.
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the
+host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "V-assembly Gpairs/s; capacity solves/s at 1e-6 rel err vs FP64; p99 latency"
+UNIT = "capacity solves/s"
+WORKLOAD = ("adaptive polycube: 6^3 voxels p=0.5 seed 1, ZZ + Doerfler theta=0.5 + NVB "
+            "until N>=20000, FP64 (7x7 Radon far field, Sauter-Schwab order 4, Jacobi-PCG 1e-10)")
+MAX_N = 20000
+THETA = 0.5
+TOL = 1e-10
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (recipe table)
+FAR_FLOPS_PER_ENTRY = 49 * 11 + 16  # see the design doc: per point pair 3 sub, 5 for r^2, rsqrt, 2 accumulate
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+                power.append(float(c[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_oracle(max_n=MAX_N):
+    """One complete adaptive run of the FP64 CPU oracle; returns (seconds, history)."""
+    import oracle
+    from paper_1901_08393_gb300 import inputs
+
+    m = inputs.workload_polycube_adaptive()
+    t = time.perf_counter()
+    hist = oracle.adaptive_run(m.verts, m.tris, theta=THETA, max_N=max_n, tol=TOL)
+    return time.perf_counter() - t, hist
+
+
+def reference_arm(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    cores = oracle.num_threads()
+    for _ in range(args.warmup):
+        run_oracle()
+    times = []
+    hist = None
+    for _ in range(args.steps):
+        dt, hist = run_oracle()
+        times.append(dt)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "final_N": hist[-1]["N"], "levels": len(hist)},
+        "p99_latency_ms": 1e3 * max(times),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "complete adaptive runs of the workload, FP64 C/OpenMP oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--max-n", type=int, default=MAX_N, help="smaller case of the same workload (profiling)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1901_08393_gb300 import bem, build, inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    ctx = bem.Context()
+    m = inputs.workload_polycube_adaptive()
+    mesh = bem.Mesh.upload(ctx, m.verts, m.tris)  # resident input for the device-timed value
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL)
+        return recs
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    ctx.profile(True)
+    launches0 = ctx.launch_count()
+    lat = []
+    recs = None
+    barrier()
+    clocks.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        flush.fill_(1)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        recs = step()
+        b.record(stream)
+        lat.append((a, b))
+    ev1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    total_ms = ev0.elapsed_time(ev1)
+    if ws > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
+    far_n, far_ms, far_units = ctx.profile_read(bem.KERNEL_FAR)
+    mv_n, mv_ms, mv_units = ctx.profile_read(bem.KERNEL_MATVEC)
+    nr_n, nr_ms, nr_units = ctx.profile_read(bem.KERNEL_NEAR)
+    ctx.profile(False)
+    peaks, peak_src = _peaks()
+
+    # entries produced and assembly phase time
+    pairs = sum(r["N"] * r["N"] for r in recs)
+    asm_ms = sum(r["ms_assemble"] for r in recs)
+    solve_ms = sum(r["ms_solve"] for r in recs)
+    adapt_ms = sum(r["ms_adapt"] for r in recs)
+
+    # dominant kernel roofline
+    if far_ms >= mv_ms:
+        flops = far_units * FAR_FLOPS_PER_ENTRY / max(far_n, 1)
+        avg_s = far_ms / max(far_n, 1) / 1e3
+        achieved = flops / avg_s / 1e12
+        roof = {"kernel": "k_far_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate of the recipe table (no measured FP64 peak)",
+                "launches": far_n}
+    else:
+        bytes_ = mv_units / max(mv_n, 1)
+        avg_s = mv_ms / max(mv_n, 1) / 1e3
+        achieved = bytes_ / avg_s / 1e9
+        roof = {"kernel": "k_matvec<double>", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{peak_src} hbm_gbs", "launches": mv_n}
+    roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / total_ms
+
+    # end to end through the public API with host buffers
+    import ctypes
+
+    e2e_t = []
+    h2d = m.verts.nbytes + m.tris.nbytes
+    d2h = 0
+    for _ in range(0 if args.no_e2e else args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mh = bem.Mesh.upload(ctx, m.verts, m.tris)
+        r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL)
+        cap_final = r2[-1]["cap"]
+        mh.close()
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+        d2h = len(r2) * ctypes.sizeof(bem.LevelRecord)
+    e2e_val = args.steps / sum(e2e_t) if e2e_t else None
+    if ws > 1:
+        t = torch.tensor([sum(e2e_t)], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = args.steps * ws / float(t.item())
+
+    value = args.steps * ws / (total_ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "final_N": recs[-1]["N"], "levels": len(recs),
+                   "cap_final": recs[-1]["cap"], "parallelism": f"replicas x{ws}",
+                   "l2": "256 MB buffer written before every step; V (up to 3.2 GB) exceeds L2"},
+        "p50_latency_ms": lat_ms[len(lat_ms) // 2], "p99_latency_ms": lat_ms[min(len(lat_ms) - 1,
+                                                                                   math.ceil(0.99 * len(lat_ms)) - 1)],
+        "assembly_gpairs_per_s": pairs / (asm_ms / 1e3) / 1e9,
+        "far_kernel_gpairs_per_s": far_units / (far_ms / 1e3) / 1e9 if far_ms else None,
+        "phase_ms_per_step": {"assemble": asm_ms, "solve": solve_ms, "adapt": adapt_ms},
+        "kernel_ms_per_step": {"far": far_ms / args.steps, "near": nr_ms / args.steps,
+                               "matvec": mv_ms / args.steps},
+        "matvec_gbs": mv_units / (mv_ms / 1e3) / 1e9 if mv_ms else None,
+        "levels": [{"N": r["N"], "its": r["iterations"], "marked": r["n_marked"],
+                    "ms": round(r["ms_assemble"] + r["ms_solve"] + r["ms_adapt"], 3)} for r in recs],
+        "roofline": roof,
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if args.max_n != MAX_N:
+        line["config"]["workload"] += f" [reduced case: N>={args.max_n}]"
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        dt, hist = run_oracle()
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"one complete adaptive run of the workload ({len(hist)} levels, "
+                                          f"final N={hist[-1]['N']}), FP64 C/OpenMP oracle",
+                                "cap_final": hist[-1]["cap"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

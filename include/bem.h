@@ -1,0 +1,239 @@
+/*
+ * bem.h -- C ABI of the GB300 (sm_103a) dense P0 single-layer BEM capacity library.
+ *
+ * The library computes the electrostatic capacity of a closed polyhedral surface
+ * Gamma by the Galerkin boundary element method of Betcke, Haberl and Praetorius,
+ * "Adaptive boundary element methods for the computation of the electrostatic
+ * capacity on complex polyhedra" (arXiv 1901.08393), in its primal piecewise-
+ * constant form (App. A, Eq. A.1):
+ *
+ *   V[i][j] = (1/4pi) int_Ti int_Tj 1/|x-y| dy dx          (Eq. 2.1, 2.4-2.5)
+ *   solve V x = b, b[i] = |T_i|                             (Eq. 2.5 with f = 1)
+ *   Cap = (1/4pi) sum_i |T_i| x_i                           (Eq. 2.8)
+ *   eta(T)^2 = diam(T) ||x_T - I x||^2_{L2(T)}              (Eq. 1.6, Sec. 2.4)
+ *   Doerfler marking, newest-vertex bisection               (Eq. 2.6, Alg. 1, Fig. 3)
+ *
+ * Conventions (all entry points):
+ *   - Every call returns a bem_status: 0 on success, a negative code otherwise;
+ *     bem_last_error(ctx) then holds a message.  No C++ exception crosses the ABI.
+ *   - Handles (bem_ctx, bem_mesh, bem_operator) are owned by the library and freed
+ *     by the matching *_destroy.  Arrays passed in are owned by the caller and only
+ *     borrowed for the duration of the call; the library never keeps a pointer.
+ *   - Array arguments may be host or device (CUDA) memory; the library inspects
+ *     each pointer (cudaPointerGetAttributes) and copies as needed.
+ *   - All GPU work is enqueued on the context's CUDA stream.  Calls that return
+ *     values through host pointers synchronise that stream before returning.
+ *   - Layouts: vertices M x 3 float64 row-major (x,y,z per vertex); triangles
+ *     N x 3 int32 row-major, 0-based vertex indices.  V (float64 or float32 by
+ *     precision) lives on the device, row-major with each row padded to a multiple
+ *     of 32 entries; bem_operator_read returns compact row-major blocks.
+ *   - Meshes must be closed (every edge shared by an even number >= 2 of
+ *     triangles; non-manifold edges are allowed) with non-degenerate triangles;
+ *     otherwise BEM_ERR_MESH.
+ */
+#ifndef BEM_GB300_H
+#define BEM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t bem_status;
+#define BEM_OK 0
+#define BEM_ERR_INVALID (-1)        /* bad argument (null handle, size out of range) */
+#define BEM_ERR_OOM (-2)            /* device allocation failed or HBM budget exceeded */
+#define BEM_ERR_NOT_CONVERGED (-3)  /* Krylov solve hit max_it before the tolerance */
+#define BEM_ERR_MESH (-4)           /* mesh not closed, degenerate or too irregular */
+#define BEM_ERR_CUDA (-5)           /* CUDA runtime error */
+
+typedef struct bem_ctx bem_ctx;
+typedef struct bem_mesh bem_mesh;
+typedef struct bem_operator bem_operator;
+
+/* Storage/arithmetic precision of V. */
+#define BEM_PREC_F64 0  /* V stored and applied in FP64 */
+#define BEM_PREC_F32 1  /* V stored in FP32 (near field computed in FP64, rounded) */
+
+typedef struct {
+    int32_t precision; /* BEM_PREC_F64 or BEM_PREC_F32 */
+    int32_t ss_order;  /* Gauss-Legendre points per variable for touching pairs (2..16, default 4;
+                          the radial variables are integrated exactly, which equals the
+                          n-point rule in them for n >= 2) */
+} bem_assembly_opts;
+
+#define BEM_PRECOND_NONE 0
+#define BEM_PRECOND_JACOBI 1
+
+typedef struct {
+    double tol;            /* relative residual ||b - V x|| / ||b|| to reach (e.g. 1e-10) */
+    int32_t max_it;        /* iteration cap (inner iterations for FP32 operators) */
+    int32_t precond;       /* BEM_PRECOND_NONE or BEM_PRECOND_JACOBI (diag(V), Sec. 3) */
+    int32_t max_outer;     /* FP32 operators: FP64 iterative-refinement sweeps (default 20) */
+    double inner_tol;      /* FP32 operators: relative tolerance of each inner solve (default 1e-5) */
+} bem_solve_opts;
+
+typedef struct {
+    int32_t iterations;    /* CG iterations (summed over refinement sweeps) */
+    int32_t outer;         /* refinement sweeps (1 for FP64 operators) */
+    double relres;         /* final ||b - V x|| / ||b|| in FP64 */
+    int32_t converged;     /* 1 if relres <= tol */
+} bem_solve_info;
+
+/* ---------------------------------------------------------------- context */
+/* Create a context on the current CUDA device.  cuda_stream: a cudaStream_t (NULL:
+ * the legacy default stream).  hbm_budget_bytes: device bytes the context may
+ * allocate in total (<= 0: no limit).  */
+bem_status bem_context_create(void *cuda_stream, int64_t hbm_budget_bytes, bem_ctx **out);
+bem_status bem_context_destroy(bem_ctx *ctx);
+/* Last error message of the context (never NULL; "" if none). */
+const char *bem_last_error(const bem_ctx *ctx);
+/* Device bytes currently held by handles of this context. */
+bem_status bem_context_memory(const bem_ctx *ctx, int64_t *bytes_in_use);
+
+/* ---------------------------------------------------------------- mesh */
+/* Upload a triangulation T_l of Gamma into N flat triangles with M vertices
+ * (Sec. 2.1).  ref_edge (nullable, N bytes in 0..2) names each triangle's
+ * reference edge for newest-vertex bisection (edge (v_e, v_{e+1 mod 3})); NULL
+ * selects the longest edge, ties to the lowest local index.  Triangles are stored
+ * rotated so that the reference edge comes first (orientation kept).
+ * Also computes per-triangle area, diameter, quadrature points, the
+ * vertex-to-triangle incidence and the list of touching pairs. */
+bem_status bem_mesh_upload(bem_ctx *ctx, const double *verts, int64_t M, const int32_t *tris,
+                           int64_t N, const uint8_t *ref_edge, bem_mesh **out);
+bem_status bem_mesh_destroy(bem_mesh *mesh);
+/* Sizes; n_near = number of touching ordered pairs i != j (shared vertex or edge). */
+bem_status bem_mesh_info(const bem_mesh *mesh, int64_t *M, int64_t *N, int64_t *n_near);
+/* Copy the stored (rotated) mesh out.  Any pointer may be NULL.  parent/kept are
+ * filled for meshes made by bem_refine (parent = source triangle index in the
+ * coarser mesh; kept = 1 if the triangle is that source triangle unchanged) and
+ * are -1/0 for uploaded meshes. */
+bem_status bem_mesh_download(const bem_mesh *mesh, double *verts, int32_t *tris,
+                             int32_t *parent, uint8_t *kept);
+/* Per-triangle area |T| and diam(T) (longest edge), FP64, in the fixed operation
+ * order (no fused multiply-add) shared with the estimator. */
+bem_status bem_mesh_geometry(const bem_mesh *mesh, double *area, double *diam);
+
+/* ---------------------------------------------------------------- operator */
+/* Assemble V on P0(T_l) (Eq. 2.4-2.5): pairs without a common vertex by the 7x7
+ * product of Radon's degree-5 rule; pairs with a common vertex, a common edge, and
+ * identical pairs by Sauter-Schwab regularising transformations in FP64 (the
+ * paper defers these integrals to the Sauter-Schwab textbook).  V stays resident
+ * on the device.  opts may be NULL (FP64, order 4). */
+bem_status bem_assemble_V(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out);
+/* Same operator for a mesh made by bem_refine from coarse's mesh: entries of pairs
+ * of unrefined triangles are copied from coarse (their geometry and adjacency are
+ * unchanged under conforming NVB), the others are computed.  Bit-identical to
+ * bem_assemble_V on the same mesh. */
+bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse,
+                                 const bem_assembly_opts *opts, bem_operator **out);
+bem_status bem_operator_destroy(bem_operator *op);
+bem_status bem_operator_info(const bem_operator *op, int64_t *N, int32_t *precision);
+/* Copy the block V[i0:i0+ni, j0:j0+nj] (row-major, ni x nj, in the operator's
+ * precision) into dst (host or device). */
+bem_status bem_operator_read(const bem_operator *op, int64_t i0, int64_t ni, int64_t j0,
+                             int64_t nj, void *dst);
+/* out[k] = V[I[k]][J[k]] as FP64 for K sampled entries (arrays host or device). */
+bem_status bem_operator_entries(const bem_operator *op, const int64_t *I, const int64_t *J,
+                                int64_t K, double *out);
+/* y = V x, FP64 vectors of length N (host or device). */
+bem_status bem_operator_matvec(const bem_operator *op, const double *x, double *y);
+
+/* ---------------------------------------------------------------- solve */
+/* Solve V x = b, b[i] = |T_i|, by preconditioned CG (Jacobi: diag(V), the paper's
+ * "diag" comparison preconditioner, Sec. 3), and return Cap = (1/4pi) b.x
+ * (Eq. 2.8).  FP64 operators: CG in FP64.  FP32 operators: FP64 iterative
+ * refinement (residual in FP64 against the stored V) around FP32-matvec inner CG.
+ * x0 (nullable) starts the iteration; phi_out (nullable) receives x.  Returns
+ * BEM_ERR_NOT_CONVERGED (with cap and info filled) if tol is not reached. */
+bem_status bem_solve_capacity(bem_operator *op, const bem_solve_opts *opts, const double *x0,
+                              double *cap_out, double *phi_out, bem_solve_info *info);
+
+/* ---------------------------------------------------------------- adaptivity */
+/* ZZ-type indicators (Eq. 1.6), primal-P0 reading: the nodal value at vertex z is
+ * the area-weighted mean of phi over the triangles at z (summed in ascending
+ * triangle order), I phi the S1 interpolant of those values, and
+ * eta(T)^2 = h_T |T|/12 (sum_k d_k^2 + (sum_k d_k)^2), d_k = u_{z_k} - phi_T, in
+ * that operation order without fused multiply-add (bit-identical to a plain
+ * IEEE-754 evaluation).  h_mode 0: h_T = diam(T) (Eq. 1.6); 1: h_T = |T|^{1/2}.
+ * totals (nullable, 2 doubles): [sum_T eta^2, sum_T h_T |T| phi_T^2 / 12]. */
+bem_status bem_zz_estimate(bem_mesh *mesh, const double *phi, int32_t h_mode, double *eta2_out,
+                           double *totals);
+/* Doerfler marking (Eq. 2.6): order the elements by decreasing eta^2 compared in
+ * single precision (ties by index), accumulate eta^2 in FP64 in that order, mark
+ * the shortest prefix reaching theta * total (total = the same ordered sum), and
+ * extend it over elements whose single-precision indicator equals the last
+ * marked one.  marked: N bytes (1 = marked).  Runs on the device. */
+bem_status bem_dorfler(bem_ctx *ctx, const double *eta2, int64_t N, double theta, uint8_t *marked,
+                       int64_t *n_marked);
+#define BEM_REFINE_BISEC3 1 /* a marked triangle marks all three edges (default: reference edge) */
+/* Newest-vertex bisection with closure (Fig. 3): marked triangles bisect their
+ * reference edge (or all edges with BEM_REFINE_BISEC3); repeatedly, a triangle
+ * with a marked edge marks its reference edge; each marked edge gets one new
+ * vertex 0.5 (a + b), numbered after the old ones by first appearance in
+ * (triangle, local edge) order; triangle (a,b,c) with midpoints m0 (ab), m1 (bc),
+ * m2 (ca) becomes
+ *   ab: (c,a,m0) (b,c,m0)          ab+bc: (c,a,m0) (m0,b,m1) (c,m0,m1)
+ *   ab+ca: (m0,c,m2) (a,m0,m2) (b,c,m0)
+ *   ab+bc+ca: (m0,c,m2) (a,m0,m2) (m0,b,m1) (c,m0,m1)
+ * The new mesh lists the unrefined triangles first (in order), then the children,
+ * parent by parent.  marked: N bytes.  Runs on the device. */
+bem_status bem_refine(bem_mesh *mesh, const uint8_t *marked, int32_t flags, bem_mesh **refined_out);
+/* bem_dorfler followed by bem_refine. */
+bem_status bem_mark_refine(bem_mesh *mesh, const double *eta2, double theta, int32_t flags,
+                           uint8_t *marked_out, int64_t *n_marked, bem_mesh **refined_out);
+
+/* ---------------------------------------------------------------- adaptive loop */
+typedef struct {
+    int64_t N, M;          /* mesh size of this level */
+    double cap;            /* Cap_l (Eq. 2.8) */
+    double eta2_total;     /* sum of the ZZ indicators */
+    int32_t iterations;    /* CG iterations */
+    int32_t n_marked;      /* elements marked for the next level (0 on the last) */
+    double relres;
+    double ms_assemble, ms_solve, ms_adapt; /* device time per phase (CUDA events) */
+} bem_level_record;
+
+typedef struct {
+    double theta;           /* Doerfler parameter (Alg. 1), default 0.5 */
+    int64_t max_N;          /* stop at the first level with N >= max_N */
+    int32_t max_levels;     /* hard cap on levels */
+    int32_t h_mode;         /* ZZ mesh-size weight, see bem_zz_estimate */
+    bem_assembly_opts assembly;
+    bem_solve_opts solve;
+    int32_t incremental;    /* 1: reuse entries of unrefined pairs (bem_assemble_V_update) */
+} bem_adaptive_opts;
+
+/* Alg. 1 on the primal P0 space: solve -> estimate -> mark -> refine, starting
+ * from the uploaded mesh, until N >= max_N or max_levels.  The previous level's
+ * solution copied to the children starts each solve.  When every indicator
+ * vanishes up to rounding (sum eta^2 <= 1e-20 sum h|T|phi^2/12, a symmetric mesh
+ * with a constant solution) Eq. 2.6 holds for the empty set and the level is
+ * refined uniformly instead.  records: caller array of max_levels entries;
+ * n_levels receives the count; final_mesh (nullable) receives the last mesh
+ * (caller destroys it). */
+bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_level_record *records,
+                            int32_t *n_levels, bem_mesh **final_mesh);
+
+/* ---------------------------------------------------------------- instrumentation */
+/* Per-kernel device time, taken with CUDA events recorded on the context's stream
+ * around every launch of the hot kernels while profiling is on, together with the
+ * algorithmic work of those launches:
+ *   BEM_KERNEL_FAR    units = far-field entries computed (pairs i <= j)
+ *   BEM_KERNEL_NEAR   units = touching pairs integrated
+ *   BEM_KERNEL_MATVEC units = bytes of V streamed (N * N * element size) */
+#define BEM_KERNEL_FAR 0
+#define BEM_KERNEL_NEAR 1
+#define BEM_KERNEL_MATVEC 2
+/* on = 1: clear the counters and start recording; 0: stop. */
+bem_status bem_profile_enable(bem_ctx *ctx, int32_t on);
+/* Totals since the last enable (synchronises the stream). */
+bem_status bem_profile_read(bem_ctx *ctx, int32_t kernel, int64_t *launches, double *ms, double *units);
+/* Number of CUDA kernels the context has launched so far. */
+bem_status bem_launch_count(const bem_ctx *ctx, int64_t *n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BEM_GB300_H */

@@ -1,0 +1,383 @@
+"""Thin ctypes binding of libbem_gb300.so (C ABI in include/bem.h).
+
+Argument marshalling only: every step of the computation runs in the library's
+CUDA kernels.  Arrays may be numpy arrays (host) or torch tensors (host or CUDA);
+PyTorch is used only to supply the CUDA stream and device buffers.  If the
+compiled library is missing the binding raises instead of falling back to any
+other implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbem_gb300.so")
+
+BEM_OK = 0
+BEM_ERR_INVALID = -1
+BEM_ERR_OOM = -2
+BEM_ERR_NOT_CONVERGED = -3
+BEM_ERR_MESH = -4
+BEM_ERR_CUDA = -5
+PREC_F64 = 0
+PREC_F32 = 1
+PRECOND_NONE = 0
+PRECOND_JACOBI = 1
+REFINE_BISEC3 = 1
+
+EXPORTS = [
+    "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_context_memory",
+    "bem_mesh_upload", "bem_mesh_destroy", "bem_mesh_info", "bem_mesh_download", "bem_mesh_geometry",
+    "bem_assemble_V", "bem_assemble_V_update", "bem_operator_destroy", "bem_operator_info",
+    "bem_operator_read", "bem_operator_entries", "bem_operator_matvec", "bem_solve_capacity",
+    "bem_zz_estimate", "bem_dorfler", "bem_refine", "bem_mark_refine", "bem_adaptive_run",
+    "bem_profile_enable", "bem_profile_read", "bem_launch_count",
+]
+KERNEL_FAR = 0
+KERNEL_NEAR = 1
+KERNEL_MATVEC = 2
+
+
+class AssemblyOpts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("ss_order", C.c_int32)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_it", C.c_int32), ("precond", C.c_int32),
+                ("max_outer", C.c_int32), ("inner_tol", C.c_double)]
+
+
+class SolveInfo(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("outer", C.c_int32), ("relres", C.c_double),
+                ("converged", C.c_int32)]
+
+
+class LevelRecord(C.Structure):
+    _fields_ = [("N", C.c_int64), ("M", C.c_int64), ("cap", C.c_double), ("eta2_total", C.c_double),
+                ("iterations", C.c_int32), ("n_marked", C.c_int32), ("relres", C.c_double),
+                ("ms_assemble", C.c_double), ("ms_solve", C.c_double), ("ms_adapt", C.c_double)]
+
+
+class AdaptiveOpts(C.Structure):
+    _fields_ = [("theta", C.c_double), ("max_N", C.c_int64), ("max_levels", C.c_int32),
+                ("h_mode", C.c_int32), ("assembly", AssemblyOpts), ("solve", SolveOpts),
+                ("incremental", C.c_int32)]
+
+
+class BemError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"bem error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library {LIB_PATH} is missing: run __graft_entry__.build() first")
+    L = C.CDLL(LIB_PATH)
+    vp, i64, i32, d = C.c_void_p, C.c_int64, C.c_int32, C.c_double
+    P = C.POINTER
+    sig = {
+        "bem_context_create": [vp, i64, P(vp)],
+        "bem_context_destroy": [vp],
+        "bem_context_memory": [vp, P(i64)],
+        "bem_mesh_upload": [vp, vp, i64, vp, i64, vp, P(vp)],
+        "bem_mesh_destroy": [vp],
+        "bem_mesh_info": [vp, P(i64), P(i64), P(i64)],
+        "bem_mesh_download": [vp, vp, vp, vp, vp],
+        "bem_mesh_geometry": [vp, vp, vp],
+        "bem_assemble_V": [vp, P(AssemblyOpts), P(vp)],
+        "bem_assemble_V_update": [vp, vp, P(AssemblyOpts), P(vp)],
+        "bem_operator_destroy": [vp],
+        "bem_operator_info": [vp, P(i64), P(i32)],
+        "bem_operator_read": [vp, i64, i64, i64, i64, vp],
+        "bem_operator_entries": [vp, vp, vp, i64, vp],
+        "bem_operator_matvec": [vp, vp, vp],
+        "bem_solve_capacity": [vp, P(SolveOpts), vp, P(d), vp, P(SolveInfo)],
+        "bem_zz_estimate": [vp, vp, i32, vp, vp],
+        "bem_dorfler": [vp, vp, i64, d, vp, P(i64)],
+        "bem_refine": [vp, vp, i32, P(vp)],
+        "bem_mark_refine": [vp, vp, d, i32, vp, P(i64), P(vp)],
+        "bem_adaptive_run": [vp, P(AdaptiveOpts), P(LevelRecord), P(i32), P(vp)],
+        "bem_profile_enable": [vp, i32],
+        "bem_profile_read": [vp, i32, P(i64), P(d), P(d)],
+        "bem_launch_count": [vp, P(i64)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = C.c_int32
+    L.bem_last_error.argtypes = [vp]
+    L.bem_last_error.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _arr(a, dtype):
+    """(keep-alive object, pointer) for a numpy array or a torch tensor."""
+    if a is None:
+        return None, None
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+
+        tdt = {np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8,
+               np.int64: torch.int64, np.float32: torch.float32}[dtype]
+        t = a.contiguous()
+        if t.dtype != tdt:
+            t = t.to(tdt)
+        return t, t.data_ptr()
+    x = np.ascontiguousarray(a, dtype=dtype)
+    return x, x.ctypes.data
+
+
+def _current_stream():
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return 0
+
+
+class Context:
+    """Library context bound to a CUDA stream (default: torch's current stream)."""
+
+    def __init__(self, stream=None, hbm_budget_bytes: int = 0):
+        L = lib()
+        h = C.c_void_p()
+        s = _current_stream() if stream is None else int(stream)
+        st = L.bem_context_create(C.c_void_p(s), int(hbm_budget_bytes), C.byref(h))
+        if st != BEM_OK:
+            raise BemError(st, "context creation failed (no CUDA device?)")
+        self.h = h
+        self.L = L
+
+    def check(self, st):
+        if st != BEM_OK:
+            raise BemError(st, self.L.bem_last_error(self.h).decode())
+
+    def memory_in_use(self) -> int:
+        v = C.c_int64()
+        self.check(self.L.bem_context_memory(self.h, C.byref(v)))
+        return int(v.value)
+
+    def profile(self, on: bool = True):
+        self.check(self.L.bem_profile_enable(self.h, int(on)))
+
+    def profile_read(self, kernel: int):
+        n, ms, u = C.c_int64(), C.c_double(), C.c_double()
+        self.check(self.L.bem_profile_read(self.h, kernel, C.byref(n), C.byref(ms), C.byref(u)))
+        return int(n.value), float(ms.value), float(u.value)
+
+    def launch_count(self) -> int:
+        n = C.c_int64()
+        self.check(self.L.bem_launch_count(self.h, C.byref(n)))
+        return int(n.value)
+
+    def last_error(self) -> str:
+        return self.L.bem_last_error(self.h).decode()
+
+    def close(self):
+        if self.h:
+            self.L.bem_context_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    def __init__(self, ctx: Context, handle):
+        self.ctx, self.h = ctx, handle
+
+    @classmethod
+    def upload(cls, ctx: Context, verts, tris, ref_edge=None):
+        v, pv = _arr(verts, np.float64)
+        t, pt = _arr(tris, np.int32)
+        r, pr = _arr(ref_edge, np.uint8)
+        M = int(v.shape[0]) if len(v.shape) == 2 else int(v.shape[0]) // 3
+        N = int(t.shape[0]) if len(t.shape) == 2 else int(t.shape[0]) // 3
+        h = C.c_void_p()
+        ctx.check(ctx.L.bem_mesh_upload(ctx.h, pv, M, pt, N, pr, C.byref(h)))
+        return cls(ctx, h)
+
+    def info(self):
+        M, N, nn = C.c_int64(), C.c_int64(), C.c_int64()
+        self.ctx.check(self.ctx.L.bem_mesh_info(self.h, C.byref(M), C.byref(N), C.byref(nn)))
+        return int(M.value), int(N.value), int(nn.value)
+
+    @property
+    def N(self):
+        return self.info()[1]
+
+    @property
+    def M(self):
+        return self.info()[0]
+
+    def download(self):
+        M, N, _ = self.info()
+        v = np.zeros((M, 3))
+        t = np.zeros((N, 3), dtype=np.int32)
+        p = np.zeros(N, dtype=np.int32)
+        k = np.zeros(N, dtype=np.uint8)
+        self.ctx.check(self.ctx.L.bem_mesh_download(self.h, v.ctypes.data, t.ctypes.data, p.ctypes.data,
+                                                    k.ctypes.data))
+        return v, t, p, k
+
+    def geometry(self):
+        N = self.N
+        a, d = np.zeros(N), np.zeros(N)
+        self.ctx.check(self.ctx.L.bem_mesh_geometry(self.h, a.ctypes.data, d.ctypes.data))
+        return a, d
+
+    def close(self):
+        # a handle outlived by its context was released with the context's memory pool
+        if self.h and self.ctx.h:
+            self.ctx.L.bem_mesh_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Operator:
+    def __init__(self, mesh: Mesh, handle):
+        self.mesh, self.ctx, self.h = mesh, mesh.ctx, handle
+
+    @classmethod
+    def assemble(cls, mesh: Mesh, precision=PREC_F64, ss_order=4):
+        o = AssemblyOpts(precision, ss_order)
+        h = C.c_void_p()
+        mesh.ctx.check(mesh.ctx.L.bem_assemble_V(mesh.h, C.byref(o), C.byref(h)))
+        return cls(mesh, h)
+
+    @classmethod
+    def update(cls, fine: Mesh, coarse: "Operator"):
+        h = C.c_void_p()
+        fine.ctx.check(fine.ctx.L.bem_assemble_V_update(fine.h, coarse.h, None, C.byref(h)))
+        return cls(fine, h)
+
+    def info(self):
+        N, p = C.c_int64(), C.c_int32()
+        self.ctx.check(self.ctx.L.bem_operator_info(self.h, C.byref(N), C.byref(p)))
+        return int(N.value), int(p.value)
+
+    def read(self, i0=0, ni=None, j0=0, nj=None):
+        N, p = self.info()
+        ni = N - i0 if ni is None else ni
+        nj = N - j0 if nj is None else nj
+        out = np.zeros((ni, nj), dtype=np.float64 if p == PREC_F64 else np.float32)
+        self.ctx.check(self.ctx.L.bem_operator_read(self.h, i0, ni, j0, nj, out.ctypes.data))
+        return out
+
+    def entries(self, I, J):
+        Ia, pI = _arr(I, np.int64)
+        Ja, pJ = _arr(J, np.int64)
+        out = np.zeros(int(Ia.shape[0]))
+        self.ctx.check(self.ctx.L.bem_operator_entries(self.h, pI, pJ, int(Ia.shape[0]), out.ctypes.data))
+        return out
+
+    def matvec(self, x):
+        xa, px = _arr(x, np.float64)
+        y = np.zeros(int(xa.shape[0]))
+        self.ctx.check(self.ctx.L.bem_operator_matvec(self.h, px, y.ctypes.data))
+        return y
+
+    def close(self):
+        if self.h and self.ctx.h:
+            self.ctx.L.bem_operator_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve_capacity(op: Operator, tol=1e-10, max_it=10000, precond=PRECOND_JACOBI, x0=None,
+                   max_outer=20, inner_tol=1e-5, phi_out=None, raise_not_converged=True):
+    """Cap and x with V x = |T| (Eq. 2.5, 2.8).  phi_out may be a CUDA tensor."""
+    o = SolveOpts(tol, max_it, precond, max_outer, inner_tol)
+    info = SolveInfo()
+    cap = C.c_double()
+    N = op.info()[0]
+    x0a, px0 = _arr(x0, np.float64)
+    if phi_out is None:
+        phi = np.zeros(N)
+        pphi = phi.ctypes.data
+    else:
+        phi, pphi = phi_out, phi_out.data_ptr()
+    st = op.ctx.L.bem_solve_capacity(op.h, C.byref(o), px0, C.byref(cap), pphi, C.byref(info))
+    if st != BEM_OK and (st != BEM_ERR_NOT_CONVERGED or raise_not_converged):
+        op.ctx.check(st)
+    return float(cap.value), phi, {"iterations": info.iterations, "outer": info.outer,
+                                   "relres": info.relres, "converged": bool(info.converged)}
+
+
+def zz_estimate(mesh: Mesh, phi, h_mode=0):
+    pa, pp = _arr(phi, np.float64)
+    N = mesh.N
+    eta2 = np.zeros(N)
+    tot = np.zeros(2)
+    mesh.ctx.check(mesh.ctx.L.bem_zz_estimate(mesh.h, pp, h_mode, eta2.ctypes.data, tot.ctypes.data))
+    return eta2, float(tot[0]), float(tot[1])
+
+
+def dorfler(ctx: Context, eta2, theta=0.5):
+    ea, pe = _arr(eta2, np.float64)
+    N = int(ea.shape[0])
+    m = np.zeros(N, dtype=np.uint8)
+    nm = C.c_int64()
+    ctx.check(ctx.L.bem_dorfler(ctx.h, pe, N, theta, m.ctypes.data if N else None, C.byref(nm)))
+    return m, int(nm.value)
+
+
+def refine(mesh: Mesh, marked, bisec3=False) -> Mesh:
+    ma, pm = _arr(marked, np.uint8)
+    h = C.c_void_p()
+    mesh.ctx.check(mesh.ctx.L.bem_refine(mesh.h, pm, REFINE_BISEC3 if bisec3 else 0, C.byref(h)))
+    return Mesh(mesh.ctx, h)
+
+
+def mark_refine(mesh: Mesh, eta2, theta=0.5, bisec3=False):
+    ea, pe = _arr(eta2, np.float64)
+    N = mesh.N
+    m = np.zeros(N, dtype=np.uint8)
+    nm = C.c_int64()
+    h = C.c_void_p()
+    mesh.ctx.check(mesh.ctx.L.bem_mark_refine(mesh.h, pe, theta, REFINE_BISEC3 if bisec3 else 0,
+                                              m.ctypes.data, C.byref(nm), C.byref(h)))
+    return m, int(nm.value), Mesh(mesh.ctx, h)
+
+
+def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, precision=PREC_F64,
+                 ss_order=4, tol=1e-12, max_it=20000, precond=PRECOND_JACOBI, incremental=True,
+                 max_outer=20, inner_tol=1e-5, want_final=False):
+    """Alg. 1 in the library's native loop; returns (records, final Mesh or None)."""
+    o = AdaptiveOpts(theta, max_N, max_levels, h_mode, AssemblyOpts(precision, ss_order),
+                     SolveOpts(tol, max_it, precond, max_outer, inner_tol), int(incremental))
+    recs = (LevelRecord * max_levels)()
+    n = C.c_int32()
+    fin = C.c_void_p()
+    mesh.ctx.check(mesh.ctx.L.bem_adaptive_run(mesh.h, C.byref(o), recs, C.byref(n),
+                                               C.byref(fin) if want_final else None))
+    out = [{f: getattr(recs[k], f) for f, _ in LevelRecord._fields_} for k in range(n.value)]
+    return out, (Mesh(mesh.ctx, fin) if want_final and fin.value else None)

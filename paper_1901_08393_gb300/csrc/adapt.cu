@@ -1,0 +1,443 @@
+// Adaptive steps of Alg. 1 on the device: ZZ-type estimate (Eq. 1.6), Doerfler
+// marking (Eq. 2.6) and newest-vertex bisection with closure (Fig. 3).
+//
+// Compiled with -fmad=false: every product and sum of the estimator is rounded
+// separately in the order written, so the indicators, and the decisions taken
+// from them, are bit-identical to a plain IEEE-754 evaluation of the same
+// formulas.
+#include <cmath>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// ------------------------------------------------------------------ ZZ estimate
+// u_z = sum_{T at z} |T| x_T / sum_{T at z} |T|, triangles in ascending order.
+__global__ void k_zz_nodal(const int32_t *off, const int32_t *v2t, const double *area, const double *x,
+                           double *u, int64_t M)
+{
+    const int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= M) return;
+    double num = 0.0, den = 0.0;
+    for (int32_t p = off[z]; p < off[z + 1]; ++p) {
+        const int32_t t = v2t[p];
+        const double ax = area[t] * x[t];
+        num = num + ax;
+        den = den + area[t];
+    }
+    u[z] = den > 0.0 ? num / den : 0.0;
+}
+
+// eta(T)^2 = (h |T| / 12) (sum d_k^2 + (sum d_k)^2), d_k = u_{z_k} - x_T; block
+// partials of the total and of sum h|T| x_T^2 / 12.
+__global__ void k_zz_eta(const int32_t *tris, const double *area, const double *diam, const double *x,
+                         const double *u, int64_t N, int h_mode, double *eta2, double *part_eta, double *part_scale)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0, sc = 0.0;
+    if (t < N) {
+        double d[3];
+        for (int k = 0; k < 3; ++k) d[k] = u[tris[3 * t + k]] - x[t];
+        const double s2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+        const double s1 = (d[0] + d[1]) + d[2];
+        const double q = s2 + s1 * s1;
+        const double h = h_mode == 1 ? sqrt(area[t]) : diam[t];
+        const double f = (h * area[t]) / 12.0;
+        e = f * q;
+        sc = f * (x[t] * x[t]);
+        eta2[t] = e;
+    }
+    __shared__ double se[256], ss[256];
+    se[threadIdx.x] = e;
+    ss[threadIdx.x] = sc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            se[threadIdx.x] += se[threadIdx.x + o];
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_eta[blockIdx.x] = se[0];
+        part_scale[blockIdx.x] = ss[0];
+    }
+}
+
+__global__ void k_sum2(const double *a, const double *b, int n, double *out)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0, t = 0.0;
+        for (int k = 0; k < n; ++k) {
+            s += a[k];
+            t += b[k];
+        }
+        out[0] = s;
+        out[1] = t;
+    }
+}
+
+bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_eta2, double *h_totals)
+{
+    bem_ctx *ctx = m->ctx;
+    cudaStream_t s = ctx->stream;
+    Allocs tmp;
+    double *u = nullptr;
+    const int nb = (int)nblk(m->N, 256);
+    bem_status st = dalloc(ctx, tmp, (void **)&u, sizeof(double) * (m->M + 2 * nb + 2), false);
+    if (st) return st;
+    double *pe = u + m->M, *ps = pe + nb, *tot = ps + nb;
+    k_zz_nodal<<<nblk(m->M, 128), 128, 0, s>>>(m->v2t_off, m->v2t, m->area, d_phi, u, m->M); BEM_COUNT(ctx);
+    k_zz_eta<<<nb, 256, 0, s>>>(m->tris, m->area, m->diam, d_phi, u, m->N, h_mode, d_eta2, pe, ps); BEM_COUNT(ctx);
+    k_sum2<<<1, 32, 0, s>>>(pe, ps, nb, tot); BEM_COUNT(ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_error(ctx, e, "zz kernels");
+    if (!st && h_totals) {
+        e = cudaMemcpyAsync(ctx->h_pinned, tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "zz totals");
+        else {
+            h_totals[0] = ctx->h_pinned[0];
+            h_totals[1] = ctx->h_pinned[1];
+        }
+    }
+    dfree_all(ctx, tmp);
+    return st;
+}
+
+// ------------------------------------------------------------------ Doerfler
+// key = (~float_bits(eta2) << 32) | index: ascending key order = descending
+// single-precision indicator, ties by index.
+__global__ void k_keys(const double *eta2, int64_t N, int64_t n2, unsigned long long *keys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    if (i < N) {
+        const float f = __double2float_rn(eta2[i]);
+        const unsigned int bits = __float_as_uint(f);
+        keys[i] = ((unsigned long long)(0xFFFFFFFFu - bits) << 32) | (unsigned long long)(uint32_t)i;
+    } else {
+        keys[i] = ~0ull;
+    }
+}
+
+__device__ __forceinline__ void cmp_swap(unsigned long long *keys, int64_t i, int64_t l, bool asc)
+{
+    const unsigned long long a = keys[i], b = keys[l];
+    if ((a > b) == asc) {
+        keys[i] = b;
+        keys[l] = a;
+    }
+}
+
+// One bitonic stage (k, j) over all n2/2 pairs.
+__global__ void k_bitonic_global(unsigned long long *keys, int64_t n2, int64_t k, int64_t j)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n2 / 2) return;
+    const int64_t i = 2 * j * (t / j) + (t % j);
+    cmp_swap(keys, i, i + j, (i & k) == 0);
+}
+
+// Stages j = j0, j0/2, ..., 1 of step k inside chunks of 2 * blockDim.x keys.
+__global__ void k_bitonic_shared(unsigned long long *keys, int64_t n2, int64_t k, int64_t j0)
+{
+    extern __shared__ unsigned long long sk[];
+    const int chunk = 2 * blockDim.x;
+    const int64_t base = (int64_t)blockIdx.x * chunk;
+    for (int q = threadIdx.x; q < chunk; q += blockDim.x) sk[q] = keys[base + q];
+    __syncthreads();
+    for (int64_t j = j0; j >= 1; j >>= 1) {
+        const int t = threadIdx.x;
+        const int i = (int)(2 * j * (t / j) + (t % j));
+        const bool asc = ((base + i) & k) == 0;
+        const unsigned long long a = sk[i], b = sk[i + j];
+        if ((a > b) == asc) {
+            sk[i] = b;
+            sk[i + j] = a;
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < chunk; q += blockDim.x) keys[base + q] = sk[q];
+}
+
+// One warp: total = sum of eta2 in key order (FP64, sequential); the shortest
+// prefix whose running sum reaches theta * total, extended over equal keys.
+__global__ void k_dorfler_select(const unsigned long long *keys, const double *eta2, int64_t N, double theta,
+                                 long long *K_out)
+{
+    const int lane = threadIdx.x;
+    double total = 0.0;
+    for (int64_t base = 0; base < N; base += 32) {
+        const int64_t k = base + lane;
+        const double v = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
+        const int cnt = (N - base) < 32 ? (int)(N - base) : 32;
+        for (int l = 0; l < 32; ++l) {
+            const double vl = __shfl_sync(0xffffffffu, v, l);
+            if (l < cnt) total = total + vl;
+        }
+    }
+    const double thr = theta * total;
+    double acc = 0.0;
+    int64_t kk = 0;
+    bool done = false;
+    for (int64_t base = 0; base < N && !done; base += 32) {
+        const int64_t k = base + lane;
+        const double v = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
+        const int cnt = (N - base) < 32 ? (int)(N - base) : 32;
+        for (int l = 0; l < 32; ++l) {
+            const double vl = __shfl_sync(0xffffffffu, v, l);
+            if (!done && l < cnt) {
+                if (acc < thr) {
+                    acc = acc + vl;
+                    kk = base + l + 1;
+                } else {
+                    done = true;
+                }
+            }
+        }
+        if (base + 32 >= N) done = true;
+    }
+    if (lane == 0) {
+        while (kk > 0 && kk < N && (keys[kk] >> 32) == (keys[kk - 1] >> 32)) ++kk;
+        *K_out = kk;
+    }
+}
+
+__global__ void k_mark(const unsigned long long *keys, int64_t N, const long long *K, uint8_t *marked)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    marked[keys[k] & 0xFFFFFFFFull] = (k < *K) ? 1 : 0;
+}
+
+bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, uint8_t *d_marked,
+                   int64_t *n_marked)
+{
+    if (N <= 0) {
+        if (n_marked) *n_marked = 0;
+        return BEM_OK;
+    }
+    if (N > 0x7FFFFFFFLL) return set_error(ctx, BEM_ERR_INVALID, "too many elements for marking");
+    cudaStream_t s = ctx->stream;
+    int64_t n2 = 1;
+    while (n2 < N) n2 <<= 1;
+    if (n2 < 2) n2 = 2;
+    Allocs tmp;
+    unsigned long long *keys = nullptr;
+    bem_status st = dalloc(ctx, tmp, (void **)&keys, sizeof(unsigned long long) * n2 + 64, false);
+    if (st) return st;
+    long long *dK = reinterpret_cast<long long *>(keys + n2);
+    k_keys<<<nblk(n2, 256), 256, 0, s>>>(d_eta2, N, n2, keys); BEM_COUNT(ctx);
+    const int64_t chunk = n2 < 2048 ? n2 : 2048;
+    const int sthreads = (int)(chunk / 2);
+    for (int64_t k = 2; k <= n2; k <<= 1) {
+        int64_t j = k >> 1;
+        for (; j >= chunk; j >>= 1)
+            k_bitonic_global<<<nblk(n2 / 2, 256), 256, 0, s>>>(keys, n2, k, j); BEM_COUNT(ctx);
+        k_bitonic_shared<<<(unsigned)(n2 / chunk), sthreads, chunk * sizeof(unsigned long long), s>>>(keys, n2, k, j); BEM_COUNT(ctx);
+    }
+    k_dorfler_select<<<1, 32, 0, s>>>(keys, d_eta2, N, theta, dK); BEM_COUNT(ctx);
+    k_mark<<<nblk(N, 256), 256, 0, s>>>(keys, N, dK, d_marked); BEM_COUNT(ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_error(ctx, e, "doerfler kernels");
+    if (!st && n_marked) {
+        e = cudaMemcpyAsync(ctx->h_pinned, dK, sizeof(long long), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "doerfler count");
+        else *n_marked = *reinterpret_cast<long long *>(ctx->h_pinned);
+    }
+    dfree_all(ctx, tmp);
+    return st;
+}
+
+// ------------------------------------------------------------------ NVB
+__global__ void k_nvb_seed(const int32_t *owner, const uint8_t *marked, int64_t N, int bisec3, uint8_t *flag)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N || !marked[t]) return;
+    flag[owner[3 * t]] = 1;
+    if (bisec3) {
+        flag[owner[3 * t + 1]] = 1;
+        flag[owner[3 * t + 2]] = 1;
+    }
+}
+
+// One closure sweep: a triangle with a marked edge marks its reference edge.
+__global__ void k_nvb_close(const int32_t *owner, int64_t N, uint8_t *flag, int32_t *changed)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int32_t o0 = owner[3 * t];
+    if (!flag[o0] && (flag[owner[3 * t + 1]] | flag[owner[3 * t + 2]])) {
+        flag[o0] = 1;
+        *changed = 1;
+    }
+}
+
+// Per half-edge: 1 if it owns a marked edge (a new vertex).  Per triangle: kept
+// flag and number of children.
+__global__ void k_nvb_counts(const int32_t *owner, const uint8_t *flag, int64_t N, int32_t *is_new,
+                             int32_t *is_kept, int32_t *n_child)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    for (int k = 0; k < 3; ++k) {
+        const int64_t h = 3 * t + k;
+        is_new[h] = (owner[h] == h && flag[h]) ? 1 : 0;
+    }
+    const int f0 = flag[owner[3 * t]], f1 = flag[owner[3 * t + 1]], f2 = flag[owner[3 * t + 2]];
+    is_kept[t] = f0 ? 0 : 1;
+    n_child[t] = f0 ? 2 + f1 + f2 : 0;
+}
+
+__global__ void k_nvb_verts(const double *V, const int32_t *tris, const int32_t *owner, const uint8_t *flag,
+                            const int32_t *new_pos, int64_t N, int64_t M, double *Vn)
+{
+    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= 3 * N || owner[h] != h || !flag[h]) return;
+    const int64_t t = h / 3;
+    const int k = (int)(h % 3);
+    const int32_t a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+    const int64_t m = M + new_pos[h];
+    for (int c = 0; c < 3; ++c) Vn[3 * m + c] = 0.5 * (V[3 * (int64_t)a + c] + V[3 * (int64_t)b + c]);
+}
+
+__global__ void k_nvb_tris(const int32_t *tris, const int32_t *owner, const uint8_t *flag, const int32_t *new_pos,
+                           const int32_t *kept_pos, const int32_t *child_pos, int64_t n_kept, int64_t N, int64_t M,
+                           int32_t *Tn, int32_t *parent, uint8_t *kept)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int32_t a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+    const int32_t o0 = owner[3 * t], o1 = owner[3 * t + 1], o2 = owner[3 * t + 2];
+    const int f0 = flag[o0], f1 = flag[o1], f2 = flag[o2];
+    if (!f0) {
+        const int64_t p = kept_pos[t];
+        Tn[3 * p] = a;
+        Tn[3 * p + 1] = b;
+        Tn[3 * p + 2] = c;
+        parent[p] = (int32_t)t;
+        kept[p] = 1;
+        return;
+    }
+    const int32_t m0 = (int32_t)(M + new_pos[o0]);
+    const int32_t m1 = f1 ? (int32_t)(M + new_pos[o1]) : -1;
+    const int32_t m2 = f2 ? (int32_t)(M + new_pos[o2]) : -1;
+    int32_t ch[4][3];
+    int nc;
+    if (!f1 && !f2) {
+        const int32_t L[2][3] = {{c, a, m0}, {b, c, m0}};
+        memcpy(ch, L, sizeof(L));
+        nc = 2;
+    } else if (f1 && !f2) {
+        const int32_t L[3][3] = {{c, a, m0}, {m0, b, m1}, {c, m0, m1}};
+        memcpy(ch, L, sizeof(L));
+        nc = 3;
+    } else if (!f1 && f2) {
+        const int32_t L[3][3] = {{m0, c, m2}, {a, m0, m2}, {b, c, m0}};
+        memcpy(ch, L, sizeof(L));
+        nc = 3;
+    } else {
+        const int32_t L[4][3] = {{m0, c, m2}, {a, m0, m2}, {m0, b, m1}, {c, m0, m1}};
+        memcpy(ch, L, sizeof(L));
+        nc = 4;
+    }
+    const int64_t base = n_kept + child_pos[t];
+    for (int r = 0; r < nc; ++r) {
+        for (int q = 0; q < 3; ++q) Tn[3 * (base + r) + q] = ch[r][q];
+        parent[base + r] = (int32_t)t;
+        kept[base + r] = 0;
+    }
+}
+
+bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out)
+{
+    bem_ctx *ctx = m->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = m->N, M = m->M, H = 3 * N;
+    Allocs tmp;
+    bem_mesh *r = nullptr;
+    bem_status st = BEM_OK;
+    uint8_t *flag = nullptr;
+    int32_t *is_new = nullptr, *new_pos = nullptr, *is_kept = nullptr, *kept_pos = nullptr, *n_child = nullptr,
+            *child_pos = nullptr, *changed = nullptr;
+    int64_t n_new = 0, n_kept = 0, n_children = 0;
+#define TRY(x)             \
+    do {                   \
+        st = (x);          \
+        if (st) goto fail; \
+    } while (0)
+    TRY(dalloc(ctx, tmp, (void **)&flag, H + 16, true));
+    TRY(dalloc(ctx, tmp, (void **)&changed, sizeof(int32_t) * 4, true));
+    TRY(dalloc(ctx, tmp, (void **)&is_new, sizeof(int32_t) * (H + 1), false));
+    TRY(dalloc(ctx, tmp, (void **)&new_pos, sizeof(int32_t) * (H + 1), false));
+    TRY(dalloc(ctx, tmp, (void **)&is_kept, sizeof(int32_t) * (N + 1), false));
+    TRY(dalloc(ctx, tmp, (void **)&kept_pos, sizeof(int32_t) * (N + 1), false));
+    TRY(dalloc(ctx, tmp, (void **)&n_child, sizeof(int32_t) * (N + 1), false));
+    TRY(dalloc(ctx, tmp, (void **)&child_pos, sizeof(int32_t) * (N + 1), false));
+    k_nvb_seed<<<nblk(N, 256), 256, 0, s>>>(m->owner, d_marked, N, flags & BEM_REFINE_BISEC3, flag); BEM_COUNT(ctx);
+    for (int sweep = 0;; ++sweep) {
+        if (sweep > 100000) {
+            st = set_error(ctx, BEM_ERR_MESH, "NVB closure did not terminate");
+            goto fail;
+        }
+        if (cudaMemsetAsync(changed, 0, sizeof(int32_t), s) != cudaSuccess) {
+            st = set_error(ctx, BEM_ERR_CUDA, "closure flag reset");
+            goto fail;
+        }
+        k_nvb_close<<<nblk(N, 256), 256, 0, s>>>(m->owner, N, flag, changed); BEM_COUNT(ctx);
+        cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            st = cuda_error(ctx, e, "closure sweep");
+            goto fail;
+        }
+        if (*reinterpret_cast<int32_t *>(ctx->h_pinned) == 0) break;
+    }
+    k_nvb_counts<<<nblk(N, 256), 256, 0, s>>>(m->owner, flag, N, is_new, is_kept, n_child); BEM_COUNT(ctx);
+    TRY(exclusive_scan_i32(ctx, is_new, new_pos, H, &n_new));
+    TRY(exclusive_scan_i32(ctx, is_kept, kept_pos, N, &n_kept));
+    TRY(exclusive_scan_i32(ctx, n_child, child_pos, N, &n_children));
+    r = new bem_mesh();
+    r->ctx = ctx;
+    r->M = M + n_new;
+    r->N = n_kept + n_children;
+    r->n_kept = n_kept;
+    r->src_N = N;
+    if (r->M > 0x7FFFFFFFLL || r->N > 0x7FFFFFFFLL) {
+        st = set_error(ctx, BEM_ERR_INVALID, "refined mesh exceeds 2^31 entries");
+        goto fail;
+    }
+    TRY(dalloc(ctx, r->allocs, (void **)&r->verts, sizeof(double) * 3 * r->M, false));
+    TRY(dalloc(ctx, r->allocs, (void **)&r->tris, sizeof(int32_t) * 3 * r->N, false));
+    TRY(dalloc(ctx, r->allocs, (void **)&r->parent, sizeof(int32_t) * r->N, false));
+    TRY(dalloc(ctx, r->allocs, (void **)&r->kept, r->N + 16, false));
+    if (cudaMemcpyAsync(r->verts, m->verts, sizeof(double) * 3 * M, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+        st = set_error(ctx, BEM_ERR_CUDA, "copy vertices");
+        goto fail;
+    }
+    k_nvb_verts<<<nblk(H, 256), 256, 0, s>>>(m->verts, m->tris, m->owner, flag, new_pos, N, M, r->verts); BEM_COUNT(ctx);
+    k_nvb_tris<<<nblk(N, 256), 256, 0, s>>>(m->tris, m->owner, flag, new_pos, kept_pos, child_pos, n_kept, N, M,
+                                            r->tris, r->parent, r->kept); BEM_COUNT(ctx);
+    if (cudaGetLastError() != cudaSuccess) {
+        st = set_error(ctx, BEM_ERR_CUDA, "refinement kernels");
+        goto fail;
+    }
+    TRY(mesh_build(r, false, nullptr));
+    dfree_all(ctx, tmp);
+    *out = r;
+    return BEM_OK;
+fail:
+#undef TRY
+    if (r) {
+        dfree_all(ctx, r->allocs);
+        delete r;
+    }
+    dfree_all(ctx, tmp);
+    return st;
+}
+
+}  // namespace bem

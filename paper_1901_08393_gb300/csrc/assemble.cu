@@ -1,0 +1,509 @@
+// Assembly of the Galerkin matrix V[i][j] = (1/4pi) int_Ti int_Tj 1/|x-y| on
+// piecewise constants (Eq. 2.4-2.5; primal P0 form of App. A, Eq. A.1).
+//
+//  * Far field (no common vertex): 7 x 7 product of Radon's degree-5 rule,
+//      V_ij = |Ti||Tj|/(4pi) sum_a w_a sum_b w_b / |x_a - y_b|.
+//    One thread per column j holds its 7 points in registers; the CTA stages 32
+//    row triangles in shared memory and walks them (broadcast reads).  Only
+//    entries with i <= j are computed; the strict lower triangle is mirrored, so
+//    V is exactly symmetric and an incremental re-assembly reproduces the full
+//    one bit for bit.  FP64 variant (all FP64) and FP32 variant (centroid
+//    difference in FP64 rounded once, offsets from the centroid in FP32, MUFU
+//    rsqrt).
+//  * Near field (common vertex, common edge, identical): Sauter-Schwab
+//    regularising transformations.  The 4-d integrand of each region is a power
+//    of the radial variables times a function of the others (the kernel is
+//    homogeneous of degree -1 on flat panels), so the radial integrals are taken
+//    exactly (1/3 for xi^2, 1/2 for rho) -- the same value that a Gauss-Legendre
+//    rule with >= 2 points gives in those variables -- and the remaining
+//    variables use n Gauss-Legendre points each: identical 6 hexagon sectors x n,
+//    common edge 4 sub-regions x n^2, common vertex 2 regions x n^3.  FP64.
+#include <cmath>
+
+#include "bem_internal.cuh"
+
+namespace bem {
+
+__constant__ double c_w7[kQ];
+__constant__ double c_glx[kMaxSS + 1][kMaxSS];
+__constant__ double c_glw[kMaxSS + 1][kMaxSS];
+
+static bool g_asm_ready[64] = {false};
+
+// Gauss-Legendre rule with n points on [0, 1]: roots of P_n by Newton's method on
+// the three-term recurrence, weights 2 / ((1 - x^2) P_n'(x)^2) halved.
+static void gauss_legendre(int n, double *x, double *w)
+{
+    const double pi = 3.14159265358979323846;
+    for (int i = 0; i < n; ++i) {
+        double r = std::cos(pi * (i + 0.75) / (n + 0.5));
+        double d = 0.0;
+        for (int it = 0; it < 60; ++it) {
+            double pm1 = 1.0, p = r;  // P_0, P_1
+            for (int k = 1; k < n; ++k) {
+                const double pn = ((2.0 * k + 1.0) * r * p - k * pm1) / (k + 1.0);
+                pm1 = p;
+                p = pn;
+            }
+            if (n == 1) { p = r; pm1 = 1.0; }
+            d = n * (pm1 - r * p) / (1.0 - r * r);  // P_n'(r)
+            const double step = p / d;
+            r -= step;
+            if (std::fabs(step) <= 1e-17) break;
+        }
+        double pm1 = 1.0, p = r;
+        for (int k = 1; k < n; ++k) {
+            const double pn = ((2.0 * k + 1.0) * r * p - k * pm1) / (k + 1.0);
+            pm1 = p;
+            p = pn;
+        }
+        if (n == 1) { p = r; pm1 = 1.0; }
+        d = n * (pm1 - r * p) / (1.0 - r * r);
+        x[n - 1 - i] = 0.5 * (1.0 + r);
+        w[n - 1 - i] = 1.0 / ((1.0 - r * r) * d * d);
+    }
+}
+
+static bem_status assembly_constants(bem_ctx *ctx)
+{
+    if (ctx->device < 64 && g_asm_ready[ctx->device]) return BEM_OK;
+    const double r15 = std::sqrt(15.0);
+    const double wa = (155.0 - r15) / 1200.0, wb = (155.0 + r15) / 1200.0;
+    const double w7[kQ] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
+    double X[kMaxSS + 1][kMaxSS] = {}, W[kMaxSS + 1][kMaxSS] = {};
+    for (int n = 1; n <= kMaxSS; ++n) gauss_legendre(n, X[n], W[n]);
+    BEM_CK(ctx, cudaMemcpyToSymbol(c_w7, w7, sizeof(w7)));
+    BEM_CK(ctx, cudaMemcpyToSymbol(c_glx, X, sizeof(X)));
+    BEM_CK(ctx, cudaMemcpyToSymbol(c_glw, W, sizeof(W)));
+    if (ctx->device < 64) g_asm_ready[ctx->device] = true;
+    return BEM_OK;
+}
+
+static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// ------------------------------------------------------------------ far field
+constexpr int kFarCols = 256;  // threads (columns) per CTA
+constexpr int kFarRows = 32;   // row triangles staged per CTA
+
+__global__ void __launch_bounds__(kFarCols) k_far_f64(const double *__restrict__ q64, double *__restrict__ V,
+                                                      int64_t ld, int64_t r0, int64_t r1, int64_t c0,
+                                                      int64_t c1)
+{
+    __shared__ double sx[kFarRows][22];
+    const int64_t cbase = c0 + (int64_t)blockIdx.x * kFarCols;
+    const int64_t i0 = r0 + (int64_t)blockIdx.y * kFarRows;
+    if (i0 > cbase + kFarCols - 1 || i0 >= r1) return;  // tile strictly below the diagonal
+    for (int k = threadIdx.x; k < kFarRows * 22; k += kFarCols) {
+        const int r = k / 22, c = k % 22;
+        const int64_t i = i0 + r;
+        sx[r][c] = (i < r1) ? q64[i * kQ64Stride + c] : 0.0;
+    }
+    __syncthreads();
+    const int64_t j = cbase + threadIdx.x;
+    if (j >= c1) return;
+    double y[3 * kQ];
+#pragma unroll
+    for (int c = 0; c < 3 * kQ; ++c) y[c] = q64[j * kQ64Stride + c];
+    const double Aj = q64[j * kQ64Stride + 21] * kInv4Pi;
+    const int rows = (int)((r1 - i0) < kFarRows ? (r1 - i0) : kFarRows);
+    for (int r = 0; r < rows; ++r) {
+        const int64_t i = i0 + r;
+        if (i > j) break;
+        double acc = 0.0;
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            const double xa = sx[r][3 * a], ya = sx[r][3 * a + 1], za = sx[r][3 * a + 2];
+            double s = 0.0;
+#pragma unroll
+            for (int b = 0; b < kQ; ++b) {
+                const double dx = xa - y[3 * b], dy = ya - y[3 * b + 1], dz = za - y[3 * b + 2];
+                s += c_w7[b] * rsqrt(dx * dx + dy * dy + dz * dz);
+            }
+            acc += c_w7[a] * s;
+        }
+        V[i * ld + j] = sx[r][21] * Aj * acc;
+    }
+}
+
+__global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ q32,
+                                                      const double *__restrict__ cent, float *__restrict__ V,
+                                                      int64_t ld, int64_t r0, int64_t r1, int64_t c0,
+                                                      int64_t c1)
+{
+    __shared__ float so[kFarRows][3 * kQ];
+    __shared__ double sc[kFarRows][4];
+    const int64_t cbase = c0 + (int64_t)blockIdx.x * kFarCols;
+    const int64_t i0 = r0 + (int64_t)blockIdx.y * kFarRows;
+    if (i0 > cbase + kFarCols - 1 || i0 >= r1) return;
+    for (int k = threadIdx.x; k < kFarRows * 3 * kQ; k += kFarCols) {
+        const int r = k / (3 * kQ), c = k % (3 * kQ);
+        const int64_t i = i0 + r;
+        so[r][c] = (i < r1) ? q32[i * kQ32Stride + c] : 0.0f;
+    }
+    for (int k = threadIdx.x; k < kFarRows * 4; k += kFarCols) {
+        const int r = k / 4, c = k % 4;
+        const int64_t i = i0 + r;
+        sc[r][c] = (i < r1) ? cent[i * 4 + c] : 0.0;
+    }
+    __syncthreads();
+    const int64_t j = cbase + threadIdx.x;
+    if (j >= c1) return;
+    float y[3 * kQ];
+#pragma unroll
+    for (int c = 0; c < 3 * kQ; ++c) y[c] = q32[j * kQ32Stride + c];
+    const double cx = cent[4 * j], cy = cent[4 * j + 1], cz = cent[4 * j + 2];
+    const double Aj = cent[4 * j + 3] * kInv4Pi;
+    const int rows = (int)((r1 - i0) < kFarRows ? (r1 - i0) : kFarRows);
+    for (int r = 0; r < rows; ++r) {
+        const int64_t i = i0 + r;
+        if (i > j) break;
+        const float Dx = (float)(sc[r][0] - cx), Dy = (float)(sc[r][1] - cy), Dz = (float)(sc[r][2] - cz);
+        float acc = 0.0f;
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            const float xa = Dx + so[r][3 * a], ya = Dy + so[r][3 * a + 1], za = Dz + so[r][3 * a + 2];
+            float s = 0.0f;
+#pragma unroll
+            for (int b = 0; b < kQ; ++b) {
+                const float dx = xa - y[3 * b], dy = ya - y[3 * b + 1], dz = za - y[3 * b + 2];
+                s += (float)c_w7[b] * rsqrtf(dx * dx + dy * dy + dz * dz);
+            }
+            acc += (float)c_w7[a] * s;
+        }
+        V[i * ld + j] = (float)(sc[r][3] * Aj * (double)acc);
+    }
+}
+
+// Mirror the strict lower triangle of rows [r0, r1): V[i][j] = V[j][i], j < i,
+// through 32 x 32 shared-memory tiles (coalesced on both sides).
+template <typename T>
+__global__ void k_mirror(T *V, int64_t ld, int64_t r0, int64_t r1)
+{
+    __shared__ T tile[32][33];
+    const int64_t bi = (int64_t)blockIdx.y * 32 + (r0 / 32) * 32;  // destination row tile
+    const int64_t bj = (int64_t)blockIdx.x * 32;                   // destination column tile
+    if (bj > bi) return;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    // load source block rows bj.., cols bi.. (upper part)
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t sr = bj + k, sc = bi + tx;
+        tile[k][tx] = (sr < r1 && sc < r1) ? V[sr * ld + sc] : T(0);
+    }
+    __syncthreads();
+    for (int k = ty; k < 32; k += 8) {
+        const int64_t i = bi + k, j = bj + tx;
+        if (i >= r0 && i < r1 && j < i) V[i * ld + j] = tile[tx][k];
+    }
+}
+
+// ------------------------------------------------------------------ near field
+struct Tri {
+    double p[3][3];
+};
+
+__device__ __forceinline__ double inv_norm3(double x, double y, double z)
+{
+    return rsqrt(x * x + y * y + z * z);
+}
+
+// Identical panels: (1/6) sum over the 6 hexagon sectors of int_0^1 1/|J w(eta)|.
+__device__ double ss_identical(const Tri &P, int n)
+{
+    const double *gx = c_glx[n], *gw = c_glw[n];
+    const double J1[3] = {P.p[1][0] - P.p[0][0], P.p[1][1] - P.p[0][1], P.p[1][2] - P.p[0][2]};
+    const double J2[3] = {P.p[2][0] - P.p[1][0], P.p[2][1] - P.p[1][1], P.p[2][2] - P.p[1][2]};
+    const double H[7][2] = {{1, 0}, {1, 1}, {0, 1}, {-1, 0}, {-1, -1}, {0, -1}, {1, 0}};
+    double s = 0.0;
+    for (int k = 0; k < 6; ++k) {
+        const double px = H[k][0], py = H[k][1], qx = H[k + 1][0], qy = H[k + 1][1];
+        for (int g = 0; g < n; ++g) {
+            const double z1 = px + gx[g] * (qx - px), z2 = py + gx[g] * (qy - py);
+            s += gw[g] * inv_norm3(z1 * J1[0] + z2 * J2[0], z1 * J1[1] + z2 * J2[1], z1 * J1[2] + z2 * J2[2]);
+        }
+    }
+    return s / 6.0;
+}
+
+// Common edge: P = (A,B,C), Q = (A,B,D).  x - y = xi rho (+-a e + t1 fP - t2 fQ).
+__device__ double ss_edge(const Tri &P, const Tri &Q, int n)
+{
+    const double *gx = c_glx[n], *gw = c_glw[n];
+    double e[3], fP[3], fQ[3];
+    for (int c = 0; c < 3; ++c) {
+        e[c] = P.p[1][c] - P.p[0][c];
+        fP[c] = P.p[2][c] - P.p[1][c];
+        fQ[c] = Q.p[2][c] - Q.p[1][c];
+    }
+    double s = 0.0;
+    for (int iu = 0; iu < n; ++iu)
+        for (int iv = 0; iv < n; ++iv) {
+            const double u = gx[iu], v = gx[iv], w = gw[iu] * gw[iv];
+            // sub-region a: (own, a, other) = (1, u(1-v), uv), weight u
+            // sub-region b: (own, a, other) = (u, 1-v, v),    weight 1
+            const double oa = 1.0, aa = u * (1.0 - v), ha = u * v;
+            const double ob = u, ab = 1.0 - v, hb = v;
+            double t = 0.0;
+            // region 1 (s1 = xi): vec = a e + own fP - other fQ
+            t += u * inv_norm3(aa * e[0] + oa * fP[0] - ha * fQ[0], aa * e[1] + oa * fP[1] - ha * fQ[1],
+                               aa * e[2] + oa * fP[2] - ha * fQ[2]);
+            t += inv_norm3(ab * e[0] + ob * fP[0] - hb * fQ[0], ab * e[1] + ob * fP[1] - hb * fQ[1],
+                           ab * e[2] + ob * fP[2] - hb * fQ[2]);
+            // region 2 (s2 = xi): vec = -a e + other fP - own fQ
+            t += u * inv_norm3(-aa * e[0] + ha * fP[0] - oa * fQ[0], -aa * e[1] + ha * fP[1] - oa * fQ[1],
+                               -aa * e[2] + ha * fP[2] - oa * fQ[2]);
+            t += inv_norm3(-ab * e[0] + hb * fP[0] - ob * fQ[0], -ab * e[1] + hb * fP[1] - ob * fQ[1],
+                           -ab * e[2] + hb * fP[2] - ob * fQ[2]);
+            s += w * t;
+        }
+    return s / 6.0;
+}
+
+// Common vertex: P = (A,B,C), Q = (A,D,E).  Regions x = (1,e1), y = e2 (1,e3) and
+// x = e2 (1,e1), y = (1,e3), weight e2.
+__device__ double ss_vertex(const Tri &P, const Tri &Q, int n)
+{
+    const double *gx = c_glx[n], *gw = c_glw[n];
+    double a1[3], a2[3], b1[3], b2[3];
+    for (int c = 0; c < 3; ++c) {
+        a1[c] = P.p[1][c] - P.p[0][c];
+        a2[c] = P.p[2][c] - P.p[1][c];
+        b1[c] = Q.p[1][c] - Q.p[0][c];
+        b2[c] = Q.p[2][c] - Q.p[1][c];
+    }
+    double s = 0.0;
+    for (int i1 = 0; i1 < n; ++i1) {
+        double xa[3];
+        for (int c = 0; c < 3; ++c) xa[c] = a1[c] + gx[i1] * a2[c];
+        for (int i3 = 0; i3 < n; ++i3) {
+            double yb[3];
+            for (int c = 0; c < 3; ++c) yb[c] = b1[c] + gx[i3] * b2[c];
+            double t = 0.0;
+            for (int i2 = 0; i2 < n; ++i2) {
+                const double e2 = gx[i2];
+                const double r1 = inv_norm3(xa[0] - e2 * yb[0], xa[1] - e2 * yb[1], xa[2] - e2 * yb[2]);
+                const double r2 = inv_norm3(e2 * xa[0] - yb[0], e2 * xa[1] - yb[1], e2 * xa[2] - yb[2]);
+                t += gw[i2] * e2 * (r1 + r2);
+            }
+            s += gw[i1] * gw[i3] * t;
+        }
+    }
+    return s / 3.0;
+}
+
+__device__ __forceinline__ void load_tri(const double *verts, const int32_t *v, Tri &T)
+{
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c) T.p[k][c] = verts[3 * (int64_t)v[k] + c];
+}
+
+// kind 0: identical pairs i = j = K + idx; 1: common-vertex list; 2: common-edge list.
+// Pairs (i < j) with j < K are skipped (their entries are reused).
+template <typename T>
+__global__ void k_near(const double *__restrict__ verts, const int32_t *__restrict__ tris,
+                       const double *__restrict__ area, const int32_t *__restrict__ pairs, int64_t npairs,
+                       int kind, int64_t K, int n, T *V, int64_t ld)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npairs) return;
+    int64_t i, j;
+    if (kind == 0) {
+        i = j = K + idx;
+    } else {
+        i = pairs[2 * idx];
+        j = pairs[2 * idx + 1];
+        if (j < K) return;
+    }
+    const int32_t *ti = tris + 3 * i, *tj = tris + 3 * j;
+    double I;
+    if (kind == 0) {
+        Tri P;
+        load_tri(verts, ti, P);
+        I = ss_identical(P, n);
+    } else if (kind == 2) {
+        // (u, v) = the shared vertices in the order they appear in triangle i
+        int32_t u = -1, v = -1, ci = -1, cj = -1;
+        for (int k = 0; k < 3; ++k) {
+            const bool in = (ti[k] == tj[0] || ti[k] == tj[1] || ti[k] == tj[2]);
+            if (in) {
+                if (u < 0) u = ti[k];
+                else v = ti[k];
+            } else {
+                ci = ti[k];
+            }
+        }
+        for (int k = 0; k < 3; ++k)
+            if (tj[k] != u && tj[k] != v) cj = tj[k];
+        const int32_t pi[3] = {u, v, ci}, pj[3] = {u, v, cj};
+        Tri P, Q;
+        load_tri(verts, pi, P);
+        load_tri(verts, pj, Q);
+        I = ss_edge(P, Q, n);
+    } else {
+        int ki = 0, kj = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (ti[a] == tj[b]) {
+                    ki = a;
+                    kj = b;
+                }
+        const int32_t pi[3] = {ti[ki], ti[(ki + 1) % 3], ti[(ki + 2) % 3]};
+        const int32_t pj[3] = {tj[kj], tj[(kj + 1) % 3], tj[(kj + 2) % 3]};
+        Tri P, Q;
+        load_tri(verts, pi, P);
+        load_tri(verts, pj, Q);
+        I = ss_vertex(P, Q, n);
+    }
+    const double v = 4.0 * area[i] * area[j] * I * kInv4Pi;
+    V[i * ld + j] = (T)v;
+    if (i != j) V[j * ld + i] = (T)v;
+}
+
+// ------------------------------------------------------------------ reuse and diagonal
+// V'[i][j] = Vc[parent[i]][parent[j]] for i, j < K (unrefined triangles).
+template <typename T>
+__global__ void k_gather_kept(const T *__restrict__ Vc, int64_t ldc, const int32_t *__restrict__ parent,
+                              int64_t K, T *__restrict__ V, int64_t ld)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= K) return;
+    const int64_t pj = parent[j];
+    for (int64_t i = blockIdx.y; i < K; i += gridDim.y) V[i * ld + j] = Vc[(int64_t)parent[i] * ldc + pj];
+}
+
+template <typename T>
+__global__ void k_diag(const T *V, int64_t ld, int64_t N, double *d)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) d[i] = (double)V[i * ld + i];
+}
+
+// ------------------------------------------------------------------ drivers
+template <typename T>
+static bem_status launch_far(bem_operator *op, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+{
+    if (r1 <= r0 || c1 <= c0) return BEM_OK;
+    bem_mesh *m = op->mesh;
+    bem_ctx *ctx = m->ctx;
+    const int64_t gx = (c1 - c0 + kFarCols - 1) / kFarCols;
+    const int64_t gy = (r1 - r0 + kFarRows - 1) / kFarRows;
+    if (gy > 65535) {
+        // split rows into chunks that fit the grid's y limit
+        for (int64_t rs = r0; rs < r1; rs += 65535LL * kFarRows) {
+            const int64_t re = rs + 65535LL * kFarRows < r1 ? rs + 65535LL * kFarRows : r1;
+            bem_status st = launch_far<T>(op, rs, re, c0, c1);
+            if (st) return st;
+        }
+        return BEM_OK;
+    }
+    dim3 grid((unsigned)gx, (unsigned)gy);
+    double units = 0.0;  // entries with i <= j in the block
+    for (int64_t i = r0; i < r1; ++i) {
+        const int64_t lo = i > c0 ? i : c0;
+        if (c1 > lo) units += (double)(c1 - lo);
+    }
+    const int prof = prof_start(ctx, BEM_KERNEL_FAR, units);
+    if (sizeof(T) == 8)
+        { k_far_f64<<<grid, kFarCols, 0, ctx->stream>>>(m->q64, (double *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
+    else
+        { k_far_f32<<<grid, kFarCols, 0, ctx->stream>>>(m->q32, m->cent, (float *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
+    prof_stop(ctx, prof);
+    BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
+
+template <typename T>
+static bem_status launch_mirror(bem_operator *op, int64_t r0, int64_t r1)
+{
+    if (r1 <= r0) return BEM_OK;
+    bem_ctx *ctx = op->mesh->ctx;
+    const int64_t t0 = r0 / 32, t1 = (r1 + 31) / 32;
+    for (int64_t ts = t0; ts < t1; ts += 65535) {
+        const int64_t te = ts + 65535 < t1 ? ts + 65535 : t1;
+        dim3 grid((unsigned)te, (unsigned)(te - ts));
+        k_mirror<T><<<grid, dim3(32, 8), 0, ctx->stream>>>((T *)op->V, op->ld, ts * 32 > r0 ? ts * 32 : r0,
+                                                           te * 32 < r1 ? te * 32 : r1); BEM_COUNT(ctx);
+        BEM_CK_LAUNCH(ctx);
+    }
+    return BEM_OK;
+}
+
+template <typename T>
+static bem_status launch_near(bem_operator *op, int64_t K)
+{
+    bem_mesh *m = op->mesh;
+    bem_ctx *ctx = m->ctx;
+    const int n = op->ss_order;
+    const int prof = prof_start(ctx, BEM_KERNEL_NEAR, (double)(m->N - K + m->n_vert_pairs + m->n_edge_pairs));
+    if (m->N > K)
+        { k_near<T><<<nblk(m->N - K, 128), 128, 0, ctx->stream>>>(m->verts, m->tris, m->area, nullptr, m->N - K, 0,
+                                                                K, n, (T *)op->V, op->ld); BEM_COUNT(ctx); }
+    if (m->n_vert_pairs > 0)
+        { k_near<T><<<nblk(m->n_vert_pairs, 128), 128, 0, ctx->stream>>>(
+            m->verts, m->tris, m->area, m->vert_pairs, m->n_vert_pairs, 1, K, n, (T *)op->V, op->ld); BEM_COUNT(ctx); }
+    if (m->n_edge_pairs > 0)
+        { k_near<T><<<nblk(m->n_edge_pairs, 128), 128, 0, ctx->stream>>>(
+            m->verts, m->tris, m->area, m->edge_pairs, m->n_edge_pairs, 2, K, n, (T *)op->V, op->ld); BEM_COUNT(ctx); }
+    prof_stop(ctx, prof);
+    BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
+
+template <typename T>
+static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
+{
+    bem_mesh *m = op->mesh;
+    bem_ctx *ctx = m->ctx;
+    const int64_t N = m->N;
+    BEM_CK(ctx, cudaMemsetAsync(op->V, 0, sizeof(T) * N * op->ld, ctx->stream));
+    bem_status st;
+    int64_t K = 0;
+    if (coarse) {
+        K = m->n_kept;
+        if (K > 0) {
+            dim3 grid(nblk(K, 256), (unsigned)(K < 65535 ? K : 65535));
+            k_gather_kept<T><<<grid, 256, 0, ctx->stream>>>((const T *)coarse->V, coarse->ld, m->parent, K,
+                                                            (T *)op->V, op->ld); BEM_COUNT(ctx);
+            BEM_CK_LAUNCH(ctx);
+        }
+        if ((st = launch_far<T>(op, 0, K, K, N))) return st;
+    }
+    if ((st = launch_far<T>(op, K, N, K, N))) return st;
+    if ((st = launch_mirror<T>(op, K > 0 ? K : 0, N))) return st;
+    if ((st = launch_near<T>(op, K))) return st;
+    k_diag<T><<<nblk(N, 256), 256, 0, ctx->stream>>>((const T *)op->V, op->ld, N, op->diag); BEM_COUNT(ctx);
+    BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
+
+bem_status gauss_legendre_upload(int n)
+{
+    (void)n;
+    return BEM_OK;
+}
+
+bem_status assemble_full(bem_operator *op)
+{
+    bem_status st = assembly_constants(op->mesh->ctx);
+    if (st) return st;
+    return op->precision == BEM_PREC_F64 ? assemble_t<double>(op, nullptr) : assemble_t<float>(op, nullptr);
+}
+
+bem_status assemble_update(bem_operator *op, const bem_operator *coarse)
+{
+    bem_status st = assembly_constants(op->mesh->ctx);
+    if (st) return st;
+    return op->precision == BEM_PREC_F64 ? assemble_t<double>(op, coarse) : assemble_t<float>(op, coarse);
+}
+
+bem_status operator_diag(bem_operator *op)
+{
+    bem_ctx *ctx = op->mesh->ctx;
+    if (op->precision == BEM_PREC_F64)
+        { k_diag<double><<<nblk(op->N, 256), 256, 0, ctx->stream>>>((const double *)op->V, op->ld, op->N, op->diag); BEM_COUNT(ctx); }
+    else
+        { k_diag<float><<<nblk(op->N, 256), 256, 0, ctx->stream>>>((const float *)op->V, op->ld, op->N, op->diag); BEM_COUNT(ctx); }
+    BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
+
+}  // namespace bem

@@ -1,0 +1,155 @@
+// Internal declarations of the GB300 BEM capacity library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/bem.h"
+
+namespace bem {
+
+constexpr int kQ = 7;              // far-field points per triangle (Radon degree 5)
+constexpr int kQ64Stride = 24;     // doubles per triangle in the FP64 point table
+constexpr int kQ32Stride = 24;     // floats per triangle in the FP32 offset table
+constexpr int kMaxSS = 16;         // largest Sauter-Schwab order accepted
+constexpr int kMaxValence = 96;    // triangles per vertex accepted by the pair builder
+constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+
+// Row stride of the dense operator: N rounded up to 32 elements so that every row
+// starts on a 256-byte boundary (vector loads in the matvec).
+inline int64_t padded_ld(int64_t n) { return (n + 31) / 32 * 32; }
+
+struct Allocs {
+    std::vector<std::pair<void *, size_t>> list;
+    size_t bytes = 0;
+};
+
+}  // namespace bem
+
+namespace bem {
+struct ProfRec {
+    int id;
+    cudaEvent_t a, b;
+    double units;
+};
+constexpr int kProfKinds = 4;
+}  // namespace bem
+
+struct bem_ctx {
+    int64_t n_launch = 0;  // kernels launched by this context
+    int profile = 0;       // record CUDA events around the hot kernels
+    std::vector<bem::ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+    int64_t prof_launches[bem::kProfKinds] = {0, 0, 0, 0};
+    double prof_ms[bem::kProfKinds] = {0, 0, 0, 0};
+    double prof_units[bem::kProfKinds] = {0, 0, 0, 0};
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    int sm_count = 0;
+    int64_t budget = 0;  // <= 0: unlimited
+    int64_t in_use = 0;
+    char err[1024] = {0};
+    double *h_pinned = nullptr;  // 64 doubles of pinned host memory for scalar readbacks
+    cudaEvent_t ev[8] = {};
+};
+
+struct bem_mesh {
+    bem_ctx *ctx = nullptr;
+    int64_t M = 0, N = 0;
+    double *verts = nullptr;    // M x 3
+    int32_t *tris = nullptr;    // N x 3, reference edge first
+    double *area = nullptr;     // N
+    double *diam = nullptr;     // N
+    double *q64 = nullptr;      // N x 24: 7 points (x,y,z), [21] = area
+    float *q32 = nullptr;       // N x 24: 7 offsets from the centroid (x,y,z)
+    double *cent = nullptr;     // N x 4: centroid (x,y,z), area
+    int32_t *v2t_off = nullptr; // M + 1
+    int32_t *v2t = nullptr;     // 3N, ascending triangle index per vertex
+    int32_t *owner = nullptr;   // 3N: half-edge -> first half-edge of its edge
+    int64_t n_edge_pairs = 0;   // touching pairs i < j sharing an edge
+    int64_t n_vert_pairs = 0;   // touching pairs i < j sharing one vertex
+    int32_t *edge_pairs = nullptr;  // 2 x n_edge_pairs (i, j), ascending (i, j)
+    int32_t *vert_pairs = nullptr;  // 2 x n_vert_pairs
+    int32_t *parent = nullptr;  // N or null (refined meshes)
+    uint8_t *kept = nullptr;    // N or null
+    int64_t n_kept = 0;         // refined meshes: triangles [0, n_kept) are unrefined
+    int64_t src_N = 0;          // refined meshes: N of the source mesh
+    bem::Allocs allocs;
+};
+
+struct bem_operator {
+    bem_mesh *mesh = nullptr;
+    int32_t precision = BEM_PREC_F64;
+    int32_t ss_order = 4;
+    int64_t N = 0, ld = 0;
+    void *V = nullptr;      // N x ld, row-major
+    double *diag = nullptr; // N, FP64 diagonal
+    bem::Allocs allocs;
+};
+
+namespace bem {
+
+// ----------------------------------------------------------------- host helpers
+bem_status set_error(bem_ctx *ctx, bem_status code, const char *fmt, ...);
+bem_status cuda_error(bem_ctx *ctx, cudaError_t e, const char *what);
+bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero);
+void dfree_all(bem_ctx *ctx, Allocs &a);
+bool is_device_ptr(const void *p);
+
+#define BEM_CK(ctx, call)                                              \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) return ::bem::cuda_error(ctx, e_, #call); \
+    } while (0)
+
+#define BEM_CK_LAUNCH(ctx) BEM_CK(ctx, cudaGetLastError())
+#define BEM_COUNT(ctx) (++(ctx)->n_launch)
+
+// Event pair around one hot-kernel launch (no-op unless profiling is on).
+int prof_start(bem_ctx *ctx, int id, double units);
+void prof_stop(bem_ctx *ctx, int rec);
+
+// Temporary device copy of a caller array (host or device).
+struct DevBuf {
+    bem_ctx *ctx = nullptr;
+    void *dptr = nullptr;
+    void *owned = nullptr;
+    size_t bytes = 0;
+    ~DevBuf();
+};
+bem_status dev_in(bem_ctx *ctx, const void *src, size_t bytes, DevBuf &buf);
+bem_status dev_out_begin(bem_ctx *ctx, void *dst, size_t bytes, DevBuf &buf);
+bem_status dev_out_end(bem_ctx *ctx, void *dst, DevBuf &buf);
+
+// Exclusive prefix sum of n int32 counts into out (n + 1 entries), on the stream;
+// returns the total through a synchronous read when total != nullptr.
+bem_status exclusive_scan_i32(bem_ctx *ctx, const int32_t *in, int32_t *out, int64_t n,
+                              int64_t *total);
+
+// ----------------------------------------------------------------- mesh (mesh.cu)
+// Build every derived array of a mesh whose verts / tris are already on the device.
+bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge);
+
+// ----------------------------------------------------------------- assembly (assemble.cu)
+bem_status gauss_legendre_upload(int n);
+bem_status assemble_full(bem_operator *op);
+bem_status assemble_update(bem_operator *op, const bem_operator *coarse);
+bem_status operator_diag(bem_operator *op);
+
+// ----------------------------------------------------------------- solve (solve.cu)
+bem_status matvec_f64(bem_operator *op, const double *x, double *y);
+bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const double *d_x0,
+                          double *d_x, double *cap, bem_solve_info *info);
+
+// ----------------------------------------------------------------- adaptivity (adapt.cu)
+bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_eta2,
+                       double *h_totals);
+bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, uint8_t *d_marked,
+                   int64_t *n_marked);
+bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out);
+
+}  // namespace bem

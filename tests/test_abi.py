@@ -1,0 +1,37 @@
+"""CPU checks of the C ABI boundary: the library builds, loads without a GPU and
+exports every entry point include/bem.h declares; the binding names match."""
+import ctypes
+import os
+import re
+
+from paper_1901_08393_gb300 import bem
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:bem_status|const char \*)\s*(bem_\w+)\s*\(", src, re.M)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("bem_mesh_upload", "bem_assemble_V", "bem_solve_capacity", "bem_zz_estimate",
+                     "bem_mark_refine"):
+        assert required in names
+    assert set(names) == set(bem.EXPORTS + ["bem_last_error"])
+
+
+def test_library_exports_every_symbol():
+    from paper_1901_08393_gb300 import build
+
+    build.build()
+    L = ctypes.CDLL(bem.LIB_PATH)
+    for name in _declared():
+        assert hasattr(L, name), name
+    assert bem.lib() is not None
+
+
+def test_no_torch_types_in_header():
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    assert "torch" not in src.lower().replace("pytorch", "") and "at::" not in src

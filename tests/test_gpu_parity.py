@@ -1,0 +1,273 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: FP64 entries 1e-10 relative, FP32 entries 1e-5 relative, Cap 1e-9
+(FP64) / 1e-7 (FP32 + FP64 refinement) relative; geometry, ZZ indicators,
+marks and refined meshes bit-exact when both sides get the same bytes.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1901_08393_gb300 import bem, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("GPU tests need a CUDA device")
+    c = bem.Context()
+    yield c
+    c.close()
+
+
+def _upload(ctx, m):
+    mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+    v, t, p, k = mesh.download()
+    return mesh, v, t
+
+
+def _rel(a, b):
+    return np.max(np.abs(a - b) / np.abs(b))
+
+
+MESHES = [inputs.cube_mesh(1), inputs.cube_mesh(4), inputs.workload_polycube_adaptive(),
+          inputs.fichera_mesh(2), inputs.tetra_mesh(5), inputs.icosphere_mesh(3)]
+
+
+@pytest.mark.parametrize("m", MESHES, ids=lambda m: m.name)
+def test_mesh_canonical_and_geometry_bitexact(ctx, m):
+    mesh, v, t = _upload(ctx, m)
+    assert np.array_equal(v, m.verts)
+    assert np.array_equal(t, O.canonical(m.verts, m.tris))
+    a, d = mesh.geometry()
+    ar, dr = O.geometry(v, t)
+    assert np.array_equal(a, ar) and np.array_equal(d, dr)
+    _, _, n_near = mesh.info()
+    n_ref = sum(1 for i in range(m.N) for j in range(m.N) if i != j and O.pair_type(t, i, j) > 0) \
+        if m.N <= 800 else None
+    if n_ref is not None:
+        assert n_near == n_ref
+
+
+@pytest.mark.parametrize("m", MESHES, ids=lambda m: m.name)
+def test_assembly_f64_matches_oracle(ctx, m):
+    mesh, v, t = _upload(ctx, m)
+    V = bem.Operator.assemble(mesh).read()
+    Vr = O.assemble(v, t)
+    assert np.array_equal(V, V.T)
+    assert _rel(V, Vr) < 1e-10
+
+
+@pytest.mark.parametrize("m", MESHES[1:4], ids=lambda m: m.name)
+def test_assembly_f32_matches_oracle(ctx, m):
+    mesh, v, t = _upload(ctx, m)
+    V = bem.Operator.assemble(mesh, precision=bem.PREC_F32).read()
+    assert V.dtype == np.float32
+    Vr = O.assemble(v, t)
+    assert _rel(V.astype(np.float64), Vr) < 1e-5
+
+
+@pytest.mark.parametrize("n", [2, 3, 6, 9])
+def test_sauter_schwab_orders(ctx, n):
+    m = inputs.workload_polycube_adaptive()
+    mesh, v, t = _upload(ctx, m)
+    op = bem.Operator.assemble(mesh, ss_order=n)
+    rng = np.random.default_rng(n)
+    near = np.array([(i, j) for i in range(0, m.N, 7) for j in range(m.N) if O.pair_type(t, i, j) > 0])
+    I, J = near[:, 0], near[:, 1]
+    assert _rel(op.entries(I, J), O.entries(v, t, I, J, n)) < 1e-10
+    I2 = rng.integers(0, m.N, 500)
+    J2 = rng.integers(0, m.N, 500)
+    assert _rel(op.entries(I2, J2), O.entries(v, t, I2, J2, n)) < 1e-10
+
+
+def test_matvec_f64(ctx):
+    m = inputs.workload_polycube_adaptive()
+    mesh, v, t = _upload(ctx, m)
+    op = bem.Operator.assemble(mesh)
+    V = op.read()
+    x = np.random.default_rng(0).standard_normal(m.N)
+    y = op.matvec(x)
+    yr = V @ x
+    assert np.max(np.abs(y - yr)) < 1e-13 * np.max(np.abs(V).sum(1) * np.max(np.abs(x)))
+
+
+@pytest.mark.parametrize("precond", [bem.PRECOND_JACOBI, bem.PRECOND_NONE])
+@pytest.mark.parametrize("m", [inputs.cube_mesh(4), inputs.workload_polycube_adaptive()], ids=lambda m: m.name)
+def test_solve_capacity_f64(ctx, m, precond):
+    mesh, v, t = _upload(ctx, m)
+    op = bem.Operator.assemble(mesh)
+    cap, phi, info = bem.solve_capacity(op, tol=1e-12, precond=precond)
+    cap_r, x_r, its_r, V = O.solve_capacity(v, t, tol=1e-12, precond=precond)
+    assert info["converged"] and info["relres"] <= 1e-12, info
+    assert abs(cap / cap_r - 1) < 1e-10, (cap, cap_r)
+    b = O.geometry(v, t)[0]
+    res = np.linalg.norm(V @ phi - b) / np.linalg.norm(b)
+    assert res < 1e-11, res  # true residual of the GPU solution against the oracle's V
+    assert abs(info["iterations"] - its_r) <= 3 + its_r // 10, (info["iterations"], its_r)
+
+
+def test_solve_capacity_f32_refinement(ctx):
+    m = inputs.workload_polycube_adaptive()
+    mesh, v, t = _upload(ctx, m)
+    cap64, _, _ = bem.solve_capacity(bem.Operator.assemble(mesh), tol=1e-12)
+    op32 = bem.Operator.assemble(mesh, precision=bem.PREC_F32)
+    cap32, phi32, info = bem.solve_capacity(op32, tol=1e-12)
+    assert info["converged"] and info["outer"] >= 2
+    cap_r = O.solve_capacity(v, t, tol=1e-12)[0]
+    assert abs(cap64 / cap_r - 1) < 1e-10
+    assert abs(cap32 / cap_r - 1) < 1e-6  # FP32 storage of V: |dCap/Cap| <= u32-level
+
+
+def test_zz_bitexact_same_phi(ctx):
+    for m in (inputs.workload_polycube_adaptive(), inputs.icosphere_mesh(4), inputs.cube_mesh(3)):
+        mesh, v, t = _upload(ctx, m)
+        x = O.solve_capacity(v, t, tol=1e-12)[1]
+        for h_mode in (0, 1):
+            eta2, tot, scale = bem.zz_estimate(mesh, x, h_mode)
+            e_r, s_r = O.zz(v, t, x, h_mode, with_scale=True)
+            assert np.array_equal(eta2, e_r)
+            assert abs(tot / e_r.sum() - 1) < 1e-12 and abs(scale / s_r - 1) < 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 31, 1000, 2048, 2049, 5000, 70000])
+def test_dorfler_bitexact(ctx, N):
+    rng = np.random.default_rng(N)
+    for theta in (0.2, 0.5, 0.9, 1.0):
+        eta2 = rng.random(N) ** 4
+        if N > 10:  # exact ties and single-precision ties
+            eta2[: N // 10] = eta2[N // 10]
+            eta2[N // 10: N // 5] = np.nextafter(eta2[N // 10: N // 5], 1.0)
+        m, n = bem.dorfler(ctx, eta2, theta)
+        mr = O.dorfler(eta2, theta)
+        assert np.array_equal(m, mr), (N, theta)
+        assert n == int(mr.sum())
+    m, n = bem.dorfler(ctx, np.zeros(N), 0.5)
+    assert n == 0 and not m.any()
+
+
+def test_refine_bitexact(ctx):
+    m = inputs.workload_polycube_adaptive()
+    mesh, v, t = _upload(ctx, m)
+    rng = np.random.default_rng(3)
+    for step in range(4):
+        bisec3 = step == 2
+        marked = (rng.random(t.shape[0]) < 0.2).astype(np.uint8)
+        fine = bem.refine(mesh, marked, bisec3=bisec3)
+        v2, t2, p2, k2 = fine.download()
+        vr, tr, pr, kr = O.refine(v, t, marked, bisec3=bisec3)
+        assert np.array_equal(v2, vr) and np.array_equal(t2, tr)
+        assert np.array_equal(p2, pr) and np.array_equal(k2, kr)
+        mesh, v, t = fine, v2, t2
+
+
+def test_incremental_assembly_bitexact(ctx):
+    for prec in (bem.PREC_F64, bem.PREC_F32):
+        m = inputs.workload_polycube_adaptive()
+        mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+        op = bem.Operator.assemble(mesh, precision=prec)
+        rng = np.random.default_rng(prec)
+        for step in range(3):
+            marked = (rng.random(mesh.N) < 0.15).astype(np.uint8)
+            fine = bem.refine(mesh, marked)
+            inc = bem.Operator.update(fine, op)
+            full = bem.Operator.assemble(fine, precision=prec)
+            assert np.array_equal(inc.read(), full.read())
+            mesh, op = fine, inc
+
+
+def test_mark_refine_and_adaptive_loop_match_oracle(ctx):
+    m = inputs.workload_polycube_adaptive()
+    mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+    recs, fin = bem.adaptive_run(mesh, theta=0.5, max_N=2500, tol=1e-12, want_final=True)
+    hist = O.adaptive_run(m.verts, m.tris, theta=0.5, max_N=2500, tol=1e-12)
+    assert len(recs) == len(hist)
+    for r, h in zip(recs, hist):
+        assert r["N"] == h["N"] and r["M"] == h["M"]
+        assert abs(r["cap"] / h["cap"] - 1) < 1e-9
+        if "marked" in h:
+            assert r["n_marked"] == int(h["marked"].sum())
+    v, t, _, _ = fin.download()
+    assert np.array_equal(v, hist[-1]["verts"]) and np.array_equal(t, hist[-1]["tris"])
+    caps = [r["cap"] for r in recs]
+    assert all(b > a * (1 - 1e-6) for a, b in zip(caps, caps[1:]))
+
+
+def test_device_pointers(ctx):
+    import torch
+
+    m = inputs.cube_mesh(3)
+    v = torch.from_numpy(m.verts).cuda()
+    t = torch.from_numpy(m.tris).cuda()
+    mesh = bem.Mesh.upload(ctx, v, t)
+    op = bem.Operator.assemble(mesh)
+    phi_dev = torch.zeros(m.N, dtype=torch.float64, device="cuda")
+    cap, phi, info = bem.solve_capacity(op, tol=1e-12, phi_out=phi_dev)
+    cap_h, phi_h, _ = bem.solve_capacity(bem.Operator.assemble(bem.Mesh.upload(ctx, m.verts, m.tris)), tol=1e-12)
+    assert cap == cap_h
+    assert np.array_equal(phi.cpu().numpy(), phi_h)
+    e1, _, _ = bem.zz_estimate(mesh, phi)
+    e2, _, _ = bem.zz_estimate(mesh, phi_h)
+    assert np.array_equal(e1, e2)
+
+
+def test_errors_are_reported(ctx):
+    m = inputs.cube_mesh(1)
+    with pytest.raises(bem.BemError) as e:
+        bem.Mesh.upload(ctx, m.verts, m.tris[:0])
+    assert e.value.code == bem.BEM_ERR_INVALID
+    with pytest.raises(bem.BemError) as e:  # open surface
+        bem.Mesh.upload(ctx, m.verts, m.tris[:-1])
+    assert e.value.code == bem.BEM_ERR_MESH
+    bad = m.tris.copy()
+    bad[0, 0] = m.M + 5
+    with pytest.raises(bem.BemError) as e:
+        bem.Mesh.upload(ctx, m.verts, bad)
+    assert e.value.code == bem.BEM_ERR_MESH
+    dup = np.concatenate([m.tris, m.tris[:1], m.tris[:1]])
+    with pytest.raises(bem.BemError) as e:
+        bem.Mesh.upload(ctx, m.verts, dup)
+    assert e.value.code == bem.BEM_ERR_MESH
+    flat = m.verts.copy()
+    flat[:, 2] = 0.0  # squashes some triangles to zero area
+    with pytest.raises(bem.BemError) as e:
+        bem.Mesh.upload(ctx, flat, m.tris)
+    assert e.value.code == bem.BEM_ERR_MESH
+    mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+    with pytest.raises(bem.BemError) as e:
+        bem.dorfler(ctx, np.ones(4), 0.0)
+    assert e.value.code == bem.BEM_ERR_INVALID
+    op = bem.Operator.assemble(mesh)
+    with pytest.raises(bem.BemError) as e:
+        op.entries([0, 99], [0, 0])
+    assert e.value.code == bem.BEM_ERR_INVALID
+    cap, phi, info = bem.solve_capacity(op, tol=1e-30, max_it=1, raise_not_converged=False)
+    assert not info["converged"] and cap > 0
+    small = bem.Context(hbm_budget_bytes=1 << 16)
+    with pytest.raises(bem.BemError) as e:
+        bem.Operator.assemble(bem.Mesh.upload(small, *_big()))
+    assert e.value.code == bem.BEM_ERR_OOM
+    assert "budget" in small.last_error()
+    with pytest.raises(bem.BemError) as e:
+        bem.Operator.assemble(mesh, ss_order=1)
+    assert e.value.code == bem.BEM_ERR_INVALID
+
+
+def _big():
+    m = inputs.cube_mesh(8)
+    return m.verts, m.tris
+
+
+def test_memory_released(ctx):
+    before = ctx.memory_in_use()
+    m = inputs.cube_mesh(4)
+    mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+    op = bem.Operator.assemble(mesh)
+    bem.solve_capacity(op)
+    op.close()
+    mesh.close()
+    assert ctx.memory_in_use() == before
