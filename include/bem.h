@@ -53,11 +53,15 @@ typedef struct bem_mesh bem_mesh;
 typedef struct bem_operator bem_operator;
 
 /* Storage/arithmetic precision of V. */
-#define BEM_PREC_F64 0  /* V stored and applied in FP64 */
+#define BEM_PREC_F64 0  /* V stored and applied in native FP64 */
 #define BEM_PREC_F32 1  /* V stored in FP32 (near field computed in FP64, rounded) */
+#define BEM_PREC_DF64 2 /* FP64-accurate "double-float": V stored as pairs hi + lo of FP32
+                           (48-bit significand, entries within ~4e-15 relative of FP64);
+                           far field and V x computed with error-free FP32 transformations
+                           on the FP32 pipe, near field in FP64 */
 
 typedef struct {
-    int32_t precision; /* BEM_PREC_F64 or BEM_PREC_F32 */
+    int32_t precision; /* BEM_PREC_F64, BEM_PREC_F32 or BEM_PREC_DF64 */
     int32_t ss_order;  /* Gauss-Legendre points per variable for touching pairs (2..16, default 4;
                           the radial variables are integrated exactly, which equals the
                           n-point rule in them for n >= 2) */
@@ -130,14 +134,15 @@ bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse,
                                  const bem_assembly_opts *opts, bem_operator **out);
 bem_status bem_operator_destroy(bem_operator *op);
 bem_status bem_operator_info(const bem_operator *op, int64_t *N, int32_t *precision);
-/* Copy the block V[i0:i0+ni, j0:j0+nj] (row-major, ni x nj, in the operator's
- * precision) into dst (host or device). */
+/* Copy the block V[i0:i0+ni, j0:j0+nj] (row-major, ni x nj) into dst (host or
+ * device): float64 for F64 and DF64 operators (DF64 entries as hi + lo), float32
+ * for F32 operators. */
 bem_status bem_operator_read(const bem_operator *op, int64_t i0, int64_t ni, int64_t j0,
                              int64_t nj, void *dst);
 /* out[k] = V[I[k]][J[k]] as FP64 for K sampled entries (arrays host or device). */
 bem_status bem_operator_entries(const bem_operator *op, const int64_t *I, const int64_t *J,
                                 int64_t K, double *out);
-/* y = V x, FP64 vectors of length N (host or device). */
+/* y = V x, FP64 vectors of length N (host or device), in the operator's arithmetic. */
 bem_status bem_operator_matvec(const bem_operator *op, const double *x, double *y);
 
 /* ---------------------------------------------------------------- solve */

@@ -24,6 +24,7 @@ BEM_ERR_MESH = -4
 BEM_ERR_CUDA = -5
 PREC_F64 = 0
 PREC_F32 = 1
+PREC_DF64 = 2
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 REFINE_BISEC3 = 1
@@ -283,7 +284,7 @@ class Operator:
         N, p = self.info()
         ni = N - i0 if ni is None else ni
         nj = N - j0 if nj is None else nj
-        out = np.zeros((ni, nj), dtype=np.float64 if p == PREC_F64 else np.float32)
+        out = np.zeros((ni, nj), dtype=np.float32 if p == PREC_F32 else np.float64)
         self.ctx.check(self.ctx.L.bem_operator_read(self.h, i0, ni, j0, nj, out.ctypes.data))
         return out
 

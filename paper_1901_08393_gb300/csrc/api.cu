@@ -5,6 +5,7 @@
 #include <new>
 
 #include "bem_internal.cuh"
+#include "dfloat.cuh"
 
 namespace bem {
 
@@ -124,6 +125,28 @@ __global__ void k_entries(const T *V, int64_t ld, int64_t N, const int64_t *I, c
         return;
     }
     out[k] = (double)V[i * ld + j];
+}
+
+__global__ void k_entries_df(const float2 *V, int64_t ld, int64_t N, const int64_t *I, const int64_t *J, int64_t K,
+                             double *out, int32_t *bad)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const int64_t i = I[k], j = J[k];
+    if (i < 0 || j < 0 || i >= N || j >= N) {
+        out[k] = NAN;
+        atomicOr(bad, 1);
+        return;
+    }
+    out[k] = df_to_double(V[i * ld + j]);
+}
+
+// dst[r * nj + c] = V[(i0 + r) * ld + j0 + c] as FP64
+__global__ void k_block_df(const float2 *V, int64_t ld, int64_t i0, int64_t ni, int64_t j0, int64_t nj, double *dst)
+{
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t r = blockIdx.y; r < ni; r += gridDim.y)
+        if (c < nj) dst[r * nj + c] = df_to_double(V[(i0 + r) * ld + j0 + c]);
 }
 
 __global__ void k_prolong(const double *xc, const int32_t *parent, int64_t N, double *x)
@@ -362,7 +385,7 @@ static bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, be
     bem_ctx *ctx = mesh->ctx;
     const int prec = opts ? opts->precision : BEM_PREC_F64;
     const int ss = (opts && opts->ss_order > 0) ? opts->ss_order : 4;
-    CHECK_ARG(ctx, prec == BEM_PREC_F64 || prec == BEM_PREC_F32, "unknown precision");
+    CHECK_ARG(ctx, prec == BEM_PREC_F64 || prec == BEM_PREC_F32 || prec == BEM_PREC_DF64, "unknown precision");
     CHECK_ARG(ctx, ss >= 2 && ss <= kMaxSS, "ss_order outside 2..16");
     bem_operator *op = new (std::nothrow) bem_operator();
     if (!op) return set_error(ctx, BEM_ERR_OOM, "host allocation");
@@ -371,7 +394,7 @@ static bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, be
     op->ss_order = ss;
     op->N = mesh->N;
     op->ld = padded_ld(mesh->N);
-    const size_t es = prec == BEM_PREC_F64 ? 8 : 4;
+    const size_t es = prec == BEM_PREC_F32 ? 4 : 8;
     bem_status st = dalloc(ctx, op->allocs, &op->V, es * (size_t)op->N * (size_t)op->ld, false);
     if (!st) st = dalloc(ctx, op->allocs, (void **)&op->diag, sizeof(double) * op->N, false);
     if (st) {
@@ -458,6 +481,20 @@ bem_status bem_operator_read(const bem_operator *op, int64_t i0, int64_t ni, int
     CHECK_ARG(ctx, i0 >= 0 && j0 >= 0 && ni >= 0 && nj >= 0 && i0 + ni <= op->N && j0 + nj <= op->N,
               "block outside the operator");
     if (ni == 0 || nj == 0) return BEM_OK;
+    if (op->precision == BEM_PREC_DF64) {
+        Allocs tmp;
+        double *blk = nullptr;
+        bem_status st = dalloc(ctx, tmp, (void **)&blk, sizeof(double) * ni * nj, false);
+        if (st) return st;
+        dim3 grid(nblk(nj, 256), (unsigned)(ni < 65535 ? ni : 65535));
+        k_block_df<<<grid, 256, 0, ctx->stream>>>((const float2 *)op->V, op->ld, i0, ni, j0, nj, blk); BEM_COUNT(ctx);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, blk, sizeof(double) * ni * nj, cudaMemcpyDefault, ctx->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "operator read");
+        dfree_all(ctx, tmp);
+        return st;
+    }
     const size_t es = op->precision == BEM_PREC_F64 ? 8 : 4;
     const char *src = static_cast<const char *>(op->V) + es * (size_t)(i0 * op->ld + j0);
     BEM_CK(ctx, cudaMemcpy2DAsync(dst, es * nj, src, es * op->ld, es * nj, ni, cudaMemcpyDefault, ctx->stream));
@@ -480,7 +517,11 @@ bem_status bem_operator_entries(const bem_operator *op, const int64_t *I, const 
     Allocs tmp;
     int32_t *bad = nullptr;
     if ((st = dalloc(ctx, tmp, (void **)&bad, sizeof(int32_t), true))) return st;
-    if (op->precision == BEM_PREC_F64)
+    if (op->precision == BEM_PREC_DF64)
+        { k_entries_df<<<nblk(K, 256), 256, 0, ctx->stream>>>((const float2 *)op->V, op->ld, op->N,
+                                                               (const int64_t *)dI.dptr, (const int64_t *)dJ.dptr, K,
+                                                               (double *)dO.dptr, bad); BEM_COUNT(ctx); }
+    else if (op->precision == BEM_PREC_F64)
         { k_entries<double><<<nblk(K, 256), 256, 0, ctx->stream>>>((const double *)op->V, op->ld, op->N,
                                                                  (const int64_t *)dI.dptr, (const int64_t *)dJ.dptr, K,
                                                                  (double *)dO.dptr, bad); BEM_COUNT(ctx); }

@@ -7,9 +7,15 @@
 //    row triangles in shared memory and walks them (broadcast reads).  Only
 //    entries with i <= j are computed; the strict lower triangle is mirrored, so
 //    V is exactly symmetric and an incremental re-assembly reproduces the full
-//    one bit for bit.  FP64 variant (all FP64) and FP32 variant (centroid
-//    difference in FP64 rounded once, offsets from the centroid in FP32, MUFU
-//    rsqrt).
+//    one bit for bit.  Three arithmetic variants:
+//      DF64 -- FP64-accurate double-float on the FP32 pipe: x_a - y_b is formed as
+//              (c_i - c_j) + (o_a - o_b) with the centroid difference taken exactly
+//              from three-float centroids and the offsets o from the centroid as
+//              hi/lo pairs; |r|^2 by two-product/two-sum; 1/|r| by the MUFU
+//              reciprocal square root and one Newton step in double-float (error
+//              ~1.5 e^2 ~ 1e-14); sums by two-sum.  V stored as hi/lo pairs.
+//      F64  -- native FP64 (GB300 issues FP64 at 1/64 of the FP32 rate).
+//      F32  -- centroid difference in FP64 rounded once, offsets in FP32, MUFU rsqrt.
 //  * Near field (common vertex, common edge, identical): Sauter-Schwab
 //    regularising transformations.  The 4-d integrand of each region is a power
 //    of the radial variables times a function of the others (the kernel is
@@ -21,10 +27,13 @@
 #include <cmath>
 
 #include "bem_internal.cuh"
+#include "dfloat.cuh"
 
 namespace bem {
 
 __constant__ double c_w7[kQ];
+__constant__ float2 c_w7df[kQ];
+__constant__ float2 c_inv4pi_df;
 __constant__ double c_glx[kMaxSS + 1][kMaxSS];
 __constant__ double c_glw[kMaxSS + 1][kMaxSS];
 
@@ -72,7 +81,16 @@ static bem_status assembly_constants(bem_ctx *ctx)
     const double w7[kQ] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
     double X[kMaxSS + 1][kMaxSS] = {}, W[kMaxSS + 1][kMaxSS] = {};
     for (int n = 1; n <= kMaxSS; ++n) gauss_legendre(n, X[n], W[n]);
+    float2 w7df[kQ];
+    for (int a = 0; a < kQ; ++a) {
+        const float h = (float)w7[a];
+        w7df[a] = make_float2(h, (float)(w7[a] - (double)h));
+    }
     BEM_CK(ctx, cudaMemcpyToSymbol(c_w7, w7, sizeof(w7)));
+    BEM_CK(ctx, cudaMemcpyToSymbol(c_w7df, w7df, sizeof(w7df)));
+    const float ih = (float)kInv4Pi;
+    const float2 inv4pi = make_float2(ih, (float)(kInv4Pi - (double)ih));
+    BEM_CK(ctx, cudaMemcpyToSymbol(c_inv4pi_df, &inv4pi, sizeof(inv4pi)));
     BEM_CK(ctx, cudaMemcpyToSymbol(c_glx, X, sizeof(X)));
     BEM_CK(ctx, cudaMemcpyToSymbol(c_glw, W, sizeof(W)));
     if (ctx->device < 64) g_asm_ready[ctx->device] = true;
@@ -80,6 +98,21 @@ static bem_status assembly_constants(bem_ctx *ctx)
 }
 
 static inline unsigned nblk(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// Element storage: FP64, double-float hi/lo pair, or FP32.
+template <typename T> struct Elem;
+template <> struct Elem<double> {
+    __device__ static double from_double(double v) { return v; }
+    __host__ __device__ static double to_double(double v) { return v; }
+};
+template <> struct Elem<float> {
+    __device__ static float from_double(double v) { return (float)v; }
+    __host__ __device__ static double to_double(float v) { return (double)v; }
+};
+template <> struct Elem<float2> {
+    __device__ static float2 from_double(double v) { return df_from_double(v); }
+    __host__ __device__ static double to_double(float2 v) { return df_to_double(v); }
+};
 
 // ------------------------------------------------------------------ far field
 constexpr int kFarCols = 256;  // threads (columns) per CTA
@@ -174,6 +207,116 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
     }
 }
 
+// Double-float far field: see the file comment.
+__global__ void __launch_bounds__(kFarCols) k_far_df(const float *__restrict__ qdf, float2 *__restrict__ V,
+                                                     int64_t ld, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+{
+    __shared__ float sq[kFarRows][53];
+    const int64_t cbase = c0 + (int64_t)blockIdx.x * kFarCols;
+    const int64_t i0 = r0 + (int64_t)blockIdx.y * kFarRows;
+    if (i0 > cbase + kFarCols - 1 || i0 >= r1) return;
+    for (int k = threadIdx.x; k < kFarRows * 53; k += kFarCols) {
+        const int r = k / 53, c = k % 53;
+        const int64_t i = i0 + r;
+        sq[r][c] = (i < r1) ? qdf[i * kQdfStride + c] : 0.0f;
+    }
+    __syncthreads();
+    const int64_t j = cbase + threadIdx.x;
+    if (j >= c1) return;
+    const float *qj = qdf + j * kQdfStride;
+    float oh[3 * kQ], ol[3 * kQ], cj[9];
+#pragma unroll
+    for (int k = 0; k < 3 * kQ; ++k) {
+        oh[k] = qj[2 * k];
+        ol[k] = qj[2 * k + 1];
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) cj[k] = qj[42 + k];
+    const float2 Aj = df_mul(make_float2(qj[51], qj[52]), c_inv4pi_df);
+    const int rows = (int)((r1 - i0) < kFarRows ? (r1 - i0) : kFarRows);
+    for (int r = 0; r < rows; ++r) {
+        const int64_t i = i0 + r;
+        if (i > j) break;
+        const float *qi = sq[r];
+        // centroid difference c_i - c_j from the three-float centroids
+        float Dh[3], Dl[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s1, e1, s2, e2, h, l;
+            two_sum(qi[42 + 3 * c], -cj[3 * c], s1, e1);
+            two_sum(qi[43 + 3 * c], -cj[3 * c + 1], s2, e2);
+            const float s3 = __fsub_rn(qi[44 + 3 * c], cj[3 * c + 2]);
+            two_sum(s1, s2, h, l);
+            l = __fadd_rn(l, __fadd_rn(__fadd_rn(e1, e2), s3));
+            fast_two_sum(h, l, Dh[c], Dl[c]);
+        }
+        float acc_h = 0.0f, acc_l = 0.0f;
+#pragma unroll
+        for (int a = 0; a < kQ; ++a) {
+            float eh[3], el[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float s, e;
+                two_sum(Dh[c], qi[2 * (3 * a + c)], s, e);
+                e = __fadd_rn(e, __fadd_rn(Dl[c], qi[2 * (3 * a + c) + 1]));
+                fast_two_sum(s, e, eh[c], el[c]);
+            }
+            float sh = 0.0f, sl = 0.0f;
+#pragma unroll
+            for (int b = 0; b < kQ; ++b) {
+                // d = e_a - o_b; |d|^2 = sum h^2 + 2 h l (two-product, two-sum)
+                float Sh = 0.0f, Sl = 0.0f;
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float h, e;
+                    two_sum(eh[c], -oh[3 * b + c], h, e);
+                    const float l = __fadd_rn(e, __fsub_rn(el[c], ol[3 * b + c]));
+                    float p, pe;
+                    two_prod(h, h, p, pe);
+                    pe = __fmaf_rn(__fmul_rn(2.0f, h), l, pe);
+                    if (c == 0) {
+                        Sh = p;
+                        Sl = pe;
+                    } else {
+                        float t, te;
+                        two_sum(Sh, p, t, te);
+                        Sh = t;
+                        Sl = __fadd_rn(Sl, __fadd_rn(pe, te));
+                    }
+                }
+                // 1/|d| = y + yl: MUFU estimate y, one Newton step in double-float
+                const float y = rsqrtf(Sh);
+                float y2, y2e, m, me;
+                two_prod(y, y, y2, y2e);
+                two_prod(Sh, y2, m, me);
+                float t = __fsub_rn(1.0f, m);
+                t = __fsub_rn(t, me);
+                t = __fmaf_rn(-Sh, y2e, t);
+                t = __fmaf_rn(-Sl, y2, t);
+                const float yl = __fmul_rn(__fmul_rn(0.5f, y), t);
+                // s += w_b (y + yl)
+                float ph, pe, u, ue;
+                two_prod(c_w7df[b].x, y, ph, pe);
+                pe = __fmaf_rn(c_w7df[b].x, yl, pe);
+                pe = __fmaf_rn(c_w7df[b].y, y, pe);
+                two_sum(sh, ph, u, ue);
+                sh = u;
+                sl = __fadd_rn(sl, __fadd_rn(pe, ue));
+            }
+            float ph, pe, u, ue;
+            two_prod(c_w7df[a].x, sh, ph, pe);
+            pe = __fmaf_rn(c_w7df[a].x, sl, pe);
+            pe = __fmaf_rn(c_w7df[a].y, sh, pe);
+            two_sum(acc_h, ph, u, ue);
+            acc_h = u;
+            acc_l = __fadd_rn(acc_l, __fadd_rn(pe, ue));
+        }
+        float h, l;
+        fast_two_sum(acc_h, acc_l, h, l);
+        V[i * ld + j] = df_mul(df_mul(make_float2(qi[51], qi[52]), Aj), make_float2(h, l));
+    }
+}
+
 // Mirror the strict lower triangle of rows [r0, r1): V[i][j] = V[j][i], j < i,
 // through 32 x 32 shared-memory tiles (coalesced on both sides).
 template <typename T>
@@ -187,7 +330,7 @@ __global__ void k_mirror(T *V, int64_t ld, int64_t r0, int64_t r1)
     // load source block rows bj.., cols bi.. (upper part)
     for (int k = ty; k < 32; k += 8) {
         const int64_t sr = bj + k, sc = bi + tx;
-        tile[k][tx] = (sr < r1 && sc < r1) ? V[sr * ld + sc] : T(0);
+        tile[k][tx] = (sr < r1 && sc < r1) ? V[sr * ld + sc] : T();
     }
     __syncthreads();
     for (int k = ty; k < 32; k += 8) {
@@ -354,8 +497,9 @@ __global__ void k_near(const double *__restrict__ verts, const int32_t *__restri
         I = ss_vertex(P, Q, n);
     }
     const double v = 4.0 * area[i] * area[j] * I * kInv4Pi;
-    V[i * ld + j] = (T)v;
-    if (i != j) V[j * ld + i] = (T)v;
+    const T e = Elem<T>::from_double(v);
+    V[i * ld + j] = e;
+    if (i != j) V[j * ld + i] = e;
 }
 
 // ------------------------------------------------------------------ reuse and diagonal
@@ -374,7 +518,7 @@ template <typename T>
 __global__ void k_diag(const T *V, int64_t ld, int64_t N, double *d)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) d[i] = (double)V[i * ld + i];
+    if (i < N) d[i] = Elem<T>::to_double(V[i * ld + i]);
 }
 
 // ------------------------------------------------------------------ drivers
@@ -402,8 +546,10 @@ static bem_status launch_far(bem_operator *op, int64_t r0, int64_t r1, int64_t c
         if (c1 > lo) units += (double)(c1 - lo);
     }
     const int prof = prof_start(ctx, BEM_KERNEL_FAR, units);
-    if (sizeof(T) == 8)
+    if (op->precision == BEM_PREC_F64)
         { k_far_f64<<<grid, kFarCols, 0, ctx->stream>>>(m->q64, (double *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
+    else if (op->precision == BEM_PREC_DF64)
+        { k_far_df<<<grid, kFarCols, 0, ctx->stream>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
     else
         { k_far_f32<<<grid, kFarCols, 0, ctx->stream>>>(m->q32, m->cent, (float *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
     prof_stop(ctx, prof);
@@ -454,7 +600,7 @@ static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
     bem_mesh *m = op->mesh;
     bem_ctx *ctx = m->ctx;
     const int64_t N = m->N;
-    BEM_CK(ctx, cudaMemsetAsync(op->V, 0, sizeof(T) * N * op->ld, ctx->stream));
+    BEM_CK(ctx, cudaMemsetAsync(op->V, 0, sizeof(T) * N * op->ld, ctx->stream));  // padding columns stay zero
     bem_status st;
     int64_t K = 0;
     if (coarse) {
@@ -485,14 +631,18 @@ bem_status assemble_full(bem_operator *op)
 {
     bem_status st = assembly_constants(op->mesh->ctx);
     if (st) return st;
-    return op->precision == BEM_PREC_F64 ? assemble_t<double>(op, nullptr) : assemble_t<float>(op, nullptr);
+    if (op->precision == BEM_PREC_F64) return assemble_t<double>(op, nullptr);
+    if (op->precision == BEM_PREC_DF64) return assemble_t<float2>(op, nullptr);
+    return assemble_t<float>(op, nullptr);
 }
 
 bem_status assemble_update(bem_operator *op, const bem_operator *coarse)
 {
     bem_status st = assembly_constants(op->mesh->ctx);
     if (st) return st;
-    return op->precision == BEM_PREC_F64 ? assemble_t<double>(op, coarse) : assemble_t<float>(op, coarse);
+    if (op->precision == BEM_PREC_F64) return assemble_t<double>(op, coarse);
+    if (op->precision == BEM_PREC_DF64) return assemble_t<float2>(op, coarse);
+    return assemble_t<float>(op, coarse);
 }
 
 bem_status operator_diag(bem_operator *op)
@@ -500,6 +650,8 @@ bem_status operator_diag(bem_operator *op)
     bem_ctx *ctx = op->mesh->ctx;
     if (op->precision == BEM_PREC_F64)
         { k_diag<double><<<nblk(op->N, 256), 256, 0, ctx->stream>>>((const double *)op->V, op->ld, op->N, op->diag); BEM_COUNT(ctx); }
+    else if (op->precision == BEM_PREC_DF64)
+        { k_diag<float2><<<nblk(op->N, 256), 256, 0, ctx->stream>>>((const float2 *)op->V, op->ld, op->N, op->diag); BEM_COUNT(ctx); }
     else
         { k_diag<float><<<nblk(op->N, 256), 256, 0, ctx->stream>>>((const float *)op->V, op->ld, op->N, op->diag); BEM_COUNT(ctx); }
     BEM_CK_LAUNCH(ctx);

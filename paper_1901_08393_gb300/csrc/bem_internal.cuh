@@ -15,13 +15,17 @@ namespace bem {
 constexpr int kQ = 7;              // far-field points per triangle (Radon degree 5)
 constexpr int kQ64Stride = 24;     // doubles per triangle in the FP64 point table
 constexpr int kQ32Stride = 24;     // floats per triangle in the FP32 offset table
+constexpr int kQdfStride = 56;     // floats per triangle in the double-float table:
+                                   // [0,42) offsets hi/lo, [42,51) centroid as 3 floats
+                                   // per coordinate, [51,53) area hi/lo
 constexpr int kMaxSS = 16;         // largest Sauter-Schwab order accepted
 constexpr int kMaxValence = 96;    // triangles per vertex accepted by the pair builder
-constexpr double kInv4Pi = 0.07957747154594767;  // 1 / (4 pi)
+constexpr double kInv4Pi = 0.079577471545947668;  // 1 / (4 pi)
 
-// Row stride of the dense operator: N rounded up to 32 elements so that every row
-// starts on a 256-byte boundary (vector loads in the matvec).
-inline int64_t padded_ld(int64_t n) { return (n + 31) / 32 * 32; }
+// Row stride of the dense operator: N rounded up to 64 elements so that every row
+// starts on a 256-byte boundary (vector loads) and whole 64 x 64 tiles fit (the
+// symmetric matvec); the padding columns are zero.
+inline int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
 struct Allocs {
     std::vector<std::pair<void *, size_t>> list;
@@ -67,6 +71,7 @@ struct bem_mesh {
     double *q64 = nullptr;      // N x 24: 7 points (x,y,z), [21] = area
     float *q32 = nullptr;       // N x 24: 7 offsets from the centroid (x,y,z)
     double *cent = nullptr;     // N x 4: centroid (x,y,z), area
+    float *qdf = nullptr;       // N x 56: double-float table (see kQdfStride)
     int32_t *v2t_off = nullptr; // M + 1
     int32_t *v2t = nullptr;     // 3N, ascending triangle index per vertex
     int32_t *owner = nullptr;   // 3N: half-edge -> first half-edge of its edge
@@ -86,7 +91,7 @@ struct bem_operator {
     int32_t precision = BEM_PREC_F64;
     int32_t ss_order = 4;
     int64_t N = 0, ld = 0;
-    void *V = nullptr;      // N x ld, row-major
+    void *V = nullptr;      // N x ld, row-major: double (F64), float2 hi/lo (DF64), float (F32)
     double *diag = nullptr; // N, FP64 diagonal
     bem::Allocs allocs;
 };

@@ -164,8 +164,25 @@ __global__ void k_canonical(const double *verts, const int32_t *tin, const uint8
 // Per triangle: |T| = |(P1-P0) x (P2-P0)|/2 and diam = longest edge in the fixed
 // operation order; the 7 Radon points (FP64), their offsets from the centroid
 // (FP32) and the centroid (FP64).
+__device__ __forceinline__ void split2(double v, float *out)
+{
+    const float h = __double2float_rn(v);
+    out[0] = h;
+    out[1] = __double2float_rn(v - (double)h);
+}
+
+__device__ __forceinline__ void split3(double v, float *out)
+{
+    const float a = __double2float_rn(v);
+    const double r = v - (double)a;  // exact
+    const float b = __double2float_rn(r);
+    out[0] = a;
+    out[1] = b;
+    out[2] = __double2float_rn(r - (double)b);
+}
+
 __global__ void k_geometry(const double *verts, const int32_t *tris, int64_t N, double *area,
-                           double *diam, double *q64, float *q32, double *cent, int32_t *bad)
+                           double *diam, double *q64, float *q32, double *cent, float *qdf, int32_t *bad)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
@@ -202,6 +219,21 @@ __global__ void k_geometry(const double *verts, const int32_t *tris, int64_t N, 
     q[22] = d;
     q[23] = 0.0;
     o[21] = o[22] = o[23] = 0.0f;
+    // double-float table: offsets lambda . (P - c) from the centroid, the centroid
+    // itself as an exact sum of three floats, and the area
+    float *f = qdf + (int64_t)kQdfStride * t;
+    double R[3][3];
+    for (int k = 0; k < 3; ++k)
+        for (int c = 0; c < 3; ++c) R[k][c] = P[k][c] - c3[c];
+    for (int a = 0; a < kQ; ++a)
+        for (int c = 0; c < 3; ++c) {
+            const double off = c_radon_bary[a][0] * R[0][c] + c_radon_bary[a][1] * R[1][c] +
+                               c_radon_bary[a][2] * R[2][c];
+            split2(off, f + 2 * (3 * a + c));
+        }
+    for (int c = 0; c < 3; ++c) split3(c3[c], f + 42 + 3 * c);
+    split2(A, f + 51);
+    f[53] = f[54] = f[55] = 0.0f;
     cent[4 * t + 0] = c3[0];
     cent[4 * t + 1] = c3[1];
     cent[4 * t + 2] = c3[2];
@@ -388,8 +420,9 @@ bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge)
     TRY(dalloc(ctx, m->allocs, (void **)&m->q64, sizeof(double) * kQ64Stride * N, false));
     TRY(dalloc(ctx, m->allocs, (void **)&m->q32, sizeof(float) * kQ32Stride * N, false));
     TRY(dalloc(ctx, m->allocs, (void **)&m->cent, sizeof(double) * 4 * N, false));
+    TRY(dalloc(ctx, m->allocs, (void **)&m->qdf, sizeof(float) * kQdfStride * N, false));
     k_geometry<<<nblk(N, 128), 128, 0, s>>>(m->verts, m->tris, N, m->area, m->diam, m->q64, m->q32,
-                                            m->cent, bad); BEM_COUNT(ctx);
+                                            m->cent, m->qdf, bad); BEM_COUNT(ctx);
     {
         int32_t *cnt = nullptr, *cursor = nullptr;
         TRY(dalloc(ctx, m->allocs, (void **)&m->v2t_off, sizeof(int32_t) * (M + 1), false));

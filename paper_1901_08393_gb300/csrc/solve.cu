@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "bem_internal.cuh"
+#include "dfloat.cuh"
 
 namespace bem {
 
@@ -124,6 +125,221 @@ __global__ void __launch_bounds__(kMvThreads) k_matvec(const T *__restrict__ V, 
     }
 }
 
+// Double-float y = V x for V entries stored as hi/lo pairs (float2) or as FP32
+// (float), x given as hi/lo pairs: every product is exact up to the neglected
+// lo*lo term and every sum is a two-sum, so y carries ~2^-46 relative error while
+// only the FP32 pipe is used (HBM-bound on GB300, where FP64 FMA would not be).
+__device__ __forceinline__ void acc_df(float &sh, float &sl, float vh, float vl, float xh, float xl)
+{
+    float p, e, s, t;
+    two_prod(vh, xh, p, e);
+    e = __fmaf_rn(vh, xl, e);
+    e = __fmaf_rn(vl, xh, e);
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(e, t));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMvThreads) k_matvec_df(const T *__restrict__ V, int64_t ld, int64_t N,
+                                                          const float2 *__restrict__ xdf, double *__restrict__ y,
+                                                          const double *__restrict__ w, double *dot_partial)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t row = (int64_t)blockIdx.x * kMvRows + warp;
+    double acc = 0.0;
+    if (row < N) {
+        float sh = 0.0f, sl = 0.0f;
+        const float4 *r = reinterpret_cast<const float4 *>(V + row * ld);
+        const float4 *xv = reinterpret_cast<const float4 *>(xdf);
+        if (sizeof(T) == 8) {
+            const int64_t n2 = ld / 2;
+#pragma unroll 4
+            for (int64_t k = lane; k < n2; k += 32) {
+                const float4 a = __ldcs(r + k);
+                const float4 b = __ldg(xv + k);
+                acc_df(sh, sl, a.x, a.y, b.x, b.y);
+                acc_df(sh, sl, a.z, a.w, b.z, b.w);
+            }
+        } else {
+            const int64_t n4 = ld / 4;
+#pragma unroll 4
+            for (int64_t k = lane; k < n4; k += 32) {
+                const float4 a = __ldcs(r + k);
+                const float4 b0 = __ldg(xv + 2 * k), b1 = __ldg(xv + 2 * k + 1);
+                acc_df(sh, sl, a.x, 0.0f, b0.x, b0.y);
+                acc_df(sh, sl, a.y, 0.0f, b0.z, b0.w);
+                acc_df(sh, sl, a.z, 0.0f, b1.x, b1.y);
+                acc_df(sh, sl, a.w, 0.0f, b1.z, b1.w);
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, sh, o), ol = __shfl_xor_sync(0xffffffffu, sl, o);
+            const float2 t = df_add(make_float2(sh, sl), make_float2(oh, ol));
+            sh = t.x;
+            sl = t.y;
+        }
+        acc = (double)sh + (double)sl;
+        if (lane == 0) y[row] = acc;
+    }
+    if (dot_partial) {
+        __shared__ double sd[kMvRows];
+        if (lane == 0) sd[warp] = (row < N) ? w[row] * acc : 0.0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int k = 0; k < kMvRows; ++k) t += sd[k];
+            dot_partial[blockIdx.x] = t;
+        }
+    }
+}
+
+// Symmetric V x from the upper triangle only (half the HBM traffic).  A
+// persistent CTA walks a list of tiles (I, J), I <= J, of 64 x 64 entries; each
+// tile is streamed once into shared memory by 16-byte cp.async copies, double
+// buffered so that the next tile is in flight while this one is used, into rows
+// padded to 68 pairs (bank-conflict-free for both passes).  Row pass: four threads
+// per row form V_IJ x_J (row partials of block I); column pass, off the diagonal:
+// four threads per column form V_IJ^T x_I (column partials of block J).  All sums
+// in double-float.  k_symv_reduce adds the partials of each row in a fixed order.
+constexpr int kSB = 64;
+constexpr int kSP = 68;  // padded row stride (pairs)
+constexpr int kSymThreads = 256;
+constexpr size_t kSymSmem = 2 * (kSB * kSP + 2 * kSB) * sizeof(float2) + 4 * kSB * sizeof(float2);
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid)
+{
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;  // src-size 0: zero fill
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Stage tile (I, J) and the x segments of blocks I and J into one buffer.
+__device__ __forceinline__ void symv_stage(const float2 *V, int64_t ld, int64_t N, const float2 *xdf, int2 tj,
+                                           float2 *tile, float2 *xs)
+{
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int id = t + kSymThreads * k;  // 2048 chunks of 16 bytes
+        const int r = id >> 5, c16 = id & 31;
+        const int64_t row = (int64_t)tj.x * kSB + r;
+        const bool ok = row < N;
+        const float2 *src = V + (ok ? row : 0) * ld + (int64_t)tj.y * kSB + 2 * c16;
+        cp_async16(tile + r * kSP + 2 * c16, src, ok);
+    }
+    if (t < 64) {  // x_I (pairs 0..63) then x_J (64..127), 2 pairs per copy
+        const int blk = t < 32 ? tj.x : tj.y;
+        const int off = 2 * (t & 31);
+        cp_async16(xs + (t < 32 ? 0 : kSB) + off, xdf + (int64_t)blk * kSB + off, true);
+    }
+}
+
+__global__ void __launch_bounds__(kSymThreads) k_symv_df(const float2 *__restrict__ V, int64_t ld, int64_t N, int nb,
+                                                         const int2 *__restrict__ tiles, int ntiles,
+                                                         const float2 *__restrict__ xdf, float2 *__restrict__ prow,
+                                                         float2 *__restrict__ pcol)
+{
+    extern __shared__ float2 sm[];
+    // [tile buffer 0][tile buffer 1][x segments 0][x segments 1][column partials 4 x 64]
+    float2 *const xs0 = sm + 2 * kSB * kSP;
+    float2 *cpart = sm + 2 * kSB * kSP + 4 * kSB;
+    const int t = threadIdx.x;
+    int it = 0;
+    if ((int)blockIdx.x < ntiles) symv_stage(V, ld, N, xdf, tiles[blockIdx.x], sm, xs0);
+    cp_async_commit();
+    for (int k = blockIdx.x; k < ntiles; k += gridDim.x, ++it) {
+        const int cur = it & 1;
+        const int nk = k + gridDim.x;
+        if (nk < ntiles) symv_stage(V, ld, N, xdf, tiles[nk], sm + (cur ^ 1) * kSB * kSP, xs0 + (cur ^ 1) * 2 * kSB);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        const int2 tj = tiles[k];
+        const float2 *T = sm + cur * kSB * kSP;
+        const float2 *xi = xs0 + cur * 2 * kSB, *xj = xi + kSB;
+        const int64_t base = (int64_t)k * kSB;
+        {  // row pass: row r, columns q, q+4, ..., q+60
+            const int r = t >> 2, q = t & 3;
+            float h = 0.f, l = 0.f;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int c = q + 4 * m;
+                const float2 v = T[r * kSP + c], x = xj[c];
+                acc_df(h, l, v.x, v.y, x.x, x.y);
+            }
+#pragma unroll
+            for (int o = 1; o < 4; o <<= 1) {
+                const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+                const float2 s = df_add(make_float2(h, l), make_float2(oh, ol));
+                h = s.x;
+                l = s.y;
+            }
+            if (q == 0) prow[base + r] = make_float2(h, l);
+        }
+        if (tj.x != tj.y) {  // column pass: column c, rows 16 q .. 16 q + 15
+            const int c = t & 63, q = t >> 6;
+            float h = 0.f, l = 0.f;
+#pragma unroll
+            for (int m = 0; m < 16; ++m) {
+                const int r = 16 * q + m;
+                const float2 v = T[r * kSP + c], x = xi[r];
+                acc_df(h, l, v.x, v.y, x.x, x.y);
+            }
+            cpart[q * kSB + c] = make_float2(h, l);
+            __syncthreads();
+            if (t < kSB) {
+                float2 s = cpart[t];
+                s = df_add(s, cpart[kSB + t]);
+                s = df_add(s, cpart[2 * kSB + t]);
+                s = df_add(s, cpart[3 * kSB + t]);
+                pcol[base + t] = s;
+            }
+        }
+        __syncthreads();  // buffer cur is refilled in the next iteration
+    }
+}
+
+// y_i = sum of the column partials of tiles (J', I), J' < I, then of the row
+// partials of tiles (I, J), J >= I (tile (a, b) sits at position
+// a nb - a (a - 1) / 2 + (b - a) of the list); optional block partials of sum w_i y_i.
+__device__ __forceinline__ int64_t tile_pos(int a, int b, int nb)
+{
+    return (int64_t)a * nb - (int64_t)a * (a - 1) / 2 + (b - a);
+}
+
+__global__ void k_symv_reduce(const float2 *__restrict__ prow, const float2 *__restrict__ pcol, int nb, int64_t N,
+                              double *__restrict__ y, const double *__restrict__ w, double *dot_partial)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double v = 0.0;
+    if (i < N) {
+        const int I = (int)(i / kSB), r = (int)(i % kSB);
+        float2 s = make_float2(0.f, 0.f);
+        for (int J = 0; J < I; ++J) s = df_add(s, pcol[tile_pos(J, I, nb) * kSB + r]);
+        for (int J = I; J < nb; ++J) s = df_add(s, prow[tile_pos(I, J, nb) * kSB + r]);
+        v = df_to_double(s);
+        y[i] = v;
+    }
+    if (dot_partial) block_partial(i < N ? w[i] * v : 0.0, dot_partial);
+}
+
+__global__ void k_tile_list(int nb, int2 *tiles)
+{
+    const int I = blockIdx.x;
+    for (int J = I + threadIdx.x; J < nb; J += blockDim.x) tiles[tile_pos(I, J, nb)] = make_int2(I, J);
+}
+
+// x (FP64, N) -> hi/lo pairs, zero-padded to ld
+__global__ void k_to_df(const double *x, int64_t N, int64_t ld, float2 *xdf)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < ld) xdf[i] = i < N ? df_from_double(x[i]) : make_float2(0.0f, 0.0f);
+}
+
 // r = b - q; z = M^-1 r; p = z; partials of r.z, r.r, b.b
 __global__ void k_pcg_init(int64_t N, const double *b, const double *q, const double *d, int precond,
                            double *r, double *z, double *p, double *prz, double *prr, double *pbb)
@@ -223,44 +439,95 @@ __global__ void k_residual(int64_t N, const double *b, const double *q, double *
 // ------------------------------------------------------------------ host side
 struct Work {
     double *r, *z, *p, *q, *b, *x, *d;  // vectors of length ld
+    float2 *xdf;                        // hi/lo copy of the matvec input (double-float paths)
+    float2 *prow, *pcol;                // symmetric matvec tile partials (DF64), one 64-vector per tile
+    int2 *tiles;                        // upper-triangle tile list
     double *part1, *part2, *part3;      // per-block partials
     double *scal;                       // device scalars: [0..1] rz slots, [2] rr, [3..5] reduce3
     int nb_vec, nb_mv;
 };
 
-bem_status matvec_f64(bem_operator *op, const double *x, double *y)
-{
-    bem_ctx *ctx = op->mesh->ctx;
-    const unsigned g = nblk(op->N, kMvRows);
-    if (op->precision == BEM_PREC_F64)
-        { k_matvec<double, true><<<g, kMvThreads, 0, ctx->stream>>>((const double *)op->V, op->ld, op->N, x, y,
-                                                                  nullptr, nullptr); BEM_COUNT(ctx); }
-    else
-        { k_matvec<float, true><<<g, kMvThreads, 0, ctx->stream>>>((const float *)op->V, op->ld, op->N, x, y,
-                                                                 nullptr, nullptr); BEM_COUNT(ctx); }
-    BEM_CK_LAUNCH(ctx);
-    return BEM_OK;
-}
-
+// y = V x.  acc64: FP64-accurate products and sums (double-float arithmetic for
+// DF64 and F32 storage, native FP64 for F64); otherwise FP32 (F32 storage only).
+// xdf: scratch of ld hi/lo pairs for the double-float paths.
 static bem_status launch_mv(bem_operator *op, bool acc64, const double *x, double *y, const double *w,
-                            double *part)
+                            double *part, float2 *xdf, float2 *prow, float2 *pcol, const int2 *tiles, int *nparts)
 {
     bem_ctx *ctx = op->mesh->ctx;
     const unsigned g = nblk(op->N, kMvRows);
-    const double es = op->precision == BEM_PREC_F64 ? 8.0 : 4.0;
-    const int prof = prof_start(ctx, BEM_KERNEL_MATVEC, es * (double)op->N * (double)op->N);
-    if (op->precision == BEM_PREC_F64)
+    const double es = op->precision == BEM_PREC_F32 ? 4.0 : 8.0;
+    const bool df = op->precision == BEM_PREC_DF64 || (op->precision == BEM_PREC_F32 && acc64);
+    const bool sym = op->precision == BEM_PREC_DF64 && prow && pcol && tiles;
+    if (df) {
+        k_to_df<<<nblk(op->ld, 256), 256, 0, ctx->stream>>>(x, op->N, op->ld, xdf); BEM_COUNT(ctx);
+    }
+    // algorithmic bytes: the half of V that a symmetric product must read, else all of V
+    const double bytes = es * (double)op->N * (double)op->N * (sym ? 0.5 : 1.0);
+    const int prof = prof_start(ctx, BEM_KERNEL_MATVEC, bytes);
+    if (nparts) *nparts = (int)g;
+    if (sym) {
+        const int nb = (int)(op->ld / kSB);
+        const int ntiles = nb * (nb + 1) / 2;
+        BEM_CK(ctx, cudaFuncSetAttribute(k_symv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
+        const int grid = ntiles < 3 * ctx->sm_count ? ntiles : 3 * ctx->sm_count;
+        k_symv_df<<<grid, kSymThreads, kSymSmem, ctx->stream>>>((const float2 *)op->V, op->ld, op->N, nb, tiles, ntiles,
+                                                                xdf, prow, pcol); BEM_COUNT(ctx);
+        k_symv_reduce<<<nblk(op->N, kVecThreads), kVecThreads, 0, ctx->stream>>>(prow, pcol, nb, op->N, y, w, part); BEM_COUNT(ctx);
+        if (nparts) *nparts = (int)nblk(op->N, kVecThreads);
+    } else if (op->precision == BEM_PREC_F64)
         { k_matvec<double, true><<<g, kMvThreads, 0, ctx->stream>>>((const double *)op->V, op->ld, op->N, x, y, w,
                                                                   part); BEM_COUNT(ctx); }
+    else if (op->precision == BEM_PREC_DF64)
+        { k_matvec_df<float2><<<g, kMvThreads, 0, ctx->stream>>>((const float2 *)op->V, op->ld, op->N, xdf, y, w,
+                                                                part); BEM_COUNT(ctx); }
     else if (acc64)
-        { k_matvec<float, true><<<g, kMvThreads, 0, ctx->stream>>>((const float *)op->V, op->ld, op->N, x, y, w,
-                                                                 part); BEM_COUNT(ctx); }
+        { k_matvec_df<float><<<g, kMvThreads, 0, ctx->stream>>>((const float *)op->V, op->ld, op->N, xdf, y, w,
+                                                               part); BEM_COUNT(ctx); }
     else
         { k_matvec<float, false><<<g, kMvThreads, 0, ctx->stream>>>((const float *)op->V, op->ld, op->N, x, y, w,
                                                                   part); BEM_COUNT(ctx); }
     prof_stop(ctx, prof);
     BEM_CK_LAUNCH(ctx);
     return BEM_OK;
+}
+
+// Scratch of the symmetric product: per tile 64 hi/lo pairs for rows and for
+// columns, then the tile list.
+static size_t symv_scratch_bytes(const bem_operator *op)
+{
+    if (op->precision != BEM_PREC_DF64) return 0;
+    const size_t nb = (size_t)(op->ld / kSB), nt = nb * (nb + 1) / 2;
+    return 2 * nt * kSB * sizeof(float2) + nt * sizeof(int2);
+}
+
+// Carve the scratch and write the tile list.
+static bem_status symv_setup(bem_operator *op, void *scratch, float2 **prow, float2 **pcol, int2 **tiles)
+{
+    const int nb = (int)(op->ld / kSB);
+    const size_t nt = (size_t)nb * (nb + 1) / 2;
+    *prow = static_cast<float2 *>(scratch);
+    *pcol = *prow + nt * kSB;
+    *tiles = reinterpret_cast<int2 *>(*pcol + nt * kSB);
+    bem_ctx *ctx = op->mesh->ctx;
+    k_tile_list<<<nb, 128, 0, ctx->stream>>>(nb, *tiles); BEM_COUNT(ctx);
+    BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
+
+bem_status matvec_f64(bem_operator *op, const double *x, double *y)
+{
+    bem_ctx *ctx = op->mesh->ctx;
+    Allocs tmp;
+    float2 *xdf = nullptr, *pr = nullptr, *pc = nullptr;
+    int2 *tl = nullptr;
+    void *scr = nullptr;
+    const size_t ps = symv_scratch_bytes(op);
+    bem_status st = dalloc(ctx, tmp, (void **)&xdf, sizeof(float2) * op->ld, false);
+    if (!st && ps) st = dalloc(ctx, tmp, &scr, ps, false);
+    if (!st && ps) st = symv_setup(op, scr, &pr, &pc, &tl);
+    if (!st) st = launch_mv(op, true, x, y, nullptr, nullptr, xdf, pr, pc, tl, nullptr);
+    dfree_all(ctx, tmp);
+    return st;
 }
 
 static bem_status read_scalars(bem_ctx *ctx, const double *d, int n, double *h)
@@ -280,7 +547,7 @@ static bem_status pcg(bem_operator *op, Work &W, const double *rhs, double tol, 
     cudaStream_t s = ctx->stream;
     const int64_t N = op->N;
     bem_status st;
-    if ((st = launch_mv(op, acc64, W.x, W.q, nullptr, nullptr))) return st;
+    if ((st = launch_mv(op, acc64, W.x, W.q, nullptr, nullptr, W.xdf, W.prow, W.pcol, W.tiles, nullptr))) return st;
     k_pcg_init<<<W.nb_vec, kVecThreads, 0, s>>>(N, rhs, W.q, W.d, precond, W.r, W.z, W.p, W.part1, W.part2,
                                                 W.part3); BEM_COUNT(ctx);
     k_reduce3<<<1, 1024, 0, s>>>(W.part1, W.part2, W.part3, W.nb_vec, W.scal + 3); BEM_COUNT(ctx);
@@ -292,9 +559,10 @@ static bem_status pcg(bem_operator *op, Work &W, const double *rhs, double tol, 
     double rel = std::sqrt(h[1]) / bnorm;
     int it = 0;
     while (rel > tol && it < max_it) {
-        if ((st = launch_mv(op, acc64, W.p, W.q, W.p, W.part3))) return st;
+        int npq = 0;
+        if ((st = launch_mv(op, acc64, W.p, W.q, W.p, W.part3, W.xdf, W.prow, W.pcol, W.tiles, &npq))) return st;
         const int cur = it & 1, nxt = cur ^ 1;
-        k_pcg_update1<<<W.nb_vec, kVecThreads, 0, s>>>(N, W.part3, W.nb_mv, W.scal + cur, W.x, W.r, W.z, W.p,
+        k_pcg_update1<<<W.nb_vec, kVecThreads, 0, s>>>(N, W.part3, npq, W.scal + cur, W.x, W.r, W.z, W.p,
                                                        W.q, W.d, precond, W.part1, W.part2); BEM_COUNT(ctx);
         k_pcg_update2<<<W.nb_vec, kVecThreads, 0, s>>>(N, W.part1, W.part2, W.nb_vec, W.scal + cur,
                                                        W.scal + nxt, W.scal + 2, W.z, W.p); BEM_COUNT(ctx);
@@ -334,6 +602,19 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     double *base = nullptr;
     const size_t vecs = 7;
     if ((st = dalloc(ctx, tmp, (void **)&base, sizeof(double) * (vecs * L + 3 * np + 8), true))) return st;
+    if ((st = dalloc(ctx, tmp, (void **)&W.xdf, sizeof(float2) * L, true))) {
+        dfree_all(ctx, tmp);
+        return st;
+    }
+    W.prow = W.pcol = nullptr;
+    W.tiles = nullptr;
+    if (const size_t ps = symv_scratch_bytes(op)) {
+        void *scr = nullptr;
+        if ((st = dalloc(ctx, tmp, &scr, ps, false)) || (st = symv_setup(op, scr, &W.prow, &W.pcol, &W.tiles))) {
+            dfree_all(ctx, tmp);
+            return st;
+        }
+    }
     W.r = base;
     W.z = base + L;
     W.p = base + 2 * L;
@@ -357,7 +638,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         st = cuda_error(ctx, e, "solve setup");
         goto out;
     }
-    if (op->precision == BEM_PREC_F64) {
+    if (op->precision != BEM_PREC_F32) {
         st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
         outer = 1;
     } else {
@@ -372,7 +653,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         double bb = 0.0;
         for (outer = 0; outer < max_outer; ++outer) {
             // rhs = b - V xs in FP64 accumulation
-            if ((st = launch_mv(op, true, xs, W.q, nullptr, nullptr))) goto out;
+            if ((st = launch_mv(op, true, xs, W.q, nullptr, nullptr, W.xdf, W.prow, W.pcol, W.tiles, nullptr))) goto out;
             k_residual<<<W.nb_vec, kVecThreads, 0, s>>>(N, W.b, W.q, rhs, W.part1); BEM_COUNT(ctx);
             k_dot_partial<<<W.nb_vec, kVecThreads, 0, s>>>(N, W.b, W.b, W.part2); BEM_COUNT(ctx);
             k_reduce3<<<1, 1024, 0, s>>>(W.part1, W.part2, nullptr, W.nb_vec, W.scal + 3); BEM_COUNT(ctx);
@@ -391,7 +672,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         }
         if (outer == max_outer) {
             // residual of the last update
-            if ((st = launch_mv(op, true, xs, W.q, nullptr, nullptr))) goto out;
+            if ((st = launch_mv(op, true, xs, W.q, nullptr, nullptr, W.xdf, W.prow, W.pcol, W.tiles, nullptr))) goto out;
             k_residual<<<W.nb_vec, kVecThreads, 0, s>>>(N, W.b, W.q, rhs, W.part1); BEM_COUNT(ctx);
             k_reduce3<<<1, 1024, 0, s>>>(W.part1, nullptr, nullptr, W.nb_vec, W.scal + 3); BEM_COUNT(ctx);
             double h[3];

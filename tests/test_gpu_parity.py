@@ -53,10 +53,11 @@ def test_mesh_canonical_and_geometry_bitexact(ctx, m):
         assert n_near == n_ref
 
 
+@pytest.mark.parametrize("prec", [bem.PREC_F64, bem.PREC_DF64], ids=["f64", "df64"])
 @pytest.mark.parametrize("m", MESHES, ids=lambda m: m.name)
-def test_assembly_f64_matches_oracle(ctx, m):
+def test_assembly_f64_matches_oracle(ctx, m, prec):
     mesh, v, t = _upload(ctx, m)
-    V = bem.Operator.assemble(mesh).read()
+    V = bem.Operator.assemble(mesh, precision=prec).read()
     Vr = O.assemble(v, t)
     assert np.array_equal(V, V.T)
     assert _rel(V, Vr) < 1e-10
@@ -85,10 +86,11 @@ def test_sauter_schwab_orders(ctx, n):
     assert _rel(op.entries(I2, J2), O.entries(v, t, I2, J2, n)) < 1e-10
 
 
-def test_matvec_f64(ctx):
+@pytest.mark.parametrize("prec", [bem.PREC_F64, bem.PREC_DF64], ids=["f64", "df64"])
+def test_matvec_f64(ctx, prec):
     m = inputs.workload_polycube_adaptive()
     mesh, v, t = _upload(ctx, m)
-    op = bem.Operator.assemble(mesh)
+    op = bem.Operator.assemble(mesh, precision=prec)
     V = op.read()
     x = np.random.default_rng(0).standard_normal(m.N)
     y = op.matvec(x)
@@ -96,18 +98,20 @@ def test_matvec_f64(ctx):
     assert np.max(np.abs(y - yr)) < 1e-13 * np.max(np.abs(V).sum(1) * np.max(np.abs(x)))
 
 
+@pytest.mark.parametrize("prec", [bem.PREC_F64, bem.PREC_DF64], ids=["f64", "df64"])
 @pytest.mark.parametrize("precond", [bem.PRECOND_JACOBI, bem.PRECOND_NONE])
 @pytest.mark.parametrize("m", [inputs.cube_mesh(4), inputs.workload_polycube_adaptive()], ids=lambda m: m.name)
-def test_solve_capacity_f64(ctx, m, precond):
+def test_solve_capacity_f64(ctx, m, precond, prec):
     mesh, v, t = _upload(ctx, m)
-    op = bem.Operator.assemble(mesh)
-    cap, phi, info = bem.solve_capacity(op, tol=1e-12, precond=precond)
-    cap_r, x_r, its_r, V = O.solve_capacity(v, t, tol=1e-12, precond=precond)
-    assert info["converged"] and info["relres"] <= 1e-12, info
+    op = bem.Operator.assemble(mesh, precision=prec)
+    tol = 1e-12 if prec == bem.PREC_F64 else 1e-11
+    cap, phi, info = bem.solve_capacity(op, tol=tol, precond=precond)
+    cap_r, x_r, its_r, V = O.solve_capacity(v, t, tol=tol, precond=precond)
+    assert info["converged"] and info["relres"] <= tol, info
     assert abs(cap / cap_r - 1) < 1e-10, (cap, cap_r)
     b = O.geometry(v, t)[0]
     res = np.linalg.norm(V @ phi - b) / np.linalg.norm(b)
-    assert res < 1e-11, res  # true residual of the GPU solution against the oracle's V
+    assert res < 10 * tol, res  # true residual of the GPU solution against the oracle's V
     assert abs(info["iterations"] - its_r) <= 3 + its_r // 10, (info["iterations"], its_r)
 
 
@@ -166,7 +170,7 @@ def test_refine_bitexact(ctx):
 
 
 def test_incremental_assembly_bitexact(ctx):
-    for prec in (bem.PREC_F64, bem.PREC_F32):
+    for prec in (bem.PREC_F64, bem.PREC_F32, bem.PREC_DF64):
         m = inputs.workload_polycube_adaptive()
         mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
         op = bem.Operator.assemble(mesh, precision=prec)
@@ -180,10 +184,12 @@ def test_incremental_assembly_bitexact(ctx):
             mesh, op = fine, inc
 
 
-def test_mark_refine_and_adaptive_loop_match_oracle(ctx):
+@pytest.mark.parametrize("prec", [bem.PREC_F64, bem.PREC_DF64], ids=["f64", "df64"])
+def test_mark_refine_and_adaptive_loop_match_oracle(ctx, prec):
     m = inputs.workload_polycube_adaptive()
     mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
-    recs, fin = bem.adaptive_run(mesh, theta=0.5, max_N=2500, tol=1e-12, want_final=True)
+    recs, fin = bem.adaptive_run(mesh, theta=0.5, max_N=2500, tol=1e-12 if prec == bem.PREC_F64 else 1e-11,
+                                 precision=prec, want_final=True)
     hist = O.adaptive_run(m.verts, m.tris, theta=0.5, max_N=2500, tol=1e-12)
     assert len(recs) == len(hist)
     for r, h in zip(recs, hist):
