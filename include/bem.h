@@ -145,6 +145,21 @@ bem_status bem_operator_entries(const bem_operator *op, const int64_t *I, const 
 /* y = V x, FP64 vectors of length N (host or device), in the operator's arithmetic. */
 bem_status bem_operator_matvec(const bem_operator *op, const double *x, double *y);
 
+/* No-allocation variant of bem_operator_matvec (the paper has no counterpart: it
+ * serves callers that must not have device memory allocated during a call, such
+ * as code being captured into a CUDA graph, where cudaMalloc and cudaFree are not
+ * permitted, serving loops with a fixed pre-reserved footprint, and hosts whose
+ * device memory belongs to another framework's allocator).  y = V x for a
+ * BEM_PREC_DF64 operator with N <= 4096; x and y are FP64 device pointers of
+ * length N (host pointers are rejected, staging them would allocate).  The
+ * scratch is a static device array of about 2.1 MiB that every GPU loading the
+ * library keeps until exit; the first call on a device looks up its address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Enqueued on the context's stream without synchronising.  All calls share the
+ * one array: calls that overlap on the GPU race.  Larger N, other precisions,
+ * host pointers or another current device: BEM_ERR_INVALID with a message. */
+bem_status bem_operator_matvec_noalloc(const bem_operator *op, const double *x, double *y);
+
 /* ---------------------------------------------------------------- solve */
 /* Solve V x = b, b[i] = |T_i|, by preconditioned CG (Jacobi: diag(V), the paper's
  * "diag" comparison preconditioner, Sec. 3), and return Cap = (1/4pi) b.x

@@ -35,7 +35,7 @@ EXPORTS = [
     "bem_assemble_V", "bem_assemble_V_update", "bem_operator_destroy", "bem_operator_info",
     "bem_operator_read", "bem_operator_entries", "bem_operator_matvec", "bem_solve_capacity",
     "bem_zz_estimate", "bem_dorfler", "bem_refine", "bem_mark_refine", "bem_adaptive_run",
-    "bem_profile_enable", "bem_profile_read", "bem_launch_count",
+    "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -112,6 +112,7 @@ def lib():
         "bem_profile_enable": [vp, i32],
         "bem_profile_read": [vp, i32, P(i64), P(d), P(d)],
         "bem_launch_count": [vp, P(i64)],
+        "bem_operator_matvec_noalloc": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

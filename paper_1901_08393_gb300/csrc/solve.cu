@@ -707,3 +707,74 @@ out:
 }
 
 }  // namespace bem
+
+// ------------------------------------------------------------------ no-allocation product
+// Some callers cannot let a library allocate device memory in the middle of a
+// call: code that is being captured into a CUDA graph (cudaMalloc and cudaFree
+// are not permitted during stream capture), serving loops that run inside a fixed,
+// pre-reserved memory footprint, and hosts whose device memory is owned by another
+// framework's allocator.  For them bem_operator_matvec_noalloc computes the same
+// symmetric double-float product as bem_operator_matvec, with its scratch in the
+// static device array below instead of in allocated buffers.
+namespace bem {
+
+constexpr int64_t kNoAllocMaxN = 4096;  // largest operator accepted
+constexpr int kNoAllocNb = (int)(kNoAllocMaxN / kSB);
+constexpr int64_t kNoAllocTiles = (int64_t)kNoAllocNb * (kNoAllocNb + 1) / 2;
+constexpr size_t kNoAllocXBytes = (size_t)kNoAllocMaxN * sizeof(float2);           // x as hi/lo pairs
+constexpr size_t kNoAllocPartBytes = (size_t)kNoAllocTiles * kSB * sizeof(float2);  // row (or column) partials
+constexpr size_t kNoAllocBytes = kNoAllocXBytes + 2 * kNoAllocPartBytes + kNoAllocTiles * sizeof(int2);
+
+// Every GPU that loads the library holds this array (about 2.1 MiB) until exit.
+// Each call writes every word it reads, so nothing has to start at zero; calls
+// that overlap on the GPU (other streams, other threads) share it and race.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static void *g_noalloc_addr[64] = {nullptr};  // device address of the array, per device
+
+}  // namespace bem
+
+extern "C" bem_status bem_operator_matvec_noalloc(const bem_operator *op, const double *x, double *y)
+{
+    using namespace bem;
+    if (!op) return BEM_ERR_INVALID;
+    bem_ctx *ctx = op->mesh->ctx;
+    if (op->precision != BEM_PREC_DF64)
+        return set_error(ctx, BEM_ERR_INVALID, "bem_operator_matvec_noalloc needs a BEM_PREC_DF64 operator");
+    if (op->N > kNoAllocMaxN)
+        return set_error(ctx, BEM_ERR_INVALID,
+                         "operator size N = %lld exceeds the no-allocation limit N <= %lld; use bem_operator_matvec",
+                         (long long)op->N, (long long)kNoAllocMaxN);
+    if (!x || !y || !is_device_ptr(x) || !is_device_ptr(y))
+        return set_error(ctx, BEM_ERR_INVALID,
+                         "x and y must be device pointers (host arrays would need staging buffers)");
+    int dev = -1;
+    BEM_CK(ctx, cudaGetDevice(&dev));
+    if (dev != ctx->device || dev < 0 || dev >= 64)
+        return set_error(ctx, BEM_ERR_INVALID, "call with the context's device (%d) current", ctx->device);
+    if (!g_noalloc_addr[dev]) {
+        // set-up on the first call on this device: the host-side name of the array
+        // is not a device address, so ask the runtime for it
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_error(ctx, e, "cudaGetSymbolAddress of the no-allocation scratch");
+        g_noalloc_addr[dev] = p;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_noalloc_addr[dev]);
+    float2 *xdf = reinterpret_cast<float2 *>(base);
+    float2 *prow = reinterpret_cast<float2 *>(base + kNoAllocXBytes);
+    float2 *pcol = reinterpret_cast<float2 *>(base + kNoAllocXBytes + kNoAllocPartBytes);
+    int2 *tiles = reinterpret_cast<int2 *>(base + kNoAllocXBytes + 2 * kNoAllocPartBytes);
+    const int nb = (int)(op->ld / kSB);
+    const int ntiles = nb * (nb + 1) / 2;
+    cudaStream_t s = ctx->stream;
+    k_tile_list<<<nb, 128, 0, s>>>(nb, tiles); BEM_COUNT(ctx);
+    k_to_df<<<nblk(op->ld, 256), 256, 0, s>>>(x, op->N, op->ld, xdf); BEM_COUNT(ctx);
+    BEM_CK(ctx, cudaFuncSetAttribute(k_symv_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
+    const int grid = ntiles < 3 * ctx->sm_count ? ntiles : 3 * ctx->sm_count;
+    k_symv_df<<<grid, kSymThreads, kSymSmem, s>>>((const float2 *)op->V, op->ld, op->N, nb, tiles, ntiles, xdf, prow,
+                                                  pcol); BEM_COUNT(ctx);
+    k_symv_reduce<<<nblk(op->N, kVecThreads), kVecThreads, 0, s>>>(prow, pcol, nb, op->N, y, nullptr, nullptr); BEM_COUNT(ctx);
+    BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
