@@ -261,7 +261,8 @@ def main():
         bytes_ = mv_units / max(mv_n, 1)
         avg_s = mv_ms / max(mv_n, 1) / 1e3
         achieved = bytes_ / avg_s / 1e9
-        roof = {"kernel": {0: "k_matvec<double>", 1: "k_matvec<float>", 2: "k_matvec_df<float2>"}[PREC], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+        roof = {"kernel": {0: "k_matvec<double>", 1: "k_matvec<float>",
+                           2: "k_pcg_df (persistent PCG, symmetric tile products)"}[PREC], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
                 "peak_source": f"{peak_src} hbm_gbs", "launches": mv_n}
     roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / total_ms

@@ -132,6 +132,8 @@ bem_status bem_assemble_V(bem_mesh *mesh, const bem_assembly_opts *opts, bem_ope
  * bem_assemble_V on the same mesh. */
 bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse,
                                  const bem_assembly_opts *opts, bem_operator **out);
+/* An operator may be destroyed before or after its mesh; every other call on it
+ * needs its mesh alive. */
 bem_status bem_operator_destroy(bem_operator *op);
 bem_status bem_operator_info(const bem_operator *op, int64_t *N, int32_t *precision);
 /* Copy the block V[i0:i0+ni, j0:j0+nj] (row-major, ni x nj) into dst (host or
@@ -242,7 +244,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
  * algorithmic work of those launches:
  *   BEM_KERNEL_FAR    units = far-field entries computed (pairs i <= j)
  *   BEM_KERNEL_NEAR   units = touching pairs integrated
- *   BEM_KERNEL_MATVEC units = bytes of V streamed (N * N * element size) */
+ *   BEM_KERNEL_MATVEC units = bytes of V a product must read (N * N * element size, half
+ *                     of it for the symmetric DF64 product); the persistent DF64 solver
+ *                     is recorded as one launch carrying all its products */
 #define BEM_KERNEL_FAR 0
 #define BEM_KERNEL_NEAR 1
 #define BEM_KERNEL_MATVEC 2
@@ -250,6 +254,10 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
 bem_status bem_profile_enable(bem_ctx *ctx, int32_t on);
 /* Totals since the last enable (synchronises the stream). */
 bem_status bem_profile_read(bem_ctx *ctx, int32_t kernel, int64_t *launches, double *ms, double *units);
+/* DF64 solves run as one persistent cooperative launch (on = 1, the default) or
+ * as a host-driven loop of kernels (on = 0; also used when a cooperative launch is
+ * not possible).  Both give the same iterates up to the order of the reductions. */
+bem_status bem_context_set_persistent(bem_ctx *ctx, int32_t on);
 /* Number of CUDA kernels the context has launched so far. */
 bem_status bem_launch_count(const bem_ctx *ctx, int64_t *n);
 

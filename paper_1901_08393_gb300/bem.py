@@ -35,7 +35,7 @@ EXPORTS = [
     "bem_assemble_V", "bem_assemble_V_update", "bem_operator_destroy", "bem_operator_info",
     "bem_operator_read", "bem_operator_entries", "bem_operator_matvec", "bem_solve_capacity",
     "bem_zz_estimate", "bem_dorfler", "bem_refine", "bem_mark_refine", "bem_adaptive_run",
-    "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc",
+    "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc", "bem_context_set_persistent",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -113,6 +113,7 @@ def lib():
         "bem_profile_read": [vp, i32, P(i64), P(d), P(d)],
         "bem_launch_count": [vp, P(i64)],
         "bem_operator_matvec_noalloc": [vp, vp, vp],
+        "bem_context_set_persistent": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -181,6 +182,9 @@ class Context:
         n, ms, u = C.c_int64(), C.c_double(), C.c_double()
         self.check(self.L.bem_profile_read(self.h, kernel, C.byref(n), C.byref(ms), C.byref(u)))
         return int(n.value), float(ms.value), float(u.value)
+
+    def set_persistent(self, on: bool):
+        self.check(self.L.bem_context_set_persistent(self.h, int(on)))
 
     def launch_count(self) -> int:
         n = C.c_int64()

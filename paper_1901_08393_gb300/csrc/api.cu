@@ -180,6 +180,11 @@ void prof_stop(bem_ctx *ctx, int rec)
     if (rec >= 0 && rec < (int)ctx->prof.size()) cudaEventRecord(ctx->prof[rec].b, ctx->stream);
 }
 
+void prof_set_units(bem_ctx *ctx, int rec, double units)
+{
+    if (rec >= 0 && rec < (int)ctx->prof.size()) ctx->prof[rec].units = units;
+}
+
 static void prof_collect(bem_ctx *ctx)
 {
     if (ctx->prof.empty()) return;
@@ -253,6 +258,13 @@ bem_status bem_profile_read(bem_ctx *ctx, int32_t kernel, int64_t *launches, dou
     if (launches) *launches = ctx->prof_launches[kernel];
     if (ms) *ms = ctx->prof_ms[kernel];
     if (units) *units = ctx->prof_units[kernel];
+    return BEM_OK;
+}
+
+bem_status bem_context_set_persistent(bem_ctx *ctx, int32_t on)
+{
+    if (!ctx) return BEM_ERR_INVALID;
+    ctx->persistent_solver = on ? 1 : 0;
     return BEM_OK;
 }
 
@@ -390,6 +402,7 @@ static bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, be
     bem_operator *op = new (std::nothrow) bem_operator();
     if (!op) return set_error(ctx, BEM_ERR_OOM, "host allocation");
     op->mesh = mesh;
+    op->ctx = mesh->ctx;
     op->precision = prec;
     op->ss_order = ss;
     op->N = mesh->N;
@@ -460,7 +473,7 @@ bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse, con
 bem_status bem_operator_destroy(bem_operator *op)
 {
     if (!op) return BEM_ERR_INVALID;
-    dfree_all(op->mesh->ctx, op->allocs);
+    dfree_all(op->ctx, op->allocs);
     delete op;
     return BEM_OK;
 }

@@ -46,6 +46,7 @@ constexpr int kProfKinds = 4;
 struct bem_ctx {
     int64_t n_launch = 0;  // kernels launched by this context
     int profile = 0;       // record CUDA events around the hot kernels
+    int persistent_solver = 1;  // DF64 solves in one cooperative launch
     std::vector<bem::ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
     int64_t prof_launches[bem::kProfKinds] = {0, 0, 0, 0};
@@ -88,6 +89,7 @@ struct bem_mesh {
 
 struct bem_operator {
     bem_mesh *mesh = nullptr;
+    bem_ctx *ctx = nullptr;  // kept apart from mesh: an operator may be destroyed after its mesh
     int32_t precision = BEM_PREC_F64;
     int32_t ss_order = 4;
     int64_t N = 0, ld = 0;
@@ -117,6 +119,7 @@ bool is_device_ptr(const void *p);
 // Event pair around one hot-kernel launch (no-op unless profiling is on).
 int prof_start(bem_ctx *ctx, int id, double units);
 void prof_stop(bem_ctx *ctx, int rec);
+void prof_set_units(bem_ctx *ctx, int rec, double units);
 
 // Temporary device copy of a caller array (host or device).
 struct DevBuf {

@@ -216,6 +216,7 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool va
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // Stage tile (I, J) and the x segments of blocks I and J into one buffer.
 __device__ __forceinline__ void symv_stage(const float2 *V, int64_t ld, int64_t N, const float2 *xdf, int2 tj,
@@ -238,22 +239,22 @@ __device__ __forceinline__ void symv_stage(const float2 *V, int64_t ld, int64_t 
     }
 }
 
-__global__ void __launch_bounds__(kSymThreads) k_symv_df(const float2 *__restrict__ V, int64_t ld, int64_t N, int nb,
-                                                         const int2 *__restrict__ tiles, int ntiles,
-                                                         const float2 *__restrict__ xdf, float2 *__restrict__ prow,
-                                                         float2 *__restrict__ pcol)
+// Tile loop of the symmetric product for CTA cta of G (shared by the standalone
+// kernel and the persistent solver); sm: kSymSmem bytes of dynamic shared memory.
+__device__ void symv_tiles(const float2 *__restrict__ V, int64_t ld, int64_t N, const int2 *__restrict__ tiles,
+                           int ntiles, const float2 *__restrict__ xdf, float2 *__restrict__ prow,
+                           float2 *__restrict__ pcol, float2 *sm, int cta, int G)
 {
-    extern __shared__ float2 sm[];
     // [tile buffer 0][tile buffer 1][x segments 0][x segments 1][column partials 4 x 64]
     float2 *const xs0 = sm + 2 * kSB * kSP;
     float2 *cpart = sm + 2 * kSB * kSP + 4 * kSB;
     const int t = threadIdx.x;
     int it = 0;
-    if ((int)blockIdx.x < ntiles) symv_stage(V, ld, N, xdf, tiles[blockIdx.x], sm, xs0);
+    if (cta < ntiles) symv_stage(V, ld, N, xdf, tiles[cta], sm, xs0);
     cp_async_commit();
-    for (int k = blockIdx.x; k < ntiles; k += gridDim.x, ++it) {
+    for (int k = cta; k < ntiles; k += G, ++it) {
         const int cur = it & 1;
-        const int nk = k + gridDim.x;
+        const int nk = k + G;
         if (nk < ntiles) symv_stage(V, ld, N, xdf, tiles[nk], sm + (cur ^ 1) * kSB * kSP, xs0 + (cur ^ 1) * 2 * kSB);
         cp_async_commit();
         cp_async_wait1();
@@ -301,27 +302,46 @@ __global__ void __launch_bounds__(kSymThreads) k_symv_df(const float2 *__restric
         }
         __syncthreads();  // buffer cur is refilled in the next iteration
     }
+    cp_async_wait_all();
+}
+
+__global__ void __launch_bounds__(kSymThreads) k_symv_df(const float2 *__restrict__ V, int64_t ld, int64_t N, int nb,
+                                                         const int2 *__restrict__ tiles, int ntiles,
+                                                         const float2 *__restrict__ xdf, float2 *__restrict__ prow,
+                                                         float2 *__restrict__ pcol)
+{
+    extern __shared__ float2 sm[];
+    (void)nb;
+    symv_tiles(V, ld, N, tiles, ntiles, xdf, prow, pcol, sm, blockIdx.x, gridDim.x);
 }
 
 // y_i = sum of the column partials of tiles (J', I), J' < I, then of the row
 // partials of tiles (I, J), J >= I (tile (a, b) sits at position
-// a nb - a (a - 1) / 2 + (b - a) of the list); optional block partials of sum w_i y_i.
+// a nb - a (a - 1) / 2 + (b - a) of the list).  Loads bypass L1 (the partials are
+// written by other CTAs of the persistent solver).
 __device__ __forceinline__ int64_t tile_pos(int a, int b, int nb)
 {
     return (int64_t)a * nb - (int64_t)a * (a - 1) / 2 + (b - a);
 }
 
+__device__ __forceinline__ double symv_row(const float2 *__restrict__ prow, const float2 *__restrict__ pcol, int nb,
+                                           int64_t i)
+{
+    const int I = (int)(i / kSB), r = (int)(i % kSB);
+    float2 s = make_float2(0.f, 0.f);
+    for (int J = 0; J < I; ++J) s = df_add(s, __ldcg(pcol + tile_pos(J, I, nb) * kSB + r));
+    for (int J = I; J < nb; ++J) s = df_add(s, __ldcg(prow + tile_pos(I, J, nb) * kSB + r));
+    return df_to_double(s);
+}
+
+// y = reduction of the tile partials; optional block partials of sum w_i y_i.
 __global__ void k_symv_reduce(const float2 *__restrict__ prow, const float2 *__restrict__ pcol, int nb, int64_t N,
                               double *__restrict__ y, const double *__restrict__ w, double *dot_partial)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     double v = 0.0;
     if (i < N) {
-        const int I = (int)(i / kSB), r = (int)(i % kSB);
-        float2 s = make_float2(0.f, 0.f);
-        for (int J = 0; J < I; ++J) s = df_add(s, pcol[tile_pos(J, I, nb) * kSB + r]);
-        for (int J = I; J < nb; ++J) s = df_add(s, prow[tile_pos(I, J, nb) * kSB + r]);
-        v = df_to_double(s);
+        v = symv_row(prow, pcol, nb, i);
         y[i] = v;
     }
     if (dot_partial) block_partial(i < N ? w[i] * v : 0.0, dot_partial);
@@ -434,6 +454,180 @@ __global__ void k_residual(int64_t N, const double *b, const double *q, double *
         r[i] = v;
     }
     block_partial(v * v, prr);
+}
+
+// ------------------------------------------------------------------ persistent DF64 solver
+// The whole Jacobi-PCG of a DF64 operator in one cooperative launch: every CTA
+// takes part in the tile loop of the symmetric product, then owns rows
+// cta*256 + t + k*G*256 for the vector updates; global sums are fixed-order sums
+// of per-CTA partials that every CTA evaluates identically, so all CTAs take the
+// same convergence decision.  CTAs meet at a grid barrier whose wait is bounded
+// (about 1.7 s): on time-out it raises err and the kernel returns.
+struct PcgArgs {
+    const float2 *V;
+    int64_t ld, N;
+    int nb, ntiles;
+    const int2 *tiles;
+    float2 *prow, *pcol, *pdf;
+    double *x, *r, *z, *p, *q;
+    const double *d, *b;
+    double *part;             // 3 x G per-CTA partials
+    unsigned *bar;            // [0] arrivals, [1] generation
+    int *err;
+    double *out;              // [0] r.r, [1] b.b, [2] iterations
+    double tol;
+    int max_it, precond, has_x0;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        volatile unsigned *gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long spins = 0;
+            while (*gen == g) {
+                if (++spins > (1ll << 24)) {
+                    atomicExch(err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok && *(volatile int *)err == 0;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// Per-CTA partial of one value per thread (fixed tree) into slot[blockIdx.x].
+__device__ __forceinline__ void cta_partial(double v, double *slot)
+{
+    __shared__ double sw[kSymThreads / 32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sw[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kSymThreads / 32; ++k) t += sw[k];
+        slot[blockIdx.x] = t;
+    }
+    __syncthreads();
+}
+
+// Fixed-order sum of the G per-CTA partials (L2 loads: written by other CTAs).
+__device__ __forceinline__ double grid_total(const double *slot)
+{
+    __shared__ double sw[kSymThreads / 32];
+    __shared__ double res;
+    double v = 0.0;
+    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) v += __ldcg(slot + k);
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sw[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int k = 0; k < kSymThreads / 32; ++k) t += sw[k];
+        res = t;
+    }
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(kSymThreads) k_pcg_df(PcgArgs a)
+{
+    extern __shared__ float2 sm[];
+    const int G = gridDim.x, cta = blockIdx.x;
+    const int64_t stride = (int64_t)G * kSymThreads;
+    const int64_t i0 = (int64_t)cta * kSymThreads + threadIdx.x;
+    double *pA = a.part, *pB = a.part + G, *pC = a.part + 2 * G;
+    // r = b - V x0 (or b), z = M^-1 r, p = z
+    if (a.has_x0) {
+        for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.x[i]) : make_float2(0.f, 0.f);
+        if (!grid_barrier(a.bar, a.err)) return;
+        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G);
+        if (!grid_barrier(a.bar, a.err)) return;
+    }
+    double rz_l = 0.0, rr_l = 0.0, bb_l = 0.0;
+    for (int64_t i = i0; i < a.ld; i += stride) {
+        if (i < a.N) {
+            const double ri = a.b[i] - (a.has_x0 ? symv_row(a.prow, a.pcol, a.nb, i) : 0.0);
+            const double zi = a.precond ? ri / a.d[i] : ri;
+            a.r[i] = ri;
+            a.z[i] = zi;
+            a.p[i] = zi;
+            a.pdf[i] = df_from_double(zi);
+            rz_l += ri * zi;
+            rr_l += ri * ri;
+            bb_l += a.b[i] * a.b[i];
+        } else {
+            a.pdf[i] = make_float2(0.f, 0.f);
+        }
+    }
+    cta_partial(rz_l, pA);
+    cta_partial(rr_l, pB);
+    cta_partial(bb_l, pC);
+    if (!grid_barrier(a.bar, a.err)) return;
+    double rz = grid_total(pA), rr = grid_total(pB);
+    const double bb = grid_total(pC);
+    const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
+    int it = 0;
+    if (!grid_barrier(a.bar, a.err)) return;  // partial slots are reused below
+    while (!(rr <= thr) && it < a.max_it) {
+        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G);
+        if (!grid_barrier(a.bar, a.err)) return;
+        double pq_l = 0.0;
+        for (int64_t i = i0; i < a.N; i += stride) {
+            const double qi = symv_row(a.prow, a.pcol, a.nb, i);
+            a.q[i] = qi;
+            pq_l += a.p[i] * qi;
+        }
+        cta_partial(pq_l, pA);
+        if (!grid_barrier(a.bar, a.err)) return;
+        const double alpha = rz / grid_total(pA);
+        double rz_n = 0.0;
+        rr_l = 0.0;
+        for (int64_t i = i0; i < a.N; i += stride) {
+            a.x[i] += alpha * a.p[i];
+            const double ri = a.r[i] - alpha * a.q[i];
+            const double zi = a.precond ? ri / a.d[i] : ri;
+            a.r[i] = ri;
+            a.z[i] = zi;
+            rz_n += ri * zi;
+            rr_l += ri * ri;
+        }
+        cta_partial(rz_n, pB);
+        cta_partial(rr_l, pC);
+        if (!grid_barrier(a.bar, a.err)) return;
+        const double rz_new = grid_total(pB);
+        rr = grid_total(pC);
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        for (int64_t i = i0; i < a.N; i += stride) {
+            const double pi = a.z[i] + beta * a.p[i];
+            a.p[i] = pi;
+            a.pdf[i] = df_from_double(pi);
+        }
+        ++it;
+        if (!grid_barrier(a.bar, a.err)) return;
+    }
+    if (cta == 0 && threadIdx.x == 0) {
+        a.out[0] = rr;
+        a.out[1] = bb;
+        a.out[2] = (double)it;
+    }
 }
 
 // ------------------------------------------------------------------ host side
@@ -577,6 +771,85 @@ static bem_status pcg(bem_operator *op, Work &W, const double *rhs, double tol, 
     return BEM_OK;
 }
 
+// The persistent DF64 solver (k_pcg_df).  Returns BEM_OK with *ran = false when a
+// cooperative launch of the needed size is not possible (the caller then runs the
+// host-driven loop).
+static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, bool has_x0, double tol, int max_it,
+                                 int precond, int *its_out, double *rel_out, bool *ran)
+{
+    bem_ctx *ctx = op->mesh->ctx;
+    *ran = false;
+    int coop = 0, per_sm = 0;
+    BEM_CK(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+    if (!coop || !W.tiles) return BEM_OK;
+    BEM_CK(ctx, cudaFuncSetAttribute(k_pcg_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
+    BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_df, kSymThreads, kSymSmem));
+    if (per_sm < 1) return BEM_OK;
+    const int G = (per_sm < 3 ? per_sm : 3) * ctx->sm_count;
+    Allocs tmp;
+    double *part = nullptr;
+    bem_status st = dalloc(ctx, tmp, (void **)&part, sizeof(double) * (3 * G + 8) + 64, true);
+    if (st) return st;
+    double *out = part + 3 * G;
+    unsigned *bar = reinterpret_cast<unsigned *>(out + 4);
+    int *err = reinterpret_cast<int *>(bar + 2);
+    PcgArgs a;
+    a.V = (const float2 *)op->V;
+    a.ld = op->ld;
+    a.N = op->N;
+    a.nb = (int)(op->ld / kSB);
+    a.ntiles = a.nb * (a.nb + 1) / 2;
+    a.tiles = W.tiles;
+    a.prow = W.prow;
+    a.pcol = W.pcol;
+    a.pdf = W.xdf;
+    a.x = W.x;
+    a.r = W.r;
+    a.z = W.z;
+    a.p = W.p;
+    a.q = W.q;
+    a.d = W.d;
+    a.b = rhs;
+    a.part = part;
+    a.bar = bar;
+    a.err = err;
+    a.out = out;
+    a.tol = tol;
+    a.max_it = max_it;
+    a.precond = precond;
+    a.has_x0 = has_x0 ? 1 : 0;
+    void *args[] = {&a};
+    const int prof = prof_start(ctx, BEM_KERNEL_MATVEC, 0.0);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_pcg_df, dim3(G), dim3(kSymThreads), args, kSymSmem,
+                                                ctx->stream);
+    BEM_COUNT(ctx);
+    prof_stop(ctx, prof);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        dfree_all(ctx, tmp);
+        return BEM_OK;  // not launchable here: fall back
+    }
+    double h[4];
+    e = cudaMemcpyAsync(ctx->h_pinned, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 4, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) st = cuda_error(ctx, e, "persistent solve");
+    if (!st) {
+        memcpy(h, ctx->h_pinned, sizeof(h));
+        const int err_h = *reinterpret_cast<int *>(ctx->h_pinned + 4);
+        if (err_h) {
+            st = set_error(ctx, BEM_ERR_CUDA, "persistent solve: grid barrier timed out");
+        } else {
+            *ran = true;
+            *its_out = (int)h[2];
+            *rel_out = std::sqrt(h[0] / (h[1] > 0.0 ? h[1] : 1.0));
+            prof_set_units(ctx, prof, 4.0 * (double)op->N * (double)op->N * (h[2] + (has_x0 ? 1.0 : 0.0)));
+        }
+    }
+    dfree_all(ctx, tmp);
+    return st;
+}
+
 __global__ void k_capacity(int64_t N, const double *area, const double *x, double *out)
 {
     double v = 0.0;
@@ -639,7 +912,10 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         goto out;
     }
     if (op->precision != BEM_PREC_F32) {
-        st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
+        bool ran = false;
+        if (op->precision == BEM_PREC_DF64 && ctx->persistent_solver)
+            st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, &its, &rel, &ran);
+        if (!st && !ran) st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
         outer = 1;
     } else {
         // FP64 iterative refinement around FP32-product inner CG

@@ -277,3 +277,24 @@ def test_memory_released(ctx):
     op.close()
     mesh.close()
     assert ctx.memory_in_use() == before
+
+
+def test_persistent_solver_matches_host_loop(ctx):
+    """The one-launch DF64 solver and the host-driven loop give the same solve."""
+    for m in (inputs.cube_mesh(4), inputs.workload_polycube_adaptive(), inputs.cube_mesh(1)):
+        mesh, v, t = _upload(ctx, m)
+        op = bem.Operator.assemble(mesh, precision=bem.PREC_DF64)
+        x0 = np.full(m.N, 0.1)
+        res = []
+        for persistent in (True, False):
+            ctx.set_persistent(persistent)
+            for start in (None, x0):
+                res.append(bem.solve_capacity(op, tol=1e-11, x0=start))
+        ctx.set_persistent(True)
+        (c1, p1, i1), (c2, p2, i2), (c3, p3, i3), (c4, p4, i4) = res
+        assert i1["converged"] and i3["converged"]
+        assert abs(c1 / c3 - 1) < 1e-10 and abs(c2 / c4 - 1) < 1e-10  # different reduction orders
+        assert abs(i1["iterations"] - i3["iterations"]) <= 1 and abs(i2["iterations"] - i4["iterations"]) <= 1
+        assert np.max(np.abs(p1 - p3)) < 1e-9 * np.max(np.abs(p3))
+        cap_r = O.solve_capacity(v, t, tol=1e-12)[0]
+        assert abs(c1 / cap_r - 1) < 1e-10 and abs(c2 / cap_r - 1) < 1e-10
