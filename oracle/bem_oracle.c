@@ -331,8 +331,10 @@ int orc_pair_type(const int32_t *T, int64_t i, int64_t j)
     return shared_count(T + 3 * i, T + 3 * j);
 }
 
-/* V[i][j] with Sauter-Schwab order n for touching pairs. */
-double orc_entry(const double *V, const int32_t *T, int64_t i, int64_t j, int n)
+/* The integral with triangle i as the first panel (Sauter-Schwab order n for
+ * touching pairs).  For touching pairs this is not symmetric in (i, j) at finite
+ * n; the matrix entry is orc_entry. */
+double orc_entry_raw(const double *V, const int32_t *T, int64_t i, int64_t j, int n)
 {
     const int32_t *ti = T + 3 * i, *tj = T + 3 * j;
     double P[3][3], Q[3][3];
@@ -382,11 +384,25 @@ double orc_entry(const double *V, const int32_t *T, int64_t i, int64_t j, int n)
     return NAN; /* duplicate triangle: not a valid mesh */
 }
 
+/* V[i][j]: the entry with i <= j is computed and mirrored. */
+double orc_entry(const double *V, const int32_t *T, int64_t i, int64_t j, int n)
+{
+    return i <= j ? orc_entry_raw(V, T, i, j, n) : orc_entry_raw(V, T, j, i, n);
+}
+
 int orc_entries(const double *V, const int32_t *T, const int64_t *I, const int64_t *J,
                 int64_t K, int n, double *out)
 {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t k = 0; k < K; ++k) out[k] = orc_entry(V, T, I[k], J[k], n);
+    return 0;
+}
+
+int orc_entries_raw(const double *V, const int32_t *T, const int64_t *I, const int64_t *J,
+                    int64_t K, int n, double *out)
+{
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < K; ++k) out[k] = orc_entry_raw(V, T, I[k], J[k], n);
     return 0;
 }
 
@@ -396,7 +412,7 @@ int orc_assemble(const double *V, int64_t M, const int32_t *T, int64_t N, int n,
     (void)M;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int64_t i = 0; i < N; ++i)
-        for (int64_t j = i; j < N; ++j) out[i * N + j] = orc_entry(V, T, i, j, n);
+        for (int64_t j = i; j < N; ++j) out[i * N + j] = orc_entry_raw(V, T, i, j, n);
     for (int64_t i = 0; i < N; ++i)
         for (int64_t j = 0; j < i; ++j) out[i * N + j] = out[j * N + i];
     return 0;

@@ -63,6 +63,7 @@ def lib():
             L.orc_entry.argtypes = [vp, vp, i64, i64, i32]
             L.orc_entry.restype = d
             L.orc_entries.argtypes = [vp, vp, vp, vp, i64, i32, vp]
+            L.orc_entries_raw.argtypes = [vp, vp, vp, vp, i64, i32, vp]
             L.orc_assemble.argtypes = [vp, i64, vp, i64, i32, vp]
             L.orc_pcg.argtypes = [vp, i64, vp, vp, vp, d, i32, i32, vp, vp]
             L.orc_matvec.argtypes = [vp, i64, vp, vp]
@@ -144,12 +145,15 @@ def entry(verts, tris, i, j, n=4) -> float:
     return float(lib().orc_entry(_p(v), _p(t), i, j, n))
 
 
-def entries(verts, tris, I, J, n=4):
+def entries(verts, tris, I, J, n=4, raw=False):
+    """V[I[k]][J[k]] (the matrix: i <= j computed, mirrored); raw=True evaluates with
+    triangle I[k] as the first panel (not symmetric at finite order)."""
     v, t = _f64(verts), _i32(tris)
     I = np.ascontiguousarray(I, dtype=np.int64)
     J = np.ascontiguousarray(J, dtype=np.int64)
     out = np.zeros(I.shape[0])
-    lib().orc_entries(_p(v), _p(t), _p(I), _p(J), I.shape[0], n, _p(out))
+    f = lib().orc_entries_raw if raw else lib().orc_entries
+    f(_p(v), _p(t), _p(I), _p(J), I.shape[0], n, _p(out))
     return out
 
 

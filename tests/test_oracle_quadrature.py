@@ -133,9 +133,11 @@ def test_sauter_schwab_converges_on_mesh(n_lo, n_hi):
     near = [(i, j) for i in range(m.N) for j in range(m.N) if O.pair_type(t, i, j) > 0][:200]
     I = np.array([p[0] for p in near])
     J = np.array([p[1] for p in near])
-    lo = O.entries(m.verts, t, I, J, n_lo)
-    hi = O.entries(m.verts, t, I, J, n_hi)
+    lo = O.entries(m.verts, t, I, J, n_lo, raw=True)
+    hi = O.entries(m.verts, t, I, J, n_hi, raw=True)
     assert np.all(np.abs(lo / hi - 1) < 2e-3)
-    # V_ij and V_ji computed separately (panel roles swapped) agree
-    hi_t = O.entries(m.verts, t, J, I, n_hi)
-    assert np.all(np.abs(hi_t / hi - 1) < 1e-13)
+    # V_ij and V_ji computed separately (panel roles swapped) agree to quadrature accuracy
+    hi_t = O.entries(m.verts, t, J, I, n_hi, raw=True)
+    assert np.all(np.abs(hi_t / hi - 1) < 1e-9)
+    # the matrix entry is the mirrored one
+    assert np.array_equal(O.entries(m.verts, t, J, I, 4), O.entries(m.verts, t, I, J, 4))
