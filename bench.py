@@ -161,6 +161,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--max-n", type=int, default=MAX_N, help="smaller case of the same workload (profiling)")
+    ap.add_argument("--workload", default="adaptive", choices=["adaptive", "graded60k"],
+                    help="adaptive: the default workload above; graded60k: precision form (one FP32 "
+                         "assembly + FP64-refined solve on the 60,492-triangle graded cube per step)")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
@@ -182,12 +185,31 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     ctx = bem.Context()
-    m = inputs.workload_polycube_adaptive()
+    graded = args.workload == "graded60k"
+    if graded:
+        PREC = 1
+        args.precision = "f32"
+    m = inputs.workload_graded_cube_60k() if graded else inputs.workload_polycube_adaptive()
     mesh = bem.Mesh.upload(ctx, m.verts, m.tris)  # resident input for the device-timed value
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
+    def step_graded(msh):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
+        op = bem.Operator.assemble(msh, precision=bem.PREC_F32)
+        ev[1].record(stream)
+        cap, _, info = bem.solve_capacity(op, tol=TOL, max_it=5000)
+        ev[2].record(stream)
+        op.close()
+        torch.cuda.synchronize()
+        return [{"N": m.N, "M": m.M, "cap": cap, "iterations": info["iterations"], "n_marked": 0,
+                 "relres": info["relres"], "ms_assemble": ev[0].elapsed_time(ev[1]),
+                 "ms_solve": ev[1].elapsed_time(ev[2]), "ms_adapt": 0.0, "outer": info["outer"]}]
+
     def step():
+        if graded:
+            return step_graded(mesh)
         recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC)
         return recs
 
@@ -241,7 +263,17 @@ def main():
     adapt_ms = sum(r["ms_adapt"] for r in recs)
 
     # dominant kernel roofline
-    if far_ms >= mv_ms and PREC == 2:
+    if far_ms >= mv_ms and PREC == 1:
+        rs = far_units * 49 / max(far_n, 1)
+        avg_s = far_ms / max(far_n, 1) / 1e3
+        achieved = rs / avg_s / 1e12
+        peak = 152 * 16 * 2.07e9 / 1e12
+        roof = {"kernel": "k_far_f32", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T rsqrt/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MUFU reciprocal-square-root issue peak from unit counts and clock "
+                               "(152 SMs x 16 per clock x 2.07 GHz); 49 per entry",
+                "launches": far_n}
+    elif far_ms >= mv_ms and PREC == 2:
         ops = far_units * DF_FAR_OPS_PER_ENTRY / max(far_n, 1)
         avg_s = far_ms / max(far_n, 1) / 1e3
         achieved = ops / avg_s / 1e12
@@ -278,7 +310,10 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         mh = bem.Mesh.upload(ctx, m.verts, m.tris)
-        r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC)
+        if graded:
+            r2 = step_graded(mh)
+        else:
+            r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC)
         cap_final = r2[-1]["cap"]
         mh.close()
         torch.cuda.synchronize()
@@ -315,6 +350,13 @@ def main():
     }
     if args.max_n != MAX_N:
         line["config"]["workload"] += f" [reduced case: N>={args.max_n}]"
+    if graded:
+        line["config"]["workload"] = ("precision form: unit cube graded toward edges and corners, 60,492 triangles; "
+                                      "per step one FP32 assembly (FP64 near field) + FP64 iterative refinement "
+                                      "of V x = |T| to 1e-10")
+        line["config"]["refinement_sweeps"] = recs[-1].get("outer")
+        args.no_cpu_baseline = True
+        line["cpu_baseline"] = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
 

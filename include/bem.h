@@ -165,8 +165,9 @@ bem_status bem_operator_matvec_noalloc(const bem_operator *op, const double *x, 
 /* ---------------------------------------------------------------- solve */
 /* Solve V x = b, b[i] = |T_i|, by preconditioned CG (Jacobi: diag(V), the paper's
  * "diag" comparison preconditioner, Sec. 3), and return Cap = (1/4pi) b.x
- * (Eq. 2.8).  FP64 operators: CG in FP64.  FP32 operators: FP64 iterative
- * refinement (residual in FP64 against the stored V) around FP32-matvec inner CG.
+ * (Eq. 2.8).  FP64 / DF64 operators: CG with FP64 recurrences.  FP32 operators:
+ * FP64 iterative refinement (residual with FP64-accurate accumulation against the
+ * stored FP32 V) around inner CG solves of the correction.
  * x0 (nullable) starts the iteration; phi_out (nullable) receives x.  Returns
  * BEM_ERR_NOT_CONVERGED (with cap and info filled) if tol is not reached. */
 bem_status bem_solve_capacity(bem_operator *op, const bem_solve_opts *opts, const double *x0,

@@ -6,8 +6,10 @@
 // The PCG recurrences (Jacobi preconditioner diag(V), the paper's "diag",
 // Sec. 3) run in FP64 in three launches per iteration; every global sum is taken
 // over per-block partials in a fixed order, so a solve is bit-reproducible.
-// FP32 operators: FP64 iterative refinement -- r = b - V x with FP64
-// accumulation, an inner PCG with FP32 products on that residual, x += d.
+// FP32 operators: FP64 iterative refinement -- r = b - V x with FP64-accurate
+// accumulation, an inner PCG on that residual, x += d.  The inner products also
+// accumulate in double-float: with FP32 sums the error (~sqrt(N) 2^-24, 1.5e-5 at
+// N = 60k) would sit at the inner tolerance, and the product is HBM-bound either way.
 #include <cmath>
 
 #include "bem_internal.cuh"
@@ -941,7 +943,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
             cudaMemsetAsync(W.x, 0, sizeof(double) * L, s);
             int it_in = 0;
             double rel_in = 0.0;
-            if ((st = pcg(op, W, rhs, inner_tol, max_it, precond, false, &it_in, &rel_in))) goto out;
+            if ((st = pcg(op, W, rhs, inner_tol, max_it, precond, true, &it_in, &rel_in))) goto out;
             its += it_in;
             k_axpy<<<W.nb_vec, kVecThreads, 0, s>>>(N, 1.0, W.x, xs); BEM_COUNT(ctx);
             BEM_CK_LAUNCH(ctx);
