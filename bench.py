@@ -152,6 +152,122 @@ def reference_arm(args):
     return 0
 
 
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
+
+
+def server_workload(args):
+    """Serving (BASELINE config 5) and batching (config 4) through bem_server_*.
+
+    serve: requests of inputs.serving_requests (seed 5, Poisson 50 req/s: polycubes,
+    rotated/scaled cubes, tetrahedra, 100..2000 triangles, 3..6 adaptive levels capped
+    at N = 40,000) are submitted on their arrival clock; one step = one stream of
+    --requests requests; value = completed requests per second of the step, latency =
+    completion - submission.  A second pass submits the same stream at once
+    (saturation throughput).
+    batch: inputs.batch_meshes (seed 4: polycubes g in 3..10, p in [0.3, 0.7], uniform
+    meshes, log-uniform 500..30,000 triangles), one level each (assembly + solve),
+    all submitted at once; one step = --batch meshes.
+    Both in FP32 with FP64 iterative refinement to 1e-10 (the mixed-precision form).
+    """
+    import threading
+
+    import torch
+
+    from paper_1901_08393_gb300 import bem, build, inputs
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(free * 0.8, 200 << 30))
+    if args.workload == "serve":
+        reqs = inputs.serving_requests(count=args.requests, seed=5 + rank, rate=50.0)
+        jobs = [(r["mesh"], r["steps"], 40000, r["t_arrive"]) for r in reqs]
+        label = ("serving: Poisson 50 req/s, polycubes / rotated+scaled cubes / tetrahedra with 100..2000 "
+                 "triangles, 3..6 adaptive ZZ/Doerfler/NVB levels (N <= 40,000), FP32 V + FP64 refinement "
+                 f"to 1e-10, {args.slots} slots, HBM budget {budget >> 30} GiB")
+    else:
+        ms = inputs.batch_meshes(count=args.batch, seed=4 + rank)
+        jobs = [(m, 1, m.N, 0.0) for m in ms]
+        label = (f"batch: {args.batch} uniform polycube meshes (g 3..10, p 0.3..0.7, log-uniform 500..30,000 "
+                 f"triangles), one assembly + solve each, FP32 V + FP64 refinement to 1e-10, {args.slots} slots, "
+                 f"HBM budget {budget >> 30} GiB")
+    srv = bem.Server(slots=args.slots, hbm_budget_bytes=budget, precision=bem.PREC_F32, tol=TOL)
+
+    def run_stream(realtime):
+        ids = []
+        t0 = time.perf_counter()
+
+        def submitter():
+            for m, lv, mx, ta in jobs:
+                if realtime:
+                    dt = t0 + ta - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                ids.append(srv.submit(m.verts, m.tris, lv, mx))
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        res = [srv.wait(i) for i in ids]
+        return res
+
+    for _ in range(max(args.warmup, 0)):
+        run_stream(False)
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    lat, tp, spans, fails, solves = [], [], [], 0, 0
+    levels = 0
+    for _ in range(args.steps):
+        res = run_stream(args.workload == "serve")
+        span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+        tp.append(len(res) / span)
+        spans.append(span)
+        lat += [1e3 * (r["t_done"] - r["t_submit"]) for r in res]
+        fails += sum(1 for r in res if r["status"] != 0)
+        solves += sum(r["levels"] for r in res)
+        levels = solves
+    clk = clocks.stop()
+    sat = None
+    if args.workload == "serve":
+        res = run_stream(False)
+        sat = len(res) / (max(r["t_done"] for r in res) - min(r["t_submit"] for r in res))
+    stats = srv.stats()
+    srv.close()
+    value = sum(tp) / len(tp)
+    if ws > 1:
+        t = torch.tensor([value], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t)
+        value = float(t.item())
+    line = {
+        "metric": METRIC, "value": value, "unit": "capacity requests/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(spans) / len(spans),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-refinement",
+        "data": "synthetic",
+        "config": {"workload": label, "requests_per_step": len(jobs), "slots": args.slots,
+                   "peak_in_flight": stats["peak_in_flight"], "peak_bytes": stats["peak_bytes"],
+                   "failed": fails, "level_solves": levels},
+        "p50_latency_ms": _pct(lat, 0.5), "p99_latency_ms": _pct(lat, 0.99),
+        "saturation_requests_per_s": sat, "clocks": clk, "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": value, "unit": "capacity requests/s",
+                "h2d_bytes_per_step": int(sum(m.verts.nbytes + m.tris.nbytes for m, _, _, _ in jobs)),
+                "d2h_bytes_per_step": len(jobs) * 512},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,14 +277,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--max-n", type=int, default=MAX_N, help="smaller case of the same workload (profiling)")
-    ap.add_argument("--workload", default="adaptive", choices=["adaptive", "graded60k"],
+    ap.add_argument("--workload", default="adaptive", choices=["adaptive", "graded60k", "serve", "batch"],
                     help="adaptive: the default workload above; graded60k: precision form (one FP32 "
-                         "assembly + FP64-refined solve on the 60,492-triangle graded cube per step)")
+                         "assembly + FP64-refined solve on the 60,492-triangle graded cube per step); "
+                         "serve: Poisson stream of adaptive requests through the continuous-batching server; "
+                         "batch: uniform polycube meshes solved through the server")
+    ap.add_argument("--requests", type=int, default=200, help="serve: requests per step")
+    ap.add_argument("--batch", type=int, default=64, help="batch: meshes per step")
+    ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload in ("serve", "batch"):
+        return server_workload(args)
 
     import numpy as np
     import torch

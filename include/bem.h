@@ -26,7 +26,7 @@
  *   - Layouts: vertices M x 3 float64 row-major (x,y,z per vertex); triangles
  *     N x 3 int32 row-major, 0-based vertex indices.  V (float64 or float32 by
  *     precision) lives on the device, row-major with each row padded to a multiple
- *     of 32 entries; bem_operator_read returns compact row-major blocks.
+ *     of 64 entries; bem_operator_read returns compact row-major blocks.
  *   - Meshes must be closed (every edge shared by an even number >= 2 of
  *     triangles; non-manifold edges are allowed) with non-degenerate triangles;
  *     otherwise BEM_ERR_MESH.
@@ -238,6 +238,52 @@ typedef struct {
  * (caller destroys it). */
 bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_level_record *records,
                             int32_t *n_levels, bem_mesh **final_mesh);
+
+/* ---------------------------------------------------------------- serving */
+/* Continuous-batching server for adaptive capacity requests (the paper has no
+ * counterpart: it serves many polyhedra of different sizes arriving over time).
+ * `slots` host threads, each with its own CUDA stream and context on the device
+ * current at creation, take requests in arrival order; a request is admitted when
+ * a slot is free and its device-memory estimate (one operator at N for a single
+ * level, else two operators at min(1.5 max_N, N 2.2^(levels-1)); plus tables) fits
+ * in hbm_budget_bytes next to the running requests -- the first
+ * queued request that fits, so small requests backfill around large ones; with
+ * nothing running the first request is always admitted.  Admitted requests run
+ * bem_adaptive_run with `opts` (max_levels and max_N taken per request) on their
+ * own stream, so their kernels overlap; each keeps its mesh, operator and Krylov
+ * state on the device across levels and is held to its estimate by the context's
+ * HBM budget.  A request's result does not depend on what else runs. */
+typedef struct bem_server bem_server;
+#define BEM_SERVER_HISTORY 16
+typedef struct {
+    int64_t id;
+    int32_t status;          /* bem_status of the request */
+    int32_t done;            /* 1 once finished */
+    int32_t levels;
+    int64_t N_final;
+    double cap;              /* Cap of the last level */
+    double t_submit, t_start, t_done;  /* seconds since the server started (steady clock) */
+    int64_t estimate_bytes;  /* admission estimate */
+    double cap_history[BEM_SERVER_HISTORY];
+    int64_t N_history[BEM_SERVER_HISTORY];
+    char message[256];       /* error message when status != 0 */
+} bem_request_result;
+typedef struct {
+    int64_t queued, in_flight, peak_in_flight, in_flight_bytes, peak_bytes, budget;
+    double clock;            /* seconds since the server started */
+} bem_server_stats_t;
+
+bem_status bem_server_create(int32_t slots, int64_t hbm_budget_bytes, const bem_adaptive_opts *opts,
+                             bem_server **out);
+/* Queue a request: the mesh arrays (host memory) are copied; max_levels >= 1 levels or
+ * until N >= max_N.  Never blocks on the GPU. */
+bem_status bem_server_submit(bem_server *s, const double *verts, int64_t M, const int32_t *tris, int64_t N,
+                             int32_t max_levels, int64_t max_N, int64_t *id_out);
+/* Block until request id has finished, return its result and forget it. */
+bem_status bem_server_wait(bem_server *s, int64_t id, bem_request_result *out);
+bem_status bem_server_stats(bem_server *s, bem_server_stats_t *out);
+/* Finish every queued request, then stop the slot threads and free the server. */
+bem_status bem_server_destroy(bem_server *s);
 
 /* ---------------------------------------------------------------- instrumentation */
 /* Per-kernel device time, taken with CUDA events recorded on the context's stream

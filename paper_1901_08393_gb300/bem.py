@@ -36,6 +36,7 @@ EXPORTS = [
     "bem_operator_read", "bem_operator_entries", "bem_operator_matvec", "bem_solve_capacity",
     "bem_zz_estimate", "bem_dorfler", "bem_refine", "bem_mark_refine", "bem_adaptive_run",
     "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc", "bem_context_set_persistent",
+    "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -66,6 +67,23 @@ class AdaptiveOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("max_N", C.c_int64), ("max_levels", C.c_int32),
                 ("h_mode", C.c_int32), ("assembly", AssemblyOpts), ("solve", SolveOpts),
                 ("incremental", C.c_int32)]
+
+
+SERVER_HISTORY = 16
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("done", C.c_int32), ("levels", C.c_int32),
+                ("N_final", C.c_int64), ("cap", C.c_double), ("t_submit", C.c_double), ("t_start", C.c_double),
+                ("t_done", C.c_double), ("estimate_bytes", C.c_int64),
+                ("cap_history", C.c_double * SERVER_HISTORY), ("N_history", C.c_int64 * SERVER_HISTORY),
+                ("message", C.c_char * 256)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("in_flight", C.c_int64), ("peak_in_flight", C.c_int64),
+                ("in_flight_bytes", C.c_int64), ("peak_bytes", C.c_int64), ("budget", C.c_int64),
+                ("clock", C.c_double)]
 
 
 class BemError(RuntimeError):
@@ -114,6 +132,11 @@ def lib():
         "bem_launch_count": [vp, P(i64)],
         "bem_operator_matvec_noalloc": [vp, vp, vp],
         "bem_context_set_persistent": [vp, i32],
+        "bem_server_create": [i32, i64, P(AdaptiveOpts), P(vp)],
+        "bem_server_submit": [vp, vp, i64, vp, i64, i32, i64, P(i64)],
+        "bem_server_wait": [vp, i64, P(RequestResult)],
+        "bem_server_stats": [vp, P(ServerStats)],
+        "bem_server_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -387,3 +410,55 @@ def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, pr
                                                C.byref(fin) if want_final else None))
     out = [{f: getattr(recs[k], f) for f, _ in LevelRecord._fields_} for k in range(n.value)]
     return out, (Mesh(mesh.ctx, fin) if want_final and fin.value else None)
+
+
+class Server:
+    """Continuous-batching server (bem_server_*): submit meshes, wait for results."""
+
+    def __init__(self, slots=4, hbm_budget_bytes=64 << 30, theta=0.5, precision=PREC_F32, tol=1e-10,
+                 max_it=20000, h_mode=0, ss_order=4, incremental=True, max_outer=20, inner_tol=1e-5):
+        self.L = lib()
+        o = AdaptiveOpts(theta, 0, 1, h_mode, AssemblyOpts(precision, ss_order),
+                         SolveOpts(tol, max_it, PRECOND_JACOBI, max_outer, inner_tol), int(incremental))
+        h = C.c_void_p()
+        st = self.L.bem_server_create(slots, int(hbm_budget_bytes), C.byref(o), C.byref(h))
+        if st != BEM_OK:
+            raise BemError(st, "server creation failed")
+        self.h = h
+
+    def submit(self, verts, tris, max_levels, max_N):
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        rid = C.c_int64()
+        st = self.L.bem_server_submit(self.h, v.ctypes.data, v.shape[0], t.ctypes.data, t.shape[0],
+                                      int(max_levels), int(max_N), C.byref(rid))
+        if st != BEM_OK:
+            raise BemError(st, "submit failed")
+        return int(rid.value)
+
+    def wait(self, rid):
+        r = RequestResult()
+        st = self.L.bem_server_wait(self.h, rid, C.byref(r))
+        if st != BEM_OK:
+            raise BemError(st, "unknown request")
+        n = min(r.levels, SERVER_HISTORY)
+        return {"id": r.id, "status": r.status, "levels": r.levels, "N_final": r.N_final, "cap": r.cap,
+                "t_submit": r.t_submit, "t_start": r.t_start, "t_done": r.t_done,
+                "estimate_bytes": r.estimate_bytes, "caps": list(r.cap_history[:n]),
+                "Ns": list(r.N_history[:n]), "message": r.message.decode(errors="replace")}
+
+    def stats(self):
+        s = ServerStats()
+        self.L.bem_server_stats(self.h, C.byref(s))
+        return {f: getattr(s, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.h:
+            self.L.bem_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

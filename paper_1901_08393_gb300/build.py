@@ -19,7 +19,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libbem_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "mesh.cu", "assemble.cu", "solve.cu", "adapt.cu"]
+SOURCES = ["api.cu", "mesh.cu", "assemble.cu", "solve.cu", "adapt.cu", "server.cu"]
 NO_FMA = {"mesh.cu", "adapt.cu"}
 
 

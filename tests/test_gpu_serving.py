@@ -1,0 +1,78 @@
+"""Continuous-batching server (bem_server_*): results in the mix equal results alone,
+admission respects the HBM budget, and a bad request fails alone."""
+import numpy as np
+import pytest
+
+from paper_1901_08393_gb300 import bem, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    rng = inputs.SplitMix64(11)
+    reqs = [
+        (inputs.polycube_mesh(4, 0.5, 3), 4, 2500),
+        (inputs.transformed(inputs.cube_mesh(3), inputs.random_rotation(rng), 1.7), 3, 2000),
+        (inputs.tetra_mesh(6), 4, 2500),
+        (inputs.polycube_mesh(5, 0.4, 8), 3, 3000),
+        (inputs.icosphere_mesh(3), 3, 1500),
+        (inputs.fichera_mesh(2), 5, 2500),
+    ]
+    return reqs
+
+
+@pytest.fixture(scope="module")
+def cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+
+
+@pytest.mark.parametrize("prec", [bem.PREC_F32, bem.PREC_DF64], ids=["f32", "df64"])
+def test_mix_equals_alone(cuda, prec):
+    reqs = _requests()
+    srv = bem.Server(slots=4, hbm_budget_bytes=16 << 30, precision=prec)
+    ids = [srv.submit(m.verts, m.tris, lv, mx) for m, lv, mx in reqs]
+    mixed = [srv.wait(i) for i in ids]
+    st = srv.stats()
+    srv.close()
+    assert st["peak_in_flight"] >= 2  # the requests really overlapped
+    alone = []
+    for m, lv, mx in reqs:
+        s1 = bem.Server(slots=1, hbm_budget_bytes=16 << 30, precision=prec)
+        alone.append(s1.wait(s1.submit(m.verts, m.tris, lv, mx)))
+        s1.close()
+    for a, b in zip(mixed, alone):
+        assert a["status"] == 0 and b["status"] == 0, (a["message"], b["message"])
+        assert a["Ns"] == b["Ns"]
+        assert a["caps"] == b["caps"]  # bit-identical: every kernel reduces in a fixed order
+        assert a["t_submit"] <= a["t_start"] <= a["t_done"]
+    # the same requests through the single-request entry point
+    ctx = bem.Context()
+    m, lv, mx = reqs[0]
+    recs, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), max_N=mx, max_levels=lv, precision=prec,
+                               tol=1e-10)
+    assert [r["cap"] for r in recs] == mixed[0]["caps"]
+
+
+def test_admission_budget_and_bad_request(cuda):
+    reqs = _requests()[:3]
+    one = bem.Server(slots=1, hbm_budget_bytes=1 << 40)
+    est = one.wait(one.submit(reqs[0][0].verts, reqs[0][0].tris, 1, reqs[0][2]))["estimate_bytes"]
+    one.close()
+    # budget for one request at a time: four slots, but never two in flight
+    srv = bem.Server(slots=4, hbm_budget_bytes=int(est * 1.2))
+    ids = [srv.submit(m.verts, m.tris, lv, reqs[0][2]) for m, lv, mx in reqs]
+    bad = inputs.cube_mesh(2)
+    bad_id = srv.submit(bad.verts, bad.tris[:-1], 3, 1000)  # open surface
+    res = [srv.wait(i) for i in ids]
+    rb = srv.wait(bad_id)
+    st = srv.stats()
+    srv.close()
+    assert st["peak_in_flight"] == 1 and st["peak_bytes"] <= int(est * 1.2)
+    assert all(r["status"] == 0 for r in res)
+    assert rb["status"] == bem.BEM_ERR_MESH and "closed" in rb["message"]
+    # served one after another, in arrival order of the fitting requests
+    starts = sorted((r["t_start"], r["t_done"]) for r in res)
+    assert all(b[0] >= a[1] - 1e-6 for a, b in zip(starts, starts[1:]))
