@@ -175,14 +175,12 @@ def server_workload(args):
 
     import torch
 
-    from paper_1901_08393_gb300 import bem, build, inputs
+    from paper_1901_08393_gb300 import bem, build, inputs, replicas
 
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        replicas.init("nccl", device=torch.device("cuda", local))
     build.build()
     free, total = torch.cuda.mem_get_info()
     budget = int(min(free * 0.8, 200 << 30))
@@ -242,11 +240,7 @@ def server_workload(args):
         sat = len(res) / (max(r["t_done"] for r in res) - min(r["t_submit"] for r in res))
     stats = srv.stats()
     srv.close()
-    value = sum(tp) / len(tp)
-    if ws > 1:
-        t = torch.tensor([value], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t)
-        value = float(t.item())
+    value = replicas.reduce_sum(sum(tp) / len(tp))
     line = {
         "metric": METRIC, "value": value, "unit": "capacity requests/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * sum(spans) / len(spans),
@@ -296,16 +290,14 @@ def main():
     import numpy as np
     import torch
 
-    from paper_1901_08393_gb300 import bem, build, inputs
+    from paper_1901_08393_gb300 import bem, build, inputs, replicas
 
     global PREC
     PREC = PRECISIONS[args.precision]
     ws, rank, local = _dist()
     torch.cuda.set_device(local)
     if ws > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        replicas.init("nccl", device=torch.device("cuda", local))
     build.build()
     ctx = bem.Context()
     graded = args.workload == "graded60k"
@@ -368,10 +360,7 @@ def main():
     clk = clocks.stop()
     launches = ctx.launch_count() - launches0
     total_ms = ev0.elapsed_time(ev1)
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = replicas.reduce_max(total_ms)
     lat_ms = sorted(a.elapsed_time(b) for a, b in lat)
     far_n, far_ms, far_units = ctx.profile_read(bem.KERNEL_FAR)
     mv_n, mv_ms, mv_units = ctx.profile_read(bem.KERNEL_MATVEC)
@@ -443,10 +432,8 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
         d2h = len(r2) * ctypes.sizeof(bem.LevelRecord)
     e2e_val = args.steps / sum(e2e_t) if e2e_t else None
-    if ws > 1:
-        t = torch.tensor([sum(e2e_t)], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = args.steps * ws / float(t.item())
+    if ws > 1 and e2e_t:
+        e2e_val = args.steps * ws / replicas.reduce_max(sum(e2e_t))
 
     value = args.steps * ws / (total_ms / 1e3)
     line = {
