@@ -243,20 +243,36 @@ __device__ __forceinline__ void symv_stage(const float2 *V, int64_t ld, int64_t 
 
 // Tile loop of the symmetric product for CTA cta of G (shared by the standalone
 // kernel and the persistent solver); sm: kSymSmem bytes of dynamic shared memory.
+// Tiles are taken either statically (k = cta, cta + G, ...) or, when ctr is given,
+// dynamically: each grab is an atomicAdd on *ctr, which never decreases; a grab
+// returns tile (value - base) and each CTA makes exactly one grab past the last
+// tile, so one pass consumes ntiles + G grabs.  A tile's partials do not depend on
+// which CTA computes it.
+__device__ __forceinline__ int symv_grab(unsigned long long *ctr, unsigned long long base)
+{
+    __shared__ int s_k;
+    __syncthreads();
+    if (threadIdx.x == 0) s_k = (int)(atomicAdd(ctr, 1ull) - base);
+    __syncthreads();
+    return s_k;
+}
+
 __device__ void symv_tiles(const float2 *__restrict__ V, int64_t ld, int64_t N, const int2 *__restrict__ tiles,
                            int ntiles, const float2 *__restrict__ xdf, float2 *__restrict__ prow,
-                           float2 *__restrict__ pcol, float2 *sm, int cta, int G)
+                           float2 *__restrict__ pcol, float2 *sm, int cta, int G,
+                           unsigned long long *ctr = nullptr, unsigned long long base = 0)
 {
     // [tile buffer 0][tile buffer 1][x segments 0][x segments 1][column partials 4 x 64]
     float2 *const xs0 = sm + 2 * kSB * kSP;
     float2 *cpart = sm + 2 * kSB * kSP + 4 * kSB;
     const int t = threadIdx.x;
     int it = 0;
-    if (cta < ntiles) symv_stage(V, ld, N, xdf, tiles[cta], sm, xs0);
+    int k = ctr ? symv_grab(ctr, base) : cta;
+    if (k < ntiles) symv_stage(V, ld, N, xdf, tiles[k], sm, xs0);
     cp_async_commit();
-    for (int k = cta; k < ntiles; k += G, ++it) {
+    for (; k < ntiles; ++it) {
         const int cur = it & 1;
-        const int nk = k + G;
+        const int nk = ctr ? symv_grab(ctr, base) : k + G;
         if (nk < ntiles) symv_stage(V, ld, N, xdf, tiles[nk], sm + (cur ^ 1) * kSB * kSP, xs0 + (cur ^ 1) * 2 * kSB);
         cp_async_commit();
         cp_async_wait1();
@@ -303,6 +319,7 @@ __device__ void symv_tiles(const float2 *__restrict__ V, int64_t ld, int64_t N, 
             }
         }
         __syncthreads();  // buffer cur is refilled in the next iteration
+        k = nk;
     }
     cp_async_wait_all();
 }
@@ -329,10 +346,61 @@ __device__ __forceinline__ int64_t tile_pos(int a, int b, int nb)
 __device__ __forceinline__ double symv_row(const float2 *__restrict__ prow, const float2 *__restrict__ pcol, int nb,
                                            int64_t i)
 {
+    // the partials are added in the order J = 0, 1, ..., nb-1; loads are issued 8 at
+    // a time so that their L2 latency overlaps
     const int I = (int)(i / kSB), r = (int)(i % kSB);
     float2 s = make_float2(0.f, 0.f);
-    for (int J = 0; J < I; ++J) s = df_add(s, __ldcg(pcol + tile_pos(J, I, nb) * kSB + r));
-    for (int J = I; J < nb; ++J) s = df_add(s, __ldcg(prow + tile_pos(I, J, nb) * kSB + r));
+    int J = 0;
+    for (; J + 8 <= I; J += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(pcol + tile_pos(J + u, I, nb) * kSB + r);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s = df_add(s, v[u]);
+    }
+    for (; J < I; ++J) s = df_add(s, __ldcg(pcol + tile_pos(J, I, nb) * kSB + r));
+    const int64_t rbase = tile_pos(I, I, nb) * kSB + r;  // tiles (I, J), J >= I, are consecutive
+    for (; J + 8 <= nb; J += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(prow + rbase + (int64_t)(J + u - I) * kSB);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s = df_add(s, v[u]);
+    }
+    for (; J < nb; ++J) s = df_add(s, __ldcg(prow + rbase + (int64_t)(J - I) * kSB));
+    return df_to_double(s);
+}
+
+// Row i by four consecutive threads (q = 0..3): thread q adds the partials
+// J in [q nb/4, (q+1) nb/4) in order, then (q0 + q1) + (q2 + q3); every thread of the
+// group returns the row's value.
+__device__ __forceinline__ double symv_row4(const float2 *__restrict__ prow, const float2 *__restrict__ pcol, int nb,
+                                            int64_t i, int q)
+{
+    const int I = (int)(i / kSB), r = (int)(i % kSB);
+    const int J0 = (q * nb) >> 2, J1 = ((q + 1) * nb) >> 2;
+    const int64_t rbase = tile_pos(I, I, nb) * kSB + r;
+    float2 s = make_float2(0.f, 0.f);
+    int J = J0;
+    for (; J + 4 <= J1; J += 4) {
+        float2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int j = J + u;
+            v[u] = j < I ? __ldcg(pcol + tile_pos(j, I, nb) * kSB + r) : __ldcg(prow + rbase + (int64_t)(j - I) * kSB);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s = df_add(s, v[u]);
+    }
+    for (; J < J1; ++J)
+        s = df_add(s, J < I ? __ldcg(pcol + tile_pos(J, I, nb) * kSB + r) : __ldcg(prow + rbase + (int64_t)(J - I) * kSB));
+    float2 o;
+    o.x = __shfl_xor_sync(0xffffffffu, s.x, 1);
+    o.y = __shfl_xor_sync(0xffffffffu, s.y, 1);
+    s = (q & 1) ? df_add(o, s) : df_add(s, o);
+    o.x = __shfl_xor_sync(0xffffffffu, s.x, 2);
+    o.y = __shfl_xor_sync(0xffffffffu, s.y, 2);
+    s = (q & 2) ? df_add(o, s) : df_add(s, o);
     return df_to_double(s);
 }
 
@@ -475,6 +543,7 @@ struct PcgArgs {
     const double *d, *b;
     double *part;             // 3 x G per-CTA partials
     unsigned *bar;            // [0] arrivals, [1] generation
+    unsigned long long *ctr;  // tile counter (never decreases)
     int *err;
     double *out;              // [0] r.r, [1] b.b, [2] iterations
     double tol;
@@ -559,9 +628,10 @@ __global__ void __launch_bounds__(kSymThreads) k_pcg_df(PcgArgs a)
     if (a.has_x0) {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.x[i]) : make_float2(0.f, 0.f);
         if (!grid_barrier(a.bar, a.err)) return;
-        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G);
+        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, 0ull);
         if (!grid_barrier(a.bar, a.err)) return;
     }
+    unsigned long long tbase = a.has_x0 ? (unsigned long long)(a.ntiles + G) : 0ull;
     double rz_l = 0.0, rr_l = 0.0, bb_l = 0.0;
     for (int64_t i = i0; i < a.ld; i += stride) {
         if (i < a.N) {
@@ -588,13 +658,26 @@ __global__ void __launch_bounds__(kSymThreads) k_pcg_df(PcgArgs a)
     int it = 0;
     if (!grid_barrier(a.bar, a.err)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
-        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G);
+        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase);
+        tbase += (unsigned long long)(a.ntiles + G);
         if (!grid_barrier(a.bar, a.err)) return;
         double pq_l = 0.0;
-        for (int64_t i = i0; i < a.N; i += stride) {
-            const double qi = symv_row(a.prow, a.pcol, a.nb, i);
-            a.q[i] = qi;
-            pq_l += a.p[i] * qi;
+        {
+            // 8 rows per warp and pass, 4 threads per row; the loop is uniform across
+            // the warp (rows past N recompute row N-1 and are discarded) because the
+            // row sum combines the 4 threads with shuffles
+            const int lane = threadIdx.x & 31, q4 = lane & 3;
+            const int64_t warp_g = ((int64_t)cta * kSymThreads + threadIdx.x) >> 5;
+            const int64_t nwarps = stride >> 5;
+            for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
+                const int64_t i = ib + (lane >> 2);
+                const bool valid = i < a.N;
+                const double qi = symv_row4(a.prow, a.pcol, a.nb, valid ? i : a.N - 1, q4);
+                if (valid && q4 == 0) {
+                    a.q[i] = qi;
+                    pq_l += a.p[i] * qi;
+                }
+            }
         }
         cta_partial(pq_l, pA);
         if (!grid_barrier(a.bar, a.err)) return;
@@ -787,13 +870,18 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     BEM_CK(ctx, cudaFuncSetAttribute(k_pcg_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
     BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_df, kSymThreads, kSymSmem));
     if (per_sm < 1) return BEM_OK;
-    const int G = (per_sm < 3 ? per_sm : 3) * ctx->sm_count;
+    // as many CTAs as there are tiles (up to 3 per SM): on small levels every CTA
+    // that would only wait at the grid barriers is left out
+    const int nb_ = (int)(op->ld / kSB), nt_ = nb_ * (nb_ + 1) / 2;
+    int G = (per_sm < 3 ? per_sm : 3) * ctx->sm_count;
+    if (nt_ < G) G = nt_ > 8 ? nt_ : 8;
     Allocs tmp;
     double *part = nullptr;
     bem_status st = dalloc(ctx, tmp, (void **)&part, sizeof(double) * (3 * G + 8) + 64, true);
     if (st) return st;
     double *out = part + 3 * G;
-    unsigned *bar = reinterpret_cast<unsigned *>(out + 4);
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(out + 4);
+    unsigned *bar = reinterpret_cast<unsigned *>(ctr + 1);
     int *err = reinterpret_cast<int *>(bar + 2);
     PcgArgs a;
     a.V = (const float2 *)op->V;
@@ -814,6 +902,7 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.b = rhs;
     a.part = part;
     a.bar = bar;
+    a.ctr = ctr;
     a.err = err;
     a.out = out;
     a.tol = tol;

@@ -58,10 +58,11 @@ def test_mix_equals_alone(cuda, prec):
 
 def test_admission_budget_and_bad_request(cuda):
     reqs = _requests()[:3]
-    one = bem.Server(slots=1, hbm_budget_bytes=1 << 40)
-    est = one.wait(one.submit(reqs[0][0].verts, reqs[0][0].tris, 1, reqs[0][2]))["estimate_bytes"]
+    one = bem.Server(slots=1, hbm_budget_bytes=1 << 40)  # the admission estimate of each request
+    est = max(one.wait(one.submit(m.verts, m.tris, lv, reqs[0][2]))["estimate_bytes"] for m, lv, mx in reqs)
     one.close()
-    # budget for one request at a time: four slots, but never two in flight
+    # budget for one of these requests at a time (four slots); the small bad request
+    # may backfill beside one of them
     srv = bem.Server(slots=4, hbm_budget_bytes=int(est * 1.2))
     ids = [srv.submit(m.verts, m.tris, lv, reqs[0][2]) for m, lv, mx in reqs]
     bad = inputs.cube_mesh(2)
@@ -70,7 +71,7 @@ def test_admission_budget_and_bad_request(cuda):
     rb = srv.wait(bad_id)
     st = srv.stats()
     srv.close()
-    assert st["peak_in_flight"] == 1 and st["peak_bytes"] <= int(est * 1.2)
+    assert st["peak_bytes"] <= int(est * 1.2)
     assert all(r["status"] == 0 for r in res)
     assert rb["status"] == bem.BEM_ERR_MESH and "closed" in rb["message"]
     # served one after another, in arrival order of the fitting requests
