@@ -76,11 +76,19 @@ typedef struct {
     int32_t precond;       /* BEM_PRECOND_NONE or BEM_PRECOND_JACOBI (diag(V), Sec. 3) */
     int32_t max_outer;     /* FP32 operators: FP64 iterative-refinement sweeps (default 20) */
     double inner_tol;      /* FP32 operators: relative tolerance of each inner solve (default 1e-5) */
+    double reliable_delta; /* DF64 operators, persistent solver: the iteration's products use the
+                              FP32 hi parts of V (a packed copy of the upper triangle, 2 N^2 bytes
+                              while the solve runs), and r is replaced by b - V x formed with the
+                              DF64 product whenever ||r|| has dropped by this factor since the
+                              last such residual and before convergence is declared, so tol
+                              holds for the DF64 operator.  0: default 1e-2; < 0 or >= 1: DF64
+                              products only */
 } bem_solve_opts;
 
 typedef struct {
     int32_t iterations;    /* CG iterations (summed over refinement sweeps) */
-    int32_t outer;         /* refinement sweeps (1 for FP64 operators) */
+    int32_t outer;         /* FP32 operators: refinement sweeps; DF64 operators: residuals formed
+                              with the DF64 product (initial one included); FP64: 1 */
     double relres;         /* final ||b - V x|| / ||b|| in FP64 */
     int32_t converged;     /* 1 if relres <= tol */
 } bem_solve_info;

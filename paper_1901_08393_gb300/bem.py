@@ -49,7 +49,7 @@ class AssemblyOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_it", C.c_int32), ("precond", C.c_int32),
-                ("max_outer", C.c_int32), ("inner_tol", C.c_double)]
+                ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("reliable_delta", C.c_double)]
 
 
 class SolveInfo(C.Structure):
@@ -342,9 +342,9 @@ class Operator:
 
 
 def solve_capacity(op: Operator, tol=1e-10, max_it=10000, precond=PRECOND_JACOBI, x0=None,
-                   max_outer=20, inner_tol=1e-5, phi_out=None, raise_not_converged=True):
+                   max_outer=20, inner_tol=1e-5, phi_out=None, raise_not_converged=True, reliable_delta=0.0):
     """Cap and x with V x = |T| (Eq. 2.5, 2.8).  phi_out may be a CUDA tensor."""
-    o = SolveOpts(tol, max_it, precond, max_outer, inner_tol)
+    o = SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta)
     info = SolveInfo()
     cap = C.c_double()
     N = op.info()[0]
@@ -399,10 +399,10 @@ def mark_refine(mesh: Mesh, eta2, theta=0.5, bisec3=False):
 
 def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, precision=PREC_F64,
                  ss_order=4, tol=1e-12, max_it=20000, precond=PRECOND_JACOBI, incremental=True,
-                 max_outer=20, inner_tol=1e-5, want_final=False):
+                 max_outer=20, inner_tol=1e-5, want_final=False, reliable_delta=0.0):
     """Alg. 1 in the library's native loop; returns (records, final Mesh or None)."""
     o = AdaptiveOpts(theta, max_N, max_levels, h_mode, AssemblyOpts(precision, ss_order),
-                     SolveOpts(tol, max_it, precond, max_outer, inner_tol), int(incremental))
+                     SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta), int(incremental))
     recs = (LevelRecord * max_levels)()
     n = C.c_int32()
     fin = C.c_void_p()
@@ -416,10 +416,12 @@ class Server:
     """Continuous-batching server (bem_server_*): submit meshes, wait for results."""
 
     def __init__(self, slots=4, hbm_budget_bytes=64 << 30, theta=0.5, precision=PREC_F32, tol=1e-10,
-                 max_it=20000, h_mode=0, ss_order=4, incremental=True, max_outer=20, inner_tol=1e-5):
+                 max_it=20000, h_mode=0, ss_order=4, incremental=True, max_outer=20, inner_tol=1e-5,
+                 reliable_delta=0.0):
         self.L = lib()
         o = AdaptiveOpts(theta, 0, 1, h_mode, AssemblyOpts(precision, ss_order),
-                         SolveOpts(tol, max_it, PRECOND_JACOBI, max_outer, inner_tol), int(incremental))
+                         SolveOpts(tol, max_it, PRECOND_JACOBI, max_outer, inner_tol, reliable_delta),
+                         int(incremental))
         h = C.c_void_p()
         st = self.L.bem_server_create(slots, int(hbm_budget_bytes), C.byref(o), C.byref(h))
         if st != BEM_OK:

@@ -582,6 +582,7 @@ static bem_solve_opts default_solve_opts()
     o.precond = BEM_PRECOND_JACOBI;
     o.max_outer = 20;
     o.inner_tol = 1e-5;
+    o.reliable_delta = 0.0;
     return o;
 }
 

@@ -257,10 +257,14 @@ __device__ __forceinline__ int symv_grab(unsigned long long *ctr, unsigned long 
     return s_k;
 }
 
+// pack (nullable): also write the FP32 hi parts of each staged tile, row-major
+// 64 x 64 at pack + 4096 k for tile k of the list (the packed upper triangle).
+constexpr int kTileF = kSB * kSB;
+
 __device__ void symv_tiles(const float2 *__restrict__ V, int64_t ld, int64_t N, const int2 *__restrict__ tiles,
                            int ntiles, const float2 *__restrict__ xdf, float2 *__restrict__ prow,
                            float2 *__restrict__ pcol, float2 *sm, int cta, int G,
-                           unsigned long long *ctr = nullptr, unsigned long long base = 0)
+                           unsigned long long *ctr = nullptr, unsigned long long base = 0, float *pack = nullptr)
 {
     // [tile buffer 0][tile buffer 1][x segments 0][x segments 1][column partials 4 x 64]
     float2 *const xs0 = sm + 2 * kSB * kSP;
@@ -281,6 +285,15 @@ __device__ void symv_tiles(const float2 *__restrict__ V, int64_t ld, int64_t N, 
         const float2 *T = sm + cur * kSB * kSP;
         const float2 *xi = xs0 + cur * 2 * kSB, *xj = xi + kSB;
         const int64_t base = (int64_t)k * kSB;
+        if (pack) {
+            float4 *dst = reinterpret_cast<float4 *>(pack + (int64_t)k * kTileF);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int f = t + kSymThreads * u;  // float4 f: row f / 16, columns 4 (f % 16) ..
+                const float2 *src = T + (f >> 4) * kSP + 4 * (f & 15);
+                dst[f] = make_float4(src[0].x, src[1].x, src[2].x, src[3].x);
+            }
+        }
         {  // row pass: row r, columns q, q+4, ..., q+60
             const int r = t >> 2, q = t & 3;
             float h = 0.f, l = 0.f;
@@ -402,6 +415,104 @@ __device__ __forceinline__ double symv_row4(const float2 *__restrict__ prow, con
     o.y = __shfl_xor_sync(0xffffffffu, s.y, 2);
     s = (q & 2) ? df_add(o, s) : df_add(s, o);
     return df_to_double(s);
+}
+
+// Product of the packed FP32 hi parts V_hi with a double-float vector (the
+// iteration products of the mixed-precision solver): exact FP32 x FP32 products
+// and double-float sums, as the DF64 product but reading 4 instead of 8 bytes per
+// entry.  Each warp takes whole tiles from the counter (one 16 KB contiguous
+// block per tile); lane l covers columns 4 (l % 16) .. +3 and rows 32 (l / 16) ..
+// +31, eight rows per step.  Row partials (V_IJ x_J) are summed over the 16 lanes
+// of a row half by a halving butterfly, column partials (V_IJ^T x_I, off the
+// diagonal) over the two row halves; both in the DF64 partial layout.
+// xsw: 128 pairs of shared memory per warp.
+__device__ __forceinline__ int warp_grab(unsigned long long *ctr, unsigned long long base)
+{
+    int k = 0;
+    if ((threadIdx.x & 31) == 0) k = (int)(atomicAdd(ctr, 1ull) - base);
+    return __shfl_sync(0xffffffffu, k, 0);
+}
+
+// sh + sl += v (xh + xl): acc_df with a single-float matrix entry
+__device__ __forceinline__ void acc_hi(float &sh, float &sl, float v, float xh, float xl)
+{
+    float p, e, s, t;
+    two_prod(v, xh, p, e);
+    e = __fmaf_rn(v, xl, e);
+    two_sum(sh, p, s, t);
+    sh = s;
+    sl = __fadd_rn(sl, __fadd_rn(e, t));
+}
+
+__device__ __forceinline__ float2 shfl_df(float2 v, int o)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
+}
+
+__device__ void symv_hi_tiles(const float *__restrict__ vp, const int2 *__restrict__ tiles, int ntiles,
+                              const float2 *__restrict__ xdf, float2 *__restrict__ prow, float2 *__restrict__ pcol,
+                              float2 *xsw, unsigned long long *ctr, unsigned long long base)
+{
+    const int lane = threadIdx.x & 31, cg = lane & 15, par = lane >> 4;
+    const bool b1 = lane & 2, b2 = lane & 4, b3 = lane & 8;
+    for (int k = warp_grab(ctr, base); k < ntiles; k = warp_grab(ctr, base)) {
+        const int2 tj = tiles[k];
+        __syncwarp();
+        // x_I in xsw[0..63] (lanes 0..15), x_J in xsw[64..127] (lanes 16..31)
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(xdf + (int64_t)(par ? tj.y : tj.x) * kSB) + 2 * cg;
+            float4 *dst = reinterpret_cast<float4 *>(xsw) + 2 * lane;
+            dst[0] = __ldcg(src);
+            dst[1] = __ldcg(src + 1);
+        }
+        __syncwarp();
+        float2 xc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xc[u] = xsw[kSB + 4 * cg + u];
+        const float4 *T = reinterpret_cast<const float4 *>(vp + (int64_t)k * kTileF);
+        float2 cs[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) cs[u] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+            const int r0 = 32 * par + 8 * ch;
+            float4 v[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) v[m] = __ldcs(T + (r0 + m) * 16 + cg);
+            float2 sr[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float2 xr = xsw[r0 + m];
+                const float e[4] = {v[m].x, v[m].y, v[m].z, v[m].w};
+                float h = 0.f, l = 0.f;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    acc_hi(h, l, e[u], xc[u].x, xc[u].y);
+                    acc_hi(cs[u].x, cs[u].y, e[u], xr.x, xr.y);
+                }
+                sr[m] = make_float2(h, l);
+            }
+            // rows m of this lane: 8 -> 4 (xor 8) -> 2 (xor 4) -> 1 (xor 2), then xor 1;
+            // lane keeps row (l / 2) % 8
+            float2 t4[4], t2[2];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) t4[j] = df_add(b3 ? sr[j + 4] : sr[j], shfl_df(b3 ? sr[j] : sr[j + 4], 8));
+#pragma unroll
+            for (int j = 0; j < 2; ++j) t2[j] = df_add(b2 ? t4[j + 2] : t4[j], shfl_df(b2 ? t4[j] : t4[j + 2], 4));
+            float2 w = df_add(b1 ? t2[1] : t2[0], shfl_df(b1 ? t2[0] : t2[1], 2));
+            const float2 o = shfl_df(w, 1);
+            w = (lane & 1) ? df_add(o, w) : df_add(w, o);
+            if (!(lane & 1)) prow[(int64_t)k * kSB + r0 + ((lane >> 1) & 7)] = w;
+        }
+        if (tj.x != tj.y) {  // lane keeps columns 4 (l % 16) + 2 (l / 16) + {0, 1}, rows 0..31 first
+            const float2 a0 = shfl_df(par ? cs[0] : cs[2], 16), a1 = shfl_df(par ? cs[1] : cs[3], 16);
+            float4 out;
+            const float2 s0 = par ? df_add(a0, cs[2]) : df_add(cs[0], a0);
+            const float2 s1 = par ? df_add(a1, cs[3]) : df_add(cs[1], a1);
+            out = make_float4(s0.x, s0.y, s1.x, s1.y);
+            reinterpret_cast<float4 *>(pcol + (int64_t)k * kSB)[2 * cg + par] = out;
+        }
+    }
 }
 
 // y = reduction of the tile partials; optional block partials of sum w_i y_i.
@@ -545,8 +656,9 @@ struct PcgArgs {
     unsigned *bar;            // [0] arrivals, [1] generation
     unsigned long long *ctr;  // tile counter (never decreases)
     int *err;
-    double *out;              // [0] r.r, [1] b.b, [2] iterations
-    double tol;
+    double *out;              // [0] r.r, [1] b.b, [2] iterations, [3] DF64 residuals
+    float *vp;                // packed FP32 hi parts of the tiles (mixed mode), else null
+    double tol, delta2;
     int max_it, precond, has_x0;
 };
 
@@ -617,21 +729,31 @@ __device__ __forceinline__ double grid_total(const double *slot)
     return res;
 }
 
-__global__ void __launch_bounds__(kSymThreads) k_pcg_df(PcgArgs a)
+__global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
 {
     extern __shared__ float2 sm[];
     const int G = gridDim.x, cta = blockIdx.x;
     const int64_t stride = (int64_t)G * kSymThreads;
     const int64_t i0 = (int64_t)cta * kSymThreads + threadIdx.x;
     double *pA = a.part, *pB = a.part + G, *pC = a.part + 2 * G;
-    // r = b - V x0 (or b), z = M^-1 r, p = z
-    if (a.has_x0) {
+    const bool mixed = a.vp != nullptr;
+    float2 *const xsw = sm + (threadIdx.x >> 5) * 2 * kSB;
+    const int lane = threadIdx.x & 31, q4 = lane & 3;
+    const int64_t warp_g = ((int64_t)cta * kSymThreads + threadIdx.x) >> 5, nwarps = stride >> 5;
+    unsigned long long tbase = 0ull;
+    // DF64 product V x into the tile partials (x = the FP64 iterate); the first one
+    // of the mixed mode also packs the hi parts
+    auto df64_product = [&](bool pack) -> bool {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.x[i]) : make_float2(0.f, 0.f);
-        if (!grid_barrier(a.bar, a.err)) return;
-        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, 0ull);
-        if (!grid_barrier(a.bar, a.err)) return;
-    }
-    unsigned long long tbase = a.has_x0 ? (unsigned long long)(a.ntiles + G) : 0ull;
+        if (!grid_barrier(a.bar, a.err)) return false;
+        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase,
+                   pack ? a.vp : nullptr);
+        tbase += (unsigned long long)(a.ntiles + G);
+        return grid_barrier(a.bar, a.err);
+    };
+    // r = b - V x0 (or b), z = M^-1 r, p = z
+    const bool prod0 = a.has_x0 || mixed;
+    if (prod0 && !df64_product(mixed)) return;
     double rz_l = 0.0, rr_l = 0.0, bb_l = 0.0;
     for (int64_t i = i0; i < a.ld; i += stride) {
         if (i < a.N) {
@@ -655,28 +777,30 @@ __global__ void __launch_bounds__(kSymThreads) k_pcg_df(PcgArgs a)
     double rz = grid_total(pA), rr = grid_total(pB);
     const double bb = grid_total(pC);
     const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
-    int it = 0;
+    double rr_true = rr;  // r.r at the last residual formed with the DF64 product
+    int it = 0, ndf = prod0 ? 1 : 0;
     if (!grid_barrier(a.bar, a.err)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
-        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase);
-        tbase += (unsigned long long)(a.ntiles + G);
+        if (mixed) {
+            symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
+            tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+        } else {
+            symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase);
+            tbase += (unsigned long long)(a.ntiles + G);
+        }
         if (!grid_barrier(a.bar, a.err)) return;
         double pq_l = 0.0;
-        {
-            // 8 rows per warp and pass, 4 threads per row; the loop is uniform across
-            // the warp (rows past N recompute row N-1 and are discarded) because the
-            // row sum combines the 4 threads with shuffles
-            const int lane = threadIdx.x & 31, q4 = lane & 3;
-            const int64_t warp_g = ((int64_t)cta * kSymThreads + threadIdx.x) >> 5;
-            const int64_t nwarps = stride >> 5;
-            for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
-                const int64_t i = ib + (lane >> 2);
-                const bool valid = i < a.N;
-                const double qi = symv_row4(a.prow, a.pcol, a.nb, valid ? i : a.N - 1, q4);
-                if (valid && q4 == 0) {
-                    a.q[i] = qi;
-                    pq_l += a.p[i] * qi;
-                }
+        // 8 rows per warp and pass, 4 threads per row; the loop is uniform across the
+        // warp (rows past N recompute row N-1 and are discarded) because the row sum
+        // combines the 4 threads with shuffles
+        for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
+            const int64_t i = ib + (lane >> 2);
+            const bool valid = i < a.N;
+            const int64_t ic = valid ? i : a.N - 1;
+            const double qi = symv_row4(a.prow, a.pcol, a.nb, ic, q4);
+            if (valid && q4 == 0) {
+                a.q[i] = qi;
+                pq_l += a.p[i] * qi;
             }
         }
         cta_partial(pq_l, pA);
@@ -696,8 +820,36 @@ __global__ void __launch_bounds__(kSymThreads) k_pcg_df(PcgArgs a)
         cta_partial(rz_n, pB);
         cta_partial(rr_l, pC);
         if (!grid_barrier(a.bar, a.err)) return;
-        const double rz_new = grid_total(pB);
+        double rz_new = grid_total(pB);
         rr = grid_total(pC);
+        ++it;
+        if (mixed && (rr <= a.delta2 * rr_true || rr <= thr)) {
+            // reliable update: replace the recursive residual by b - V x with the
+            // DF64 product (the direction p is kept)
+            if (!df64_product(false)) return;
+            rz_n = 0.0;
+            rr_l = 0.0;
+            for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
+                const int64_t i = ib + (lane >> 2);
+                const bool valid = i < a.N;
+                const double vi = symv_row4(a.prow, a.pcol, a.nb, valid ? i : a.N - 1, q4);
+                if (valid && q4 == 0) {
+                    const double ri = a.b[i] - vi;
+                    const double zi = a.precond ? ri / a.d[i] : ri;
+                    a.r[i] = ri;
+                    a.z[i] = zi;
+                    rz_n += ri * zi;
+                    rr_l += ri * ri;
+                }
+            }
+            cta_partial(rz_n, pB);
+            cta_partial(rr_l, pC);
+            if (!grid_barrier(a.bar, a.err)) return;
+            rz_new = grid_total(pB);
+            rr = grid_total(pC);
+            rr_true = rr;
+            ++ndf;
+        }
         const double beta = rz_new / rz;
         rz = rz_new;
         for (int64_t i = i0; i < a.N; i += stride) {
@@ -705,13 +857,13 @@ __global__ void __launch_bounds__(kSymThreads) k_pcg_df(PcgArgs a)
             a.p[i] = pi;
             a.pdf[i] = df_from_double(pi);
         }
-        ++it;
         if (!grid_barrier(a.bar, a.err)) return;
     }
     if (cta == 0 && threadIdx.x == 0) {
         a.out[0] = rr;
         a.out[1] = bb;
         a.out[2] = (double)it;
+        a.out[3] = (double)ndf;
     }
 }
 
@@ -859,8 +1011,13 @@ static bem_status pcg(bem_operator *op, Work &W, const double *rhs, double tol, 
 // The persistent DF64 solver (k_pcg_df).  Returns BEM_OK with *ran = false when a
 // cooperative launch of the needed size is not possible (the caller then runs the
 // host-driven loop).
+// delta > 0 selects the mixed mode: the products of the iteration use the packed
+// FP32 hi parts of the upper triangle, and the residual is recomputed with the DF64
+// product whenever ||r|| has dropped by delta since the last such residual (and at
+// convergence).  Without room for the packed copy in the context's budget the
+// solve runs with DF64 products only.
 static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, bool has_x0, double tol, int max_it,
-                                 int precond, int *its_out, double *rel_out, bool *ran)
+                                 int precond, double delta, int *its_out, int *ndf_out, double *rel_out, bool *ran)
 {
     bem_ctx *ctx = op->mesh->ctx;
     *ran = false;
@@ -883,6 +1040,16 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(out + 4);
     unsigned *bar = reinterpret_cast<unsigned *>(ctr + 1);
     int *err = reinterpret_cast<int *>(bar + 2);
+    float *vp = nullptr;
+    if (delta > 0.0) {
+        const size_t vbytes = (size_t)nt_ * kTileF * sizeof(float);
+        if (ctx->budget <= 0 || ctx->in_use + (int64_t)vbytes + 256 <= ctx->budget) {
+            if ((st = dalloc(ctx, tmp, (void **)&vp, vbytes, false))) {
+                dfree_all(ctx, tmp);
+                return st;
+            }
+        }
+    }
     PcgArgs a;
     a.V = (const float2 *)op->V;
     a.ld = op->ld;
@@ -905,7 +1072,9 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.ctr = ctr;
     a.err = err;
     a.out = out;
+    a.vp = vp;
     a.tol = tol;
+    a.delta2 = delta * delta;
     a.max_it = max_it;
     a.precond = precond;
     a.has_x0 = has_x0 ? 1 : 0;
@@ -933,8 +1102,14 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
         } else {
             *ran = true;
             *its_out = (int)h[2];
+            *ndf_out = vp ? (int)h[3] : 1;
             *rel_out = std::sqrt(h[0] / (h[1] > 0.0 ? h[1] : 1.0));
-            prof_set_units(ctx, prof, 4.0 * (double)op->N * (double)op->N * (h[2] + (has_x0 ? 1.0 : 0.0)));
+            // algorithmic bytes: a DF64 product reads the upper triangle of V
+            // (8 bytes x N^2 / 2); a mixed-mode iteration reads the packed FP32 upper
+            // triangle (4 x N^2 / 2), written once by the first product
+            const double n2 = (double)op->N * (double)op->N;
+            const double bytes = vp ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0) : 4.0 * n2 * (h[2] + h[3]);
+            prof_set_units(ctx, prof, bytes);
         }
     }
     dfree_all(ctx, tmp);
@@ -1004,10 +1179,17 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     }
     if (op->precision != BEM_PREC_F32) {
         bool ran = false;
-        if (op->precision == BEM_PREC_DF64 && ctx->persistent_solver)
-            st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, &its, &rel, &ran);
-        if (!st && !ran) st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
         outer = 1;
+        // DF64: FP32 products of the packed hi parts between DF64 residuals whenever
+        // ||r|| drops by reliable_delta (default 1e-2; < 0: DF64 products only)
+        const double delta = o->reliable_delta == 0.0 ? 1e-2 : (o->reliable_delta > 0.0 ? o->reliable_delta : 0.0);
+        if (op->precision == BEM_PREC_DF64 && ctx->persistent_solver)
+            st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, &its,
+                                &outer, &rel, &ran);
+        if (!st && !ran) {
+            st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
+            outer = 1;
+        }
     } else {
         // FP64 iterative refinement around FP32-product inner CG
         const int max_outer = o->max_outer > 0 ? o->max_outer : 20;
