@@ -40,6 +40,7 @@ FAR_FLOPS_PER_ENTRY = 49 * 11 + 16  # FP64 far field: per point pair 3 sub, 5 fo
 # row point, 92 per pair), against the FP32 issue peak 152 SMs x 128 lanes x 2.07 GHz.
 DF_FAR_OPS_PER_ENTRY = 49 * 74 + 7 * 45 + 92
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+PCG_TRAFFIC_RATIO = 31.483 / 31.541  # ncu DRAM bytes / algorithmic bytes of the persistent solver
 PRECISIONS = {"df64": 2, "f64": 0, "f32": 1}
 PREC = 2
 
@@ -405,9 +406,14 @@ def main():
         bytes_ = mv_units / max(mv_n, 1)
         avg_s = mv_ms / max(mv_n, 1) / 1e3
         achieved = bytes_ / avg_s / 1e9
+        # DRAM bytes (read + write) over algorithmic bytes of one ncu capture of k_pcg_df
+        # (adaptive polycube level N = 12,558: 31.48 GB measured, 31.54 GB algorithmic);
+        # traffic scales with the bytes of the products, so the ratio carries to full size
+        traffic = PCG_TRAFFIC_RATIO * bytes_ if PREC == 2 else None
         roof = {"kernel": {0: "k_matvec<double>", 1: "k_matvec<float>",
-                           2: "k_pcg_df (persistent PCG, symmetric tile products)"}[PREC], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                           2: "k_pcg_df (persistent mixed-precision PCG: packed FP32 hi-part tile products, "
+                              "DF64 residual replacement)"}[PREC], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
                 "peak_source": f"{peak_src} hbm_gbs", "launches": mv_n}
     roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / total_ms
 
@@ -451,7 +457,7 @@ def main():
         "kernel_ms_per_step": {"far": far_ms / args.steps, "near": nr_ms / args.steps,
                                "matvec": mv_ms / args.steps},
         "matvec_gbs": mv_units / (mv_ms / 1e3) / 1e9 if mv_ms else None,
-        "levels": [{"N": r["N"], "its": r["iterations"], "marked": r["n_marked"],
+        "levels": [{"N": r["N"], "its": r["iterations"], "df64_residuals": r["outer"], "marked": r["n_marked"],
                     "ms": round(r["ms_assemble"] + r["ms_solve"] + r["ms_adapt"], 3)} for r in recs],
         "roofline": roof,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -224,6 +224,7 @@ typedef struct {
     int32_t n_marked;      /* elements marked for the next level (0 on the last) */
     double relres;
     double ms_assemble, ms_solve, ms_adapt; /* device time per phase (CUDA events) */
+    int32_t outer;          /* bem_solve_info.outer of the level's solve */
 } bem_level_record;
 
 typedef struct {

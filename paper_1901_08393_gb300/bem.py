@@ -60,7 +60,8 @@ class SolveInfo(C.Structure):
 class LevelRecord(C.Structure):
     _fields_ = [("N", C.c_int64), ("M", C.c_int64), ("cap", C.c_double), ("eta2_total", C.c_double),
                 ("iterations", C.c_int32), ("n_marked", C.c_int32), ("relres", C.c_double),
-                ("ms_assemble", C.c_double), ("ms_solve", C.c_double), ("ms_adapt", C.c_double)]
+                ("ms_assemble", C.c_double), ("ms_solve", C.c_double), ("ms_adapt", C.c_double),
+                ("outer", C.c_int32)]
 
 
 class AdaptiveOpts(C.Structure):

@@ -742,6 +742,7 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         st = solve_capacity(op, &opts->solve, x0, x, &cap, &info);
         rec.cap = cap;
         rec.iterations = info.iterations;
+        rec.outer = info.outer;
         rec.relres = info.relres;
         if (st) { dfree_all(ctx, lv); bem_operator_destroy(op); break; }
         cudaEventRecord(ctx->ev[2], s);
