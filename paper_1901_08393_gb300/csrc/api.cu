@@ -4,6 +4,9 @@
 #include <cstdarg>
 #include <new>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "bem_internal.cuh"
 #include "dfloat.cuh"
 
@@ -34,7 +37,7 @@ bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero)
     if (ctx->budget > 0 && ctx->in_use + (int64_t)bytes > ctx->budget)
         return set_error(ctx, BEM_ERR_OOM, "HBM budget exceeded: %lld in use + %zu requested > %lld",
                          (long long)ctx->in_use, bytes, (long long)ctx->budget);
-    cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -85,7 +88,7 @@ bem_status dev_in(bem_ctx *ctx, const void *src, size_t bytes, DevBuf &buf)
         buf.dptr = const_cast<void *>(src);
         return BEM_OK;
     }
-    BEM_CK(ctx, cudaMallocAsync(&buf.owned, bytes ? bytes : 16, ctx->stream));
+    BEM_CK(ctx, cudaMallocFromPoolAsync(&buf.owned, bytes ? bytes : 16, ctx->pool, ctx->stream));
     buf.dptr = buf.owned;
     if (bytes) BEM_CK(ctx, cudaMemcpyAsync(buf.owned, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
     return BEM_OK;
@@ -99,7 +102,7 @@ bem_status dev_out_begin(bem_ctx *ctx, void *dst, size_t bytes, DevBuf &buf)
         buf.dptr = dst;
         return BEM_OK;
     }
-    BEM_CK(ctx, cudaMallocAsync(&buf.owned, bytes ? bytes : 16, ctx->stream));
+    BEM_CK(ctx, cudaMallocFromPoolAsync(&buf.owned, bytes ? bytes : 16, ctx->pool, ctx->stream));
     buf.dptr = buf.owned;
     return BEM_OK;
 }
@@ -214,6 +217,48 @@ using namespace bem;
 
 extern "C" {
 
+// One stream-ordered memory pool per device for all contexts of the library.  Its
+// release threshold keeps freed blocks reserved, so that the operators of successive
+// adaptive levels (up to several GB each) reuse mapped memory instead of returning
+// it to the driver at every synchronisation; the pool is trimmed when the last
+// context of the device is destroyed.
+namespace {
+std::mutex g_pool_mu;
+std::unordered_map<int, std::pair<cudaMemPool_t, int>> g_pools;  // device -> (pool, contexts)
+
+cudaError_t pool_acquire(int device, cudaMemPool_t *out)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(device);
+    if (it == g_pools.end()) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        it = g_pools.emplace(device, std::make_pair(pool, 0)).first;
+    }
+    it->second.second += 1;
+    *out = it->second.first;
+    return cudaSuccess;
+}
+
+void pool_release(int device)
+{
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(device);
+    if (it != g_pools.end() && --it->second.second == 0) cudaMemPoolTrimTo(it->second.first, 0);
+}
+}  // namespace
+
 bem_status bem_context_create(void *cuda_stream, int64_t hbm_budget_bytes, bem_ctx **out)
 {
     if (!out) return BEM_ERR_INVALID;
@@ -224,8 +269,12 @@ bem_status bem_context_create(void *cuda_stream, int64_t hbm_budget_bytes, bem_c
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_pinned, 64 * sizeof(double));
     for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreate(&ctx->ev[k]);
+    if (e == cudaSuccess) e = pool_acquire(ctx->device, &ctx->pool);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        for (int k = 0; k < 8; ++k)
+            if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
+        if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
         delete ctx;
         return BEM_ERR_CUDA;
     }
@@ -284,6 +333,7 @@ bem_status bem_context_destroy(bem_ctx *ctx)
     for (int k = 0; k < 8; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->pool) pool_release(ctx->device);
     delete ctx;
     return BEM_OK;
 }

@@ -53,6 +53,7 @@ struct bem_ctx {
     double prof_ms[bem::kProfKinds] = {0, 0, 0, 0};
     double prof_units[bem::kProfKinds] = {0, 0, 0, 0};
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;  // the library's stream-ordered pool of this device
     int device = 0;
     int sm_count = 0;
     int64_t budget = 0;  // <= 0: unlimited

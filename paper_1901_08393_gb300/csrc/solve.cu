@@ -10,6 +10,7 @@
 // accumulation, an inner PCG on that residual, x += d.  The inner products also
 // accumulate in double-float: with FP32 sums the error (~sqrt(N) 2^-24, 1.5e-5 at
 // N = 60k) would sit at the inner tolerance, and the product is HBM-bound either way.
+#include <algorithm>
 #include <cmath>
 
 #include "bem_internal.cuh"
@@ -1027,29 +1028,30 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     BEM_CK(ctx, cudaFuncSetAttribute(k_pcg_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
     BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_df, kSymThreads, kSymSmem));
     if (per_sm < 1) return BEM_OK;
-    // as many CTAs as there are tiles (up to 3 per SM): on small levels every CTA
-    // that would only wait at the grid barriers is left out
     const int nb_ = (int)(op->ld / kSB), nt_ = nb_ * (nb_ + 1) / 2;
-    int G = (per_sm < 3 ? per_sm : 3) * ctx->sm_count;
-    if (nt_ < G) G = nt_ > 8 ? nt_ : 8;
     Allocs tmp;
+    bem_status st = BEM_OK;
+    float *vp = nullptr;
+    if (delta > 0.0) {
+        const size_t vbytes = (size_t)nt_ * kTileF * sizeof(float);
+        if (ctx->budget <= 0 || ctx->in_use + (int64_t)vbytes + (64 << 10) <= ctx->budget)
+            if ((st = dalloc(ctx, tmp, (void **)&vp, vbytes, false))) return st;
+    }
+    // Up to 3 CTAs per SM.  On small levels, CTAs that would only wait at the grid
+    // barriers are left out: DF64 products take one tile per CTA, the mixed mode's
+    // products one tile per warp (8 per CTA), its row passes 8 rows per warp.
+    const int Gmax = (per_sm < 3 ? per_sm : 3) * ctx->sm_count;
+    int G = vp ? (int)std::max<int64_t>((nt_ + 7) / 8, (op->N + 63) / 64) : nt_;
+    G = std::min(std::max(G, 8), Gmax);
     double *part = nullptr;
-    bem_status st = dalloc(ctx, tmp, (void **)&part, sizeof(double) * (3 * G + 8) + 64, true);
-    if (st) return st;
+    if ((st = dalloc(ctx, tmp, (void **)&part, sizeof(double) * (3 * G + 8) + 64, true))) {
+        dfree_all(ctx, tmp);
+        return st;
+    }
     double *out = part + 3 * G;
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(out + 4);
     unsigned *bar = reinterpret_cast<unsigned *>(ctr + 1);
     int *err = reinterpret_cast<int *>(bar + 2);
-    float *vp = nullptr;
-    if (delta > 0.0) {
-        const size_t vbytes = (size_t)nt_ * kTileF * sizeof(float);
-        if (ctx->budget <= 0 || ctx->in_use + (int64_t)vbytes + 256 <= ctx->budget) {
-            if ((st = dalloc(ctx, tmp, (void **)&vp, vbytes, false))) {
-                dfree_all(ctx, tmp);
-                return st;
-            }
-        }
-    }
     PcgArgs a;
     a.V = (const float2 *)op->V;
     a.ld = op->ld;
