@@ -30,7 +30,9 @@ if ROOT not in sys.path:
 METRIC = "V-assembly Gpairs/s; capacity solves/s at 1e-6 rel err vs FP64; p99 latency"
 UNIT = "capacity solves/s"
 WORKLOAD = ("adaptive polycube: 6^3 voxels p=0.5 seed 1, ZZ + Doerfler theta=0.5 + NVB "
-            "until N>=20000, FP64 (7x7 Radon far field, Sauter-Schwab order 4, Jacobi-PCG 1e-10)")
+            "until N>=20000, FP64 (7x7 Radon far field, Sauter-Schwab order 4, PCG to 1e-10)")
+PC_LABEL = {"block": "block-Jacobi preconditioner on Morton clusters of 64 triangles",
+            "jacobi": "Jacobi preconditioner diag(V)"}
 MAX_N = 20000
 THETA = 0.5
 TOL = 1e-10
@@ -43,6 +45,7 @@ FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 PCG_TRAFFIC_RATIO = 31.483 / 31.541  # ncu DRAM bytes / algorithmic bytes of the persistent solver
 PRECISIONS = {"df64": 2, "f64": 0, "f32": 1}
 PREC = 2
+PC = 1
 
 
 def _peaks():
@@ -143,7 +146,8 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "final_N": hist[-1]["N"], "levels": len(hist)},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "final_N": hist[-1]["N"], "levels": len(hist),
+                                        "preconditioner": PC_LABEL["jacobi"]},
         "p99_latency_ms": 1e3 * max(times),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "complete adaptive runs of the workload, FP64 C/OpenMP oracle"},
@@ -280,6 +284,8 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per step")
     ap.add_argument("--batch", type=int, default=64, help="batch: meshes per step")
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
+    ap.add_argument("--precond", default="block", choices=["block", "jacobi"],
+                    help="PCG preconditioner of the adaptive workload (block: DF64 only)")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
@@ -305,6 +311,9 @@ def main():
     if graded:
         PREC = 1
         args.precision = "f32"
+    global PC
+    pc_name = args.precond if PREC == 2 else "jacobi"  # the block preconditioner runs in the DF64 solver
+    PC = bem.PRECOND_BLOCK if pc_name == "block" else bem.PRECOND_JACOBI
     m = inputs.workload_graded_cube_60k() if graded else inputs.workload_polycube_adaptive()
     mesh = bem.Mesh.upload(ctx, m.verts, m.tris)  # resident input for the device-timed value
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
@@ -326,7 +335,7 @@ def main():
     def step():
         if graded:
             return step_graded(mesh)
-        recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC)
+        recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC)
         return recs
 
     for _ in range(max(args.warmup, 0)):
@@ -431,7 +440,7 @@ def main():
         if graded:
             r2 = step_graded(mh)
         else:
-            r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC)
+            r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC)
         cap_final = r2[-1]["cap"]
         mh.close()
         torch.cuda.synchronize()
@@ -446,7 +455,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "final_N": recs[-1]["N"], "levels": len(recs),
+        "config": {"workload": WORKLOAD, "precision": args.precision, "preconditioner": PC_LABEL[pc_name],
+                   "final_N": recs[-1]["N"], "levels": len(recs),
                    "cap_final": recs[-1]["cap"], "parallelism": f"replicas x{ws}",
                    "l2": "256 MB buffer written before every step; V (up to 3.2 GB) exceeds L2"},
         "p50_latency_ms": lat_ms[len(lat_ms) // 2], "p99_latency_ms": lat_ms[min(len(lat_ms) - 1,

@@ -69,11 +69,16 @@ typedef struct {
 
 #define BEM_PRECOND_NONE 0
 #define BEM_PRECOND_JACOBI 1
+/* Block Jacobi on spatial clusters: the triangles sorted by the Morton code of their
+ * centroid (10 bits per axis over the centroids' bounding box, ties by index) form
+ * consecutive clusters of 64; M = the block diagonal of V over the clusters, each
+ * block inverted in FP64 (Cholesky).  DF64 operators, persistent solver. */
+#define BEM_PRECOND_BLOCK 2
 
 typedef struct {
     double tol;            /* relative residual ||b - V x|| / ||b|| to reach (e.g. 1e-10) */
     int32_t max_it;        /* iteration cap (inner iterations for FP32 operators) */
-    int32_t precond;       /* BEM_PRECOND_NONE or BEM_PRECOND_JACOBI (diag(V), Sec. 3) */
+    int32_t precond;       /* BEM_PRECOND_NONE, _JACOBI (diag(V), Sec. 3) or _BLOCK */
     int32_t max_outer;     /* FP32 operators: FP64 iterative-refinement sweeps (default 20) */
     double inner_tol;      /* FP32 operators: relative tolerance of each inner solve (default 1e-5) */
     double reliable_delta; /* DF64 operators, persistent solver: the iteration's products use the

@@ -25,7 +25,7 @@ __all__ = [
     "build", "lib", "gauss_legendre01", "radon7", "geometry", "pair_far", "pair_identical",
     "pair_edge", "pair_vertex", "pair_type", "entry", "entries", "assemble", "pcg",
     "solve_cholesky", "capacity", "zz", "dorfler", "canonical", "refine", "num_threads",
-    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA",
+    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_pcg",
 ]
 
 
@@ -258,6 +258,60 @@ def solve_capacity(verts, tris, n_ss=4, tol=1e-12, maxit=20000, precond=1, x0=No
     area, _ = geometry(verts, tris)
     x, its, rr, rc = pcg(V, area, x0=x0, tol=tol, maxit=maxit, precond=precond)
     return capacity(area, x), x, its, V
+
+
+def cluster_order(verts, tris, B=64):
+    """Triangle order of the block-Jacobi preconditioner (not part of the paper's
+    method, which preconditions differently; any SPD preconditioner leaves the
+    solution of Eq. 2.8 unchanged): Morton code of the centroid ((v0 + v1) + v2) / 3,
+    10 bits per axis over the centroids' bounding box (q = trunc((c - lo) * (1023 /
+    (hi - lo))), clamped to 0..1023; bit b of axis k at bit 3b + k), ascending, ties
+    by index.  Consecutive groups of B triangles form the clusters."""
+    v, t = _f64(verts), _i32(tris)
+    c = (v[t[:, 0]] + v[t[:, 1]] + v[t[:, 2]]) / 3.0
+    lo = c.min(axis=0)
+    ext = c.max(axis=0) - lo
+    code = np.zeros(t.shape[0], dtype=np.int64)
+    for k in range(3):
+        sc = 1023.0 / ext[k] if ext[k] > 0.0 else 0.0
+        q = np.clip((c[:, k] - lo[k]) * sc, 0.0, 1023.0).astype(np.int64)
+        for b in range(10):
+            code |= ((q >> b) & 1) << (3 * b + k)
+    return np.lexsort((np.arange(t.shape[0]), code))
+
+
+def block_jacobi_pcg(V, b, order, B=64, tol=1e-12, maxit=20000, x0=None):
+    """CG on V x = b preconditioned by the inverse of the block diagonal of V over
+    the clusters order[kB:(k+1)B] (numpy inverses, a library primitive); stops at
+    ||r|| <= tol ||b||.  Returns (x, iterations)."""
+    V, b = np.asarray(V, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    blocks = [order[k:k + B] for k in range(0, len(b), B)]
+    inv = [np.linalg.inv(V[np.ix_(ix, ix)]) for ix in blocks]
+
+    def apply(r):
+        z = np.empty_like(r)
+        for ix, Mi in zip(blocks, inv):
+            z[ix] = Mi @ r[ix]
+        return z
+
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - V @ x
+    z = apply(r)
+    p = z.copy()
+    rz = float(r @ z)
+    bn = float(np.linalg.norm(b))
+    for it in range(maxit + 1):
+        if np.linalg.norm(r) <= tol * bn or it == maxit:
+            return x, it
+        q = V @ p
+        alpha = rz / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        z = apply(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit
 
 
 def adaptive_run(verts, tris, theta=0.5, max_N=2000, n_ss=4, tol=1e-12, h_mode=0,

@@ -27,6 +27,7 @@ PREC_F32 = 1
 PREC_DF64 = 2
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
+PRECOND_BLOCK = 2
 REFINE_BISEC3 = 1
 
 EXPORTS = [

@@ -163,47 +163,51 @@ __global__ void k_bitonic_shared(unsigned long long *keys, int64_t n2, int64_t k
     for (int q = threadIdx.x; q < chunk; q += blockDim.x) keys[base + q] = sk[q];
 }
 
-// One warp: total = sum of eta2 in key order (FP64, sequential); the shortest
-// prefix whose running sum reaches theta * total, extended over equal keys.
-__global__ void k_dorfler_select(const unsigned long long *keys, const double *eta2, int64_t N, double theta,
-                                 long long *K_out)
+// One warp forms the running FP64 sums of eta2 in key order, sequentially (every
+// lane performs the same additions, in order; lane l keeps the sum after element
+// base + l): prefix[k] = (((v_0 + v_1) + v_2) + ... + v_k).  The values of the next
+// 32 keys are loaded while the current 32 are added.
+__global__ void k_dorfler_prefix(const unsigned long long *keys, const double *eta2, int64_t N, double *prefix)
 {
     const int lane = threadIdx.x;
-    double total = 0.0;
-    for (int64_t base = 0; base < N; base += 32) {
-        const int64_t k = base + lane;
-        const double v = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
-        const int cnt = (N - base) < 32 ? (int)(N - base) : 32;
-        for (int l = 0; l < 32; ++l) {
-            const double vl = __shfl_sync(0xffffffffu, v, l);
-            if (l < cnt) total = total + vl;
-        }
-    }
-    const double thr = theta * total;
     double acc = 0.0;
-    int64_t kk = 0;
-    bool done = false;
-    for (int64_t base = 0; base < N && !done; base += 32) {
-        const int64_t k = base + lane;
-        const double v = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
-        const int cnt = (N - base) < 32 ? (int)(N - base) : 32;
+    double v = lane < N ? eta2[keys[lane] & 0xFFFFFFFFull] : 0.0;
+    for (int64_t base = 0; base < N; base += 32) {
+        const int64_t kn = base + 32 + lane;
+        const double vn = kn < N ? eta2[keys[kn] & 0xFFFFFFFFull] : 0.0;
+        double mine = 0.0;
+#pragma unroll
         for (int l = 0; l < 32; ++l) {
-            const double vl = __shfl_sync(0xffffffffu, v, l);
-            if (!done && l < cnt) {
-                if (acc < thr) {
-                    acc = acc + vl;
-                    kk = base + l + 1;
-                } else {
-                    done = true;
-                }
-            }
+            acc = acc + __shfl_sync(0xffffffffu, v, l);  // past N: adds +0.0, acc >= 0 unchanged
+            if (l == lane) mine = acc;
         }
-        if (base + 32 >= N) done = true;
+        if (base + lane < N) prefix[base + lane] = mine;
+        v = vn;
     }
-    if (lane == 0) {
-        while (kk > 0 && kk < N && (keys[kk] >> 32) == (keys[kk - 1] >> 32)) ++kk;
-        *K_out = kk;
+}
+
+// The shortest prefix whose running sum reaches theta * total (total = prefix[N-1];
+// none if theta * total <= 0), by bisection over the non-decreasing prefix sums,
+// then extended over equal keys.
+__global__ void k_dorfler_select(const unsigned long long *keys, const double *prefix, int64_t N, double theta,
+                                 long long *K_out)
+{
+    const double thr = theta * prefix[N - 1];
+    int64_t kk = 0;
+    if (0.0 < thr) {
+        int64_t lo = 0, hi = N - 1;  // prefix[hi] >= thr
+        if (!(prefix[hi] >= thr)) lo = hi = N;
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if (prefix[mid] >= thr)
+                hi = mid;
+            else
+                lo = mid + 1;
+        }
+        kk = lo < N ? lo + 1 : N;
     }
+    while (kk > 0 && kk < N && (keys[kk] >> 32) == (keys[kk - 1] >> 32)) ++kk;
+    *K_out = kk;
 }
 
 __global__ void k_mark(const unsigned long long *keys, int64_t N, const long long *K, uint8_t *marked)
@@ -211,6 +215,19 @@ __global__ void k_mark(const unsigned long long *keys, int64_t N, const long lon
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= N) return;
     marked[keys[k] & 0xFFFFFFFFull] = (k < *K) ? 1 : 0;
+}
+
+void sort_u64(bem_ctx *ctx, unsigned long long *keys, int64_t n2)
+{
+    cudaStream_t s = ctx->stream;
+    const int64_t chunk = n2 < 2048 ? n2 : 2048;
+    const int sthreads = (int)(chunk / 2);
+    for (int64_t k = 2; k <= n2; k <<= 1) {
+        int64_t j = k >> 1;
+        for (; j >= chunk; j >>= 1)
+            { k_bitonic_global<<<nblk(n2 / 2, 256), 256, 0, s>>>(keys, n2, k, j); BEM_COUNT(ctx); }
+        k_bitonic_shared<<<(unsigned)(n2 / chunk), sthreads, chunk * sizeof(unsigned long long), s>>>(keys, n2, k, j); BEM_COUNT(ctx);
+    }
 }
 
 bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, uint8_t *d_marked,
@@ -227,19 +244,14 @@ bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, 
     if (n2 < 2) n2 = 2;
     Allocs tmp;
     unsigned long long *keys = nullptr;
-    bem_status st = dalloc(ctx, tmp, (void **)&keys, sizeof(unsigned long long) * n2 + 64, false);
+    bem_status st = dalloc(ctx, tmp, (void **)&keys, sizeof(unsigned long long) * n2 + sizeof(double) * N + 64, false);
     if (st) return st;
-    long long *dK = reinterpret_cast<long long *>(keys + n2);
+    double *prefix = reinterpret_cast<double *>(keys + n2);
+    long long *dK = reinterpret_cast<long long *>(prefix + N);
     k_keys<<<nblk(n2, 256), 256, 0, s>>>(d_eta2, N, n2, keys); BEM_COUNT(ctx);
-    const int64_t chunk = n2 < 2048 ? n2 : 2048;
-    const int sthreads = (int)(chunk / 2);
-    for (int64_t k = 2; k <= n2; k <<= 1) {
-        int64_t j = k >> 1;
-        for (; j >= chunk; j >>= 1)
-            k_bitonic_global<<<nblk(n2 / 2, 256), 256, 0, s>>>(keys, n2, k, j); BEM_COUNT(ctx);
-        k_bitonic_shared<<<(unsigned)(n2 / chunk), sthreads, chunk * sizeof(unsigned long long), s>>>(keys, n2, k, j); BEM_COUNT(ctx);
-    }
-    k_dorfler_select<<<1, 32, 0, s>>>(keys, d_eta2, N, theta, dK); BEM_COUNT(ctx);
+    sort_u64(ctx, keys, n2);
+    k_dorfler_prefix<<<1, 32, 0, s>>>(keys, d_eta2, N, prefix); BEM_COUNT(ctx);
+    k_dorfler_select<<<1, 1, 0, s>>>(keys, prefix, N, theta, dK); BEM_COUNT(ctx);
     k_mark<<<nblk(N, 256), 256, 0, s>>>(keys, N, dK, d_marked); BEM_COUNT(ctx);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = cuda_error(ctx, e, "doerfler kernels");
@@ -379,7 +391,9 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
     TRY(dalloc(ctx, tmp, (void **)&n_child, sizeof(int32_t) * (N + 1), false));
     TRY(dalloc(ctx, tmp, (void **)&child_pos, sizeof(int32_t) * (N + 1), false));
     k_nvb_seed<<<nblk(N, 256), 256, 0, s>>>(m->owner, d_marked, N, flags & BEM_REFINE_BISEC3, flag); BEM_COUNT(ctx);
-    for (int sweep = 0;; ++sweep) {
+    // closure sweeps, four per check of the changed flag (a sweep after the fixed
+    // point changes nothing)
+    for (int sweep = 0;; sweep += 4) {
         if (sweep > 100000) {
             st = set_error(ctx, BEM_ERR_MESH, "NVB closure did not terminate");
             goto fail;
@@ -388,7 +402,8 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
             st = set_error(ctx, BEM_ERR_CUDA, "closure flag reset");
             goto fail;
         }
-        k_nvb_close<<<nblk(N, 256), 256, 0, s>>>(m->owner, N, flag, changed); BEM_COUNT(ctx);
+        for (int k = 0; k < 4; ++k)
+            { k_nvb_close<<<nblk(N, 256), 256, 0, s>>>(m->owner, N, flag, changed); BEM_COUNT(ctx); }
         cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {

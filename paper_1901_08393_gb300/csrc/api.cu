@@ -643,7 +643,7 @@ bem_status bem_solve_capacity(bem_operator *op, const bem_solve_opts *opts, cons
     bem_ctx *ctx = op->mesh->ctx;
     CHECK_ARG(ctx, cap_out != nullptr, "null cap_out");
     const bem_solve_opts o = opts ? *opts : default_solve_opts();
-    CHECK_ARG(ctx, o.precond == BEM_PRECOND_NONE || o.precond == BEM_PRECOND_JACOBI, "unknown preconditioner");
+    CHECK_ARG(ctx, o.precond >= BEM_PRECOND_NONE && o.precond <= BEM_PRECOND_BLOCK, "unknown preconditioner");
     CHECK_ARG(ctx, !(o.tol < 0), "negative tolerance");
     const size_t vb = sizeof(double) * op->N;
     DevBuf dx0, dphi;

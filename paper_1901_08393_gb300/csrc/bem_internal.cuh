@@ -157,6 +157,8 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
 // ----------------------------------------------------------------- adaptivity (adapt.cu)
 bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_eta2,
                        double *h_totals);
+// Ascending sort of n2 (a power of two) 64-bit keys on the context's stream.
+void sort_u64(bem_ctx *ctx, unsigned long long *keys, int64_t n2);
 bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, uint8_t *d_marked,
                    int64_t *n_marked);
 bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out);

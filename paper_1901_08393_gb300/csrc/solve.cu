@@ -638,6 +638,183 @@ __global__ void k_residual(int64_t N, const double *b, const double *q, double *
     block_partial(v * v, prr);
 }
 
+// ------------------------------------------------------------------ block-Jacobi clusters
+// Spatial clusters of kBJ triangles: Morton order of the centroids (10 bits per axis
+// over the bounding box of the centroids, ties by index), cut into consecutive
+// groups; the preconditioner is the block diagonal of V over the clusters, each block
+// inverted in FP64 (Cholesky, inverse of the factor, Gram product: symmetric positive
+// definite by construction).
+constexpr int kBJ = 64;
+
+__global__ void k_cent_box(const double *cent, int64_t N, double *box)
+{
+    __shared__ double s[6][256];
+    double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+        for (int c = 0; c < 3; ++c) {
+            const double x = cent[4 * i + c];
+            v[c] = fmin(v[c], x);
+            v[3 + c] = fmax(v[3 + c], x);
+        }
+    for (int c = 0; c < 6; ++c) s[c][threadIdx.x] = v[c];
+    __syncthreads();
+    if (threadIdx.x < 6) {
+        const int c = threadIdx.x;
+        double r = s[c][0];
+        for (int k = 1; k < (int)blockDim.x; ++k) r = c < 3 ? fmin(r, s[c][k]) : fmax(r, s[c][k]);
+        box[c] = r;
+    }
+}
+
+__device__ __forceinline__ unsigned spread3(unsigned q)  // bit b of q -> bit 3b
+{
+    unsigned r = 0;
+    for (int b = 0; b < 10; ++b) r |= ((q >> b) & 1u) << (3 * b);
+    return r;
+}
+
+__global__ void k_morton_keys(const double *cent, int64_t N, int64_t n2, const double *box,
+                              unsigned long long *keys)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n2) return;
+    if (i >= N) {
+        keys[i] = ~0ull;
+        return;
+    }
+    unsigned code = 0;
+    for (int c = 0; c < 3; ++c) {
+        const double lo = box[c], ext = __dsub_rn(box[3 + c], lo);
+        const double sc = ext > 0.0 ? __ddiv_rn(1023.0, ext) : 0.0;
+        double t = __dmul_rn(__dsub_rn(cent[4 * i + c], lo), sc);
+        t = t < 0.0 ? 0.0 : (t > 1023.0 ? 1023.0 : t);
+        code |= spread3((unsigned)t) << c;
+    }
+    keys[i] = ((unsigned long long)code << 32) | (unsigned long long)(uint32_t)i;
+}
+
+__global__ void k_cluster_perm(const unsigned long long *keys, int64_t N, int64_t nperm, int32_t *perm)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nperm) perm[k] = k < N ? (int32_t)(keys[k] & 0xFFFFFFFFull) : -1;
+}
+
+__device__ __forceinline__ double elem_f64(const double *V, int64_t o) { return V[o]; }
+__device__ __forceinline__ double elem_f64(const float2 *V, int64_t o) { return (double)V[o].x + (double)V[o].y; }
+__device__ __forceinline__ double elem_f64(const float *V, int64_t o) { return (double)V[o]; }
+
+// One CTA per cluster block: A = V[perm, perm] (identity on padding), A = L L^T,
+// L^-1 column by column, M^-1 = L^-T L^-1 (upper triangle formed, mirrored).
+template <typename T>
+__global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, int64_t ld,
+                                                       const int32_t *__restrict__ perm, double *__restrict__ binv)
+{
+    extern __shared__ double smb[];
+    double(*A)[kBJ + 1] = reinterpret_cast<double(*)[kBJ + 1]>(smb);
+    double(*B)[kBJ + 1] = reinterpret_cast<double(*)[kBJ + 1]>(smb + kBJ * (kBJ + 1));
+    const int t = threadIdx.x;
+    const int32_t *pk = perm + (int64_t)blockIdx.x * kBJ;
+    for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
+        const int i = idx / kBJ, j = idx % kBJ;
+        const int32_t gi = pk[i], gj = pk[j];
+        A[i][j] = (gi >= 0 && gj >= 0) ? elem_f64(V, (int64_t)gi * ld + gj) : (i == j ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int k = 0; k < kBJ; ++k) {
+        if (t == 0) {
+            const double d = A[k][k];
+            A[k][k] = d > 0.0 ? sqrt(d) : 1.0;  // a principal block of the SPD V: d > 0
+        }
+        __syncthreads();
+        for (int i = k + 1 + t; i < kBJ; i += blockDim.x) A[i][k] /= A[k][k];
+        __syncthreads();
+        for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
+            const int i = idx / kBJ, j = idx % kBJ;
+            if (j > k && j <= i) A[i][j] -= A[i][k] * A[j][k];
+        }
+        __syncthreads();
+    }
+    if (t < kBJ) {  // column t of L^-1 (lower), forward substitution
+        const int c = t;
+        for (int i = 0; i < kBJ; ++i) {
+            double v = 0.0;
+            if (i >= c) {
+                v = i == c ? 1.0 : 0.0;
+                for (int k = c; k < i; ++k) v -= A[i][k] * B[k][c];
+                v /= A[i][i];
+            }
+            B[i][c] = v;
+        }
+    }
+    __syncthreads();
+    double *out = binv + (int64_t)blockIdx.x * kBJ * kBJ;
+    for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
+        const int i = idx / kBJ, j = idx % kBJ;
+        if (i > j) continue;
+        double v = 0.0;
+        for (int k = j; k < kBJ; ++k) v += B[k][i] * B[k][j];
+        out[i * kBJ + j] = v;
+        out[j * kBJ + i] = v;
+    }
+}
+
+// z = M^-1 r on the rows of cluster blk, by one CTA.  Thread t < 64 handles row t of
+// the cluster: with update, x += alpha p and r -= alpha q first; r is staged in rs
+// (64 doubles of shared memory).  Then 4 threads per row (t = 4 i + c) add 16
+// products each and combine them by shuffles ((c0 + c1) + (c2 + c3)).  init: also
+// p = z and pdf = z in double-float.  Adds the cluster's r.z and r.r to the thread's
+// partials.
+__device__ __forceinline__ void block_apply(const int32_t *__restrict__ perm, const double *__restrict__ binv, int blk,
+                                            double *x, double *r, double *z, double *p, const double *q,
+                                            float2 *pdf, double alpha, bool update, bool init, double *rs,
+                                            double &rz_l, double &rr_l)
+{
+    const int t = threadIdx.x;
+    const int32_t *pk = perm + (int64_t)blk * kBJ;
+    if (t < kBJ) {
+        const int32_t g = pk[t];
+        double v = 0.0;
+        if (g >= 0) {
+            if (update) {
+                x[g] += alpha * p[g];
+                v = r[g] - alpha * q[g];
+                r[g] = v;
+            } else {
+                v = r[g];
+            }
+        }
+        rs[t] = v;
+    }
+    __syncthreads();
+    const int i = t >> 2, c = t & 3;
+    const double2 *Mi = reinterpret_cast<const double2 *>(binv + (int64_t)blk * kBJ * kBJ + i * kBJ + 16 * c);
+    double2 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = Mi[u];
+    double sacc = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        sacc += m[u].x * rs[16 * c + 2 * u];
+        sacc += m[u].y * rs[16 * c + 2 * u + 1];
+    }
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 1);
+    sacc += __shfl_xor_sync(0xffffffffu, sacc, 2);
+    if (c == 0) {
+        const int32_t g = pk[i];
+        if (g >= 0) {
+            const double rv = rs[i];
+            z[g] = sacc;
+            if (init) {
+                p[g] = sacc;
+                pdf[g] = df_from_double(sacc);
+            }
+            rz_l += rv * sacc;
+            rr_l += rv * rv;
+        }
+    }
+    __syncthreads();  // rs is refilled for the next cluster
+}
+
 // ------------------------------------------------------------------ persistent DF64 solver
 // The whole Jacobi-PCG of a DF64 operator in one cooperative launch: every CTA
 // takes part in the tile loop of the symmetric product, then owns rows
@@ -659,8 +836,10 @@ struct PcgArgs {
     int *err;
     double *out;              // [0] r.r, [1] b.b, [2] iterations, [3] DF64 residuals
     float *vp;                // packed FP32 hi parts of the tiles (mixed mode), else null
+    const int32_t *bperm;     // block preconditioner: cluster order (nbj x kBJ, -1 padding)
+    const double *binv;       // block preconditioner: inverse blocks (nbj x kBJ x kBJ)
     double tol, delta2;
-    int max_it, precond, has_x0;
+    int max_it, precond, has_x0, nbj;
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
@@ -738,7 +917,9 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
     const int64_t i0 = (int64_t)cta * kSymThreads + threadIdx.x;
     double *pA = a.part, *pB = a.part + G, *pC = a.part + 2 * G;
     const bool mixed = a.vp != nullptr;
+    const bool blockpc = a.precond == BEM_PRECOND_BLOCK, jacobi = a.precond == BEM_PRECOND_JACOBI;
     float2 *const xsw = sm + (threadIdx.x >> 5) * 2 * kSB;
+    __shared__ double rs[kBJ];
     const int lane = threadIdx.x & 31, q4 = lane & 3;
     const int64_t warp_g = ((int64_t)cta * kSymThreads + threadIdx.x) >> 5, nwarps = stride >> 5;
     unsigned long long tbase = 0ull;
@@ -759,17 +940,24 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
     for (int64_t i = i0; i < a.ld; i += stride) {
         if (i < a.N) {
             const double ri = a.b[i] - (a.has_x0 ? symv_row(a.prow, a.pcol, a.nb, i) : 0.0);
-            const double zi = a.precond ? ri / a.d[i] : ri;
             a.r[i] = ri;
-            a.z[i] = zi;
-            a.p[i] = zi;
-            a.pdf[i] = df_from_double(zi);
-            rz_l += ri * zi;
-            rr_l += ri * ri;
             bb_l += a.b[i] * a.b[i];
+            if (!blockpc) {
+                const double zi = jacobi ? ri / a.d[i] : ri;
+                a.z[i] = zi;
+                a.p[i] = zi;
+                a.pdf[i] = df_from_double(zi);
+                rz_l += ri * zi;
+                rr_l += ri * ri;
+            }
         } else {
             a.pdf[i] = make_float2(0.f, 0.f);
         }
+    }
+    if (blockpc) {  // z = M^-1 r over whole clusters: every r written first
+        if (!grid_barrier(a.bar, a.err)) return;
+        for (int blk = cta; blk < a.nbj; blk += G)
+            block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, true, rs, rz_l, rr_l);
     }
     cta_partial(rz_l, pA);
     cta_partial(rr_l, pB);
@@ -809,14 +997,19 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
         const double alpha = rz / grid_total(pA);
         double rz_n = 0.0;
         rr_l = 0.0;
-        for (int64_t i = i0; i < a.N; i += stride) {
-            a.x[i] += alpha * a.p[i];
-            const double ri = a.r[i] - alpha * a.q[i];
-            const double zi = a.precond ? ri / a.d[i] : ri;
-            a.r[i] = ri;
-            a.z[i] = zi;
-            rz_n += ri * zi;
-            rr_l += ri * ri;
+        if (blockpc) {
+            for (int blk = cta; blk < a.nbj; blk += G)
+                block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, alpha, true, false, rs, rz_n, rr_l);
+        } else {
+            for (int64_t i = i0; i < a.N; i += stride) {
+                a.x[i] += alpha * a.p[i];
+                const double ri = a.r[i] - alpha * a.q[i];
+                const double zi = jacobi ? ri / a.d[i] : ri;
+                a.r[i] = ri;
+                a.z[i] = zi;
+                rz_n += ri * zi;
+                rr_l += ri * ri;
+            }
         }
         cta_partial(rz_n, pB);
         cta_partial(rr_l, pC);
@@ -836,12 +1029,20 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
                 const double vi = symv_row4(a.prow, a.pcol, a.nb, valid ? i : a.N - 1, q4);
                 if (valid && q4 == 0) {
                     const double ri = a.b[i] - vi;
-                    const double zi = a.precond ? ri / a.d[i] : ri;
                     a.r[i] = ri;
-                    a.z[i] = zi;
-                    rz_n += ri * zi;
-                    rr_l += ri * ri;
+                    if (!blockpc) {
+                        const double zi = jacobi ? ri / a.d[i] : ri;
+                        a.z[i] = zi;
+                        rz_n += ri * zi;
+                        rr_l += ri * ri;
+                    }
                 }
+            }
+            if (blockpc) {
+                if (!grid_barrier(a.bar, a.err)) return;
+                for (int blk = cta; blk < a.nbj; blk += G)
+                    block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, false, rs, rz_n,
+                                rr_l);
             }
             cta_partial(rz_n, pB);
             cta_partial(rr_l, pC);
@@ -1012,13 +1213,53 @@ static bem_status pcg(bem_operator *op, Work &W, const double *rhs, double tol, 
 // The persistent DF64 solver (k_pcg_df).  Returns BEM_OK with *ran = false when a
 // cooperative launch of the needed size is not possible (the caller then runs the
 // host-driven loop).
+// Cluster order and inverse blocks of the block-Jacobi preconditioner (scratch in tmp).
+static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out, double **binv_out, int *nbj_out)
+{
+    bem_ctx *ctx = op->mesh->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = op->N;
+    const int nbj = (int)((N + kBJ - 1) / kBJ);
+    int64_t n2 = 2;
+    while (n2 < N) n2 <<= 1;
+    unsigned long long *keys = nullptr;
+    double *binv = nullptr;
+    const size_t kb = sizeof(unsigned long long) * n2, pb = sizeof(int32_t) * nbj * kBJ;
+    bem_status st = dalloc(ctx, tmp, (void **)&keys, kb + pb + 6 * sizeof(double) + 64, false);
+    if (!st) st = dalloc(ctx, tmp, (void **)&binv, sizeof(double) * kBJ * kBJ * nbj, false);
+    if (st) return st;
+    int32_t *perm = reinterpret_cast<int32_t *>(keys + n2);
+    double *box = reinterpret_cast<double *>(reinterpret_cast<char *>(perm) + (pb + 7) / 8 * 8);
+    k_cent_box<<<1, 256, 0, s>>>(op->mesh->cent, N, box); BEM_COUNT(ctx);
+    k_morton_keys<<<nblk(n2, 256), 256, 0, s>>>(op->mesh->cent, N, n2, box, keys); BEM_COUNT(ctx);
+    sort_u64(ctx, keys, n2);
+    k_cluster_perm<<<nblk((int64_t)nbj * kBJ, 256), 256, 0, s>>>(keys, N, (int64_t)nbj * kBJ, perm); BEM_COUNT(ctx);
+    const int smem = 2 * kBJ * (kBJ + 1) * (int)sizeof(double);
+    if (op->precision == BEM_PREC_DF64) {
+        BEM_CK(ctx, cudaFuncSetAttribute(k_block_inverse<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_block_inverse<float2><<<nbj, 256, smem, s>>>((const float2 *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
+    } else if (op->precision == BEM_PREC_F64) {
+        BEM_CK(ctx, cudaFuncSetAttribute(k_block_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_block_inverse<double><<<nbj, 256, smem, s>>>((const double *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
+    } else {
+        BEM_CK(ctx, cudaFuncSetAttribute(k_block_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        k_block_inverse<float><<<nbj, 256, smem, s>>>((const float *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
+    }
+    BEM_CK_LAUNCH(ctx);
+    *perm_out = perm;
+    *binv_out = binv;
+    *nbj_out = nbj;
+    return BEM_OK;
+}
+
 // delta > 0 selects the mixed mode: the products of the iteration use the packed
 // FP32 hi parts of the upper triangle, and the residual is recomputed with the DF64
 // product whenever ||r|| has dropped by delta since the last such residual (and at
 // convergence).  Without room for the packed copy in the context's budget the
 // solve runs with DF64 products only.
 static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, bool has_x0, double tol, int max_it,
-                                 int precond, double delta, int *its_out, int *ndf_out, double *rel_out, bool *ran)
+                                 int precond, double delta, const int32_t *bperm, const double *binv, int nbj,
+                                 int *its_out, int *ndf_out, double *rel_out, bool *ran)
 {
     bem_ctx *ctx = op->mesh->ctx;
     *ran = false;
@@ -1075,6 +1316,9 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.err = err;
     a.out = out;
     a.vp = vp;
+    a.bperm = bperm;
+    a.binv = binv;
+    a.nbj = nbj;
     a.tol = tol;
     a.delta2 = delta * delta;
     a.max_it = max_it;
@@ -1134,6 +1378,10 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     bem_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
     const int64_t N = op->N, L = op->ld;
+    if (o->precond < BEM_PRECOND_NONE || o->precond > BEM_PRECOND_BLOCK)
+        return set_error(ctx, BEM_ERR_INVALID, "unknown preconditioner %d", o->precond);
+    if (o->precond == BEM_PRECOND_BLOCK && (op->precision != BEM_PREC_DF64 || !ctx->persistent_solver))
+        return set_error(ctx, BEM_ERR_INVALID, "BEM_PRECOND_BLOCK is implemented by the persistent DF64 solver");
     Allocs tmp;
     Work W{};
     W.nb_vec = (int)nblk(N, kVecThreads);
@@ -1185,9 +1433,15 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         // DF64: FP32 products of the packed hi parts between DF64 residuals whenever
         // ||r|| drops by reliable_delta (default 1e-2; < 0: DF64 products only)
         const double delta = o->reliable_delta == 0.0 ? 1e-2 : (o->reliable_delta > 0.0 ? o->reliable_delta : 0.0);
+        int32_t *bperm = nullptr;
+        double *binv = nullptr;
+        int nbj = 0;
+        if (precond == BEM_PRECOND_BLOCK && (st = block_setup(op, tmp, &bperm, &binv, &nbj))) goto out;
         if (op->precision == BEM_PREC_DF64 && ctx->persistent_solver)
-            st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, &its,
-                                &outer, &rel, &ran);
+            st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, bperm,
+                                binv, nbj, &its, &outer, &rel, &ran);
+        if (!st && !ran && precond == BEM_PRECOND_BLOCK)
+            st = set_error(ctx, BEM_ERR_CUDA, "BEM_PRECOND_BLOCK: the persistent solver could not be launched");
         if (!st && !ran) {
             st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
             outer = 1;

@@ -1,6 +1,7 @@
 """Parity at the full size of the benchmark workload, in the configuration bench.py
 times: adaptive polycube (6^3, p=0.5, seed 1), ZZ + Doerfler theta=0.5 + NVB until
-N >= 20,000, DF64 operator, Jacobi-PCG to 1e-10.
+N >= 20,000, DF64 operator, PCG to 1e-10 with the block-Jacobi preconditioner (the
+oracle runs Jacobi PCG: the solutions agree to the solver tolerance).
 
 * the level sizes of the GPU run equal the oracle's own adaptive run, and every
   Cap_l agrees to 1e-8 (the bench's 1e-6 requirement, with margin);
@@ -31,7 +32,7 @@ def run():
     m = inputs.workload_polycube_adaptive()
     mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
     recs, fin = bem.adaptive_run(mesh, theta=THETA, max_N=MAX_N, tol=TOL, precision=bem.PREC_DF64,
-                                 want_final=True)
+                                 precond=bem.PRECOND_BLOCK, want_final=True)
     hist = O.adaptive_run(m.verts, m.tris, theta=THETA, max_N=MAX_N, tol=1e-12)
     return ctx, recs, fin, hist
 
@@ -64,7 +65,7 @@ def test_final_mesh_entries_and_cap(run):
     got = op.entries(I, J)
     ref = O.entries(v, t, I, J)
     assert np.max(np.abs(got / ref - 1)) < 1e-10
-    cap, phi, info = bem.solve_capacity(op, tol=TOL)
+    cap, phi, info = bem.solve_capacity(op, tol=TOL, precond=bem.PRECOND_BLOCK)
     assert info["converged"]
     cap_ref = hist[-1]["cap"]  # the oracle's FP64 PCG (1e-12) on this mesh
     assert abs(cap / cap_ref - 1) < 1e-8
@@ -75,7 +76,7 @@ def test_full_size_decisions_bitexact(run):
     ctx, recs, fin, hist = run
     v, t, _, _ = fin.download()
     op = bem.Operator.assemble(fin, precision=bem.PREC_DF64)
-    _, phi, _ = bem.solve_capacity(op, tol=TOL)
+    _, phi, _ = bem.solve_capacity(op, tol=TOL, precond=bem.PRECOND_BLOCK)
     eta2, tot, scale = bem.zz_estimate(fin, phi)
     assert np.array_equal(eta2, O.zz(v, t, phi))
     marked, nm = bem.dorfler(ctx, eta2, THETA)

@@ -332,3 +332,33 @@ def test_mixed_solver_falls_back_without_room(ctx):
     c_df, _, i_df = bem.solve_capacity(op2, tol=1e-11)
     assert i_df["outer"] == 1 and i_df["converged"]
     assert abs(c_df / c_mixed - 1) < 1e-10
+
+
+@pytest.mark.parametrize("delta", [-1.0, 0.0], ids=["df64", "mixed"])
+@pytest.mark.parametrize("m", [inputs.cube_mesh(4), inputs.workload_polycube_adaptive()], ids=lambda m: m.name)
+def test_block_preconditioner(ctx, m, delta):
+    """Block Jacobi on Morton clusters of 64: the same solution as the oracle's
+    Jacobi PCG, and the iteration count of the oracle's block-Jacobi PCG."""
+    mesh, v, t = _upload(ctx, m)
+    op = bem.Operator.assemble(mesh, precision=bem.PREC_DF64)
+    tol = 1e-11
+    cap, phi, info = bem.solve_capacity(op, tol=tol, precond=bem.PRECOND_BLOCK, reliable_delta=delta)
+    cap_r, x_r, its_j, V = O.solve_capacity(v, t, tol=tol)
+    b = O.geometry(v, t)[0]
+    _, its_b = O.block_jacobi_pcg(V, b, O.cluster_order(v, t), tol=tol)
+    assert info["converged"] and info["relres"] <= tol, info
+    assert abs(cap / cap_r - 1) < 1e-10, (cap, cap_r)
+    assert np.linalg.norm(V @ phi - b) / np.linalg.norm(b) < 10 * tol
+    if delta < 0:
+        assert abs(info["iterations"] - its_b) <= 2 + its_b // 10, (info, its_b)
+    else:
+        assert info["iterations"] <= its_b + 3 * info["outer"] + its_b // 10, (info, its_b)
+
+
+def test_block_preconditioner_needs_df64(ctx):
+    mesh, v, t = _upload(ctx, inputs.cube_mesh(2))
+    for prec in (bem.PREC_F32, bem.PREC_F64):
+        op = bem.Operator.assemble(mesh, precision=prec)
+        with pytest.raises(bem.BemError) as e:
+            bem.solve_capacity(op, precond=bem.PRECOND_BLOCK)
+        assert e.value.code == bem.BEM_ERR_INVALID and "BLOCK" in str(e.value)

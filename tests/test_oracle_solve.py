@@ -101,3 +101,48 @@ def test_capacity_positive_and_rhs():
     assert cap > 0 and np.all(x > 0)  # equilibrium charge density is positive
     area, _ = O.geometry(m.verts, O.canonical(m.verts, m.tris))
     assert abs(O.capacity(area, x) - cap) == 0.0
+
+
+def test_cluster_order_morton_and_ties():
+    """Morton order of the centroids over their bounding box, ties by index."""
+    cents = [(1.0, 1.0, 1.0), (0.0, 0.5, 0.0), (0.5, 0.0, 0.0), (0.0, 0.0, 0.0), (0.5, 0.0, 0.0)]
+    d = 0.25
+    verts, tris = [], []
+    for c in cents:  # triangle (c + d e1, c + d e2, c - d e1 - d e2): centroid exactly c
+        c = np.array(c)
+        k = len(verts)
+        verts += [c + [d, 0, 0], c + [0, d, 0], c - [d, d, 0]]
+        tris.append([k, k + 1, k + 2])
+    order = O.cluster_order(np.array(verts), np.array(tris, dtype=np.int32))
+    # codes: (0,0,0) -> 0; (0.5,0,0) -> x = 511 (bits 0..8 at 3b); (0,0.5,0) -> y = 511
+    # (bits at 3b + 1, larger); (1,1,1) -> all 30 bits
+    assert list(order) == [3, 2, 4, 1, 0]
+
+
+def test_block_jacobi_pcg_special_cases():
+    """One block = V^-1 exactly: one iteration to the Cholesky solution; blocks of one
+    = Jacobi: the same iterates as the oracle's Jacobi PCG."""
+    m = inputs.cube_mesh(2)
+    t = O.canonical(m.verts, m.tris)
+    V = O.assemble(m.verts, t)
+    b = O.geometry(m.verts, t)[0]
+    order = O.cluster_order(m.verts, t)
+    x1, its1 = O.block_jacobi_pcg(V, b, order, B=len(b), tol=1e-13)
+    assert its1 == 1
+    xc = O.solve_cholesky(V, b)
+    assert np.max(np.abs(x1 - xc)) < 1e-12 * np.max(np.abs(xc))
+    xj, itsj = O.block_jacobi_pcg(V, b, np.arange(len(b)), B=1, tol=1e-12)
+    xo, itso, _, _ = O.pcg(V, b, tol=1e-12, precond=1)
+    assert abs(itsj - itso) <= 1 and np.max(np.abs(xj - xo)) < 1e-10 * np.max(np.abs(xo))
+
+
+def test_block_jacobi_fewer_iterations_on_adaptive_mesh():
+    """Spatial clusters of 64 beat the diagonal on an adaptively refined polycube."""
+    hist = O.adaptive_run(*[getattr(inputs.workload_polycube_adaptive(), k) for k in ("verts", "tris")],
+                          theta=0.5, max_N=1000, tol=1e-10)
+    v, t = hist[-1]["verts"], hist[-1]["tris"]
+    V = O.assemble(v, t)
+    b = O.geometry(v, t)[0]
+    _, its_b = O.block_jacobi_pcg(V, b, O.cluster_order(v, t), tol=1e-10)
+    _, its_j, _, _ = O.pcg(V, b, tol=1e-10, precond=1)
+    assert its_b < its_j
