@@ -86,7 +86,7 @@ typedef struct {
                               while the solve runs), and r is replaced by b - V x formed with the
                               DF64 product whenever ||r|| has dropped by this factor since the
                               last such residual and before convergence is declared, so tol
-                              holds for the DF64 operator.  0: default 1e-2; < 0 or >= 1: DF64
+                              holds for the DF64 operator.  0: default 1e-4; < 0 or >= 1: DF64
                               products only */
 } bem_solve_opts;
 

@@ -1431,8 +1431,8 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         bool ran = false;
         outer = 1;
         // DF64: FP32 products of the packed hi parts between DF64 residuals whenever
-        // ||r|| drops by reliable_delta (default 1e-2; < 0: DF64 products only)
-        const double delta = o->reliable_delta == 0.0 ? 1e-2 : (o->reliable_delta > 0.0 ? o->reliable_delta : 0.0);
+        // ||r|| drops by reliable_delta (default 1e-4; < 0: DF64 products only)
+        const double delta = o->reliable_delta == 0.0 ? 1e-4 : (o->reliable_delta > 0.0 ? o->reliable_delta : 0.0);
         int32_t *bperm = nullptr;
         double *binv = nullptr;
         int nbj = 0;
