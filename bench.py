@@ -285,7 +285,7 @@ def main():
     ap.add_argument("--batch", type=int, default=64, help="batch: meshes per step")
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
     ap.add_argument("--precond", default="block", choices=["block", "jacobi"],
-                    help="PCG preconditioner of the adaptive workload (block: DF64 only)")
+                    help="PCG preconditioner (block: DF64 and FP32 operators; FP64 runs Jacobi)")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
@@ -312,7 +312,7 @@ def main():
         PREC = 1
         args.precision = "f32"
     global PC
-    pc_name = args.precond if PREC == 2 else "jacobi"  # the block preconditioner runs in the DF64 solver
+    pc_name = args.precond if PREC != 0 else "jacobi"  # the block preconditioner: persistent DF64/FP32 solver
     PC = bem.PRECOND_BLOCK if pc_name == "block" else bem.PRECOND_JACOBI
     m = inputs.workload_graded_cube_60k() if graded else inputs.workload_polycube_adaptive()
     mesh = bem.Mesh.upload(ctx, m.verts, m.tris)  # resident input for the device-timed value
@@ -324,7 +324,7 @@ def main():
         ev[0].record(stream)
         op = bem.Operator.assemble(msh, precision=bem.PREC_F32)
         ev[1].record(stream)
-        cap, _, info = bem.solve_capacity(op, tol=TOL, max_it=5000)
+        cap, _, info = bem.solve_capacity(op, tol=TOL, max_it=5000, precond=PC)
         ev[2].record(stream)
         op.close()
         torch.cuda.synchronize()

@@ -815,6 +815,23 @@ __device__ __forceinline__ void block_apply(const int32_t *__restrict__ perm, co
     __syncthreads();  // rs is refilled for the next cluster
 }
 
+// Packed upper triangle of an FP32 operator: tile k of the list, row-major 64 x 64 at
+// vp + 4096 k (rows past N zero; columns past N are the operator's zero padding).
+__global__ void k_pack_f32(const float *__restrict__ V, int64_t ld, int64_t N, const int2 *__restrict__ tiles,
+                           int64_t ntiles, float *__restrict__ vp)
+{
+    const int64_t n4 = ntiles * (kTileF / 4);
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n4; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = f / (kTileF / 4);
+        const int e = (int)(f % (kTileF / 4)), r = e >> 4, c4 = e & 15;
+        const int2 tj = tiles[k];
+        const int64_t row = (int64_t)tj.x * kSB + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < N) v = __ldcs(reinterpret_cast<const float4 *>(V + row * ld + (int64_t)tj.y * kSB) + c4);
+        reinterpret_cast<float4 *>(vp)[f] = v;
+    }
+}
+
 // ------------------------------------------------------------------ persistent DF64 solver
 // The whole Jacobi-PCG of a DF64 operator in one cooperative launch: every CTA
 // takes part in the tile loop of the symmetric product, then owns rows
@@ -840,6 +857,7 @@ struct PcgArgs {
     const double *binv;       // block preconditioner: inverse blocks (nbj x kBJ x kBJ)
     double tol, delta2;
     int max_it, precond, has_x0, nbj;
+    int f32op;                // FP32 operator: every product (residuals too) from vp
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
@@ -928,9 +946,14 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
     auto df64_product = [&](bool pack) -> bool {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.x[i]) : make_float2(0.f, 0.f);
         if (!grid_barrier(a.bar, a.err)) return false;
-        symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase,
-                   pack ? a.vp : nullptr);
-        tbase += (unsigned long long)(a.ntiles + G);
+        if (a.f32op) {  // the stored operator is the packed copy itself
+            symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
+            tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+        } else {
+            symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase,
+                       pack ? a.vp : nullptr);
+            tbase += (unsigned long long)(a.ntiles + G);
+        }
         return grid_barrier(a.bar, a.err);
     };
     // r = b - V x0 (or b), z = M^-1 r, p = z
@@ -1128,7 +1151,7 @@ static bem_status launch_mv(bem_operator *op, bool acc64, const double *x, doubl
 // columns, then the tile list.
 static size_t symv_scratch_bytes(const bem_operator *op)
 {
-    if (op->precision != BEM_PREC_DF64) return 0;
+    if (op->precision == BEM_PREC_F64) return 0;
     const size_t nb = (size_t)(op->ld / kSB), nt = nb * (nb + 1) / 2;
     return 2 * nt * kSB * sizeof(float2) + nt * sizeof(int2);
 }
@@ -1261,11 +1284,16 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
                                  int precond, double delta, const int32_t *bperm, const double *binv, int nbj,
                                  int *its_out, int *ndf_out, double *rel_out, bool *ran)
 {
+    // FP32 operators: the products of the iteration and of the residuals read the
+    // packed copy of the stored operator (the residual, formed from x with
+    // FP64-accurate sums, confirms convergence)
+    const bool f32op = op->precision == BEM_PREC_F32;
     bem_ctx *ctx = op->mesh->ctx;
     *ran = false;
     int coop = 0, per_sm = 0;
     BEM_CK(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
     if (!coop || !W.tiles) return BEM_OK;
+    if (f32op) delta = 1.0;  // a packed copy is needed; residuals are replaced only at convergence
     BEM_CK(ctx, cudaFuncSetAttribute(k_pcg_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
     BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_df, kSymThreads, kSymSmem));
     if (per_sm < 1) return BEM_OK;
@@ -1277,6 +1305,11 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
         const size_t vbytes = (size_t)nt_ * kTileF * sizeof(float);
         if (ctx->budget <= 0 || ctx->in_use + (int64_t)vbytes + (64 << 10) <= ctx->budget)
             if ((st = dalloc(ctx, tmp, (void **)&vp, vbytes, false))) return st;
+    }
+    if (f32op && !vp) return BEM_OK;  // no room for the packed copy: host-driven refinement
+    if (f32op) {
+        k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt_ * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256, 0,
+                     ctx->stream>>>((const float *)op->V, op->ld, op->N, W.tiles, nt_, vp); BEM_COUNT(ctx);
     }
     // Up to 3 CTAs per SM.  On small levels, CTAs that would only wait at the grid
     // barriers are left out: DF64 products take one tile per CTA, the mixed mode's
@@ -1320,7 +1353,8 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.binv = binv;
     a.nbj = nbj;
     a.tol = tol;
-    a.delta2 = delta * delta;
+    a.f32op = f32op ? 1 : 0;
+    a.delta2 = f32op ? 0.0 : delta * delta;
     a.max_it = max_it;
     a.precond = precond;
     a.has_x0 = has_x0 ? 1 : 0;
@@ -1354,7 +1388,9 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
             // (8 bytes x N^2 / 2); a mixed-mode iteration reads the packed FP32 upper
             // triangle (4 x N^2 / 2), written once by the first product
             const double n2 = (double)op->N * (double)op->N;
-            const double bytes = vp ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0) : 4.0 * n2 * (h[2] + h[3]);
+            const double bytes = f32op ? 2.0 * n2 * (h[2] + h[3])
+                                 : vp  ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
+                                       : 4.0 * n2 * (h[2] + h[3]);
             prof_set_units(ctx, prof, bytes);
         }
     }
@@ -1380,8 +1416,9 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     const int64_t N = op->N, L = op->ld;
     if (o->precond < BEM_PRECOND_NONE || o->precond > BEM_PRECOND_BLOCK)
         return set_error(ctx, BEM_ERR_INVALID, "unknown preconditioner %d", o->precond);
-    if (o->precond == BEM_PRECOND_BLOCK && (op->precision != BEM_PREC_DF64 || !ctx->persistent_solver))
-        return set_error(ctx, BEM_ERR_INVALID, "BEM_PRECOND_BLOCK is implemented by the persistent DF64 solver");
+    if (o->precond == BEM_PRECOND_BLOCK && (op->precision == BEM_PREC_F64 || !ctx->persistent_solver))
+        return set_error(ctx, BEM_ERR_INVALID,
+                         "BEM_PRECOND_BLOCK is implemented by the persistent solver (DF64 and FP32 operators)");
     Allocs tmp;
     Work W{};
     W.nb_vec = (int)nblk(N, kVecThreads);
@@ -1420,6 +1457,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     const int precond = o->precond;
     int its = 0, outer = 0;
     double rel = 0.0;
+    bool ran = false;
     cudaError_t e = cudaMemcpyAsync(W.b, m->area, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(W.d, op->diag, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && d_x0) e = cudaMemcpyAsync(W.x, d_x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
@@ -1427,25 +1465,28 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         st = cuda_error(ctx, e, "solve setup");
         goto out;
     }
-    if (op->precision != BEM_PREC_F32) {
-        bool ran = false;
-        outer = 1;
-        // DF64: FP32 products of the packed hi parts between DF64 residuals whenever
-        // ||r|| drops by reliable_delta (default 1e-4; < 0: DF64 products only)
+    outer = 1;
+    {
+        // persistent solver (DF64 and FP32 operators).  DF64: FP32 products of the
+        // packed hi parts between DF64 residuals whenever ||r|| drops by
+        // reliable_delta (default 1e-4; < 0: DF64 products only).  FP32: products of
+        // the packed operator, residual confirmed at convergence.
         const double delta = o->reliable_delta == 0.0 ? 1e-4 : (o->reliable_delta > 0.0 ? o->reliable_delta : 0.0);
         int32_t *bperm = nullptr;
         double *binv = nullptr;
         int nbj = 0;
         if (precond == BEM_PRECOND_BLOCK && (st = block_setup(op, tmp, &bperm, &binv, &nbj))) goto out;
-        if (op->precision == BEM_PREC_DF64 && ctx->persistent_solver)
+        if (op->precision != BEM_PREC_F64 && ctx->persistent_solver)
             st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, bperm,
                                 binv, nbj, &its, &outer, &rel, &ran);
         if (!st && !ran && precond == BEM_PRECOND_BLOCK)
             st = set_error(ctx, BEM_ERR_CUDA, "BEM_PRECOND_BLOCK: the persistent solver could not be launched");
-        if (!st && !ran) {
-            st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
-            outer = 1;
-        }
+        if (st) goto out;
+    }
+    if (ran) {
+    } else if (op->precision != BEM_PREC_F32) {
+        st = pcg(op, W, W.b, tol, max_it, precond, true, &its, &rel);
+        outer = 1;
     } else {
         // FP64 iterative refinement around FP32-product inner CG
         const int max_outer = o->max_outer > 0 ? o->max_outer : 20;

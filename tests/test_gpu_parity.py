@@ -355,10 +355,31 @@ def test_block_preconditioner(ctx, m, delta):
         assert info["iterations"] <= its_b + 3 * info["outer"] + its_b // 10, (info, its_b)
 
 
-def test_block_preconditioner_needs_df64(ctx):
+def test_block_preconditioner_not_for_f64(ctx):
     mesh, v, t = _upload(ctx, inputs.cube_mesh(2))
-    for prec in (bem.PREC_F32, bem.PREC_F64):
-        op = bem.Operator.assemble(mesh, precision=prec)
-        with pytest.raises(bem.BemError) as e:
-            bem.solve_capacity(op, precond=bem.PRECOND_BLOCK)
-        assert e.value.code == bem.BEM_ERR_INVALID and "BLOCK" in str(e.value)
+    op = bem.Operator.assemble(mesh, precision=bem.PREC_F64)
+    with pytest.raises(bem.BemError) as e:
+        bem.solve_capacity(op, precond=bem.PRECOND_BLOCK)
+    assert e.value.code == bem.BEM_ERR_INVALID and "BLOCK" in str(e.value)
+
+
+def test_f32_operator_persistent_matches_refinement(ctx):
+    """FP32 operator: the persistent solver (products of the packed operator with
+    double-float sums, residual from x at convergence) and the host-driven FP64
+    refinement solve the same system; the block preconditioner too."""
+    m = inputs.workload_polycube_adaptive()
+    mesh, v, t = _upload(ctx, m)
+    op = bem.Operator.assemble(mesh, precision=bem.PREC_F32)
+    res = []
+    for persistent in (True, False):
+        ctx.set_persistent(persistent)
+        res.append(bem.solve_capacity(op, tol=1e-11))
+    ctx.set_persistent(True)
+    (c1, p1, i1), (c2, p2, i2) = res
+    assert i1["converged"] and i2["converged"] and i1["outer"] >= 2, (i1, i2)
+    assert abs(c1 / c2 - 1) < 1e-9 and np.max(np.abs(p1 - p2)) < 1e-8 * np.max(np.abs(p2))
+    cb, pb, ib = bem.solve_capacity(op, tol=1e-11, precond=bem.PRECOND_BLOCK)
+    assert ib["converged"] and ib["iterations"] < i1["iterations"], (ib, i1)
+    assert abs(cb / c1 - 1) < 1e-9
+    cap_r = O.solve_capacity(v, t, tol=1e-12)[0]
+    assert abs(c1 / cap_r - 1) < 1e-6  # FP32 storage of V
