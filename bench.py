@@ -201,7 +201,8 @@ def server_workload(args):
         label = (f"batch: {args.batch} uniform polycube meshes (g 3..10, p 0.3..0.7, log-uniform 500..30,000 "
                  f"triangles), one assembly + solve each, FP32 V + FP64 refinement to 1e-10, {args.slots} slots, "
                  f"HBM budget {budget >> 30} GiB")
-    srv = bem.Server(slots=args.slots, hbm_budget_bytes=budget, precision=bem.PREC_F32, tol=TOL)
+    pc = bem.PRECOND_BLOCK if args.precond == "block" else bem.PRECOND_JACOBI
+    srv = bem.Server(slots=args.slots, hbm_budget_bytes=budget, precision=bem.PREC_F32, tol=TOL, precond=pc)
 
     def run_stream(realtime):
         ids = []
@@ -253,7 +254,7 @@ def server_workload(args):
         "data": "synthetic",
         "config": {"workload": label, "requests_per_step": len(jobs), "slots": args.slots,
                    "peak_in_flight": stats["peak_in_flight"], "peak_bytes": stats["peak_bytes"],
-                   "failed": fails, "level_solves": levels},
+                   "failed": fails, "level_solves": levels, "preconditioner": PC_LABEL[args.precond]},
         "p50_latency_ms": _pct(lat, 0.5), "p99_latency_ms": _pct(lat, 0.99),
         "saturation_requests_per_s": sat, "clocks": clk, "roofline": None, "cpu_baseline": None,
         "e2e": {"value": value, "unit": "capacity requests/s",
@@ -284,13 +285,16 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per step")
     ap.add_argument("--batch", type=int, default=64, help="batch: meshes per step")
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
-    ap.add_argument("--precond", default="block", choices=["block", "jacobi"],
-                    help="PCG preconditioner (block: DF64 and FP32 operators; FP64 runs Jacobi)")
+    ap.add_argument("--precond", default="auto", choices=["auto", "block", "jacobi"],
+                    help="PCG preconditioner (block: DF64 and FP32 operators, FP64 runs Jacobi); auto: "
+                         "block, except jacobi on the graded cube (its V has indefinite diagonal blocks)")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.precond == "auto":
+        args.precond = "jacobi" if args.workload == "graded60k" else "block"
     if args.workload in ("serve", "batch"):
         return server_workload(args)
 

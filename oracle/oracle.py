@@ -25,7 +25,7 @@ __all__ = [
     "build", "lib", "gauss_legendre01", "radon7", "geometry", "pair_far", "pair_identical",
     "pair_edge", "pair_vertex", "pair_type", "entry", "entries", "assemble", "pcg",
     "solve_cholesky", "capacity", "zz", "dorfler", "canonical", "refine", "num_threads",
-    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_pcg",
+    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_inverses", "block_jacobi_pcg",
 ]
 
 
@@ -280,13 +280,28 @@ def cluster_order(verts, tris, B=64):
     return np.lexsort((np.arange(t.shape[0]), code))
 
 
+def block_jacobi_inverses(V, order, B=64):
+    """Clusters order[kB:(k+1)B] and the inverse of V on each (numpy Cholesky and
+    inverse, library primitives); a block that is not positive definite is replaced
+    by its diagonal, so that the preconditioner stays symmetric positive definite."""
+    blocks = [order[k:k + B] for k in range(0, len(order), B)]
+    inv = []
+    for ix in blocks:
+        A = V[np.ix_(ix, ix)]
+        try:
+            np.linalg.cholesky(A)
+            inv.append(np.linalg.inv(A))
+        except np.linalg.LinAlgError:
+            inv.append(np.diag(1.0 / np.diag(A)))
+    return blocks, inv
+
+
 def block_jacobi_pcg(V, b, order, B=64, tol=1e-12, maxit=20000, x0=None):
-    """CG on V x = b preconditioned by the inverse of the block diagonal of V over
-    the clusters order[kB:(k+1)B] (numpy inverses, a library primitive); stops at
-    ||r|| <= tol ||b||.  Returns (x, iterations)."""
+    """CG on V x = b preconditioned by block_jacobi_inverses (the discrete V is not
+    positive definite everywhere on strongly graded meshes: such blocks fall back to
+    their diagonal).  Stops at ||r|| <= tol ||b||.  Returns (x, iterations)."""
     V, b = np.asarray(V, dtype=np.float64), np.asarray(b, dtype=np.float64)
-    blocks = [order[k:k + B] for k in range(0, len(b), B)]
-    inv = [np.linalg.inv(V[np.ix_(ix, ix)]) for ix in blocks]
+    blocks, inv = block_jacobi_inverses(V, order, B)
 
     def apply(r):
         z = np.empty_like(r)

@@ -419,10 +419,10 @@ class Server:
 
     def __init__(self, slots=4, hbm_budget_bytes=64 << 30, theta=0.5, precision=PREC_F32, tol=1e-10,
                  max_it=20000, h_mode=0, ss_order=4, incremental=True, max_outer=20, inner_tol=1e-5,
-                 reliable_delta=0.0):
+                 reliable_delta=0.0, precond=PRECOND_JACOBI):
         self.L = lib()
         o = AdaptiveOpts(theta, 0, 1, h_mode, AssemblyOpts(precision, ss_order),
-                         SolveOpts(tol, max_it, PRECOND_JACOBI, max_outer, inner_tol, reliable_delta),
+                         SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta),
                          int(incremental))
         h = C.c_void_p()
         st = self.L.bem_server_create(slots, int(hbm_budget_bytes), C.byref(o), C.byref(h))

@@ -58,8 +58,9 @@ struct bem_server {
 
 namespace {
 
-// Device bytes a request may need: for one level, its operator (plus, for DF64,
-// the packed FP32 upper triangle the solver reads, a quarter of the operator);
+// Device bytes a request may need: for one level, its operator plus the packed FP32
+// upper triangle the solver reads (2 N^2 bytes: a quarter of a DF64 operator, half
+// of an FP32 one);
 // otherwise the operators of two consecutive levels (the coarse one is read by the
 // incremental assembly of the fine one and freed before the solve) at the largest
 // level the request can reach -- the first with N >= max_N, which Doerfler marking
@@ -72,7 +73,7 @@ int64_t estimate_bytes(int64_t N0, int64_t max_N, int32_t levels, int precision)
     const double grown = (double)N0 * std::pow(2.2, (double)(levels - 1));
     if (grown < reach) reach = grown;
     const double n = (levels <= 1 ? (double)N0 : reach) + 64.0;
-    const double ops = levels <= 1 ? (precision == BEM_PREC_DF64 ? 1.25 : 1.0) : 2.0;
+    const double ops = levels <= 1 ? (precision == BEM_PREC_DF64 ? 1.25 : precision == BEM_PREC_F32 ? 1.5 : 1.0) : 2.0;
     return (int64_t)(ops * es * n * n + 4096.0 * n) + (64ll << 20);
 }
 

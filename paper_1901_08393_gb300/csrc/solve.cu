@@ -704,7 +704,11 @@ __device__ __forceinline__ double elem_f64(const float2 *V, int64_t o) { return 
 __device__ __forceinline__ double elem_f64(const float *V, int64_t o) { return (double)V[o]; }
 
 // One CTA per cluster block: A = V[perm, perm] (identity on padding), A = L L^T,
-// L^-1 column by column, M^-1 = L^-T L^-1 (upper triangle formed, mirrored).
+// L^-1 column by column, M^-1 = L^-T L^-1 (upper triangle formed, mirrored).  The
+// discrete V is not positive definite everywhere (on strongly graded meshes the
+// fixed 7 x 7 rule for close disjoint pairs leaves some diagonal blocks with a
+// non-positive eigenvalue); a block whose Cholesky factorisation meets a pivot
+// <= 0 is replaced by its diagonal, so that M stays symmetric positive definite.
 template <typename T>
 __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, int64_t ld,
                                                        const int32_t *__restrict__ perm, double *__restrict__ binv)
@@ -712,18 +716,23 @@ __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, 
     extern __shared__ double smb[];
     double(*A)[kBJ + 1] = reinterpret_cast<double(*)[kBJ + 1]>(smb);
     double(*B)[kBJ + 1] = reinterpret_cast<double(*)[kBJ + 1]>(smb + kBJ * (kBJ + 1));
+    __shared__ double d0[kBJ];
+    __shared__ int s_fail;
     const int t = threadIdx.x;
     const int32_t *pk = perm + (int64_t)blockIdx.x * kBJ;
+    if (t == 0) s_fail = 0;
     for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
         const int i = idx / kBJ, j = idx % kBJ;
         const int32_t gi = pk[i], gj = pk[j];
         A[i][j] = (gi >= 0 && gj >= 0) ? elem_f64(V, (int64_t)gi * ld + gj) : (i == j ? 1.0 : 0.0);
     }
     __syncthreads();
+    if (t < kBJ) d0[t] = A[t][t];
     for (int k = 0; k < kBJ; ++k) {
         if (t == 0) {
             const double d = A[k][k];
-            A[k][k] = d > 0.0 ? sqrt(d) : 1.0;  // a principal block of the SPD V: d > 0
+            if (!(d > 0.0)) s_fail = 1;
+            A[k][k] = d > 0.0 ? sqrt(d) : 1.0;
         }
         __syncthreads();
         for (int i = k + 1 + t; i < kBJ; i += blockDim.x) A[i][k] /= A[k][k];
@@ -733,6 +742,14 @@ __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, 
             if (j > k && j <= i) A[i][j] -= A[i][k] * A[j][k];
         }
         __syncthreads();
+    }
+    double *out = binv + (int64_t)blockIdx.x * kBJ * kBJ;
+    if (s_fail) {  // diagonal block (Jacobi)
+        for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
+            const int i = idx / kBJ, j = idx % kBJ;
+            out[idx] = i == j ? 1.0 / d0[i] : 0.0;
+        }
+        return;
     }
     if (t < kBJ) {  // column t of L^-1 (lower), forward substitution
         const int c = t;
@@ -747,7 +764,6 @@ __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, 
         }
     }
     __syncthreads();
-    double *out = binv + (int64_t)blockIdx.x * kBJ * kBJ;
     for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
         const int i = idx / kBJ, j = idx % kBJ;
         if (i > j) continue;

@@ -146,3 +146,12 @@ def test_block_jacobi_fewer_iterations_on_adaptive_mesh():
     _, its_b = O.block_jacobi_pcg(V, b, O.cluster_order(v, t), tol=1e-10)
     _, its_j, _, _ = O.pcg(V, b, tol=1e-10, precond=1)
     assert its_b < its_j
+
+
+def test_block_jacobi_indefinite_block_falls_back_to_diagonal():
+    V = np.array([[1.0, 2.0, 0.1], [2.0, 1.0, 0.1], [0.1, 0.1, 1.0]])
+    blocks, inv = O.block_jacobi_inverses(V, np.arange(3), B=2)
+    assert np.array_equal(inv[0], np.eye(2))  # [[1, 2], [2, 1]] is indefinite
+    assert np.allclose(inv[1], [[1.0]])
+    blocks, inv = O.block_jacobi_inverses(np.eye(3) * 2 + 0.5, np.arange(3), B=2)
+    assert np.allclose(inv[0], np.linalg.inv(np.eye(2) * 2 + 0.5))
