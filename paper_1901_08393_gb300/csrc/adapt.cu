@@ -163,26 +163,55 @@ __global__ void k_bitonic_shared(unsigned long long *keys, int64_t n2, int64_t k
     for (int q = threadIdx.x; q < chunk; q += blockDim.x) keys[base + q] = sk[q];
 }
 
-// One warp forms the running FP64 sums of eta2 in key order, sequentially (every
-// lane performs the same additions, in order; lane l keeps the sum after element
-// base + l): prefix[k] = (((v_0 + v_1) + v_2) + ... + v_k).  The values of the next
-// 32 keys are loaded while the current 32 are added.
-__global__ void k_dorfler_prefix(const unsigned long long *keys, const double *eta2, int64_t N, double *prefix)
+// Running FP64 sums of eta2 in key order, sequentially: prefix[k] = (((v_0 + v_1) +
+// v_2) + ... + v_k).  One CTA: warps 1..7 gather the values of the next chunk of
+// keys into shared memory while thread 0 of warp 0 adds the current chunk (a single
+// dependent chain of FP64 additions, issued by one lane so that the narrow FP64 pipe
+// is not occupied by 31 redundant copies).
+constexpr int kPrefixChunk = 2048;
+
+__global__ void __launch_bounds__(256) k_dorfler_prefix(const unsigned long long *keys, const double *eta2, int64_t N,
+                                                        double *prefix)
 {
-    const int lane = threadIdx.x;
+    __shared__ double vals[2][kPrefixChunk];
+    const int t = threadIdx.x;
+    const int64_t nchunks = (N + kPrefixChunk - 1) / kPrefixChunk;
+    for (int q = t; q < kPrefixChunk; q += blockDim.x) {
+        const int64_t k = q;
+        vals[0][q] = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
+    }
+    __syncthreads();
     double acc = 0.0;
-    double v = lane < N ? eta2[keys[lane] & 0xFFFFFFFFull] : 0.0;
-    for (int64_t base = 0; base < N; base += 32) {
-        const int64_t kn = base + 32 + lane;
-        const double vn = kn < N ? eta2[keys[kn] & 0xFFFFFFFFull] : 0.0;
-        double mine = 0.0;
+    for (int64_t c = 0; c < nchunks; ++c) {
+        const int cur = (int)(c & 1);
+        if (t >= 32) {  // gather chunk c + 1
+            const int64_t base = (c + 1) * kPrefixChunk;
+            for (int q = t - 32; q < kPrefixChunk; q += blockDim.x - 32) {
+                const int64_t k = base + q;
+                vals[cur ^ 1][q] = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
+            }
+        } else if (t == 0) {
+            const int64_t base = c * kPrefixChunk;
+            const int n = (int)((N - base) < kPrefixChunk ? (N - base) : kPrefixChunk);
+            const double *v = vals[cur];
+            double *out = prefix + base;
+            int q = 0;
+            for (; q + 16 <= n; q += 16) {  // loads of a group issued before its additions
+                double r[16];
 #pragma unroll
-        for (int l = 0; l < 32; ++l) {
-            acc = acc + __shfl_sync(0xffffffffu, v, l);  // past N: adds +0.0, acc >= 0 unchanged
-            if (l == lane) mine = acc;
+                for (int u = 0; u < 16; ++u) r[u] = v[q + u];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    acc = acc + r[u];
+                    out[q + u] = acc;
+                }
+            }
+            for (; q < n; ++q) {
+                acc = acc + v[q];
+                out[q] = acc;
+            }
         }
-        if (base + lane < N) prefix[base + lane] = mine;
-        v = vn;
+        __syncthreads();
     }
 }
 
@@ -250,7 +279,7 @@ bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, 
     long long *dK = reinterpret_cast<long long *>(prefix + N);
     k_keys<<<nblk(n2, 256), 256, 0, s>>>(d_eta2, N, n2, keys); BEM_COUNT(ctx);
     sort_u64(ctx, keys, n2);
-    k_dorfler_prefix<<<1, 32, 0, s>>>(keys, d_eta2, N, prefix); BEM_COUNT(ctx);
+    k_dorfler_prefix<<<1, 256, 0, s>>>(keys, d_eta2, N, prefix); BEM_COUNT(ctx);
     k_dorfler_select<<<1, 1, 0, s>>>(keys, prefix, N, theta, dK); BEM_COUNT(ctx);
     k_mark<<<nblk(N, 256), 256, 0, s>>>(keys, N, dK, d_marked); BEM_COUNT(ctx);
     cudaError_t e = cudaGetLastError();

@@ -646,11 +646,13 @@ __global__ void k_residual(int64_t N, const double *b, const double *q, double *
 // definite by construction).
 constexpr int kBJ = 64;
 
-__global__ void k_cent_box(const double *cent, int64_t N, double *box)
+// Bounding box of the centroids: per-CTA min/max (part: gridDim.x x 6), then one
+// CTA folds the partials (min and max are exact, so the order does not matter).
+__global__ void __launch_bounds__(256) k_cent_box(const double *cent, int64_t N, double *part)
 {
     __shared__ double s[6][256];
     double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
-    for (int64_t i = threadIdx.x; i < N; i += blockDim.x)
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
         for (int c = 0; c < 3; ++c) {
             const double x = cent[4 * i + c];
             v[c] = fmin(v[c], x);
@@ -658,12 +660,23 @@ __global__ void k_cent_box(const double *cent, int64_t N, double *box)
         }
     for (int c = 0; c < 6; ++c) s[c][threadIdx.x] = v[c];
     __syncthreads();
-    if (threadIdx.x < 6) {
-        const int c = threadIdx.x;
-        double r = s[c][0];
-        for (int k = 1; k < (int)blockDim.x; ++k) r = c < 3 ? fmin(r, s[c][k]) : fmax(r, s[c][k]);
-        box[c] = r;
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+            for (int c = 0; c < 6; ++c)
+                s[c][threadIdx.x] = c < 3 ? fmin(s[c][threadIdx.x], s[c][threadIdx.x + w])
+                                          : fmax(s[c][threadIdx.x], s[c][threadIdx.x + w]);
+        __syncthreads();
     }
+    if (threadIdx.x < 6) part[blockIdx.x * 6 + threadIdx.x] = s[threadIdx.x][0];
+}
+
+__global__ void k_box_fold(const double *part, int nparts, double *box)
+{
+    const int c = threadIdx.x;
+    if (c >= 6) return;
+    double r = part[c];
+    for (int k = 1; k < nparts; ++k) r = c < 3 ? fmin(r, part[6 * k + c]) : fmax(r, part[6 * k + c]);
+    box[c] = r;
 }
 
 __device__ __forceinline__ unsigned spread3(unsigned q)  // bit b of q -> bit 3b
@@ -703,43 +716,55 @@ __device__ __forceinline__ double elem_f64(const double *V, int64_t o) { return 
 __device__ __forceinline__ double elem_f64(const float2 *V, int64_t o) { return (double)V[o].x + (double)V[o].y; }
 __device__ __forceinline__ double elem_f64(const float *V, int64_t o) { return (double)V[o]; }
 
-// One CTA per cluster block: A = V[perm, perm] (identity on padding), A = L L^T,
-// L^-1 column by column, M^-1 = L^-T L^-1 (upper triangle formed, mirrored).  The
-// discrete V is not positive definite everywhere (on strongly graded meshes the
-// fixed 7 x 7 rule for close disjoint pairs leaves some diagonal blocks with a
-// non-positive eigenvalue); a block whose Cholesky factorisation meets a pivot
-// <= 0 is replaced by its diagonal, so that M stays symmetric positive definite.
+// One CTA per cluster block.  A = V[perm, perm] (identity on padding) is scaled to
+// unit diagonal, S A S with S = diag(A)^-1/2 (FP64), factored A = L L^T in FP32,
+// L^-1 formed column by column in FP32, and M^-1 = S L^-T L^-1 S with the Gram sums
+// taken in double-float (exact FP32 products): symmetric (upper triangle formed,
+// mirrored) and positive definite for any nonsingular L, whatever the FP32 rounding
+// of L.  The discrete V is not positive definite everywhere (on strongly graded
+// meshes the fixed 7 x 7 rule for close disjoint pairs leaves some diagonal blocks
+// with a non-positive eigenvalue); a block whose factorisation meets a pivot <= 0
+// is replaced by its diagonal, so that M stays symmetric positive definite.
 template <typename T>
 __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, int64_t ld,
                                                        const int32_t *__restrict__ perm, double *__restrict__ binv)
 {
-    extern __shared__ double smb[];
-    double(*A)[kBJ + 1] = reinterpret_cast<double(*)[kBJ + 1]>(smb);
-    double(*B)[kBJ + 1] = reinterpret_cast<double(*)[kBJ + 1]>(smb + kBJ * (kBJ + 1));
-    __shared__ double d0[kBJ];
+    __shared__ float A[kBJ][kBJ + 1];
+    __shared__ float B[kBJ][kBJ + 1];
+    __shared__ double sc[kBJ], d0[kBJ];
     __shared__ int s_fail;
     const int t = threadIdx.x;
     const int32_t *pk = perm + (int64_t)blockIdx.x * kBJ;
     if (t == 0) s_fail = 0;
+    __syncthreads();
+    if (t < kBJ) {
+        const int32_t g = pk[t];
+        const double d = g >= 0 ? elem_f64(V, (int64_t)g * ld + g) : 1.0;
+        d0[t] = d;
+        if (!(d > 0.0)) s_fail = 1;
+        sc[t] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
+    }
+    __syncthreads();
     for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
         const int i = idx / kBJ, j = idx % kBJ;
         const int32_t gi = pk[i], gj = pk[j];
-        A[i][j] = (gi >= 0 && gj >= 0) ? elem_f64(V, (int64_t)gi * ld + gj) : (i == j ? 1.0 : 0.0);
+        const double a = (gi >= 0 && gj >= 0) ? elem_f64(V, (int64_t)gi * ld + gj) : (i == j ? 1.0 : 0.0);
+        A[i][j] = (float)(a * sc[i] * sc[j]);
     }
     __syncthreads();
-    if (t < kBJ) d0[t] = A[t][t];
+    const int ri = t >> 2, rc = t & 3;  // trailing update: row ri, columns rc + 4 m
     for (int k = 0; k < kBJ; ++k) {
         if (t == 0) {
-            const double d = A[k][k];
-            if (!(d > 0.0)) s_fail = 1;
-            A[k][k] = d > 0.0 ? sqrt(d) : 1.0;
+            const float d = A[k][k];
+            if (!(d > 0.f)) s_fail = 1;
+            A[k][k] = d > 0.f ? sqrtf(d) : 1.f;
         }
         __syncthreads();
-        for (int i = k + 1 + t; i < kBJ; i += blockDim.x) A[i][k] /= A[k][k];
+        if (t > k && t < kBJ) A[t][k] /= A[k][k];
         __syncthreads();
-        for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
-            const int i = idx / kBJ, j = idx % kBJ;
-            if (j > k && j <= i) A[i][j] -= A[i][k] * A[j][k];
+        if (ri > k) {
+            const float lik = A[ri][k];
+            for (int j = k + 1 + rc; j <= ri; j += 4) A[ri][j] -= lik * A[j][k];
         }
         __syncthreads();
     }
@@ -754,10 +779,10 @@ __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, 
     if (t < kBJ) {  // column t of L^-1 (lower), forward substitution
         const int c = t;
         for (int i = 0; i < kBJ; ++i) {
-            double v = 0.0;
+            float v = 0.f;
             if (i >= c) {
-                v = i == c ? 1.0 : 0.0;
-                for (int k = c; k < i; ++k) v -= A[i][k] * B[k][c];
+                v = i == c ? 1.f : 0.f;
+                for (int k = c; k < i; ++k) v = __fmaf_rn(-A[i][k], B[k][c], v);
                 v /= A[i][i];
             }
             B[i][c] = v;
@@ -767,8 +792,9 @@ __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, 
     for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
         const int i = idx / kBJ, j = idx % kBJ;
         if (i > j) continue;
-        double v = 0.0;
-        for (int k = j; k < kBJ; ++k) v += B[k][i] * B[k][j];
+        float h = 0.f, l = 0.f;
+        for (int k = j; k < kBJ; ++k) acc_hi(h, l, B[k][i], B[k][j], 0.f);
+        const double v = ((double)h + (double)l) * sc[i] * sc[j];
         out[i * kBJ + j] = v;
         out[j * kBJ + i] = v;
     }
@@ -1264,25 +1290,23 @@ static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out,
     unsigned long long *keys = nullptr;
     double *binv = nullptr;
     const size_t kb = sizeof(unsigned long long) * n2, pb = sizeof(int32_t) * nbj * kBJ;
-    bem_status st = dalloc(ctx, tmp, (void **)&keys, kb + pb + 6 * sizeof(double) + 64, false);
+    const int nbox = (int)std::min<int64_t>((N + 255) / 256, 64);
+    bem_status st = dalloc(ctx, tmp, (void **)&keys, kb + pb + (6 + 6 * nbox) * sizeof(double) + 64, false);
     if (!st) st = dalloc(ctx, tmp, (void **)&binv, sizeof(double) * kBJ * kBJ * nbj, false);
     if (st) return st;
     int32_t *perm = reinterpret_cast<int32_t *>(keys + n2);
     double *box = reinterpret_cast<double *>(reinterpret_cast<char *>(perm) + (pb + 7) / 8 * 8);
-    k_cent_box<<<1, 256, 0, s>>>(op->mesh->cent, N, box); BEM_COUNT(ctx);
+    k_cent_box<<<nbox, 256, 0, s>>>(op->mesh->cent, N, box + 6); BEM_COUNT(ctx);
+    k_box_fold<<<1, 32, 0, s>>>(box + 6, nbox, box); BEM_COUNT(ctx);
     k_morton_keys<<<nblk(n2, 256), 256, 0, s>>>(op->mesh->cent, N, n2, box, keys); BEM_COUNT(ctx);
     sort_u64(ctx, keys, n2);
     k_cluster_perm<<<nblk((int64_t)nbj * kBJ, 256), 256, 0, s>>>(keys, N, (int64_t)nbj * kBJ, perm); BEM_COUNT(ctx);
-    const int smem = 2 * kBJ * (kBJ + 1) * (int)sizeof(double);
     if (op->precision == BEM_PREC_DF64) {
-        BEM_CK(ctx, cudaFuncSetAttribute(k_block_inverse<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_block_inverse<float2><<<nbj, 256, smem, s>>>((const float2 *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
+        k_block_inverse<float2><<<nbj, 256, 0, s>>>((const float2 *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
     } else if (op->precision == BEM_PREC_F64) {
-        BEM_CK(ctx, cudaFuncSetAttribute(k_block_inverse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_block_inverse<double><<<nbj, 256, smem, s>>>((const double *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
+        k_block_inverse<double><<<nbj, 256, 0, s>>>((const double *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
     } else {
-        BEM_CK(ctx, cudaFuncSetAttribute(k_block_inverse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        k_block_inverse<float><<<nbj, 256, smem, s>>>((const float *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
+        k_block_inverse<float><<<nbj, 256, 0, s>>>((const float *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
     }
     BEM_CK_LAUNCH(ctx);
     *perm_out = perm;
