@@ -162,6 +162,82 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
 
 
+def batch_workload(args):
+    """Batching (BASELINE config 4) through bem_batch_*: inputs.batch_meshes (seed 4:
+    polycubes g in 3..10, p in [0.3, 0.7], uniform meshes, log-uniform 500..30,000
+    triangles), FP32 V, PCG to 1e-10 with FP64-accurate residuals.  One step = one
+    bem_batch_run: every V assembled, all systems solved by ONE cooperative launch of
+    the persistent solver (CTAs shared in proportion to N^2), every Cap formed; the
+    first run is recorded as a CUDA graph, later runs replay it.  Meshes resident;
+    value = meshes per second.  e2e: per step, the meshes uploaded from host arrays,
+    the batch created (allocations, cluster orders) and run, the results copied back."""
+    import torch
+
+    from paper_1901_08393_gb300 import bem, build, inputs, replicas
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        replicas.init("nccl", device=torch.device("cuda", local))
+    build.build()
+    ctx = bem.Context()
+    ms = inputs.batch_meshes(count=args.batch, seed=4 + rank)
+    meshes = [bem.Mesh.upload(ctx, m.verts, m.tris) for m in ms]
+    pc = bem.PRECOND_BLOCK if args.precond == "block" else bem.PRECOND_JACOBI
+    b = bem.Batch(ctx, meshes, precision=bem.PREC_F32, precond=pc, tol=TOL, max_it=5000)
+    for _ in range(max(args.warmup, 1)):
+        b.run()
+    launches0 = ctx.launch_count()
+    clocks = Clocks(local)
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks.start()
+    times, res = [], None
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        res = b.run()
+        times.append(time.perf_counter() - t)
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    info = b.info()
+    b.close()
+    e2e = []
+    h2d = sum(m.verts.nbytes + m.tris.nbytes for m in ms)
+    for _ in range(0 if args.no_e2e else args.steps):
+        t = time.perf_counter()
+        mh = [bem.Mesh.upload(ctx, m.verts, m.tris) for m in ms]
+        be = bem.Batch(ctx, mh, precision=bem.PREC_F32, precond=pc, tol=TOL, max_it=5000, use_graph=False)
+        be.run()
+        be.close()
+        for x in mh:
+            x.close()
+        e2e.append(time.perf_counter() - t)
+    total = replicas.reduce_max(sum(times))
+    value = args.steps * len(ms) * ws / total
+    e2e_val = args.steps * len(ms) * ws / replicas.reduce_max(sum(e2e)) if e2e else None
+    lat = sorted(1e3 * t for t in times)
+    line = {
+        "metric": METRIC, "value": value, "unit": "capacity solves/s (meshes)", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64-accurate residuals)", "data": "synthetic",
+        "config": {"workload": f"batch: {len(ms)} uniform polycube meshes (g 3..10, p 0.3..0.7, log-uniform "
+                               "500..30,000 triangles), one assembly + solve each, FP32 V, PCG to 1e-10",
+                   "preconditioner": PC_LABEL[args.precond], "solver_ctas": info["ctas"],
+                   "graph_replayed": bool(info["graph_used"]), "sum_N2": float(sum(m.N * m.N for m in ms)),
+                   "l2": "V of the batch (tens of GB) exceeds L2"},
+        "p50_latency_ms": lat[len(lat) // 2], "p99_latency_ms": lat[-1],
+        "caps_converged": all(r["converged"] for r in res), "max_iterations": max(r["iterations"] for r in res),
+        "clocks": clk, "roofline": None, "cpu_baseline": None, "gpu_launches": launches,
+        "e2e": {"value": e2e_val, "unit": "capacity solves/s (meshes)", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": len(ms) * 32},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def server_workload(args):
     """Serving (BASELINE config 5) and batching (config 4) through bem_server_*.
 
@@ -171,10 +247,9 @@ def server_workload(args):
     --requests requests; value = completed requests per second of the step, latency =
     completion - submission.  A second pass submits the same stream at once
     (saturation throughput).
-    batch: inputs.batch_meshes (seed 4: polycubes g in 3..10, p in [0.3, 0.7], uniform
-    meshes, log-uniform 500..30,000 triangles), one level each (assembly + solve),
-    all submitted at once; one step = --batch meshes.
-    Both in FP32 with FP64 iterative refinement to 1e-10 (the mixed-precision form).
+    batch-server: the meshes of the batch workload submitted at once to the server,
+    one level each (assembly + solve); one step = --batch meshes.
+    Both in FP32 with FP64-accurate residuals to 1e-10 (the mixed-precision form).
     """
     import threading
 
@@ -277,11 +352,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--max-n", type=int, default=MAX_N, help="smaller case of the same workload (profiling)")
-    ap.add_argument("--workload", default="adaptive", choices=["adaptive", "graded60k", "serve", "batch"],
+    ap.add_argument("--workload", default="adaptive",
+                    choices=["adaptive", "graded60k", "serve", "batch", "batch-server"],
                     help="adaptive: the default workload above; graded60k: precision form (one FP32 "
                          "assembly + FP64-refined solve on the 60,492-triangle graded cube per step); "
                          "serve: Poisson stream of adaptive requests through the continuous-batching server; "
-                         "batch: uniform polycube meshes solved through the server")
+                         "batch: uniform polycube meshes assembled and solved by bem_batch_run (one solver "
+                         "launch, CUDA graph); batch-server: the same meshes through the server")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per step")
     ap.add_argument("--batch", type=int, default=64, help="batch: meshes per step")
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
@@ -295,7 +372,9 @@ def main():
         return reference_arm(args)
     if args.precond == "auto":
         args.precond = "jacobi" if args.workload == "graded60k" else "block"
-    if args.workload in ("serve", "batch"):
+    if args.workload == "batch":
+        return batch_workload(args)
+    if args.workload in ("serve", "batch-server"):
         return server_workload(args)
 
     import numpy as np

@@ -253,6 +253,38 @@ typedef struct {
 bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_level_record *records,
                             int32_t *n_levels, bem_mesh **final_mesh);
 
+/* ---------------------------------------------------------------- batch */
+/* Many independent capacity problems assembled and solved together (the paper has
+ * no counterpart: it solves one polyhedron at a time).  bem_batch_create takes count
+ * meshes of any sizes (same context; the meshes must outlive the batch), allocates one
+ * operator per mesh (aopts->precision BEM_PREC_DF64 or BEM_PREC_F32) and everything
+ * the solves need, and, for BEM_PRECOND_BLOCK, computes the cluster orders.
+ * bem_batch_run assembles every V (Eq. 2.4-2.5; the kernels of bem_assemble_V, per
+ * mesh), then solves all V x = |T| from x = 0 in ONE cooperative launch of the
+ * persistent solver of bem_solve_capacity (sopts: tol, max_it, precond,
+ * reliable_delta), in which problem p owns a share of the CTAs in proportion to its
+ * work and has its own grid barrier, and forms every Cap (Eq. 2.8).  The work runs on
+ * a stream of the batch; with use_graph the first run records it as a CUDA graph and
+ * later runs replay that graph.  The call blocks until the results are on the host;
+ * results (nullable, count entries) receive them; BEM_ERR_NOT_CONVERGED if any
+ * problem missed tol.  At most 3 x (number of SMs) problems per batch. */
+typedef struct bem_batch bem_batch;
+typedef struct {
+    double cap;
+    int32_t iterations;
+    int32_t outer;           /* as bem_solve_info.outer */
+    double relres;
+    int32_t converged;
+    int32_t status;          /* BEM_OK, BEM_ERR_NOT_CONVERGED or BEM_ERR_CUDA (barrier time-out) */
+} bem_batch_result;
+bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes, const bem_assembly_opts *aopts,
+                            const bem_solve_opts *sopts, int32_t use_graph, bem_batch **out);
+bem_status bem_batch_run(bem_batch *b, bem_batch_result *results);
+/* count: problems; ctas: CTAs of the solver launch; graph_used: 1 if the last run
+ * replayed a captured graph. */
+bem_status bem_batch_info(const bem_batch *b, int32_t *count, int32_t *ctas, int32_t *graph_used);
+bem_status bem_batch_destroy(bem_batch *b);
+
 /* ---------------------------------------------------------------- serving */
 /* Continuous-batching server for adaptive capacity requests (the paper has no
  * counterpart: it serves many polyhedra of different sizes arriving over time).

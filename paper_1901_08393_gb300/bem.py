@@ -38,6 +38,7 @@ EXPORTS = [
     "bem_zz_estimate", "bem_dorfler", "bem_refine", "bem_mark_refine", "bem_adaptive_run",
     "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc", "bem_context_set_persistent",
     "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
+    "bem_batch_create", "bem_batch_run", "bem_batch_info", "bem_batch_destroy",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -80,6 +81,11 @@ class RequestResult(C.Structure):
                 ("t_done", C.c_double), ("estimate_bytes", C.c_int64),
                 ("cap_history", C.c_double * SERVER_HISTORY), ("N_history", C.c_int64 * SERVER_HISTORY),
                 ("message", C.c_char * 256)]
+
+
+class BatchResult(C.Structure):
+    _fields_ = [("cap", C.c_double), ("iterations", C.c_int32), ("outer", C.c_int32), ("relres", C.c_double),
+                ("converged", C.c_int32), ("status", C.c_int32)]
 
 
 class ServerStats(C.Structure):
@@ -139,6 +145,10 @@ def lib():
         "bem_server_wait": [vp, i64, P(RequestResult)],
         "bem_server_stats": [vp, P(ServerStats)],
         "bem_server_destroy": [vp],
+        "bem_batch_create": [vp, i32, vp, P(AssemblyOpts), P(SolveOpts), i32, P(vp)],
+        "bem_batch_run": [vp, vp],
+        "bem_batch_info": [vp, P(i32), P(i32), P(i32)],
+        "bem_batch_destroy": [vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -412,6 +422,46 @@ def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, pr
                                                C.byref(fin) if want_final else None))
     out = [{f: getattr(recs[k], f) for f, _ in LevelRecord._fields_} for k in range(n.value)]
     return out, (Mesh(mesh.ctx, fin) if want_final and fin.value else None)
+
+
+class Batch:
+    """Independent problems assembled and solved together (bem_batch_*): one
+    cooperative launch solves all of them; with use_graph the run is recorded as a
+    CUDA graph once and replayed."""
+
+    def __init__(self, ctx: Context, meshes, precision=PREC_DF64, ss_order=4, tol=1e-10, max_it=10000,
+                 precond=PRECOND_JACOBI, reliable_delta=0.0, use_graph=True):
+        self.ctx, self.meshes, self.h = ctx, list(meshes), None
+        arr = (C.c_void_p * len(self.meshes))(*[m.h.value if hasattr(m.h, "value") else m.h for m in self.meshes])
+        h = C.c_void_p()
+        ctx.check(ctx.L.bem_batch_create(ctx.h, len(self.meshes), arr, C.byref(AssemblyOpts(precision, ss_order)),
+                                         C.byref(SolveOpts(tol, max_it, precond, 20, 1e-5, reliable_delta)),
+                                         int(bool(use_graph)), C.byref(h)))
+        self.h = h
+
+    def run(self, raise_not_converged=True):
+        """Assemble and solve every problem; a list of result dicts."""
+        res = (BatchResult * len(self.meshes))()
+        st = self.ctx.L.bem_batch_run(self.h, res)
+        if st != BEM_OK and (st != BEM_ERR_NOT_CONVERGED or raise_not_converged):
+            self.ctx.check(st)
+        return [{f: getattr(r, f) for f, _ in BatchResult._fields_} for r in res]
+
+    def info(self):
+        n, g, used = C.c_int32(), C.c_int32(), C.c_int32()
+        self.ctx.check(self.ctx.L.bem_batch_info(self.h, C.byref(n), C.byref(g), C.byref(used)))
+        return {"count": n.value, "ctas": g.value, "graph_used": used.value}
+
+    def close(self):
+        if self.h is not None and self.ctx.h:
+            self.ctx.L.bem_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

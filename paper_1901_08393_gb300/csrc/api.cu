@@ -442,7 +442,7 @@ bem_status bem_mesh_geometry(const bem_mesh *mesh, double *area, double *diam)
 }
 
 // ------------------------------------------------------------------ operator
-static bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out)
+static bem_status operator_alloc(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out)
 {
     bem_ctx *ctx = mesh->ctx;
     const int prec = opts ? opts->precision : BEM_PREC_F64;
@@ -474,7 +474,7 @@ bem_status bem_assemble_V(bem_mesh *mesh, const bem_assembly_opts *opts, bem_ope
     if (!mesh || !out) return BEM_ERR_INVALID;
     *out = nullptr;
     bem_operator *op = nullptr;
-    bem_status st = new_operator(mesh, opts, &op);
+    bem_status st = operator_alloc(mesh, opts, &op);
     if (st) return st;
     st = assemble_full(op);
     if (!st) {
@@ -505,7 +505,7 @@ bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse, con
                   "ss_order differs from the coarse operator");
     }
     bem_operator *op = nullptr;
-    bem_status st = new_operator(fine, &o, &op);
+    bem_status st = operator_alloc(fine, &o, &op);
     if (st) return st;
     st = assemble_update(op, coarse);
     if (!st) {
@@ -856,3 +856,10 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
 }
 
 }  // extern "C"
+
+namespace bem {
+bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out)
+{
+    return operator_alloc(mesh, opts, out);
+}
+}  // namespace bem

@@ -621,6 +621,8 @@ static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
     return BEM_OK;
 }
 
+bem_status assembly_prepare(bem_ctx *ctx) { return assembly_constants(ctx); }
+
 bem_status gauss_legendre_upload(int n)
 {
     (void)n;

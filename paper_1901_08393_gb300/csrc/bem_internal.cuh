@@ -146,6 +146,9 @@ bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge)
 // ----------------------------------------------------------------- assembly (assemble.cu)
 bem_status gauss_legendre_upload(int n);
 bem_status assemble_full(bem_operator *op);
+// Operator handle with V (uninitialised) and diag allocated for mesh (api.cu).
+bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out);
+bem_status assembly_prepare(bem_ctx *ctx);  // constant tables on the device (once)
 bem_status assemble_update(bem_operator *op, const bem_operator *coarse);
 bem_status operator_diag(bem_operator *op);
 

@@ -902,7 +902,7 @@ struct PcgArgs {
     int f32op;                // FP32 operator: every product (residuals too) from vp
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int G)
 {
     __shared__ int s_ok;
     __syncthreads();
@@ -911,7 +911,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
         volatile unsigned *gen = bar + 1;
         const unsigned g = *gen;
         __threadfence();
-        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+        if (atomicAdd(bar, 1u) + 1u == (unsigned)G) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -933,8 +933,8 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err)
     return s_ok != 0;
 }
 
-// Per-CTA partial of one value per thread (fixed tree) into slot[blockIdx.x].
-__device__ __forceinline__ void cta_partial(double v, double *slot)
+// Per-CTA partial of one value per thread (fixed tree) into slot[cta].
+__device__ __forceinline__ void cta_partial(double v, double *slot, int cta)
 {
     __shared__ double sw[kSymThreads / 32];
     v = warp_sum(v);
@@ -944,18 +944,18 @@ __device__ __forceinline__ void cta_partial(double v, double *slot)
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int k = 0; k < kSymThreads / 32; ++k) t += sw[k];
-        slot[blockIdx.x] = t;
+        slot[cta] = t;
     }
     __syncthreads();
 }
 
 // Fixed-order sum of the G per-CTA partials (L2 loads: written by other CTAs).
-__device__ __forceinline__ double grid_total(const double *slot)
+__device__ __forceinline__ double grid_total(const double *slot, int G)
 {
     __shared__ double sw[kSymThreads / 32];
     __shared__ double res;
     double v = 0.0;
-    for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) v += __ldcg(slot + k);
+    for (int k = threadIdx.x; k < G; k += blockDim.x) v += __ldcg(slot + k);
     v = warp_sum(v);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     if (lane == 0) sw[w] = v;
@@ -969,10 +969,9 @@ __device__ __forceinline__ double grid_total(const double *slot)
     return res;
 }
 
-__global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
+__device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const int cta)
 {
     extern __shared__ float2 sm[];
-    const int G = gridDim.x, cta = blockIdx.x;
     const int64_t stride = (int64_t)G * kSymThreads;
     const int64_t i0 = (int64_t)cta * kSymThreads + threadIdx.x;
     double *pA = a.part, *pB = a.part + G, *pC = a.part + 2 * G;
@@ -987,7 +986,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
     // of the mixed mode also packs the hi parts
     auto df64_product = [&](bool pack) -> bool {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.x[i]) : make_float2(0.f, 0.f);
-        if (!grid_barrier(a.bar, a.err)) return false;
+        if (!grid_barrier(a.bar, a.err, G)) return false;
         if (a.f32op) {  // the stored operator is the packed copy itself
             symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
             tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
@@ -996,7 +995,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
                        pack ? a.vp : nullptr);
             tbase += (unsigned long long)(a.ntiles + G);
         }
-        return grid_barrier(a.bar, a.err);
+        return grid_barrier(a.bar, a.err, G);
     };
     // r = b - V x0 (or b), z = M^-1 r, p = z
     const bool prod0 = a.has_x0 || mixed;
@@ -1020,20 +1019,20 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
         }
     }
     if (blockpc) {  // z = M^-1 r over whole clusters: every r written first
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err, G)) return;
         for (int blk = cta; blk < a.nbj; blk += G)
             block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, true, rs, rz_l, rr_l);
     }
-    cta_partial(rz_l, pA);
-    cta_partial(rr_l, pB);
-    cta_partial(bb_l, pC);
-    if (!grid_barrier(a.bar, a.err)) return;
-    double rz = grid_total(pA), rr = grid_total(pB);
-    const double bb = grid_total(pC);
+    cta_partial(rz_l, pA, cta);
+    cta_partial(rr_l, pB, cta);
+    cta_partial(bb_l, pC, cta);
+    if (!grid_barrier(a.bar, a.err, G)) return;
+    double rz = grid_total(pA, G), rr = grid_total(pB, G);
+    const double bb = grid_total(pC, G);
     const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
     double rr_true = rr;  // r.r at the last residual formed with the DF64 product
     int it = 0, ndf = prod0 ? 1 : 0;
-    if (!grid_barrier(a.bar, a.err)) return;  // partial slots are reused below
+    if (!grid_barrier(a.bar, a.err, G)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
         if (mixed) {
             symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
@@ -1042,7 +1041,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
             symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase);
             tbase += (unsigned long long)(a.ntiles + G);
         }
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err, G)) return;
         double pq_l = 0.0;
         // 8 rows per warp and pass, 4 threads per row; the loop is uniform across the
         // warp (rows past N recompute row N-1 and are discarded) because the row sum
@@ -1057,9 +1056,9 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
                 pq_l += a.p[i] * qi;
             }
         }
-        cta_partial(pq_l, pA);
-        if (!grid_barrier(a.bar, a.err)) return;
-        const double alpha = rz / grid_total(pA);
+        cta_partial(pq_l, pA, cta);
+        if (!grid_barrier(a.bar, a.err, G)) return;
+        const double alpha = rz / grid_total(pA, G);
         double rz_n = 0.0;
         rr_l = 0.0;
         if (blockpc) {
@@ -1076,11 +1075,11 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
                 rr_l += ri * ri;
             }
         }
-        cta_partial(rz_n, pB);
-        cta_partial(rr_l, pC);
-        if (!grid_barrier(a.bar, a.err)) return;
-        double rz_new = grid_total(pB);
-        rr = grid_total(pC);
+        cta_partial(rz_n, pB, cta);
+        cta_partial(rr_l, pC, cta);
+        if (!grid_barrier(a.bar, a.err, G)) return;
+        double rz_new = grid_total(pB, G);
+        rr = grid_total(pC, G);
         ++it;
         if (mixed && (rr <= a.delta2 * rr_true || rr <= thr)) {
             // reliable update: replace the recursive residual by b - V x with the
@@ -1104,16 +1103,16 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
                 }
             }
             if (blockpc) {
-                if (!grid_barrier(a.bar, a.err)) return;
+                if (!grid_barrier(a.bar, a.err, G)) return;
                 for (int blk = cta; blk < a.nbj; blk += G)
                     block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, false, rs, rz_n,
                                 rr_l);
             }
-            cta_partial(rz_n, pB);
-            cta_partial(rr_l, pC);
-            if (!grid_barrier(a.bar, a.err)) return;
-            rz_new = grid_total(pB);
-            rr = grid_total(pC);
+            cta_partial(rz_n, pB, cta);
+            cta_partial(rr_l, pC, cta);
+            if (!grid_barrier(a.bar, a.err, G)) return;
+            rz_new = grid_total(pB, G);
+            rr = grid_total(pC, G);
             rr_true = rr;
             ++ndf;
         }
@@ -1124,7 +1123,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
             a.p[i] = pi;
             a.pdf[i] = df_from_double(pi);
         }
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err, G)) return;
     }
     if (cta == 0 && threadIdx.x == 0) {
         a.out[0] = rr;
@@ -1132,6 +1131,35 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a)
         a.out[2] = (double)it;
         a.out[3] = (double)ndf;
     }
+}
+
+__global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a) { pcg_body(a, gridDim.x, blockIdx.x); }
+
+// Independent solves in one cooperative launch: problem p owns the CTAs
+// [begin[p], begin[p + 1]) and runs the same solver on them, with its own grid
+// barrier, tile counter and partials; a problem that converges releases its CTAs.
+__global__ void __launch_bounds__(kSymThreads, 3) k_pcg_batch(const PcgArgs *__restrict__ args,
+                                                              const int *__restrict__ begin, int P)
+{
+    __shared__ PcgArgs sa;
+    __shared__ int s_p;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = P - 1;  // last p with begin[p] <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (begin[mid] <= (int)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_p = lo;
+        sa = args[lo];
+    }
+    __syncthreads();
+    const int p = s_p;
+    const int b0 = begin[p], b1 = begin[p + 1];
+    if ((int)blockIdx.x >= b1) return;  // CTAs past the last group
+    pcg_body(sa, b1 - b0, (int)blockIdx.x - b0);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1279,7 +1307,9 @@ static bem_status pcg(bem_operator *op, Work &W, const double *rhs, double tol, 
 // cooperative launch of the needed size is not possible (the caller then runs the
 // host-driven loop).
 // Cluster order and inverse blocks of the block-Jacobi preconditioner (scratch in tmp).
-static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out, double **binv_out, int *nbj_out)
+// Cluster order of the block preconditioner (depends on the mesh only): scratch and
+// perm (nbj x kBJ, -1 padding) in a.
+static bem_status cluster_setup(bem_operator *op, Allocs &a, int32_t **perm_out, int *nbj_out)
 {
     bem_ctx *ctx = op->mesh->ctx;
     cudaStream_t s = ctx->stream;
@@ -1288,11 +1318,9 @@ static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out,
     int64_t n2 = 2;
     while (n2 < N) n2 <<= 1;
     unsigned long long *keys = nullptr;
-    double *binv = nullptr;
     const size_t kb = sizeof(unsigned long long) * n2, pb = sizeof(int32_t) * nbj * kBJ;
     const int nbox = (int)std::min<int64_t>((N + 255) / 256, 64);
-    bem_status st = dalloc(ctx, tmp, (void **)&keys, kb + pb + (6 + 6 * nbox) * sizeof(double) + 64, false);
-    if (!st) st = dalloc(ctx, tmp, (void **)&binv, sizeof(double) * kBJ * kBJ * nbj, false);
+    bem_status st = dalloc(ctx, a, (void **)&keys, kb + pb + (6 + 6 * nbox) * sizeof(double) + 64, false);
     if (st) return st;
     int32_t *perm = reinterpret_cast<int32_t *>(keys + n2);
     double *box = reinterpret_cast<double *>(reinterpret_cast<char *>(perm) + (pb + 7) / 8 * 8);
@@ -1301,6 +1329,17 @@ static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out,
     k_morton_keys<<<nblk(n2, 256), 256, 0, s>>>(op->mesh->cent, N, n2, box, keys); BEM_COUNT(ctx);
     sort_u64(ctx, keys, n2);
     k_cluster_perm<<<nblk((int64_t)nbj * kBJ, 256), 256, 0, s>>>(keys, N, (int64_t)nbj * kBJ, perm); BEM_COUNT(ctx);
+    BEM_CK_LAUNCH(ctx);
+    *perm_out = perm;
+    *nbj_out = nbj;
+    return BEM_OK;
+}
+
+// Inverse blocks of the block preconditioner from the assembled operator.
+static bem_status block_inverse_launch(bem_operator *op, const int32_t *perm, int nbj, double *binv)
+{
+    bem_ctx *ctx = op->mesh->ctx;
+    cudaStream_t s = ctx->stream;
     if (op->precision == BEM_PREC_DF64) {
         k_block_inverse<float2><<<nbj, 256, 0, s>>>((const float2 *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
     } else if (op->precision == BEM_PREC_F64) {
@@ -1309,6 +1348,19 @@ static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out,
         k_block_inverse<float><<<nbj, 256, 0, s>>>((const float *)op->V, op->ld, perm, binv); BEM_COUNT(ctx);
     }
     BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
+
+// Cluster order and inverse blocks of the block-Jacobi preconditioner (scratch in tmp).
+static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out, double **binv_out, int *nbj_out)
+{
+    int32_t *perm = nullptr;
+    double *binv = nullptr;
+    int nbj = 0;
+    bem_status st = cluster_setup(op, tmp, &perm, &nbj);
+    if (!st) st = dalloc(op->mesh->ctx, tmp, (void **)&binv, sizeof(double) * kBJ * kBJ * nbj, false);
+    if (!st) st = block_inverse_launch(op, perm, nbj, binv);
+    if (st) return st;
     *perm_out = perm;
     *binv_out = binv;
     *nbj_out = nbj;
@@ -1592,7 +1644,348 @@ out:
     return st;
 }
 
+// ------------------------------------------------------------------ batch
+// Independent problems assembled and solved together (bem_batch_*): everything a run
+// needs is allocated at creation; a run enqueues the assembly kernels of every
+// problem, one cooperative launch of k_pcg_batch for all solves, the capacities, and
+// one copy of the results to pinned host memory.  With use_graph the first run
+// records that sequence as a CUDA graph on the batch's stream and later runs replay
+// it.
+struct BatchProblem {
+    bem_operator *op = nullptr;
+    double *b = nullptr, *d = nullptr, *x = nullptr, *part = nullptr;
+    size_t part_bytes = 0;
+    float *vp = nullptr;
+    int32_t *perm = nullptr;
+    double *binv = nullptr;
+    int nbj = 0;
+};
+
 }  // namespace bem
+
+struct bem_batch {
+    bem_ctx *ctx = nullptr;
+    int P = 0, use_graph = 1, graph_used = 0, G = 0, precond = BEM_PRECOND_JACOBI;
+    double tol = 1e-10;
+    int64_t launches_per_run = 0;
+    std::vector<bem::BatchProblem> prob;
+    std::vector<bem::PcgArgs> args;
+    std::vector<int> begin;
+    bem::PcgArgs *d_args = nullptr;
+    int *d_begin = nullptr;
+    double *d_res = nullptr;  // P x 8: out[0..4] of the solver, [5] Cap, [6] error flag (int)
+    double *h_res = nullptr;  // pinned copy
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bem::Allocs allocs;
+};
+
+namespace bem {
+
+constexpr int kBatchRes = 8;
+
+static bem_status batch_enqueue(bem_batch *bt)
+{
+    bem_ctx *ctx = bt->ctx;
+    cudaStream_t s = ctx->stream;
+    bem_status st;
+    for (auto &pr : bt->prob)
+        if ((st = assemble_full(pr.op))) return st;
+    BEM_CK(ctx, cudaMemsetAsync(bt->d_res, 0, sizeof(double) * kBatchRes * bt->P, s));
+    for (auto &pr : bt->prob) {
+        bem_operator *op = pr.op;
+        const int64_t N = op->N;
+        BEM_CK(ctx, cudaMemcpyAsync(pr.b, op->mesh->area, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        BEM_CK(ctx, cudaMemcpyAsync(pr.d, op->diag, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        BEM_CK(ctx, cudaMemsetAsync(pr.x, 0, sizeof(double) * op->ld, s));
+        BEM_CK(ctx, cudaMemsetAsync(pr.part, 0, pr.part_bytes, s));
+        if (op->precision == BEM_PREC_F32) {
+            const int nb = (int)(op->ld / kSB), nt = nb * (nb + 1) / 2;
+            k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256,
+                         0, s>>>((const float *)op->V, op->ld, N, bt->args[&pr - &bt->prob[0]].tiles, nt, pr.vp); BEM_COUNT(ctx);
+        }
+        if (bt->precond == BEM_PRECOND_BLOCK && (st = block_inverse_launch(op, pr.perm, pr.nbj, pr.binv))) return st;
+    }
+    {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)bt->G);
+        cfg.blockDim = dim3(kSymThreads);
+        cfg.dynamicSmemBytes = kSymSmem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        BEM_CK(ctx, cudaLaunchKernelEx(&cfg, k_pcg_batch, (const PcgArgs *)bt->d_args, (const int *)bt->d_begin,
+                                       bt->P));
+        BEM_COUNT(ctx);
+    }
+    for (int p = 0; p < bt->P; ++p) {
+        bem_operator *op = bt->prob[p].op;
+        k_capacity<<<1, 1024, 0, s>>>(op->N, op->mesh->area, bt->prob[p].x, bt->d_res + kBatchRes * p + 5); BEM_COUNT(ctx);
+    }
+    BEM_CK_LAUNCH(ctx);
+    BEM_CK(ctx, cudaMemcpyAsync(bt->h_res, bt->d_res, sizeof(double) * kBatchRes * bt->P, cudaMemcpyDeviceToHost, s));
+    return BEM_OK;
+}
+
+}  // namespace bem
+
+extern "C" {
+
+bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes, const bem_assembly_opts *aopts,
+                            const bem_solve_opts *sopts, int32_t use_graph, bem_batch **out)
+{
+    using namespace bem;
+    if (!ctx || !meshes || !out || count < 1) return ctx ? set_error(ctx, BEM_ERR_INVALID, "bad batch arguments") : BEM_ERR_INVALID;
+    *out = nullptr;
+    const int prec = aopts ? aopts->precision : BEM_PREC_DF64;
+    if (prec != BEM_PREC_DF64 && prec != BEM_PREC_F32)
+        return set_error(ctx, BEM_ERR_INVALID, "a batch needs BEM_PREC_DF64 or BEM_PREC_F32 operators");
+    const int precond = sopts ? sopts->precond : BEM_PRECOND_JACOBI;
+    if (precond < BEM_PRECOND_NONE || precond > BEM_PRECOND_BLOCK)
+        return set_error(ctx, BEM_ERR_INVALID, "unknown preconditioner %d", precond);
+    for (int p = 0; p < count; ++p)
+        if (!meshes[p] || meshes[p]->ctx != ctx) return set_error(ctx, BEM_ERR_INVALID, "mesh %d is not of this context", p);
+    int coop = 0, per_sm = 0;
+    BEM_CK(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
+    if (!coop) return set_error(ctx, BEM_ERR_CUDA, "the device has no cooperative launch");
+    BEM_CK(ctx, cudaFuncSetAttribute(k_pcg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
+    BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, kSymThreads, kSymSmem));
+    const int Gmax = (per_sm < 3 ? per_sm : 3) * ctx->sm_count;
+    if (count > Gmax) return set_error(ctx, BEM_ERR_INVALID, "at most %d problems per batch on this device", Gmax);
+    bem_status st = assembly_prepare(ctx);
+    if (st) return st;
+    BEM_CK(ctx, cudaStreamSynchronize(ctx->stream));  // meshes built on the context's stream
+    bem_batch *bt = new (std::nothrow) bem_batch();
+    if (!bt) return set_error(ctx, BEM_ERR_OOM, "host allocation");
+    bt->ctx = ctx;
+    bt->P = count;
+    bt->use_graph = use_graph ? 1 : 0;
+    bt->precond = precond;
+    bt->tol = (sopts && sopts->tol > 0) ? sopts->tol : 1e-10;
+    const int max_it = (sopts && sopts->max_it > 0) ? sopts->max_it : 10000;
+    const double rd = sopts ? sopts->reliable_delta : 0.0;
+    const double delta = rd == 0.0 ? 1e-4 : (rd > 0.0 && rd < 1.0 ? rd : 0.0);
+    bt->prob.resize(count);
+    bt->args.resize(count);
+    // CTAs per problem in proportion to its bytes per product (N^2; iteration counts
+    // are alike), at least one, at most what the single-problem rule can use (a tile
+    // per warp, 8 rows per warp), so that the problems finish at about the same time
+    std::vector<int64_t> want(count);
+    double wsum = 0.0;
+    for (int p = 0; p < count; ++p) {
+        const int64_t N = meshes[p]->N, nb = padded_ld(N) / kSB, nt = nb * (nb + 1) / 2;
+        want[p] = std::min<int64_t>(std::max<int64_t>(std::max<int64_t>((nt + 7) / 8, (N + 63) / 64), 1), Gmax);
+        wsum += (double)N * (double)N;
+    }
+    std::vector<int> g(count);
+    int gsum = 0;
+    for (int p = 0; p < count; ++p) {
+        const double N = (double)meshes[p]->N;
+        const int64_t share = (int64_t)((double)(Gmax - count) * N * N / wsum) + 1;
+        g[p] = (int)std::min<int64_t>(share, want[p]);
+        gsum += g[p];
+    }
+    while (gsum > Gmax) {  // rounding: take from the largest
+        int pm = 0;
+        for (int p = 1; p < count; ++p)
+            if (g[p] > g[pm]) pm = p;
+        --g[pm];
+        --gsum;
+    }
+    bt->begin.assign(count + 1, 0);
+    for (int p = 0; p < count; ++p) bt->begin[p + 1] = bt->begin[p] + g[p];
+    bt->G = bt->begin[count];
+    for (int p = 0; p < count && !st; ++p) {
+        BatchProblem &pr = bt->prob[p];
+        st = new_operator(meshes[p], aopts, &pr.op);
+        if (st) break;
+        bem_operator *op = pr.op;
+        const int64_t N = op->N, L = op->ld;
+        const int nb = (int)(L / kSB), nt = nb * (nb + 1) / 2;
+        double *vec = nullptr;
+        float2 *xdf = nullptr, *prow = nullptr, *pcol = nullptr;
+        int2 *tiles = nullptr;
+        void *scr = nullptr;
+        const int Gp = g[p];
+        pr.part_bytes = sizeof(double) * (3 * Gp + 8) + 64;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&vec, sizeof(double) * 7 * L, true))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&xdf, sizeof(float2) * L, true))) break;
+        if ((st = dalloc(ctx, bt->allocs, &scr, symv_scratch_bytes(op), false))) break;
+        if ((st = symv_setup(op, scr, &prow, &pcol, &tiles))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&pr.vp, (size_t)nt * kTileF * sizeof(float), false))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&pr.part, pr.part_bytes, true))) break;
+        if (precond == BEM_PRECOND_BLOCK) {
+            if ((st = cluster_setup(op, bt->allocs, &pr.perm, &pr.nbj))) break;
+            if ((st = dalloc(ctx, bt->allocs, (void **)&pr.binv, sizeof(double) * kBJ * kBJ * pr.nbj, false))) break;
+        }
+        pr.x = vec + 5 * L;
+        pr.b = vec + 4 * L;
+        pr.d = vec + 6 * L;
+        PcgArgs &a = bt->args[p];
+        a.V = prec == BEM_PREC_DF64 ? (const float2 *)op->V : nullptr;
+        a.ld = L;
+        a.N = N;
+        a.nb = nb;
+        a.ntiles = nt;
+        a.tiles = tiles;
+        a.prow = prow;
+        a.pcol = pcol;
+        a.pdf = xdf;
+        a.r = vec;
+        a.z = vec + L;
+        a.p = vec + 2 * L;
+        a.q = vec + 3 * L;
+        a.b = pr.b;
+        a.x = pr.x;
+        a.d = pr.d;
+        a.part = pr.part;
+        double *outp = pr.part + 3 * Gp;
+        a.ctr = reinterpret_cast<unsigned long long *>(outp + 4);
+        a.bar = reinterpret_cast<unsigned *>(a.ctr + 1);
+        a.out = nullptr;  // set below (d_res)
+        a.err = nullptr;
+        a.vp = pr.vp;
+        a.bperm = pr.perm;
+        a.binv = pr.binv;
+        a.nbj = pr.nbj;
+        a.tol = bt->tol;
+        a.f32op = prec == BEM_PREC_F32 ? 1 : 0;
+        a.delta2 = a.f32op ? 0.0 : (delta > 0.0 ? delta * delta : 0.0);
+        a.max_it = max_it;
+        a.precond = precond;
+        a.has_x0 = 0;
+        if (!a.f32op && delta <= 0.0) a.vp = nullptr;  // DF64 products only
+    }
+    if (!st) st = dalloc(ctx, bt->allocs, (void **)&bt->d_res, sizeof(double) * kBatchRes * count, true);
+    if (!st) st = dalloc(ctx, bt->allocs, (void **)&bt->d_args, sizeof(PcgArgs) * count, false);
+    if (!st) st = dalloc(ctx, bt->allocs, (void **)&bt->d_begin, sizeof(int) * (count + 1), false);
+    if (!st) {
+        for (int p = 0; p < count; ++p) {
+            bt->args[p].out = bt->d_res + kBatchRes * p;
+            bt->args[p].err = reinterpret_cast<int *>(bt->d_res + kBatchRes * p + 6);
+        }
+        cudaError_t e = cudaMemcpyAsync(bt->d_args, bt->args.data(), sizeof(PcgArgs) * count, cudaMemcpyHostToDevice,
+                                        ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(bt->d_begin, bt->begin.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
+                                ctx->stream);
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&bt->h_res, sizeof(double) * kBatchRes * count);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "batch set-up");
+    }
+    if (st) {
+        bem_batch_destroy(bt);
+        return st;
+    }
+    *out = bt;
+    return BEM_OK;
+}
+
+bem_status bem_batch_run(bem_batch *bt, bem_batch_result *results)
+{
+    using namespace bem;
+    if (!bt) return BEM_ERR_INVALID;
+    bem_ctx *ctx = bt->ctx;
+    cudaStream_t saved = ctx->stream;
+    const int saved_profile = ctx->profile;
+    ctx->stream = bt->stream;  // the batch's work runs on its own (capturable) stream
+    ctx->profile = 0;
+    bem_status st = BEM_OK;
+    cudaError_t e = cudaSuccess;
+    if (bt->use_graph && !bt->exec) {
+        const int64_t l0 = ctx->n_launch;
+        e = cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = batch_enqueue(bt);
+            cudaGraph_t graph = nullptr;
+            const cudaError_t e2 = cudaStreamEndCapture(bt->stream, &graph);
+            if (!st && e2 == cudaSuccess) {
+                bt->graph = graph;
+                e = cudaGraphInstantiate(&bt->exec, graph, 0);
+            } else {
+                if (graph) cudaGraphDestroy(graph);
+                if (!st) e = e2;
+            }
+        }
+        bt->launches_per_run = ctx->n_launch - l0;
+        ctx->n_launch = l0;
+        if (st || e != cudaSuccess) {
+            // not capturable here: run the sequence directly from now on
+            cudaGetLastError();
+            bt->use_graph = 0;
+            bt->exec = nullptr;
+            st = BEM_OK;
+            e = cudaSuccess;
+        }
+    }
+    if (bt->use_graph && bt->exec) {
+        e = cudaGraphLaunch(bt->exec, bt->stream);
+        ctx->n_launch += bt->launches_per_run;
+        bt->graph_used = 1;
+    } else {
+        bt->graph_used = 0;
+        st = batch_enqueue(bt);
+    }
+    if (!st && e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
+    ctx->stream = saved;
+    ctx->profile = saved_profile;
+    if (!st && e != cudaSuccess) st = cuda_error(ctx, e, "batch run");
+    if (st) return st;
+    bool timeout = false, unconverged = false;
+    for (int p = 0; p < bt->P; ++p) {
+        const double *r = bt->h_res + kBatchRes * p;
+        const int err = *reinterpret_cast<const int *>(r + 6);
+        const double rel = std::sqrt(r[0] / (r[1] > 0.0 ? r[1] : 1.0));
+        timeout |= err != 0;
+        unconverged |= !(rel <= bt->tol);
+        if (results) {
+            bem_batch_result &o = results[p];
+            o.cap = r[5];
+            o.iterations = (int32_t)r[2];
+            o.outer = (int32_t)r[3];
+            o.relres = rel;
+            o.converged = (err == 0 && rel <= bt->tol) ? 1 : 0;
+            o.status = err ? BEM_ERR_CUDA : (rel <= bt->tol ? BEM_OK : BEM_ERR_NOT_CONVERGED);
+        }
+    }
+    if (timeout) return set_error(ctx, BEM_ERR_CUDA, "batch solve: a grid barrier timed out");
+    if (unconverged) return set_error(ctx, BEM_ERR_NOT_CONVERGED, "batch solve: a problem did not reach the tolerance");
+    return BEM_OK;
+}
+
+bem_status bem_batch_info(const bem_batch *bt, int32_t *count, int32_t *ctas, int32_t *graph_used)
+{
+    if (!bt) return BEM_ERR_INVALID;
+    if (count) *count = bt->P;
+    if (ctas) *ctas = bt->G;
+    if (graph_used) *graph_used = bt->graph_used;
+    return BEM_OK;
+}
+
+bem_status bem_batch_destroy(bem_batch *bt)
+{
+    using namespace bem;
+    if (!bt) return BEM_ERR_INVALID;
+    bem_ctx *ctx = bt->ctx;
+    if (bt->stream) cudaStreamSynchronize(bt->stream);
+    if (bt->exec) cudaGraphExecDestroy(bt->exec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    for (auto &pr : bt->prob)
+        if (pr.op) bem_operator_destroy(pr.op);
+    dfree_all(ctx, bt->allocs);
+    cudaStreamSynchronize(ctx->stream);
+    if (bt->h_res) cudaFreeHost(bt->h_res);
+    if (bt->stream) cudaStreamDestroy(bt->stream);
+    delete bt;
+    return BEM_OK;
+}
+
+}  // extern "C"
 
 // ------------------------------------------------------------------ no-allocation product
 // Some callers cannot let a library allocate device memory in the middle of a
