@@ -15,7 +15,8 @@
 //              reciprocal square root and one Newton step in double-float (error
 //              ~1.5 e^2 ~ 1e-14); sums by two-sum.  V stored as hi/lo pairs.
 //      F64  -- native FP64 (GB300 issues FP64 at 1/64 of the FP32 rate).
-//      F32  -- centroid difference in FP64 rounded once, offsets in FP32, MUFU rsqrt.
+//      F32  -- centroid difference from hi + lo float centroids, offsets in FP32, MUFU rsqrt;
+//              no FP64 operation per pair (GB300 issues FP64 at 1/64 of the FP32 rate).
 //  * Near field (common vertex, common edge, identical): Sauter-Schwab
 //    regularising transformations.  The 4-d integrand of each region is a power
 //    of the radial variables times a function of the others (the kernel is
@@ -163,8 +164,11 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
                                                       int64_t ld, int64_t r0, int64_t r1, int64_t c0,
                                                       int64_t c1)
 {
+    // FP32 only in the pair loop: centroids as hi + lo floats, so that the centroid
+    // difference (hi_i - hi_j) + (lo_i - lo_j) keeps FP32 relative accuracy for
+    // distant pairs; weights and areas rounded to FP32 once
     __shared__ float so[kFarRows][3 * kQ];
-    __shared__ double sc[kFarRows][4];
+    __shared__ float sc[kFarRows][7];  // centroid hi (3), lo (3), area
     const int64_t cbase = c0 + (int64_t)blockIdx.x * kFarCols;
     const int64_t i0 = r0 + (int64_t)blockIdx.y * kFarRows;
     if (i0 > cbase + kFarCols - 1 || i0 >= r1) return;
@@ -176,7 +180,14 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
     for (int k = threadIdx.x; k < kFarRows * 4; k += kFarCols) {
         const int r = k / 4, c = k % 4;
         const int64_t i = i0 + r;
-        sc[r][c] = (i < r1) ? cent[i * 4 + c] : 0.0;
+        const double v = (i < r1) ? cent[i * 4 + c] : 0.0;
+        const float h = (float)v;
+        if (c < 3) {
+            sc[r][c] = h;
+            sc[r][3 + c] = (float)(v - (double)h);
+        } else {
+            sc[r][6] = h;
+        }
     }
     __syncthreads();
     const int64_t j = cbase + threadIdx.x;
@@ -184,13 +195,24 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
     float y[3 * kQ];
 #pragma unroll
     for (int c = 0; c < 3 * kQ; ++c) y[c] = q32[j * kQ32Stride + c];
-    const double cx = cent[4 * j], cy = cent[4 * j + 1], cz = cent[4 * j + 2];
-    const double Aj = cent[4 * j + 3] * kInv4Pi;
+    float ch[3], cl[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double v = cent[4 * j + c];
+        ch[c] = (float)v;
+        cl[c] = (float)(v - (double)ch[c]);
+    }
+    const float Aj = (float)(cent[4 * j + 3] * kInv4Pi);
+    float wf[kQ];  // the weights rounded to FP32 once (c_w7df[.].x = nearest float)
+#pragma unroll
+    for (int a = 0; a < kQ; ++a) wf[a] = c_w7df[a].x;
     const int rows = (int)((r1 - i0) < kFarRows ? (r1 - i0) : kFarRows);
     for (int r = 0; r < rows; ++r) {
         const int64_t i = i0 + r;
         if (i > j) break;
-        const float Dx = (float)(sc[r][0] - cx), Dy = (float)(sc[r][1] - cy), Dz = (float)(sc[r][2] - cz);
+        const float Dx = (sc[r][0] - ch[0]) + (sc[r][3] - cl[0]);
+        const float Dy = (sc[r][1] - ch[1]) + (sc[r][4] - cl[1]);
+        const float Dz = (sc[r][2] - ch[2]) + (sc[r][5] - cl[2]);
         float acc = 0.0f;
 #pragma unroll
         for (int a = 0; a < kQ; ++a) {
@@ -199,11 +221,11 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
 #pragma unroll
             for (int b = 0; b < kQ; ++b) {
                 const float dx = xa - y[3 * b], dy = ya - y[3 * b + 1], dz = za - y[3 * b + 2];
-                s += (float)c_w7[b] * rsqrtf(dx * dx + dy * dy + dz * dz);
+                s += wf[b] * rsqrtf(dx * dx + dy * dy + dz * dz);
             }
-            acc += (float)c_w7[a] * s;
+            acc += wf[a] * s;
         }
-        V[i * ld + j] = (float)(sc[r][3] * Aj * (double)acc);
+        V[i * ld + j] = sc[r][6] * Aj * acc;
     }
 }
 
