@@ -42,7 +42,7 @@ FAR_FLOPS_PER_ENTRY = 49 * 11 + 16  # FP64 far field: per point pair 3 sub, 5 fo
 # row point, 92 per pair), against the FP32 issue peak 152 SMs x 128 lanes x 2.07 GHz.
 DF_FAR_OPS_PER_ENTRY = 49 * 74 + 7 * 45 + 92
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
-PCG_TRAFFIC_RATIO = 31.483 / 31.541  # ncu DRAM bytes / algorithmic bytes of the persistent solver
+PCG_TRAFFIC_RATIO = 18.043 / 18.294  # ncu DRAM bytes / algorithmic bytes of the persistent solver
 PRECISIONS = {"df64": 2, "f64": 0, "f32": 1}
 PREC = 2
 PC = 1
@@ -499,7 +499,7 @@ def main():
         avg_s = mv_ms / max(mv_n, 1) / 1e3
         achieved = bytes_ / avg_s / 1e9
         # DRAM bytes (read + write) over algorithmic bytes of one ncu capture of k_pcg_df
-        # (adaptive polycube level N = 12,558: 31.48 GB measured, 31.54 GB algorithmic);
+        # (adaptive polycube level N = 12,558: 18.04 GB measured, 18.29 GB algorithmic);
         # traffic scales with the bytes of the products, so the ratio carries to full size
         traffic = PCG_TRAFFIC_RATIO * bytes_ if PREC == 2 else None
         roof = {"kernel": {0: "k_matvec<double>", 1: "k_matvec<float>",
