@@ -162,6 +162,52 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
 
 
+def condition_workload(args):
+    """Condition numbers of the systems of the adaptive loop (Sec. 3, Figs. 6 and 12,
+    for the primal P0 space): the adaptive polycube run with each preconditioner
+    (none, diag(V), block Jacobi); per level, lambda_max / lambda_min of M^-1 V
+    estimated from the CG coefficients (Lanczos; DF64 products throughout, so the
+    recurrence is not perturbed by residual replacements).  value = the estimate at
+    the final level with diag(V)."""
+    import torch
+
+    from paper_1901_08393_gb300 import bem, build, inputs
+
+    build.build()
+    ctx = bem.Context()
+    m = inputs.workload_polycube_adaptive()
+    mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+    table = {}
+    for name, pc in (("none", bem.PRECOND_NONE), ("jacobi", bem.PRECOND_JACOBI), ("block", bem.PRECOND_BLOCK)):
+        rows = []
+        cur = mesh
+        while True:
+            op = bem.Operator.assemble(cur, precision=bem.PREC_DF64)
+            _, phi, info = bem.solve_capacity(op, tol=TOL, precond=pc, reliable_delta=-1.0, max_it=20000,
+                                              raise_not_converged=False)
+            op.close()
+            rows.append({"N": cur.N, "iterations": info["iterations"],
+                         "kappa": info["lambda_max"] / info["lambda_min"] if info["lambda_min"] > 0 else None})
+            if cur.N >= args.max_n:
+                break
+            eta2, _, _ = bem.zz_estimate(cur, phi)
+            marked, _ = bem.dorfler(ctx, eta2, THETA)
+            nxt = bem.refine(cur, marked)
+            if cur is not mesh:
+                cur.close()
+            cur = nxt
+        if cur is not mesh:
+            cur.close()
+        table[name] = rows
+        torch.cuda.synchronize()
+    line = {"metric": "condition number of M^-1 V (Lanczos estimate from CG)",
+            "value": table["jacobi"][-1]["kappa"], "unit": "lambda_max / lambda_min", "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": False, "dtype": "df64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "max_n": args.max_n}, "levels": table}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def batch_workload(args):
     """Batching (BASELINE config 4) through bem_batch_*: inputs.batch_meshes (seed 4:
     polycubes g in 3..10, p in [0.3, 0.7], uniform meshes, log-uniform 500..30,000
@@ -353,7 +399,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--max-n", type=int, default=MAX_N, help="smaller case of the same workload (profiling)")
     ap.add_argument("--workload", default="adaptive",
-                    choices=["adaptive", "graded60k", "serve", "batch", "batch-server"],
+                    choices=["adaptive", "graded60k", "serve", "batch", "batch-server", "condition"],
                     help="adaptive: the default workload above; graded60k: precision form (one FP32 "
                          "assembly + FP64-refined solve on the 60,492-triangle graded cube per step); "
                          "serve: Poisson stream of adaptive requests through the continuous-batching server; "
@@ -374,6 +420,8 @@ def main():
         args.precond = "jacobi" if args.workload == "graded60k" else "block"
     if args.workload == "batch":
         return batch_workload(args)
+    if args.workload == "condition":
+        return condition_workload(args)
     if args.workload in ("serve", "batch-server"):
         return server_workload(args)
 

@@ -96,6 +96,13 @@ typedef struct {
                               with the DF64 product (initial one included); FP64: 1 */
     double relres;         /* final ||b - V x|| / ||b|| in FP64 */
     int32_t converged;     /* 1 if relres <= tol */
+    /* Estimates of the extreme eigenvalues of the preconditioned operator M^-1 V (the
+     * condition number of Sec. 3, Figs. 6 and 12, is lambda_max / lambda_min): the
+     * extreme eigenvalues of the Lanczos tridiagonal matrix formed from the CG
+     * coefficients (diagonal 1/alpha_j + beta_(j-1)/alpha_(j-1), off-diagonal
+     * sqrt(beta_j)/alpha_j).  Persistent solver only; 0 otherwise.  With residual
+     * replacements (mixed precision) the recurrence is perturbed at those steps. */
+    double lambda_min, lambda_max;
 } bem_solve_info;
 
 /* ---------------------------------------------------------------- context */

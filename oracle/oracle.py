@@ -25,7 +25,8 @@ __all__ = [
     "build", "lib", "gauss_legendre01", "radon7", "geometry", "pair_far", "pair_identical",
     "pair_edge", "pair_vertex", "pair_type", "entry", "entries", "assemble", "pcg",
     "solve_cholesky", "capacity", "zz", "dorfler", "canonical", "refine", "num_threads",
-    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_inverses", "block_jacobi_pcg",
+    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_inverses", "block_jacobi_pcg", "cg_lanczos_extremes",
+    "preconditioned_extremes",
 ]
 
 
@@ -327,6 +328,57 @@ def block_jacobi_pcg(V, b, order, B=64, tol=1e-12, maxit=20000, x0=None):
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, maxit
+
+
+def cg_lanczos_extremes(V, b, precond=1, tol=1e-12, maxit=20000):
+    """Estimates of the extreme eigenvalues of the preconditioned operator (Sec. 3,
+    Figs. 6 and 12 report its condition number) from CG: plain numpy PCG (precond 0:
+    none, 1: diag(V)) records alpha_j and beta_j; the Lanczos tridiagonal matrix has
+    diagonal 1/alpha_j + beta_(j-1)/alpha_(j-1) and off-diagonal sqrt(beta_j)/alpha_j;
+    its extreme eigenvalues (numpy eigvalsh, a library primitive).  Returns
+    (lambda_min, lambda_max, iterations)."""
+    V, b = np.asarray(V, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    dinv = 1.0 / np.diag(V) if precond == 1 else np.ones_like(b)
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = dinv * r
+    p = z.copy()
+    rz = float(r @ z)
+    bn = float(np.linalg.norm(b))
+    alphas, betas = [], []
+    for _ in range(maxit):
+        if np.linalg.norm(r) <= tol * bn:
+            break
+        q = V @ p
+        alpha = rz / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        z = dinv * r
+        rz_new = float(r @ z)
+        beta = rz_new / rz
+        alphas.append(alpha)
+        betas.append(beta)
+        p = z + beta * p
+        rz = rz_new
+    k = len(alphas)
+    T = np.zeros((k, k))
+    for j in range(k):
+        T[j, j] = 1.0 / alphas[j] + (betas[j - 1] / alphas[j - 1] if j > 0 else 0.0)
+        if j + 1 < k:
+            T[j, j + 1] = T[j + 1, j] = math.sqrt(betas[j]) / alphas[j]
+    w = np.linalg.eigvalsh(T)
+    return float(w[0]), float(w[-1]), k
+
+
+def preconditioned_extremes(V, precond=1):
+    """Exact extreme eigenvalues of D^-1/2 V D^-1/2 (precond 1, D = diag(V)) or of V
+    (precond 0), by numpy eigvalsh."""
+    V = np.asarray(V, dtype=np.float64)
+    if precond == 1:
+        s = 1.0 / np.sqrt(np.diag(V))
+        V = V * s[:, None] * s[None, :]
+    w = np.linalg.eigvalsh(V)
+    return float(w[0]), float(w[-1])
 
 
 def adaptive_run(verts, tris, theta=0.5, max_N=2000, n_ss=4, tol=1e-12, h_mode=0,

@@ -56,7 +56,7 @@ class SolveOpts(C.Structure):
 
 class SolveInfo(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("outer", C.c_int32), ("relres", C.c_double),
-                ("converged", C.c_int32)]
+                ("converged", C.c_int32), ("lambda_min", C.c_double), ("lambda_max", C.c_double)]
 
 
 class LevelRecord(C.Structure):
@@ -370,7 +370,8 @@ def solve_capacity(op: Operator, tol=1e-10, max_it=10000, precond=PRECOND_JACOBI
     if st != BEM_OK and (st != BEM_ERR_NOT_CONVERGED or raise_not_converged):
         op.ctx.check(st)
     return float(cap.value), phi, {"iterations": info.iterations, "outer": info.outer,
-                                   "relres": info.relres, "converged": bool(info.converged)}
+                                   "relres": info.relres, "converged": bool(info.converged),
+                                   "lambda_min": info.lambda_min, "lambda_max": info.lambda_max}
 
 
 def zz_estimate(mesh: Mesh, phi, h_mode=0):

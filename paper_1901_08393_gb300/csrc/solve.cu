@@ -12,6 +12,7 @@
 // N = 60k) would sit at the inner tolerance, and the product is HBM-bound either way.
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "bem_internal.cuh"
 #include "dfloat.cuh"
@@ -900,6 +901,8 @@ struct PcgArgs {
     double tol, delta2;
     int max_it, precond, has_x0, nbj;
     int f32op;                // FP32 operator: every product (residuals too) from vp
+    double *lanczos;          // nullable: (alpha_j, beta_j) of iteration j < lanczos_cap
+    int lanczos_cap;
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int G)
@@ -1117,6 +1120,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
             ++ndf;
         }
         const double beta = rz_new / rz;
+        if (a.lanczos && cta == 0 && threadIdx.x == 0 && it - 1 < a.lanczos_cap) {
+            a.lanczos[2 * (it - 1)] = alpha;
+            a.lanczos[2 * (it - 1) + 1] = beta;
+        }
         rz = rz_new;
         for (int64_t i = i0; i < a.N; i += stride) {
             const double pi = a.z[i] + beta * a.p[i];
@@ -1367,6 +1374,42 @@ static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out,
     return BEM_OK;
 }
 
+// Extreme eigenvalues of the symmetric tridiagonal matrix with diagonal d and
+// off-diagonal e, by bisection on Sturm counts inside the Gershgorin interval.
+static void tridiag_extremes(const std::vector<double> &d, const std::vector<double> &e, double *lmin, double *lmax)
+{
+    const int k = (int)d.size();
+    double gl = INFINITY, gh = -INFINITY;
+    for (int i = 0; i < k; ++i) {
+        const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0);
+        gl = std::min(gl, d[i] - r);
+        gh = std::max(gh, d[i] + r);
+    }
+    auto below = [&](double x) {  // eigenvalues < x
+        int c = 0;
+        double q = 1.0;
+        for (int i = 0; i < k; ++i) {
+            q = (d[i] - x) - (i > 0 ? e[i - 1] * e[i - 1] / q : 0.0);
+            if (q == 0.0) q = -1e-300;
+            if (q < 0.0) ++c;
+        }
+        return c;
+    };
+    auto bisect = [&](int target) {  // smallest x with below(x) >= target
+        double a = gl, b = gh;
+        for (int it = 0; it < 200 && b - a > 1e-15 * std::max(std::fabs(a), std::fabs(b)); ++it) {
+            const double m = 0.5 * (a + b);
+            if (below(m) >= target)
+                b = m;
+            else
+                a = m;
+        }
+        return b;
+    };
+    *lmin = bisect(1);
+    *lmax = bisect(k);
+}
+
 // delta > 0 selects the mixed mode: the products of the iteration use the packed
 // FP32 hi parts of the upper triangle, and the residual is recomputed with the DF64
 // product whenever ||r|| has dropped by delta since the last such residual (and at
@@ -1374,7 +1417,8 @@ static bem_status block_setup(bem_operator *op, Allocs &tmp, int32_t **perm_out,
 // solve runs with DF64 products only.
 static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, bool has_x0, double tol, int max_it,
                                  int precond, double delta, const int32_t *bperm, const double *binv, int nbj,
-                                 int *its_out, int *ndf_out, double *rel_out, bool *ran)
+                                 int *its_out, int *ndf_out, double *rel_out, bool *ran, double *lmin,
+                                 double *lmax)
 {
     // FP32 operators: the products of the iteration and of the residuals read the
     // packed copy of the stored operator (the residual, formed from x with
@@ -1418,6 +1462,12 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     unsigned long long *ctr = reinterpret_cast<unsigned long long *>(out + 4);
     unsigned *bar = reinterpret_cast<unsigned *>(ctr + 1);
     int *err = reinterpret_cast<int *>(bar + 2);
+    const int lcap = std::min(max_it, 20000);
+    double *lanczos = nullptr;
+    if ((st = dalloc(ctx, tmp, (void **)&lanczos, sizeof(double) * 2 * lcap, false))) {
+        dfree_all(ctx, tmp);
+        return st;
+    }
     PcgArgs a;
     a.V = (const float2 *)op->V;
     a.ld = op->ld;
@@ -1441,6 +1491,8 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.err = err;
     a.out = out;
     a.vp = vp;
+    a.lanczos = lanczos;
+    a.lanczos_cap = lcap;
     a.bperm = bperm;
     a.binv = binv;
     a.nbj = nbj;
@@ -1484,6 +1536,23 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
                                  : vp  ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
                                        : 4.0 * n2 * (h[2] + h[3]);
             prof_set_units(ctx, prof, bytes);
+            // Lanczos tridiagonal matrix of the CG coefficients
+            const int k = std::min((int)h[2], lcap);
+            *lmin = *lmax = 0.0;
+            if (k > 0) {
+                std::vector<double> ab(2 * (size_t)k);
+                e = cudaMemcpy(ab.data(), lanczos, sizeof(double) * 2 * k, cudaMemcpyDeviceToHost);
+                if (e != cudaSuccess) {
+                    st = cuda_error(ctx, e, "CG coefficients");
+                } else {
+                    std::vector<double> dg(k), od(k > 1 ? k - 1 : 0);
+                    for (int j = 0; j < k; ++j) {
+                        dg[j] = 1.0 / ab[2 * j] + (j > 0 ? ab[2 * j - 1] / ab[2 * (j - 1)] : 0.0);
+                        if (j + 1 < k) od[j] = std::sqrt(ab[2 * j + 1]) / ab[2 * j];
+                    }
+                    tridiag_extremes(dg, od, lmin, lmax);
+                }
+            }
         }
     }
     dfree_all(ctx, tmp);
@@ -1550,6 +1619,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     int its = 0, outer = 0;
     double rel = 0.0;
     bool ran = false;
+    double lam_min = 0.0, lam_max = 0.0;
     cudaError_t e = cudaMemcpyAsync(W.b, m->area, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(W.d, op->diag, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && d_x0) e = cudaMemcpyAsync(W.x, d_x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
@@ -1570,7 +1640,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         if (precond == BEM_PRECOND_BLOCK && (st = block_setup(op, tmp, &bperm, &binv, &nbj))) goto out;
         if (op->precision != BEM_PREC_F64 && ctx->persistent_solver)
             st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, bperm,
-                                binv, nbj, &its, &outer, &rel, &ran);
+                                binv, nbj, &its, &outer, &rel, &ran, &lam_min, &lam_max);
         if (!st && !ran && precond == BEM_PRECOND_BLOCK)
             st = set_error(ctx, BEM_ERR_CUDA, "BEM_PRECOND_BLOCK: the persistent solver could not be launched");
         if (st) goto out;
@@ -1637,6 +1707,8 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         info->outer = outer;
         info->relres = rel;
         info->converged = rel <= tol;
+        info->lambda_min = lam_min;
+        info->lambda_max = lam_max;
     }
     if (rel > tol) st = set_error(ctx, BEM_ERR_NOT_CONVERGED, "solve stopped at relative residual %.3e > %.3e", rel, tol);
 out:

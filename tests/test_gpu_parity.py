@@ -383,3 +383,20 @@ def test_f32_operator_persistent_matches_refinement(ctx):
     assert abs(cb / c1 - 1) < 1e-9
     cap_r = O.solve_capacity(v, t, tol=1e-12)[0]
     assert abs(c1 / cap_r - 1) < 1e-6  # FP32 storage of V
+
+
+@pytest.mark.parametrize("precond", [bem.PRECOND_NONE, bem.PRECOND_JACOBI], ids=["none", "jacobi"])
+@pytest.mark.parametrize("m", [inputs.cube_mesh(4), inputs.workload_polycube_adaptive()], ids=lambda m: m.name)
+def test_condition_estimate_matches_oracle(ctx, m, precond):
+    """Extreme eigenvalues of M^-1 V from the CG coefficients (Lanczos) against the
+    oracle's own CG-Lanczos estimate and the exact spectrum (Sec. 3, Figs. 6, 12)."""
+    mesh, v, t = _upload(ctx, m)
+    op = bem.Operator.assemble(mesh, precision=bem.PREC_DF64)
+    _, _, info = bem.solve_capacity(op, tol=1e-12, precond=precond, reliable_delta=-1.0)
+    V = O.assemble(v, t)
+    b = O.geometry(v, t)[0]
+    lo, hi, k = O.cg_lanczos_extremes(V, b, precond=precond, tol=1e-12)
+    elo, ehi = O.preconditioned_extremes(V, precond)
+    assert abs(info["lambda_max"] / hi - 1) < 1e-6, (info, hi)
+    assert abs(info["lambda_min"] / lo - 1) < 1e-2, (info, lo)
+    assert elo * (1 - 1e-9) <= info["lambda_min"] and info["lambda_max"] <= ehi * (1 + 1e-9)

@@ -155,3 +155,31 @@ def test_block_jacobi_indefinite_block_falls_back_to_diagonal():
     assert np.allclose(inv[1], [[1.0]])
     blocks, inv = O.block_jacobi_inverses(np.eye(3) * 2 + 0.5, np.arange(3), B=2)
     assert np.allclose(inv[0], np.linalg.inv(np.eye(2) * 2 + 0.5))
+
+
+def test_cg_lanczos_extremes():
+    """Diagonal system: the Lanczos matrix of a full CG run has exactly the eigenvalues
+    of the system; BEM matrix: the estimates approach the exact extremes of the
+    preconditioned operator, for no and for diagonal preconditioning."""
+    A = np.diag(np.arange(1.0, 11.0))
+    lo, hi, k = O.cg_lanczos_extremes(A, np.ones(10), precond=0, tol=1e-14)
+    assert k == 10 and abs(lo - 1.0) < 1e-8 and abs(hi - 10.0) < 1e-8
+    m = inputs.cube_mesh(3)
+    t = O.canonical(m.verts, m.tris)
+    V = O.assemble(m.verts, t)
+    b = O.geometry(m.verts, t)[0]
+    rnd = np.random.default_rng(0).standard_normal(len(b))
+    for pc in (0, 1):
+        elo, ehi = O.preconditioned_extremes(V, pc)
+        lo, hi, k = O.cg_lanczos_extremes(V, b, precond=pc, tol=1e-14)
+        assert abs(hi / ehi - 1) < 1e-6, (pc, hi, ehi)
+        assert lo >= elo * (1 - 1e-9) and hi <= ehi * (1 + 1e-9)  # Ritz values lie inside the spectrum
+        lo, hi, k = O.cg_lanczos_extremes(V, rnd, precond=pc, tol=1e-14)  # a right-hand side with every mode
+        assert abs(lo / elo - 1) < 1e-3 and abs(hi / ehi - 1) < 1e-6, (pc, lo, elo, hi, ehi)
+    # diagonal scaling lowers the condition number of V on a graded mesh (Sec. 3)
+    g = inputs.graded_cube_mesh(8)
+    tg = O.canonical(g.verts, g.tris)
+    Vg = O.assemble(g.verts, tg)
+    k0 = np.divide(*reversed(O.preconditioned_extremes(Vg, 0)))
+    k1 = np.divide(*reversed(O.preconditioned_extremes(Vg, 1)))
+    assert k1 < k0
