@@ -162,6 +162,47 @@ def _pct(xs, q):
     return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
 
 
+CUBE_CAP = 0.66067815409957    # unit cube, best value quoted in Sec. 3.1 (error ~1e-13)
+FICHERA_CAP = 1.2912567475     # Fichera cube, the paper's finest level (Sec. 3.2 table, l = 30)
+
+
+def rates_workload(args):
+    """theta sweep and uniform-vs-adaptive rates (Sec. 3.1-3.2): the unit cube (12
+    triangles) and the Fichera cube (48) refined by ZZ + Doerfler + NVB with theta in
+    {0.2, 0.4, 0.5, 0.6, 0.8, 1.0} (theta = 1 marks every element: uniform bisection)
+    until N >= --max-n; per level |Cap_l - Cap| / Cap against the values the paper
+    quotes; rate = least-squares slope of log err over log N on the levels with
+    N >= 1000.  The paper reports O(N^-1) for adaptive and O(N^-2/3) for uniform
+    refinement.  value = the fitted rate on the cube with theta = 0.5."""
+    import numpy as np
+
+    from paper_1901_08393_gb300 import bem, build, inputs
+
+    build.build()
+    ctx = bem.Context()
+    out = {}
+    for gname, m, ref in (("cube", inputs.cube_mesh(1), CUBE_CAP), ("fichera", inputs.fichera_mesh(1), FICHERA_CAP)):
+        out[gname] = {}
+        for theta in (0.2, 0.4, 0.5, 0.6, 0.8, 1.0):
+            mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+            recs, _ = bem.adaptive_run(mesh, theta=theta, max_N=args.max_n, max_levels=200, tol=TOL,
+                                       precision=bem.PREC_DF64, precond=bem.PRECOND_BLOCK)
+            mesh.close()
+            rows = [(r["N"], r["cap"], abs(r["cap"] - ref) / ref) for r in recs]
+            fit = [(math.log(n), math.log(e)) for n, c, e in rows if n >= 1000 and e > 0]
+            rate = float(np.polyfit(*zip(*fit), 1)[0]) if len(fit) >= 2 else None
+            out[gname][str(theta)] = {"rate": rate, "levels": [{"N": n, "cap": c, "err": e} for n, c, e in rows]}
+    line = {"metric": "convergence rate of |Cap_l - Cap| in N (theta sweep; adaptive vs uniform)",
+            "value": out["cube"]["0.5"]["rate"], "unit": "d log err / d log N", "n_gpus": 1, "steps": 1,
+            "warmup": 0, "higher_is_better": False, "dtype": "df64", "data": "synthetic",
+            "config": {"workload": "unit cube (12 triangles) and Fichera cube (48), ZZ + Doerfler + NVB, "
+                                   f"DF64, PCG to 1e-10, until N >= {args.max_n}",
+                       "references": {"cube": CUBE_CAP, "fichera": FICHERA_CAP}},
+            "results": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def condition_workload(args):
     """Condition numbers of the systems of the adaptive loop (Sec. 3, Figs. 6 and 12,
     for the primal P0 space): the adaptive polycube run with each preconditioner
@@ -399,7 +440,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--max-n", type=int, default=MAX_N, help="smaller case of the same workload (profiling)")
     ap.add_argument("--workload", default="adaptive",
-                    choices=["adaptive", "graded60k", "serve", "batch", "batch-server", "condition"],
+                    choices=["adaptive", "graded60k", "serve", "batch", "batch-server", "condition", "rates"],
                     help="adaptive: the default workload above; graded60k: precision form (one FP32 "
                          "assembly + FP64-refined solve on the 60,492-triangle graded cube per step); "
                          "serve: Poisson stream of adaptive requests through the continuous-batching server; "
@@ -422,6 +463,8 @@ def main():
         return batch_workload(args)
     if args.workload == "condition":
         return condition_workload(args)
+    if args.workload == "rates":
+        return rates_workload(args)
     if args.workload in ("serve", "batch-server"):
         return server_workload(args)
 
