@@ -452,6 +452,9 @@ def main():
     ap.add_argument("--precond", default="auto", choices=["auto", "block", "jacobi"],
                     help="PCG preconditioner (block: DF64 and FP32 operators, FP64 runs Jacobi); auto: "
                          "block, except jacobi on the graded cube (its V has indefinite diagonal blocks)")
+    ap.add_argument("--inexact", type=float, default=0.0,
+                    help="adaptive workload: stop each solve by the rule of the Remark after Alg. 1 (i), "
+                         "|||x_k - x_(k-1)||| <= LAMBDA eta(x_k) (the paper uses ~1e-3); 0: PCG to 1e-10")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
@@ -509,7 +512,8 @@ def main():
     def step():
         if graded:
             return step_graded(mesh)
-        recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC)
+        recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC,
+                                   inexact_lambda=args.inexact)
         return recs
 
     for _ in range(max(args.warmup, 0)):
@@ -614,7 +618,8 @@ def main():
         if graded:
             r2 = step_graded(mh)
         else:
-            r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC)
+            r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC,
+                                     inexact_lambda=args.inexact)
         cap_final = r2[-1]["cap"]
         mh.close()
         torch.cuda.synchronize()
@@ -629,7 +634,8 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-        "config": {"workload": WORKLOAD, "precision": args.precision, "preconditioner": PC_LABEL[pc_name],
+        "config": {"workload": WORKLOAD + (f" [inexact solves: lambda = {args.inexact}]" if args.inexact else ""),
+                   "precision": args.precision, "preconditioner": PC_LABEL[pc_name],
                    "final_N": recs[-1]["N"], "levels": len(recs),
                    "cap_final": recs[-1]["cap"], "parallelism": f"replicas x{ws}",
                    "l2": "256 MB buffer written before every step; V (up to 3.2 GB) exceeds L2"},

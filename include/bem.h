@@ -88,6 +88,12 @@ typedef struct {
                               last such residual and before convergence is declared, so tol
                               holds for the DF64 operator.  0: default 1e-4; < 0 or >= 1: DF64
                               products only */
+    double inexact_lambda; /* > 0 (persistent solver): stop as soon as the update's energy norm
+                              |||x_k - x_(k-1)||| <= inexact_lambda * eta(x_k), eta the ZZ estimator
+                              of the iterate (Remark (i) after Alg. 1; the paper uses ~1e-3);
+                              such a stop counts as converged.  0: off (tol only) */
+    int32_t h_mode;        /* ZZ weight of that estimator, as bem_zz_estimate (bem_adaptive_run
+                              takes its own h_mode) */
 } bem_solve_opts;
 
 typedef struct {

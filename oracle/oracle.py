@@ -25,7 +25,7 @@ __all__ = [
     "build", "lib", "gauss_legendre01", "radon7", "geometry", "pair_far", "pair_identical",
     "pair_edge", "pair_vertex", "pair_type", "entry", "entries", "assemble", "pcg",
     "solve_cholesky", "capacity", "zz", "dorfler", "canonical", "refine", "num_threads",
-    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_inverses", "block_jacobi_pcg", "cg_lanczos_extremes",
+    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_inverses", "block_jacobi_pcg", "cg_lanczos_extremes", "pcg_inexact",
     "preconditioned_extremes",
 ]
 
@@ -381,17 +381,59 @@ def preconditioned_extremes(V, precond=1):
     return float(w[0]), float(w[-1])
 
 
+def pcg_inexact(V, b, verts, tris, lam, x0=None, precond=1, tol=1e-12, maxit=20000, h_mode=0):
+    """Jacobi (precond 1) or plain PCG with the stopping rule of the Remark after
+    Alg. 1 (i), on the primal P0 space: after iteration k stop if
+    |||x_k - x_(k-1)|||^2 = alpha_k (r.z) <= lam^2 sum_T eta_T^2(x_k), eta the ZZ
+    indicators of the iterate (Eq. 1.6, `zz`); also at ||r|| <= tol ||b||.  Plain
+    numpy.  Returns (x, iterations, stopped_by_rule, history of (upd2, eta2))."""
+    V, b = np.asarray(V, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    dinv = 1.0 / np.diag(V) if precond == 1 else np.ones_like(b)
+    x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - V @ x
+    z = dinv * r
+    p = z.copy()
+    rz = float(r @ z)
+    bn = float(np.linalg.norm(b))
+    hist = []
+    for it in range(maxit):
+        if np.linalg.norm(r) <= tol * bn:
+            return x, it, False, hist
+        q = V @ p
+        alpha = rz / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        upd2 = alpha * rz
+        eta2 = float(np.sum(zz(verts, tris, x, h_mode)))
+        hist.append((upd2, eta2))
+        if upd2 <= lam * lam * eta2:
+            return x, it + 1, True, hist
+        z = dinv * r
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, maxit, False, hist
+
+
 def adaptive_run(verts, tris, theta=0.5, max_N=2000, n_ss=4, tol=1e-12, h_mode=0,
-                 max_levels=100, callback=None):
+                 max_levels=100, callback=None, inexact_lambda=0.0):
     """Algorithm 1 on the primal P0 space: solve -> estimate -> mark -> refine
     until the mesh has at least max_N triangles; the previous level's solution,
-    copied to the children, starts the next solve.  Returns one record per level."""
+    copied to the children, starts the next solve (inexact_lambda > 0: stopped by
+    the rule of the Remark after Alg. 1 (i), `pcg_inexact`).  Returns one record per
+    level."""
     t = canonical(verts, tris)
     v = _f64(verts)
     hist = []
     x_prev = None
     for lvl in range(max_levels):
-        cap, x, its, _ = solve_capacity(v, t, n_ss=n_ss, tol=tol, x0=x_prev)
+        if inexact_lambda > 0.0:
+            V = assemble(v, t, n_ss)
+            area = geometry(v, t)[0]
+            x, its, _, _ = pcg_inexact(V, area, v, t, inexact_lambda, x0=x_prev, tol=tol, h_mode=h_mode)
+            cap = capacity(area, x)
+        else:
+            cap, x, its, _ = solve_capacity(v, t, n_ss=n_ss, tol=tol, x0=x_prev)
         eta2, scale = zz(v, t, x, h_mode, with_scale=True)
         rec = {"level": lvl, "N": t.shape[0], "M": v.shape[0], "cap": cap, "its": its,
                "eta2_total": float(np.sum(eta2)), "x": x, "eta2": eta2,

@@ -51,7 +51,8 @@ class AssemblyOpts(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_it", C.c_int32), ("precond", C.c_int32),
-                ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("reliable_delta", C.c_double)]
+                ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
+                ("inexact_lambda", C.c_double), ("h_mode", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -354,9 +355,10 @@ class Operator:
 
 
 def solve_capacity(op: Operator, tol=1e-10, max_it=10000, precond=PRECOND_JACOBI, x0=None,
-                   max_outer=20, inner_tol=1e-5, phi_out=None, raise_not_converged=True, reliable_delta=0.0):
+                   max_outer=20, inner_tol=1e-5, phi_out=None, raise_not_converged=True, reliable_delta=0.0,
+                   inexact_lambda=0.0, h_mode=0):
     """Cap and x with V x = |T| (Eq. 2.5, 2.8).  phi_out may be a CUDA tensor."""
-    o = SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta)
+    o = SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode)
     info = SolveInfo()
     cap = C.c_double()
     N = op.info()[0]
@@ -412,10 +414,11 @@ def mark_refine(mesh: Mesh, eta2, theta=0.5, bisec3=False):
 
 def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, precision=PREC_F64,
                  ss_order=4, tol=1e-12, max_it=20000, precond=PRECOND_JACOBI, incremental=True,
-                 max_outer=20, inner_tol=1e-5, want_final=False, reliable_delta=0.0):
+                 max_outer=20, inner_tol=1e-5, want_final=False, reliable_delta=0.0, inexact_lambda=0.0):
     """Alg. 1 in the library's native loop; returns (records, final Mesh or None)."""
     o = AdaptiveOpts(theta, max_N, max_levels, h_mode, AssemblyOpts(precision, ss_order),
-                     SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta), int(incremental))
+                     SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode),
+                     int(incremental))
     recs = (LevelRecord * max_levels)()
     n = C.c_int32()
     fin = C.c_void_p()

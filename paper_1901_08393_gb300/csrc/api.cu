@@ -633,6 +633,8 @@ static bem_solve_opts default_solve_opts()
     o.max_outer = 20;
     o.inner_tol = 1e-5;
     o.reliable_delta = 0.0;
+    o.inexact_lambda = 0.0;
+    o.h_mode = 0;
     return o;
 }
 
@@ -789,7 +791,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         }
         bem_solve_info info{};
         double cap = 0.0;
-        st = solve_capacity(op, &opts->solve, x0, x, &cap, &info);
+        bem_solve_opts so = opts->solve;
+        so.h_mode = opts->h_mode;  // the estimator of the inexact stopping rule
+        st = solve_capacity(op, &so, x0, x, &cap, &info);
         rec.cap = cap;
         rec.iterations = info.iterations;
         rec.outer = info.outer;

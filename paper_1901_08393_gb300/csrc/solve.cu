@@ -903,6 +903,14 @@ struct PcgArgs {
     int f32op;                // FP32 operator: every product (residuals too) from vp
     double *lanczos;          // nullable: (alpha_j, beta_j) of iteration j < lanczos_cap
     int lanczos_cap;
+    // inexact stopping (Remark (i) after Alg. 1): stop once the energy norm of the
+    // update satisfies |||x_k - x_(k-1)|||^2 <= lam2 * eta^2(x_k), eta the ZZ estimator
+    // of the iterate (Eq. 1.6, primal P0 reading); lam2 = 0: off
+    double lam2;
+    const int32_t *tris, *v2t_off, *v2t;
+    const double *area, *hdiam;  // hdiam: diam(T), or null for h_T = |T|^1/2
+    double *u;                   // M nodal values
+    int64_t M;
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int G)
@@ -1034,7 +1042,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     const double bb = grid_total(pC, G);
     const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
     double rr_true = rr;  // r.r at the last residual formed with the DF64 product
-    int it = 0, ndf = prod0 ? 1 : 0;
+    int it = 0, ndf = prod0 ? 1 : 0, inexact_stop = 0;
     if (!grid_barrier(a.bar, a.err, G)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
         if (mixed) {
@@ -1084,6 +1092,35 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         double rz_new = grid_total(pB, G);
         rr = grid_total(pC, G);
         ++it;
+        if (a.lam2 > 0.0) {
+            // |||alpha p|||^2 = alpha^2 p.Vp = alpha (r.z); ZZ estimator of the iterate
+            const double upd2 = alpha * rz;
+            for (int64_t z = i0; z < a.M; z += stride) {
+                double num = 0.0, den = 0.0;
+                for (int32_t q = a.v2t_off[z]; q < a.v2t_off[z + 1]; ++q) {
+                    const int32_t t = a.v2t[q];
+                    num += a.area[t] * __ldcg(a.x + t);  // x of other CTAs' rows: L2
+                    den += a.area[t];
+                }
+                a.u[z] = den > 0.0 ? num / den : 0.0;
+            }
+            if (!grid_barrier(a.bar, a.err, G)) return;
+            double el = 0.0;
+            for (int64_t t = i0; t < a.N; t += stride) {
+                double d[3];
+                for (int k = 0; k < 3; ++k) d[k] = __ldcg(a.u + a.tris[3 * t + k]) - a.x[t];
+                const double s2 = (d[0] * d[0] + d[1] * d[1]) + d[2] * d[2];
+                const double s1 = (d[0] + d[1]) + d[2];
+                const double h = a.hdiam ? a.hdiam[t] : sqrt(a.area[t]);
+                el += (h * a.area[t]) / 12.0 * (s2 + s1 * s1);
+            }
+            cta_partial(el, pA, cta);
+            if (!grid_barrier(a.bar, a.err, G)) return;
+            if (upd2 <= a.lam2 * grid_total(pA, G)) {
+                inexact_stop = 1;
+                break;
+            }
+        }
         if (mixed && (rr <= a.delta2 * rr_true || rr <= thr)) {
             // reliable update: replace the recursive residual by b - V x with the
             // DF64 product (the direction p is kept)
@@ -1137,6 +1174,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         a.out[1] = bb;
         a.out[2] = (double)it;
         a.out[3] = (double)ndf;
+        a.out[4] = (double)inexact_stop;
     }
 }
 
@@ -1417,8 +1455,8 @@ static void tridiag_extremes(const std::vector<double> &d, const std::vector<dou
 // solve runs with DF64 products only.
 static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, bool has_x0, double tol, int max_it,
                                  int precond, double delta, const int32_t *bperm, const double *binv, int nbj,
-                                 int *its_out, int *ndf_out, double *rel_out, bool *ran, double *lmin,
-                                 double *lmax)
+                                 double inexact_lambda, int h_mode, int *its_out, int *ndf_out, double *rel_out,
+                                 bool *ran, double *lmin, double *lmax, bool *inexact_out)
 {
     // FP32 operators: the products of the iteration and of the residuals read the
     // packed copy of the stored operator (the residual, formed from x with
@@ -1458,11 +1496,16 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
         dfree_all(ctx, tmp);
         return st;
     }
-    double *out = part + 3 * G;
-    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(out + 4);
+    double *out = part + 3 * G;  // [0..4]: r.r, b.b, iterations, DF64 residuals, inexact stop
+    unsigned long long *ctr = reinterpret_cast<unsigned long long *>(out + 6);
     unsigned *bar = reinterpret_cast<unsigned *>(ctr + 1);
     int *err = reinterpret_cast<int *>(bar + 2);
     const int lcap = std::min(max_it, 20000);
+    double *unod = nullptr;
+    if (inexact_lambda > 0.0 && (st = dalloc(ctx, tmp, (void **)&unod, sizeof(double) * op->mesh->M, false))) {
+        dfree_all(ctx, tmp);
+        return st;
+    }
     double *lanczos = nullptr;
     if ((st = dalloc(ctx, tmp, (void **)&lanczos, sizeof(double) * 2 * lcap, false))) {
         dfree_all(ctx, tmp);
@@ -1493,6 +1536,14 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.vp = vp;
     a.lanczos = lanczos;
     a.lanczos_cap = lcap;
+    a.lam2 = inexact_lambda > 0.0 ? inexact_lambda * inexact_lambda : 0.0;
+    a.tris = op->mesh->tris;
+    a.v2t_off = op->mesh->v2t_off;
+    a.v2t = op->mesh->v2t;
+    a.area = op->mesh->area;
+    a.hdiam = h_mode == 1 ? nullptr : op->mesh->diam;
+    a.u = unod;
+    a.M = op->mesh->M;
     a.bperm = bperm;
     a.binv = binv;
     a.nbj = nbj;
@@ -1513,18 +1564,19 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
         dfree_all(ctx, tmp);
         return BEM_OK;  // not launchable here: fall back
     }
-    double h[4];
-    e = cudaMemcpyAsync(ctx->h_pinned, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 4, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    double h[5];
+    e = cudaMemcpyAsync(ctx->h_pinned, out, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 5, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) st = cuda_error(ctx, e, "persistent solve");
     if (!st) {
         memcpy(h, ctx->h_pinned, sizeof(h));
-        const int err_h = *reinterpret_cast<int *>(ctx->h_pinned + 4);
+        const int err_h = *reinterpret_cast<int *>(ctx->h_pinned + 5);
         if (err_h) {
             st = set_error(ctx, BEM_ERR_CUDA, "persistent solve: grid barrier timed out");
         } else {
             *ran = true;
+            *inexact_out = h[4] != 0.0;
             *its_out = (int)h[2];
             *ndf_out = vp ? (int)h[3] : 1;
             *rel_out = std::sqrt(h[0] / (h[1] > 0.0 ? h[1] : 1.0));
@@ -1537,7 +1589,7 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
                                        : 4.0 * n2 * (h[2] + h[3]);
             prof_set_units(ctx, prof, bytes);
             // Lanczos tridiagonal matrix of the CG coefficients
-            const int k = std::min((int)h[2], lcap);
+            const int k = std::min((int)h[2] - (h[4] != 0.0 ? 1 : 0), lcap);  // an inexact stop records no beta
             *lmin = *lmax = 0.0;
             if (k > 0) {
                 std::vector<double> ab(2 * (size_t)k);
@@ -1620,6 +1672,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     double rel = 0.0;
     bool ran = false;
     double lam_min = 0.0, lam_max = 0.0;
+    bool inexact = false;
     cudaError_t e = cudaMemcpyAsync(W.b, m->area, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(W.d, op->diag, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess && d_x0) e = cudaMemcpyAsync(W.x, d_x0, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
@@ -1640,7 +1693,8 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         if (precond == BEM_PRECOND_BLOCK && (st = block_setup(op, tmp, &bperm, &binv, &nbj))) goto out;
         if (op->precision != BEM_PREC_F64 && ctx->persistent_solver)
             st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, bperm,
-                                binv, nbj, &its, &outer, &rel, &ran, &lam_min, &lam_max);
+                                binv, nbj, o->inexact_lambda, o->h_mode, &its, &outer, &rel, &ran, &lam_min, &lam_max,
+                                &inexact);
         if (!st && !ran && precond == BEM_PRECOND_BLOCK)
             st = set_error(ctx, BEM_ERR_CUDA, "BEM_PRECOND_BLOCK: the persistent solver could not be launched");
         if (st) goto out;
@@ -1706,11 +1760,12 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         info->iterations = its;
         info->outer = outer;
         info->relres = rel;
-        info->converged = rel <= tol;
+        info->converged = rel <= tol || inexact;
         info->lambda_min = lam_min;
         info->lambda_max = lam_max;
     }
-    if (rel > tol) st = set_error(ctx, BEM_ERR_NOT_CONVERGED, "solve stopped at relative residual %.3e > %.3e", rel, tol);
+    if (rel > tol && !inexact)
+        st = set_error(ctx, BEM_ERR_NOT_CONVERGED, "solve stopped at relative residual %.3e > %.3e", rel, tol);
 out:
     dfree_all(ctx, tmp);
     return st;

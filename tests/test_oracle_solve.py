@@ -183,3 +183,23 @@ def test_cg_lanczos_extremes():
     k0 = np.divide(*reversed(O.preconditioned_extremes(Vg, 0)))
     k1 = np.divide(*reversed(O.preconditioned_extremes(Vg, 1)))
     assert k1 < k0
+
+
+def test_pcg_inexact_stopping_rule():
+    """The rule of the Remark after Alg. 1 (i): it holds at the returned iterate and at
+    no earlier one; lambda -> 0 gives the tolerance-stopped Jacobi PCG."""
+    m = inputs.workload_polycube_adaptive()
+    t = O.canonical(m.verts, m.tris)
+    V = O.assemble(m.verts, t)
+    b = O.geometry(m.verts, t)[0]
+    x, its, rule, hist = O.pcg_inexact(V, b, m.verts, t, 1e-2, tol=1e-12)
+    assert rule and len(hist) == its
+    assert hist[-1][0] <= 1e-4 * hist[-1][1]
+    assert all(u > 1e-4 * e for u, e in hist[:-1])
+    x0, its0, rule0, _ = O.pcg_inexact(V, b, m.verts, t, 0.0, tol=1e-12)
+    xo, itso, _, _ = O.pcg(V, b, tol=1e-12, precond=1)
+    assert not rule0 and abs(its0 - itso) <= 1 and its < its0
+    assert np.max(np.abs(x0 - xo)) < 1e-10 * np.max(np.abs(xo))
+    # the capacity of the early-stopped iterate is within lambda * eta of the solution
+    area = b
+    assert abs(O.capacity(area, x) / O.capacity(area, xo) - 1) < 1e-3
