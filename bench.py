@@ -203,6 +203,115 @@ def rates_workload(args):
     return 0
 
 
+def dual_workload(args):
+    """The paper's own discretisation (Sec. 2.1-2.6): piecewise constants on the dual
+    mesh.  One step = one adaptive run on the unit cube (12 triangles) in the dual
+    basis: per level the barycentric refinement, its operator (DF64), V^dual = P^T V^bary P,
+    block-Jacobi PCG to 1e-10, the ZZ estimate of Eq. 1.6 on the dual density, Doerfler
+    (theta = 0.5) and NVB of the primal mesh, until N >= --max-n (default 5,000 here:
+    the barycentric operator at that level has 30,000^2 entries).  Untimed beside it:
+    the Fichera cube in the dual basis and both geometries in the P0 basis to the same N,
+    with |Cap_l - Cap| / Cap against the values the paper quotes.  value = dual-basis
+    adaptive runs per second."""
+    import numpy as np
+    import torch
+
+    from paper_1901_08393_gb300 import bem, build, inputs
+
+    max_n = args.max_n if args.max_n != MAX_N else 5000
+    build.build()
+    ctx = bem.Context()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    cube = inputs.cube_mesh(1)
+    mesh = bem.Mesh.upload(ctx, cube.verts, cube.tris)
+
+    def run(msh, basis, n=max_n):
+        return bem.adaptive_run(msh, theta=THETA, max_N=n, max_levels=200, tol=TOL, precision=bem.PREC_DF64,
+                                precond=bem.PRECOND_BLOCK, basis=basis)[0]
+
+    for _ in range(max(args.warmup, 0)):
+        flush.fill_(1)
+        run(mesh, bem.BASIS_DUAL)
+    clocks = Clocks(torch.cuda.current_device())
+    launches0 = ctx.launch_count()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    recs = None
+    for k in range(args.steps):
+        flush.fill_(1)
+        ev[2 * k].record(stream)
+        recs = run(mesh, bem.BASIS_DUAL)
+        ev[2 * k + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    step_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
+    total_ms = sum(step_ms)
+
+    # end to end: host mesh in, level records out, through the public API
+    import ctypes
+
+    e2e_t = []
+    for _ in range(0 if args.no_e2e else args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mh = bem.Mesh.upload(ctx, cube.verts, cube.tris)
+        r2 = run(mh, bem.BASIS_DUAL)
+        mh.close()
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+
+    def table(rows, ref):
+        out = [{"N": r["N"], "M": r["M"], "cap": r["cap"], "err": abs(r["cap"] - ref) / ref,
+                "its": r["iterations"], "ms": round(r["ms_assemble"] + r["ms_solve"] + r["ms_adapt"], 3)}
+               for r in rows]
+        fit = [(math.log(r["N"]), math.log(r["err"])) for r in out if r["N"] >= 500 and r["err"] > 0]
+        rate = float(np.polyfit(*zip(*fit), 1)[0]) if len(fit) >= 2 else None
+        return {"rate": rate, "levels": out}
+
+    fich = inputs.fichera_mesh(1)
+    fmesh = bem.Mesh.upload(ctx, fich.verts, fich.tris)
+    results = {"cube_dual": table(recs, CUBE_CAP), "cube_p0": table(run(mesh, bem.BASIS_P0), CUBE_CAP),
+               "fichera_dual": table(run(fmesh, bem.BASIS_DUAL), FICHERA_CAP),
+               "fichera_p0": table(run(fmesh, bem.BASIS_P0), FICHERA_CAP)}
+    line = {"metric": "dual-basis adaptive capacity runs/s (Sec. 2.6 Galerkin system, Alg. 1)",
+            "value": args.steps / (total_ms / 1e3), "unit": "adaptive runs/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
+            "config": {"workload": f"unit cube (12 triangles), dual basis, ZZ (Eq. 1.6) + Doerfler theta=0.5 + NVB "
+                                   f"until N >= {max_n}; DF64 assembly of the barycentric operator, block-Jacobi "
+                                   "PCG to 1e-10",
+                       "final_N": recs[-1]["N"], "final_M": recs[-1]["M"], "levels": len(recs),
+                       "cap_final": recs[-1]["cap"], "references": {"cube": CUBE_CAP, "fichera": FICHERA_CAP},
+                       "l2": "256 MB buffer written before every step"},
+            "p50_latency_ms": sorted(step_ms)[len(step_ms) // 2],
+            "phase_ms_per_step": {"assemble": sum(r["ms_assemble"] for r in recs),
+                                  "solve": sum(r["ms_solve"] for r in recs),
+                                  "adapt": sum(r["ms_adapt"] for r in recs)},
+            "e2e": {"value": args.steps / sum(e2e_t) if e2e_t else None, "unit": "adaptive runs/s",
+                    "h2d_bytes_per_step": cube.verts.nbytes + cube.tris.nbytes,
+                    "d2h_bytes_per_step": len(recs) * ctypes.sizeof(bem.LevelRecord)},
+            "gpu_launches": launches, "clocks": clk, "results": results}
+    if not args.no_cpu_baseline:
+        import oracle
+        from oracle import dual as D
+
+        oracle.build()
+        n_cpu = 600
+        t0 = time.perf_counter()
+        hist = D.adaptive_run_dual(cube.verts, cube.tris, theta=THETA, max_N=n_cpu, tol=TOL)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": "adaptive runs/s", "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": f"one dual-basis adaptive run of the unit cube to "
+                                                           f"N >= {n_cpu} ({len(hist)} levels), FP64 oracle",
+                                "cap_final": hist[-1]["cap"]}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def condition_workload(args):
     """Condition numbers of the systems of the adaptive loop (Sec. 3, Figs. 6 and 12,
     for the primal P0 space): the adaptive polycube run with each preconditioner
@@ -440,12 +549,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--max-n", type=int, default=MAX_N, help="smaller case of the same workload (profiling)")
     ap.add_argument("--workload", default="adaptive",
-                    choices=["adaptive", "graded60k", "serve", "batch", "batch-server", "condition", "rates"],
+                    choices=["adaptive", "graded60k", "serve", "batch", "batch-server", "condition", "rates", "dual"],
                     help="adaptive: the default workload above; graded60k: precision form (one FP32 "
                          "assembly + FP64-refined solve on the 60,492-triangle graded cube per step); "
                          "serve: Poisson stream of adaptive requests through the continuous-batching server; "
                          "batch: uniform polycube meshes assembled and solved by bem_batch_run (one solver "
-                         "launch, CUDA graph); batch-server: the same meshes through the server")
+                         "launch, CUDA graph); batch-server: the same meshes through the server; dual: the "
+                         "adaptive loop in the dual basis of Sec. 2.6 on the unit cube")
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per step")
     ap.add_argument("--batch", type=int, default=64, help="batch: meshes per step")
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
@@ -468,6 +578,8 @@ def main():
         return condition_workload(args)
     if args.workload == "rates":
         return rates_workload(args)
+    if args.workload == "dual":
+        return dual_workload(args)
     if args.workload in ("serve", "batch-server"):
         return server_workload(args)
 

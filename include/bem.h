@@ -253,7 +253,17 @@ typedef struct {
     bem_assembly_opts assembly;
     bem_solve_opts solve;
     int32_t incremental;    /* 1: reuse entries of unrefined pairs (bem_assemble_V_update) */
+    int32_t basis;          /* BEM_BASIS_P0 (default) or BEM_BASIS_DUAL */
 } bem_adaptive_opts;
+
+/* Discrete space of the adaptive loop.  P0: piecewise constants on the triangles
+ * (Eq. 2.5).  DUAL: piecewise constants on the dual cells (Sec. 2.1, 2.6): each level
+ * builds the barycentric refinement, assembles its operator (assembly options), forms
+ * V^dual (bem_operator_dual), solves from zero, estimates with bem_zz_estimate_dual and
+ * marks and refines the primal mesh; incremental and the warm start do not apply, and
+ * solve.inexact_lambda must be 0. */
+#define BEM_BASIS_P0 0
+#define BEM_BASIS_DUAL 1
 
 /* Alg. 1 on the primal P0 space: solve -> estimate -> mark -> refine, starting
  * from the uploaded mesh, until N >= max_N or max_levels.  The previous level's
@@ -265,6 +275,31 @@ typedef struct {
  * (caller destroys it). */
 bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_level_record *records,
                             int32_t *n_levels, bem_mesh **final_mesh);
+
+/* ---------------------------------------------------------------- dual basis */
+/* The paper's own discretisation (Sec. 2.1-2.6): piecewise constants on the dual mesh.
+ * bem_mesh_barycentric: the barycentric refinement T^bary of the (stored, rotated)
+ * mesh (Sec. 2.1): each triangle (v0, v1, v2) becomes (v0, m01, c), (m01, v1, c),
+ * (v1, m12, c), (m12, v2, c), (v2, m20, c), (m20, v0, c) at positions 6T .. 6T+5;
+ * new vertices: the edge midpoints 0.5 (a + b), numbered after the old vertices by the
+ * first appearance of their edge in (triangle, local edge) order, then the centroids
+ * ((v0 + v1) + v2) / 3; the children are uploaded like any mesh (reference edge =
+ * longest edge).  The caller destroys it.
+ * bem_operator_dual: from the operator of the barycentric refinement of mesh, the
+ * Galerkin matrix of the dual basis V^dual = P^T V^bary P (Sec. 2.6; P maps the dual
+ * cell of vertex z to its children: of triangle T, children 0 and 5 belong to v0, 1 and
+ * 2 to v1, 3 and 4 to v2), an M x M operator (DF64; F64 from an F64 operator; FP64 sums
+ * over the children, z <= w, mirrored).  bem_solve_capacity on it solves V^dual x = f,
+ * f_z = |T_z^dual| = (sum of |T| at z) / 3, and returns Cap_l = (1/4 pi) sum f_z x_z
+ * (Eq. 2.8); x has one value per vertex.  (The paper solves the same Galerkin system
+ * with operator preconditioning and GMRES; any convergent solver gives the same x.)
+ * Not with inexact_lambda.  At most 65,535 vertices and 32 triangles per vertex.
+ * bem_zz_estimate_dual: eta(T)^2 = h_T ||Phi - I Phi||^2_{L2(T)} (Eq. 1.6) for the dual
+ * solution x (M values), exact per barycentric child; totals (nullable): [sum eta^2,
+ * sum h_T |T| xbar^2 / 12], xbar the mean of the three vertex values. */
+bem_status bem_mesh_barycentric(bem_mesh *mesh, bem_mesh **out);
+bem_status bem_operator_dual(bem_operator *bary_op, bem_mesh *mesh, bem_operator **out);
+bem_status bem_zz_estimate_dual(bem_mesh *mesh, const double *x, int32_t h_mode, double *eta2_out, double *totals);
 
 /* ---------------------------------------------------------------- batch */
 /* Many independent capacity problems assembled and solved together (the paper has

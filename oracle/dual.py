@@ -1,0 +1,153 @@
+"""Dual-basis Galerkin formulation of Sec. 2 (the paper's own discretisation).
+
+TEST INFRASTRUCTURE ONLY: plain numpy on top of the FP64 oracle (`oracle.assemble`,
+`oracle.pcg`, ...); shares no code with the CUDA path.
+
+* Barycentric refinement (Sec. 2.1): every triangle T = (v0, v1, v2) of the mesh is
+  split into six triangles by its centroid c and its edge midpoints m01, m12, m20:
+  (v0, m01, c), (m01, v1, c), (v1, m12, c), (m12, v2, c), (v2, m20, c), (m20, v0, c)
+  (orientation kept).  New vertices: the edge midpoints 0.5 (a + b), numbered after
+  the M old vertices by the first appearance of their edge in (triangle, local edge)
+  order, then the centroids ((v0 + v1) + v2) / 3 in triangle order.
+* Dual cells (Sec. 2.1): the cell of vertex z is the union of the barycentric
+  children that contain z: of T, children 0 and 5 belong to v0, 1 and 2 to v1, 3 and
+  4 to v2.  |T_z^dual| = (sum over the triangles T at z, ascending, of |T|) / 3.
+* V^dual = P^T V^bary P (Sec. 2.6), P the 0/1 map from dual cells to their children;
+  the Galerkin solution solves V^dual x = f^dual, f^dual_z = |T_z^dual| (f = 1), and
+  Cap_l = (1/4 pi) sum_z |T_z^dual| x_z (Eq. 2.8).  The paper solves the same Galerkin
+  system with operator preconditioning and GMRES; any convergent solver gives the same
+  x, and this oracle uses Jacobi PCG.
+* ZZ (Eq. 1.6) on the dual solution: eta(T)^2 = diam(T) ||Phi - I Phi||^2_{L2(T)}, Phi
+  piecewise constant on the dual cells, I Phi the S^1 interpolant of the cell values.
+  On each child the difference is affine; with its vertex values (a, b, c) the integral
+  is (|T|/6)/12 (a^2 + b^2 + c^2 + (a + b + c)^2).  Vertex values on the children: 0 at
+  the child's own vertex, (x_own - x_other)/2 at the midpoint, x_own - s/3 at the
+  centroid, s = (x0 + x1) + x2.  Operation order: per child q = ((a a + b b) + c c) +
+  (a + b + c)^2 with (a + b) + c; children summed in order 0..5; eta^2 = (h (|T| / 72)) q.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import oracle as O
+
+CHILD_VERTEX = (0, 1, 1, 2, 2, 0)  # local primal vertex of barycentric child k
+
+
+def barycentric(verts, tris):
+    """(verts_b, tris_b) of the barycentric refinement, children of T at 6T .. 6T+5."""
+    v = np.asarray(verts, dtype=np.float64)
+    t = np.asarray(tris, dtype=np.int32)
+    M, N = v.shape[0], t.shape[0]
+    edge_id = {}
+    mids = []
+    for ti in range(N):
+        for k in range(3):
+            a, b = int(t[ti, k]), int(t[ti, (k + 1) % 3])
+            key = (min(a, b), max(a, b))
+            if key not in edge_id:
+                edge_id[key] = M + len(mids)
+                mids.append(0.5 * (v[a] + v[b]))
+    E = len(mids)
+    cent = (v[t[:, 0]] + v[t[:, 1]] + v[t[:, 2]]) / 3.0
+    vb = np.concatenate([v, np.array(mids).reshape(E, 3), cent])
+    tb = np.zeros((6 * N, 3), dtype=np.int32)
+    for ti in range(N):
+        v0, v1, v2 = (int(x) for x in t[ti])
+        m01 = edge_id[(min(v0, v1), max(v0, v1))]
+        m12 = edge_id[(min(v1, v2), max(v1, v2))]
+        m20 = edge_id[(min(v2, v0), max(v2, v0))]
+        c = M + E + ti
+        tb[6 * ti:6 * ti + 6] = [(v0, m01, c), (m01, v1, c), (v1, m12, c), (m12, v2, c), (v2, m20, c),
+                                 (m20, v0, c)]
+    return vb, tb
+
+
+def child_cell(tris):
+    """Dual cell (primal vertex) of every barycentric child, length 6N."""
+    t = np.asarray(tris, dtype=np.int32)
+    return np.stack([t[:, k] for k in CHILD_VERTEX], axis=1).reshape(-1)
+
+
+def dual_areas(verts, tris):
+    """|T_z^dual| = (sum of |T| over the triangles at z, ascending) / 3."""
+    area = O.geometry(verts, tris)[0]
+    M = np.asarray(verts).shape[0]
+    t = np.asarray(tris, dtype=np.int32)
+    out = np.zeros(M)
+    for z in range(M):
+        s = 0.0
+        for ti in np.flatnonzero(np.any(t == z, axis=1)):
+            s = s + area[ti]
+        out[z] = s / 3.0
+    return out
+
+
+def dual_operator(Vb, cell, M):
+    """V^dual = P^T V^bary P (P[B, z] = 1 if child B belongs to cell z)."""
+    P = np.zeros((len(cell), M))
+    P[np.arange(len(cell)), cell] = 1.0
+    return P.T @ Vb @ P
+
+
+def zz_dual(verts, tris, x, h_mode=0):
+    """eta(T)^2 of Eq. 1.6 for the dual solution x (one value per vertex)."""
+    area, diam = O.geometry(verts, tris)
+    t = np.asarray(tris, dtype=np.int32)
+    xd = np.asarray(x, dtype=np.float64)
+    out = np.zeros(t.shape[0])
+    for ti in range(t.shape[0]):
+        x0, x1, x2 = (float(xd[k]) for k in t[ti])
+        s = (x0 + x1) + x2
+        c3 = s / 3.0
+        own = (x0, x1, x1, x2, x2, x0)
+        mid = (0.5 * (x0 - x1), 0.5 * (x1 - x0), 0.5 * (x1 - x2), 0.5 * (x2 - x1), 0.5 * (x2 - x0),
+               0.5 * (x0 - x2))
+        q = 0.0
+        for k in range(6):
+            # child vertex order: own vertex first for even k, midpoint first for odd k
+            a, b, c = (0.0, mid[k], own[k] - c3) if k % 2 == 0 else (mid[k], 0.0, own[k] - c3)
+            ab = a + b
+            q = q + (((a * a + b * b) + c * c) + (ab + c) * (ab + c))
+        h = math.sqrt(area[ti]) if h_mode == 1 else diam[ti]
+        out[ti] = (h * (area[ti] / 72.0)) * q
+    return out
+
+
+def solve_dual(verts, tris, tol=1e-12, precond=1, maxit=20000, n_ss=4):
+    """Cap_l, x (per vertex), iterations, V^dual of the dual-basis Galerkin system."""
+    vb, tb = barycentric(verts, tris)
+    tbc = O.canonical(vb, tb)
+    Vb = O.assemble(vb, tbc, n_ss)
+    M = np.asarray(verts).shape[0]
+    Vd = dual_operator(Vb, child_cell(tris), M)
+    f = dual_areas(verts, tris)
+    x, its, _, _ = O.pcg(Vd, f, tol=tol, maxit=maxit, precond=precond)
+    return O.capacity(f, x), x, its, Vd
+
+
+def adaptive_run_dual(verts, tris, theta=0.5, max_N=1000, tol=1e-12, h_mode=0, max_levels=100):
+    """Alg. 1 with the dual-basis solution: solve -> ZZ (Eq. 1.6) -> Doerfler -> NVB on
+    the primal mesh, each solve from zero, until N >= max_N.  The vanishing-estimator
+    rule of the primal loop applies with x_T = (x0 + x1 + x2) / 3."""
+    t = O.canonical(verts, tris)
+    v = np.asarray(verts, dtype=np.float64)
+    hist = []
+    for lvl in range(max_levels):
+        cap, x, its, _ = solve_dual(v, t, tol=tol)
+        eta2 = zz_dual(v, t, x, h_mode)
+        rec = {"level": lvl, "N": t.shape[0], "M": v.shape[0], "cap": cap, "its": its,
+               "eta2_total": float(np.sum(eta2)), "x": x, "verts": v, "tris": t}
+        hist.append(rec)
+        if t.shape[0] >= max_N:
+            break
+        area, diam = O.geometry(v, t)
+        xm = (x[t[:, 0]] + x[t[:, 1]] + x[t[:, 2]]) / 3.0
+        h = np.sqrt(area) if h_mode == 1 else diam
+        scale = float(np.sum(h * area * xm * xm / 12.0))
+        m = O.mark(eta2, scale, theta)
+        rec["marked"] = m
+        v, t, _, _ = O.refine(v, t, m)
+    return hist

@@ -29,6 +29,8 @@ PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_BLOCK = 2
 REFINE_BISEC3 = 1
+BASIS_P0 = 0
+BASIS_DUAL = 1
 
 EXPORTS = [
     "bem_context_create", "bem_context_destroy", "bem_last_error", "bem_context_memory",
@@ -39,6 +41,7 @@ EXPORTS = [
     "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc", "bem_context_set_persistent",
     "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
     "bem_batch_create", "bem_batch_run", "bem_batch_info", "bem_batch_destroy",
+    "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -70,7 +73,7 @@ class LevelRecord(C.Structure):
 class AdaptiveOpts(C.Structure):
     _fields_ = [("theta", C.c_double), ("max_N", C.c_int64), ("max_levels", C.c_int32),
                 ("h_mode", C.c_int32), ("assembly", AssemblyOpts), ("solve", SolveOpts),
-                ("incremental", C.c_int32)]
+                ("incremental", C.c_int32), ("basis", C.c_int32)]
 
 
 SERVER_HISTORY = 16
@@ -150,6 +153,9 @@ def lib():
         "bem_batch_run": [vp, vp],
         "bem_batch_info": [vp, P(i32), P(i32), P(i32)],
         "bem_batch_destroy": [vp],
+        "bem_mesh_barycentric": [vp, P(vp)],
+        "bem_operator_dual": [vp, vp, P(vp)],
+        "bem_zz_estimate_dual": [vp, vp, i32, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -280,6 +286,12 @@ class Mesh:
                                                     k.ctypes.data))
         return v, t, p, k
 
+    def barycentric(self) -> "Mesh":
+        """Barycentric refinement (Sec. 2.1): children of triangle T at 6T .. 6T+5."""
+        h = C.c_void_p()
+        self.ctx.check(self.ctx.L.bem_mesh_barycentric(self.h, C.byref(h)))
+        return Mesh(self.ctx, h)
+
     def geometry(self):
         N = self.N
         a, d = np.zeros(N), np.zeros(N)
@@ -315,6 +327,14 @@ class Operator:
         h = C.c_void_p()
         fine.ctx.check(fine.ctx.L.bem_assemble_V_update(fine.h, coarse.h, None, C.byref(h)))
         return cls(fine, h)
+
+    @classmethod
+    def dual(cls, bary_op: "Operator", mesh: Mesh):
+        """V^dual = P^T V^bary P (Sec. 2.6) of mesh, from the operator of its barycentric
+        refinement; an M x M operator, one unknown per vertex."""
+        h = C.c_void_p()
+        mesh.ctx.check(mesh.ctx.L.bem_operator_dual(bary_op.h, mesh.h, C.byref(h)))
+        return cls(mesh, h)
 
     def info(self):
         N, p = C.c_int64(), C.c_int32()
@@ -385,6 +405,15 @@ def zz_estimate(mesh: Mesh, phi, h_mode=0):
     return eta2, float(tot[0]), float(tot[1])
 
 
+def zz_estimate_dual(mesh: Mesh, x, h_mode=0):
+    """eta(T)^2 of Eq. 1.6 for the dual solution x (one value per vertex of mesh)."""
+    xa, px = _arr(x, np.float64)
+    eta2 = np.zeros(mesh.N)
+    tot = np.zeros(2)
+    mesh.ctx.check(mesh.ctx.L.bem_zz_estimate_dual(mesh.h, px, h_mode, eta2.ctypes.data, tot.ctypes.data))
+    return eta2, float(tot[0]), float(tot[1])
+
+
 def dorfler(ctx: Context, eta2, theta=0.5):
     ea, pe = _arr(eta2, np.float64)
     N = int(ea.shape[0])
@@ -414,11 +443,12 @@ def mark_refine(mesh: Mesh, eta2, theta=0.5, bisec3=False):
 
 def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, precision=PREC_F64,
                  ss_order=4, tol=1e-12, max_it=20000, precond=PRECOND_JACOBI, incremental=True,
-                 max_outer=20, inner_tol=1e-5, want_final=False, reliable_delta=0.0, inexact_lambda=0.0):
+                 max_outer=20, inner_tol=1e-5, want_final=False, reliable_delta=0.0, inexact_lambda=0.0,
+                 basis=BASIS_P0):
     """Alg. 1 in the library's native loop; returns (records, final Mesh or None)."""
     o = AdaptiveOpts(theta, max_N, max_levels, h_mode, AssemblyOpts(precision, ss_order),
                      SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode),
-                     int(incremental))
+                     int(incremental), int(basis))
     recs = (LevelRecord * max_levels)()
     n = C.c_int32()
     fin = C.c_void_p()

@@ -6,6 +6,8 @@
 // from them, are bit-identical to a plain IEEE-754 evaluation of the same
 // formulas.
 #include <cmath>
+#include <new>
+#include <type_traits>
 
 #include "bem_internal.cuh"
 
@@ -482,6 +484,314 @@ fail:
     }
     dfree_all(ctx, tmp);
     return st;
+}
+
+}  // namespace bem
+
+// ------------------------------------------------------------------ dual basis (Sec. 2.1, 2.6)
+namespace bem {
+
+// Barycentric refinement: vertices = the old ones, the edge midpoints 0.5 (a + b)
+// numbered by the first appearance of their edge in (triangle, local edge) order (the
+// owner half-edge), then the centroids ((v0 + v1) + v2) / 3; children of T at 6T .. 6T+5:
+// (v0, m01, c), (m01, v1, c), (v1, m12, c), (m12, v2, c), (v2, m20, c), (m20, v0, c).
+__global__ void k_bary_verts(const double *V, const int32_t *tris, const int32_t *owner, const int32_t *edge_pos,
+                             int64_t N, int64_t M, int64_t E, double *Vb)
+{
+    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= 3 * N) return;
+    const int64_t t = h / 3;
+    const int k = (int)(h % 3);
+    if (owner[h] == h) {
+        const int32_t a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+        const int64_t m = M + edge_pos[h];
+        for (int c = 0; c < 3; ++c) Vb[3 * m + c] = 0.5 * (V[3 * (int64_t)a + c] + V[3 * (int64_t)b + c]);
+    }
+    if (k == 0) {
+        const int32_t a = tris[3 * t], b = tris[3 * t + 1], c0 = tris[3 * t + 2];
+        for (int c = 0; c < 3; ++c)
+            Vb[3 * (M + E + t) + c] = (V[3 * (int64_t)a + c] + V[3 * (int64_t)b + c] + V[3 * (int64_t)c0 + c]) / 3.0;
+    }
+}
+
+__global__ void k_bary_tris(const int32_t *tris, const int32_t *owner, const int32_t *edge_pos, int64_t N, int64_t M,
+                            int64_t E, int32_t *Tb)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const int32_t v0 = tris[3 * t], v1 = tris[3 * t + 1], v2 = tris[3 * t + 2];
+    const int32_t m01 = (int32_t)(M + edge_pos[owner[3 * t]]), m12 = (int32_t)(M + edge_pos[owner[3 * t + 1]]),
+                  m20 = (int32_t)(M + edge_pos[owner[3 * t + 2]]);
+    const int32_t c = (int32_t)(M + E + t);
+    const int32_t ch[6][3] = {{v0, m01, c}, {m01, v1, c}, {v1, m12, c}, {m12, v2, c}, {v2, m20, c}, {m20, v0, c}};
+    for (int k = 0; k < 6; ++k)
+        for (int j = 0; j < 3; ++j) Tb[3 * (6 * t + k) + j] = ch[k][j];
+}
+
+__global__ void k_owner_flag(const int32_t *owner, int64_t H, int32_t *flag)
+{
+    const int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (h < H) flag[h] = owner[h] == h ? 1 : 0;
+}
+
+bem_status barycentric(bem_mesh *m, bem_mesh **out)
+{
+    bem_ctx *ctx = m->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = m->N, M = m->M, H = 3 * N;
+    Allocs tmp;
+    int32_t *flag = nullptr, *pos = nullptr;
+    int64_t E = 0;
+    bem_status st = dalloc(ctx, tmp, (void **)&flag, sizeof(int32_t) * (2 * H + 2), false);
+    if (st) return st;
+    pos = flag + H + 1;
+    k_owner_flag<<<nblk(H, 256), 256, 0, s>>>(m->owner, H, flag); BEM_COUNT(ctx);
+    if ((st = exclusive_scan_i32(ctx, flag, pos, H, &E))) {
+        dfree_all(ctx, tmp);
+        return st;
+    }
+    bem_mesh *r = new (std::nothrow) bem_mesh();
+    if (!r) {
+        dfree_all(ctx, tmp);
+        return set_error(ctx, BEM_ERR_OOM, "host allocation");
+    }
+    r->ctx = ctx;
+    r->M = M + E + N;
+    r->N = 6 * N;
+    if (r->M > 0x7FFFFFFFLL || r->N > 0x7FFFFFFFLL) st = set_error(ctx, BEM_ERR_INVALID, "barycentric mesh too large");
+    if (!st) st = dalloc(ctx, r->allocs, (void **)&r->verts, sizeof(double) * 3 * r->M, false);
+    if (!st) st = dalloc(ctx, r->allocs, (void **)&r->tris, sizeof(int32_t) * 3 * r->N, false);
+    if (!st) {
+        cudaError_t e = cudaMemcpyAsync(r->verts, m->verts, sizeof(double) * 3 * M, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "barycentric vertices");
+    }
+    if (!st) {
+        k_bary_verts<<<nblk(H, 256), 256, 0, s>>>(m->verts, m->tris, m->owner, pos, N, M, E, r->verts); BEM_COUNT(ctx);
+        k_bary_tris<<<nblk(N, 256), 256, 0, s>>>(m->tris, m->owner, pos, N, M, E, r->tris); BEM_COUNT(ctx);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "barycentric kernels");
+    }
+    if (!st) st = mesh_build(r, true, nullptr);
+    dfree_all(ctx, tmp);
+    if (st) {
+        dfree_all(ctx, r->allocs);
+        delete r;
+        return st;
+    }
+    *out = r;
+    return BEM_OK;
+}
+
+// Dual-cell table of the primal mesh: cell areas |T_z^dual| = (sum of |T| at z,
+// ascending) / 3 and cell "centroids" (the vertex) for the cells mesh.
+__global__ void k_dual_cells(const double *V, const int32_t *v2t_off, const int32_t *v2t, const double *area,
+                             int64_t M, double *darea, double *dcent)
+{
+    const int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= M) return;
+    double sum = 0.0;
+    for (int32_t p = v2t_off[z]; p < v2t_off[z + 1]; ++p) sum = sum + area[v2t[p]];
+    const double a = sum / 3.0;
+    darea[z] = a;
+    for (int c = 0; c < 3; ++c) dcent[4 * z + c] = V[3 * z + c];
+    dcent[4 * z + 3] = a;
+}
+
+template <typename T> __device__ __forceinline__ double vb_elem(const T *V, int64_t o);
+template <> __device__ __forceinline__ double vb_elem<double>(const double *V, int64_t o) { return V[o]; }
+template <> __device__ __forceinline__ double vb_elem<float2>(const float2 *V, int64_t o)
+{
+    return (double)V[o].x + (double)V[o].y;
+}
+template <> __device__ __forceinline__ double vb_elem<float>(const float *V, int64_t o) { return (double)V[o]; }
+
+// Children of primal vertex z that belong to its dual cell, in ascending order:
+// local vertex k of triangle t owns children 6t + {0,5} (k = 0), {1,2} (k = 1),
+// {3,4} (k = 2).
+__device__ __forceinline__ int cell_children(const int32_t *tris, const int32_t *v2t_off, const int32_t *v2t,
+                                             int64_t z, int32_t *out, int cap)
+{
+    int n = 0;
+    for (int32_t p = v2t_off[z]; p < v2t_off[z + 1]; ++p) {
+        const int32_t t = v2t[p];
+        const int k = tris[3 * t] == z ? 0 : (tris[3 * t + 1] == z ? 1 : 2);
+        const int c0 = k == 0 ? 0 : 2 * k - 1, c1 = k == 0 ? 5 : 2 * k;
+        if (n + 2 <= cap) {
+            out[n++] = 6 * t + c0;
+            out[n++] = 6 * t + c1;
+        }
+    }
+    return n;
+}
+
+// V^dual[z][w] = sum over children B of z and B' of w of V^bary[B][B'] (FP64 sums in
+// the order of the children lists), z <= w, mirrored; output double (F64) or hi/lo
+// pairs (DF64).  One thread per (z, w) of a row z; the children lists come from the
+// primal vertex-to-triangle table.
+constexpr int kMaxCellChildren = 64;  // valence <= 32
+
+template <typename T, typename O>
+__global__ void k_dual_operator(const T *__restrict__ Vb, int64_t ldb, const int32_t *tris, const int32_t *v2t_off,
+                                const int32_t *v2t, int64_t M, O *Vd, int64_t ldd, int *bad)
+{
+    const int64_t z = blockIdx.y;
+    const int64_t w = z + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ int32_t cz[kMaxCellChildren];
+    __shared__ int s_nz;
+    if (threadIdx.x == 0) s_nz = cell_children(tris, v2t_off, v2t, z, cz, kMaxCellChildren);
+    __syncthreads();
+    if (w >= M) return;
+    int32_t cw[kMaxCellChildren];
+    const int nw = cell_children(tris, v2t_off, v2t, w, cw, kMaxCellChildren);
+    if ((v2t_off[w + 1] - v2t_off[w]) * 2 > kMaxCellChildren || (v2t_off[z + 1] - v2t_off[z]) * 2 > kMaxCellChildren)
+        atomicExch(bad, 1);
+    double sum = 0.0;
+    for (int a = 0; a < s_nz; ++a) {
+        const int64_t row = (int64_t)cz[a] * ldb;
+        for (int b = 0; b < nw; ++b) sum = sum + vb_elem(Vb, row + cw[b]);
+    }
+    if constexpr (std::is_same<O, double>::value) {
+        Vd[z * ldd + w] = sum;
+        Vd[w * ldd + z] = sum;
+    } else {
+        const float h = __double2float_rn(sum);
+        const float2 v = make_float2(h, __double2float_rn(sum - (double)h));
+        Vd[z * ldd + w] = v;
+        Vd[w * ldd + z] = v;
+    }
+}
+
+// eta(T)^2 of Eq. 1.6 for a dual solution x (one value per vertex): Phi piecewise
+// constant on the dual cells, I Phi its S^1 interpolant; closed form per barycentric
+// child (see the oracle of the same name for the operation order); block partials of
+// the total and of sum h |T| xbar^2 / 12, xbar = (x0 + x1 + x2) / 3.
+__global__ void k_zz_dual(const int32_t *tris, const double *area, const double *diam, const double *x, int64_t N,
+                          int h_mode, double *eta2, double *part_eta, double *part_scale)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double e = 0.0, sc = 0.0;
+    if (t < N) {
+        const double x0 = x[tris[3 * t]], x1 = x[tris[3 * t + 1]], x2 = x[tris[3 * t + 2]];
+        const double s = (x0 + x1) + x2;
+        const double c3 = s / 3.0;
+        const double own[6] = {x0, x1, x1, x2, x2, x0};
+        const double mid[6] = {0.5 * (x0 - x1), 0.5 * (x1 - x0), 0.5 * (x1 - x2),
+                               0.5 * (x2 - x1), 0.5 * (x2 - x0), 0.5 * (x0 - x2)};
+        double q = 0.0;
+        for (int k = 0; k < 6; ++k) {
+            const double a = (k % 2 == 0) ? 0.0 : mid[k], b = (k % 2 == 0) ? mid[k] : 0.0, c = own[k] - c3;
+            const double ab = a + b;
+            q = q + (((a * a + b * b) + c * c) + (ab + c) * (ab + c));
+        }
+        const double h = h_mode == 1 ? sqrt(area[t]) : diam[t];
+        e = (h * (area[t] / 72.0)) * q;
+        const double xm = s / 3.0;
+        sc = h * area[t] * xm * xm / 12.0;
+        eta2[t] = e;
+    }
+    __shared__ double se[256], ss[256];
+    se[threadIdx.x] = e;
+    ss[threadIdx.x] = sc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) {
+            se[threadIdx.x] += se[threadIdx.x + o];
+            ss[threadIdx.x] += ss[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part_eta[blockIdx.x] = se[0];
+        part_scale[blockIdx.x] = ss[0];
+    }
+}
+
+bem_status zz_estimate_dual(bem_mesh *m, const double *d_x, int h_mode, double *d_eta2, double *h_totals)
+{
+    bem_ctx *ctx = m->ctx;
+    cudaStream_t s = ctx->stream;
+    Allocs tmp;
+    const int nb = (int)nblk(m->N, 256);
+    double *pe = nullptr;
+    bem_status st = dalloc(ctx, tmp, (void **)&pe, sizeof(double) * (2 * nb + 2), false);
+    if (st) return st;
+    double *ps = pe + nb, *tot = ps + nb;
+    k_zz_dual<<<nb, 256, 0, s>>>(m->tris, m->area, m->diam, d_x, m->N, h_mode, d_eta2, pe, ps); BEM_COUNT(ctx);
+    k_sum2<<<1, 32, 0, s>>>(pe, ps, nb, tot); BEM_COUNT(ctx);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = cuda_error(ctx, e, "dual zz kernels");
+    if (!st && h_totals) {
+        e = cudaMemcpyAsync(ctx->h_pinned, tot, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "dual zz totals");
+        else {
+            h_totals[0] = ctx->h_pinned[0];
+            h_totals[1] = ctx->h_pinned[1];
+        }
+    }
+    dfree_all(ctx, tmp);
+    return st;
+}
+
+// The dual operator of primal mesh pm from the operator of its barycentric refinement:
+// an M x M operator (DF64, or F64 for an F64 barycentric operator) over a cells mesh
+// (N = M cells: dual areas as |T|, the vertices as centroids) owned by the operator.
+bem_status dual_operator(bem_operator *ob, bem_mesh *pm, bem_operator **out)
+{
+    bem_ctx *ctx = pm->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t M = pm->M;
+    bem_mesh *cm = new (std::nothrow) bem_mesh();
+    bem_operator *op = new (std::nothrow) bem_operator();
+    if (!cm || !op) {
+        delete cm;
+        delete op;
+        return set_error(ctx, BEM_ERR_OOM, "host allocation");
+    }
+    cm->ctx = ctx;
+    cm->N = M;
+    cm->M = 0;
+    cm->cells_only = 1;
+    op->mesh = cm;
+    op->ctx = ctx;
+    op->owns_mesh = 1;
+    op->precision = ob->precision == BEM_PREC_F64 ? BEM_PREC_F64 : BEM_PREC_DF64;
+    op->ss_order = ob->ss_order;
+    op->N = M;
+    op->ld = padded_ld(M);
+    Allocs tmp;
+    int *bad = nullptr;
+    bem_status st = dalloc(ctx, cm->allocs, (void **)&cm->area, sizeof(double) * M, false);
+    if (!st) st = dalloc(ctx, cm->allocs, (void **)&cm->cent, sizeof(double) * 4 * M, false);
+    if (!st) st = dalloc(ctx, op->allocs, &op->V, 8 * (size_t)M * (size_t)op->ld, true);
+    if (!st) st = dalloc(ctx, op->allocs, (void **)&op->diag, sizeof(double) * M, false);
+    if (!st) st = dalloc(ctx, tmp, (void **)&bad, sizeof(int), true);
+    if (!st) {
+        k_dual_cells<<<nblk(M, 256), 256, 0, s>>>(pm->verts, pm->v2t_off, pm->v2t, pm->area, M, cm->area, cm->cent); BEM_COUNT(ctx);
+        const dim3 grid((unsigned)nblk(M, 128), (unsigned)M);
+        if (M > 65535) st = set_error(ctx, BEM_ERR_INVALID, "dual operator: more than 65535 vertices");
+        else if (ob->precision == BEM_PREC_F64)
+            { k_dual_operator<double, double><<<grid, 128, 0, s>>>((const double *)ob->V, ob->ld, pm->tris, pm->v2t_off, pm->v2t, M, (double *)op->V, op->ld, bad); BEM_COUNT(ctx); }
+        else if (ob->precision == BEM_PREC_DF64)
+            { k_dual_operator<float2, float2><<<grid, 128, 0, s>>>((const float2 *)ob->V, ob->ld, pm->tris, pm->v2t_off, pm->v2t, M, (float2 *)op->V, op->ld, bad); BEM_COUNT(ctx); }
+        else
+            { k_dual_operator<float, float2><<<grid, 128, 0, s>>>((const float *)ob->V, ob->ld, pm->tris, pm->v2t_off, pm->v2t, M, (float2 *)op->V, op->ld, bad); BEM_COUNT(ctx); }
+    }
+    if (!st) st = operator_diag(op);
+    if (!st) {
+        cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, "dual operator");
+        else if (*reinterpret_cast<int *>(ctx->h_pinned))
+            st = set_error(ctx, BEM_ERR_MESH, "dual operator: a vertex has more than %d triangles", kMaxCellChildren / 2);
+    }
+    dfree_all(ctx, tmp);
+    if (st) {
+        bem_operator_destroy(op);
+        return st;
+    }
+    *out = op;
+    return BEM_OK;
 }
 
 }  // namespace bem

@@ -496,6 +496,7 @@ bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse, con
     bem_ctx *ctx = fine->ctx;
     *out = nullptr;
     CHECK_ARG(ctx, coarse->mesh->ctx == ctx, "operator and mesh belong to different contexts");
+    CHECK_ARG(ctx, !coarse->mesh->cells_only, "a dual operator has no incremental update");
     CHECK_ARG(ctx, fine->parent != nullptr && fine->src_N == coarse->N,
               "mesh was not refined from the operator's mesh");
     bem_assembly_opts o{coarse->precision, coarse->ss_order};
@@ -524,8 +525,50 @@ bem_status bem_operator_destroy(bem_operator *op)
 {
     if (!op) return BEM_ERR_INVALID;
     dfree_all(op->ctx, op->allocs);
+    if (op->owns_mesh && op->mesh) {
+        dfree_all(op->ctx, op->mesh->allocs);
+        delete op->mesh;
+    }
     delete op;
     return BEM_OK;
+}
+
+bem_status bem_mesh_barycentric(bem_mesh *mesh, bem_mesh **out)
+{
+    if (!mesh || !out) return BEM_ERR_INVALID;
+    *out = nullptr;
+    CHECK_ARG(mesh->ctx, !mesh->cells_only, "not a triangle mesh");
+    bem_status st = barycentric(mesh, out);
+    if (!st) {
+        cudaError_t e = cudaStreamSynchronize(mesh->ctx->stream);
+        if (e != cudaSuccess) st = cuda_error(mesh->ctx, e, "barycentric refinement");
+    }
+    return st;
+}
+
+bem_status bem_operator_dual(bem_operator *bary_op, bem_mesh *mesh, bem_operator **out)
+{
+    if (!bary_op || !mesh || !out) return BEM_ERR_INVALID;
+    bem_ctx *ctx = mesh->ctx;
+    *out = nullptr;
+    CHECK_ARG(ctx, bary_op->ctx == ctx, "operator and mesh belong to different contexts");
+    CHECK_ARG(ctx, !mesh->cells_only && bary_op->N == 6 * mesh->N,
+              "the operator must be that of the barycentric refinement of the mesh (6 N triangles)");
+    return dual_operator(bary_op, mesh, out);
+}
+
+bem_status bem_zz_estimate_dual(bem_mesh *mesh, const double *x, int32_t h_mode, double *eta2_out, double *totals)
+{
+    if (!mesh) return BEM_ERR_INVALID;
+    bem_ctx *ctx = mesh->ctx;
+    CHECK_ARG(ctx, x && eta2_out && !mesh->cells_only, "null argument");
+    CHECK_ARG(ctx, h_mode == 0 || h_mode == 1, "h_mode must be 0 or 1");
+    DevBuf dx, de;
+    bem_status st;
+    if ((st = dev_in(ctx, x, sizeof(double) * (size_t)mesh->M, dx))) return st;
+    if ((st = dev_out_begin(ctx, eta2_out, sizeof(double) * (size_t)mesh->N, de))) return st;
+    if ((st = zz_estimate_dual(mesh, (const double *)dx.dptr, h_mode, (double *)de.dptr, totals))) return st;
+    return dev_out_end(ctx, eta2_out, de);
 }
 
 bem_status bem_operator_info(const bem_operator *op, int64_t *N, int32_t *precision)
@@ -742,6 +785,20 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b)
     return ms;
 }
 
+// Operator of one level of the dual-basis loop: barycentric refinement, its
+// operator, V^dual; the refinement and its operator are released again.
+static bem_status dual_level_operator(bem_mesh *cur, const bem_assembly_opts *aopts, bem_operator **out)
+{
+    bem_mesh *b = nullptr;
+    bem_operator *ob = nullptr;
+    bem_status st = barycentric(cur, &b);
+    if (!st) st = bem_assemble_V(b, aopts, &ob);
+    if (!st) st = dual_operator(ob, cur, out);
+    if (ob) bem_operator_destroy(ob);
+    if (b) bem_mesh_destroy(b);
+    return st;
+}
+
 bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_level_record *records, int32_t *n_levels,
                             bem_mesh **final_mesh)
 {
@@ -750,6 +807,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
     CHECK_ARG(ctx, opts && records && n_levels, "null argument");
     CHECK_ARG(ctx, opts->max_levels >= 1, "max_levels < 1");
     CHECK_ARG(ctx, opts->theta > 0.0 && opts->theta <= 1.0, "theta must lie in (0, 1]");
+    CHECK_ARG(ctx, opts->basis == BEM_BASIS_P0 || opts->basis == BEM_BASIS_DUAL, "unknown basis");
+    const bool dual = opts->basis == BEM_BASIS_DUAL;
+    CHECK_ARG(ctx, !(dual && opts->solve.inexact_lambda > 0.0), "the inexact stopping rule needs the P0 basis");
     if (final_mesh) *final_mesh = nullptr;
     *n_levels = 0;
     cudaStream_t s = ctx->stream;
@@ -766,7 +826,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         rec.M = cur->M;
         cudaEventRecord(ctx->ev[0], s);
         bem_operator *op = nullptr;
-        if (op_prev && opts->incremental && cur->parent)
+        if (dual)
+            st = dual_level_operator(cur, &opts->assembly, &op);
+        else if (op_prev && opts->incremental && cur->parent)
             st = bem_assemble_V_update(cur, op_prev, &opts->assembly, &op);
         else
             st = bem_assemble_V(cur, &opts->assembly, &op);
@@ -780,11 +842,12 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         cudaEventRecord(ctx->ev[1], s);
         Allocs lv;
         double *x0 = nullptr, *x = nullptr, *eta2 = nullptr;
-        st = dalloc(ctx, lv, (void **)&x, sizeof(double) * 3 * cur->N, false);
+        const int64_t nx = dual ? cur->M : cur->N;  // unknowns: vertices or triangles
+        st = dalloc(ctx, lv, (void **)&x, sizeof(double) * (2 * nx + cur->N), false);
         if (st) { bem_operator_destroy(op); break; }
-        x0 = x + cur->N;
-        eta2 = x + 2 * cur->N;
-        if (x_prev && cur->parent) {
+        x0 = x + nx;
+        eta2 = x + 2 * nx;
+        if (!dual && x_prev && cur->parent) {
             k_prolong<<<nblk(cur->N, 256), 256, 0, s>>>(x_prev, cur->parent, cur->N, x0); BEM_COUNT(ctx);
         } else {
             x0 = nullptr;
@@ -801,7 +864,7 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         if (st) { dfree_all(ctx, lv); bem_operator_destroy(op); break; }
         cudaEventRecord(ctx->ev[2], s);
         double tot[2] = {0.0, 0.0};
-        st = zz_estimate(cur, x, opts->h_mode, eta2, tot);
+        st = dual ? zz_estimate_dual(cur, x, opts->h_mode, eta2, tot) : zz_estimate(cur, x, opts->h_mode, eta2, tot);
         rec.eta2_total = tot[0];
         bem_mesh *next = nullptr;
         const bool last = cur->N >= opts->max_N || lvl == opts->max_levels - 1;
@@ -832,7 +895,7 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         // keep this level's solution for the warm start of the next one
         dfree_all(ctx, xprev_alloc);
         x_prev = nullptr;
-        if (!st && next) {
+        if (!st && next && !dual) {
             if ((st = dalloc(ctx, xprev_alloc, (void **)&x_prev, sizeof(double) * cur->N, false)) == BEM_OK) {
                 cudaError_t e = cudaMemcpyAsync(x_prev, x, sizeof(double) * cur->N, cudaMemcpyDeviceToDevice, s);
                 if (e != cudaSuccess) st = cuda_error(ctx, e, "warm start copy");

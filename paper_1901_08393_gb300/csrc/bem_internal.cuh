@@ -85,6 +85,7 @@ struct bem_mesh {
     uint8_t *kept = nullptr;    // N or null
     int64_t n_kept = 0;         // refined meshes: triangles [0, n_kept) are unrefined
     int64_t src_N = 0;          // refined meshes: N of the source mesh
+    int cells_only = 0;         // dual cells of an operator from bem_operator_dual: N, area, cent only
     bem::Allocs allocs;
 };
 
@@ -96,6 +97,7 @@ struct bem_operator {
     int64_t N = 0, ld = 0;
     void *V = nullptr;      // N x ld, row-major: double (F64), float2 hi/lo (DF64), float (F32)
     double *diag = nullptr; // N, FP64 diagonal
+    int owns_mesh = 0;      // 1: mesh is a cells mesh freed with the operator
     bem::Allocs allocs;
 };
 
@@ -158,6 +160,9 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
                           double *d_x, double *cap, bem_solve_info *info);
 
 // ----------------------------------------------------------------- adaptivity (adapt.cu)
+bem_status barycentric(bem_mesh *m, bem_mesh **out);
+bem_status dual_operator(bem_operator *ob, bem_mesh *pm, bem_operator **out);
+bem_status zz_estimate_dual(bem_mesh *m, const double *d_x, int h_mode, double *d_eta2, double *h_totals);
 bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_eta2,
                        double *h_totals);
 // Ascending sort of n2 (a power of two) 64-bit keys on the context's stream.

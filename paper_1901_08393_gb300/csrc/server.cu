@@ -65,14 +65,18 @@ namespace {
 // incremental assembly of the fine one and freed before the solve) at the largest
 // level the request can reach -- the first with N >= max_N, which Doerfler marking
 // can overshoot by about 1.5x, or N0 grown by at most 2.2x per level (bisection of
-// every element plus closure) -- plus per-triangle tables and solver vectors.
-int64_t estimate_bytes(int64_t N0, int64_t max_N, int32_t levels, int precision)
+// every element plus closure) -- plus per-triangle tables and solver vectors.  The
+// dual basis holds, at its largest level, the operator of the barycentric refinement
+// (6 n triangles: 36 times the bytes of a level operator; no incremental assembly)
+// and V^dual (about n / 2 vertices, DF64 plus the packed copy: 2.5 n^2 bytes).
+int64_t estimate_bytes(int64_t N0, int64_t max_N, int32_t levels, int precision, int basis)
 {
     const double es = precision == BEM_PREC_F32 ? 4.0 : 8.0;
     double reach = 1.5 * (double)(max_N > N0 ? max_N : N0);
     const double grown = (double)N0 * std::pow(2.2, (double)(levels - 1));
     if (grown < reach) reach = grown;
     const double n = (levels <= 1 ? (double)N0 : reach) + 64.0;
+    if (basis == BEM_BASIS_DUAL) return (int64_t)((36.0 * es + 2.5) * n * n + 6.0 * 4096.0 * n) + (64ll << 20);
     const double ops = levels <= 1 ? (precision == BEM_PREC_DF64 ? 1.25 : precision == BEM_PREC_F32 ? 1.5 : 1.0) : 2.0;
     return (int64_t)(ops * es * n * n + 4096.0 * n) + (64ll << 20);
 }
@@ -167,6 +171,7 @@ bem_status bem_server_create(int32_t slots, int64_t hbm_budget_bytes, const bem_
 {
     if (!out || !opts || slots < 1 || slots > 256 || hbm_budget_bytes <= 0) return BEM_ERR_INVALID;
     if (!(opts->theta > 0.0 && opts->theta <= 1.0)) return BEM_ERR_INVALID;
+    if (opts->basis != BEM_BASIS_P0 && opts->basis != BEM_BASIS_DUAL) return BEM_ERR_INVALID;
     bem_server *s = new (std::nothrow) bem_server();
     if (!s) return BEM_ERR_OOM;
     if (cudaGetDevice(&s->device) != cudaSuccess) {
@@ -192,7 +197,7 @@ bem_status bem_server_submit(bem_server *s, const double *verts, int64_t M, cons
     r->tris.assign(tris, tris + 3 * N);
     r->max_levels = max_levels;
     r->max_N = max_N > 0 ? max_N : N;
-    r->estimate = estimate_bytes(N, r->max_N, max_levels, s->opts.assembly.precision);
+    r->estimate = estimate_bytes(N, r->max_N, max_levels, s->opts.assembly.precision, s->opts.basis);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) {

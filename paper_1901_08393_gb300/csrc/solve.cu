@@ -1629,6 +1629,8 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     const int64_t N = op->N, L = op->ld;
     if (o->precond < BEM_PRECOND_NONE || o->precond > BEM_PRECOND_BLOCK)
         return set_error(ctx, BEM_ERR_INVALID, "unknown preconditioner %d", o->precond);
+    if (o->inexact_lambda > 0.0 && m->cells_only)
+        return set_error(ctx, BEM_ERR_INVALID, "the inexact stopping rule needs a triangle mesh (not a dual operator)");
     if (o->precond == BEM_PRECOND_BLOCK && (op->precision == BEM_PREC_F64 || !ctx->persistent_solver))
         return set_error(ctx, BEM_ERR_INVALID,
                          "BEM_PRECOND_BLOCK is implemented by the persistent solver (DF64 and FP32 operators)");
