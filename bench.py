@@ -226,9 +226,13 @@ def dual_workload(args):
     cube = inputs.cube_mesh(1)
     mesh = bem.Mesh.upload(ctx, cube.verts, cube.tris)
 
-    def run(msh, basis, n=max_n):
+    pcs = {"block": bem.PRECOND_BLOCK, "jacobi": bem.PRECOND_JACOBI, "calderon": bem.PRECOND_CALDERON}
+
+    def run(msh, basis, n=max_n, pc=args.precond):
+        if basis == bem.BASIS_P0 and pc == "calderon":
+            pc = "block"
         return bem.adaptive_run(msh, theta=THETA, max_N=n, max_levels=200, tol=TOL, precision=bem.PREC_DF64,
-                                precond=bem.PRECOND_BLOCK, basis=basis)[0]
+                                precond=pcs[pc], basis=basis)[0]
 
     for _ in range(max(args.warmup, 0)):
         flush.fill_(1)
@@ -277,13 +281,19 @@ def dual_workload(args):
     results = {"cube_dual": table(recs, CUBE_CAP), "cube_p0": table(run(mesh, bem.BASIS_P0), CUBE_CAP),
                "fichera_dual": table(run(fmesh, bem.BASIS_DUAL), FICHERA_CAP),
                "fichera_p0": table(run(fmesh, bem.BASIS_P0), FICHERA_CAP)}
+    # PCG iterations per level of the dual cube run with each preconditioner (untimed;
+    # the runs may break the cube's symmetric ties differently, so N is listed with them)
+    results["iterations"] = {pc: [(r["N"], r["iterations"], round(r["ms_solve"], 3)) for r in run(mesh, bem.BASIS_DUAL, pc=pc)]
+                             for pc in ("jacobi", "block", "calderon")}
     line = {"metric": "dual-basis adaptive capacity runs/s (Sec. 2.6 Galerkin system, Alg. 1)",
             "value": args.steps / (total_ms / 1e3), "unit": "adaptive runs/s", "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64", "data": "synthetic",
             "config": {"workload": f"unit cube (12 triangles), dual basis, ZZ (Eq. 1.6) + Doerfler theta=0.5 + NVB "
-                                   f"until N >= {max_n}; DF64 assembly of the barycentric operator, block-Jacobi "
-                                   "PCG to 1e-10",
+                                   f"until N >= {max_n}; DF64 assembly of the barycentric operator, PCG to 1e-10",
+                       "preconditioner": {"block": "block Jacobi (Morton clusters of 64 vertices)",
+                                          "jacobi": "diag(V^dual)",
+                                          "calderon": "operator preconditioning S D^reg S (Sec. 2.6)"}[args.precond],
                        "final_N": recs[-1]["N"], "final_M": recs[-1]["M"], "levels": len(recs),
                        "cap_final": recs[-1]["cap"], "references": {"cube": CUBE_CAP, "fichera": FICHERA_CAP},
                        "l2": "256 MB buffer written before every step"},
@@ -559,9 +569,10 @@ def main():
     ap.add_argument("--requests", type=int, default=200, help="serve: requests per step")
     ap.add_argument("--batch", type=int, default=64, help="batch: meshes per step")
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
-    ap.add_argument("--precond", default="auto", choices=["auto", "block", "jacobi"],
+    ap.add_argument("--precond", default="auto", choices=["auto", "block", "jacobi", "calderon"],
                     help="PCG preconditioner (block: DF64 and FP32 operators, FP64 runs Jacobi); auto: "
-                         "block, except jacobi on the graded cube (its V has indefinite diagonal blocks)")
+                         "block, except jacobi on the graded cube (its V has indefinite diagonal blocks); "
+                         "calderon: the operator preconditioner of Sec. 2.6 (dual workload only)")
     ap.add_argument("--inexact", type=float, default=0.0,
                     help="adaptive workload: stop each solve by the rule of the Remark after Alg. 1 (i), "
                          "|||x_k - x_(k-1)||| <= LAMBDA eta(x_k) (the paper uses ~1e-3); 0: PCG to 1e-10")
@@ -572,6 +583,8 @@ def main():
         return reference_arm(args)
     if args.precond == "auto":
         args.precond = "jacobi" if args.workload == "graded60k" else "block"
+    if args.precond == "calderon" and args.workload != "dual":
+        ap.error("--precond calderon needs --workload dual")
     if args.workload == "batch":
         return batch_workload(args)
     if args.workload == "condition":

@@ -74,11 +74,19 @@ typedef struct {
  * consecutive clusters of 64; M = the block diagonal of V over the clusters, each
  * block inverted in FP64 (Cholesky).  DF64 operators, persistent solver. */
 #define BEM_PRECOND_BLOCK 2
+/* Operator preconditioning with the regularised hypersingular operator (Sec. 2.6),
+ * for dual operators (bem_operator_dual): C = S D^reg S with D^reg = sum_m Q_m^T V^bary
+ * Q_m + a a^T and S the degree-6 Chebyshev approximation of M^-1 (M the mass matrix of
+ * hats against dual cells, Jacobi-scaled spectrum in [15/22, 36/22]; S agrees with M^-1
+ * to 2e-4 relative).  C is SPD, so CG on V^dual x = f with C has the spectrum of the
+ * paper's M^-T V^dual M^-1 D^reg (solved there by GMRES) and reaches the same x.
+ * DF64 dual operators, persistent solver, not in a batch. */
+#define BEM_PRECOND_CALDERON 3
 
 typedef struct {
     double tol;            /* relative residual ||b - V x|| / ||b|| to reach (e.g. 1e-10) */
     int32_t max_it;        /* iteration cap (inner iterations for FP32 operators) */
-    int32_t precond;       /* BEM_PRECOND_NONE, _JACOBI (diag(V), Sec. 3) or _BLOCK */
+    int32_t precond;       /* BEM_PRECOND_NONE, _JACOBI (diag(V), Sec. 3), _BLOCK or _CALDERON */
     int32_t max_outer;     /* FP32 operators: FP64 iterative-refinement sweeps (default 20) */
     double inner_tol;      /* FP32 operators: relative tolerance of each inner solve (default 1e-5) */
     double reliable_delta; /* DF64 operators, persistent solver: the iteration's products use the
@@ -277,6 +285,13 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
                             int32_t *n_levels, bem_mesh **final_mesh);
 
 /* ---------------------------------------------------------------- dual basis */
+/* bem_operator_dual also forms the operator preconditioner of Sec. 2.6 from the same
+ * V^bary (BEM_PRECOND_CALDERON): V^T = R^T V^bary R (the six children of each primal
+ * triangle summed), D_ij = sum over T at i, T' at j of (curl phi_i|T . curl phi_j|T')
+ * V^T[T][T'] with curl phi_k = (p_(k+1) - p_(k+2)) / (2 |T|) on T (the surface curl
+ * n x grad of the hat of local vertex k), plus a_i a_j, a_i = |T_i^dual| = the integral
+ * of the hat; stored in FP32 (4 M^2 bytes) with the operator, beside copies of the
+ * primal mesh's triangles, vertex-to-triangle table and areas for the mass matrix. */
 /* The paper's own discretisation (Sec. 2.1-2.6): piecewise constants on the dual mesh.
  * bem_mesh_barycentric: the barycentric refinement T^bary of the (stored, rotated)
  * mesh (Sec. 2.1): each triangle (v0, v1, v2) becomes (v0, m01, c), (m01, v1, c),
@@ -300,6 +315,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
 bem_status bem_mesh_barycentric(bem_mesh *mesh, bem_mesh **out);
 bem_status bem_operator_dual(bem_operator *bary_op, bem_mesh *mesh, bem_operator **out);
 bem_status bem_zz_estimate_dual(bem_mesh *mesh, const double *x, int32_t h_mode, double *eta2_out, double *totals);
+/* The FP32 D^reg of a dual operator, M x M row-major into dst (host or device);
+ * BEM_ERR_INVALID for an operator without it. */
+bem_status bem_operator_preconditioner(const bem_operator *op, float *dst);
 
 /* ---------------------------------------------------------------- batch */
 /* Many independent capacity problems assembled and solved together (the paper has

@@ -28,6 +28,7 @@ PREC_DF64 = 2
 PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_BLOCK = 2
+PRECOND_CALDERON = 3
 REFINE_BISEC3 = 1
 BASIS_P0 = 0
 BASIS_DUAL = 1
@@ -41,7 +42,7 @@ EXPORTS = [
     "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc", "bem_context_set_persistent",
     "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
     "bem_batch_create", "bem_batch_run", "bem_batch_info", "bem_batch_destroy",
-    "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual",
+    "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual", "bem_operator_preconditioner",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -156,6 +157,7 @@ def lib():
         "bem_mesh_barycentric": [vp, P(vp)],
         "bem_operator_dual": [vp, vp, P(vp)],
         "bem_zz_estimate_dual": [vp, vp, i32, vp, vp],
+        "bem_operator_preconditioner": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -354,6 +356,13 @@ class Operator:
         Ja, pJ = _arr(J, np.int64)
         out = np.zeros(int(Ia.shape[0]))
         self.ctx.check(self.ctx.L.bem_operator_entries(self.h, pI, pJ, int(Ia.shape[0]), out.ctypes.data))
+        return out
+
+    def preconditioner(self):
+        """D^reg of a dual operator (Sec. 2.6), FP32, M x M."""
+        N = self.info()[0]
+        out = np.zeros((N, N), dtype=np.float32)
+        self.ctx.check(self.ctx.L.bem_operator_preconditioner(self.h, out.ctypes.data))
         return out
 
     def matvec(self, x):

@@ -5,6 +5,7 @@
 // separately in the order written, so the indicators, and the decisions taken
 // from them, are bit-identical to a plain IEEE-754 evaluation of the same
 // formulas.
+#include <algorithm>
 #include <cmath>
 #include <new>
 #include <type_traits>
@@ -733,6 +734,136 @@ bem_status zz_estimate_dual(bem_mesh *m, const double *d_x, int h_mode, double *
     return st;
 }
 
+// ---- operator preconditioner (Sec. 2.6)
+// V^T[T][T'] = sum of V^bary over the 6 x 6 children of T and T' (R^T V^bary R, R the
+// map of a primal triangle to its six children): the P0 Galerkin matrix of the primal
+// triangles evaluated with the barycentric quadrature.  Rows strided over grid y.
+template <typename T>
+__global__ void k_contract_children(const T *__restrict__ Vb, int64_t ldb, int64_t N, double *__restrict__ VT)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= N) return;
+    for (int64_t i = blockIdx.y; i < N; i += gridDim.y) {
+        double s = 0.0;
+        for (int a = 0; a < 6; ++a) {
+            const int64_t row = (6 * i + a) * ldb + 6 * j;
+            for (int b = 0; b < 6; ++b) s += vb_elem(Vb, row + b);
+        }
+        VT[i * N + j] = s;
+    }
+}
+
+// Surface curl of the hat of vertex z on triangle t: n x grad phi_z = (p_(k+1) - p_(k+2))
+// / (2 |T|) for z the local vertex k of t (n the unit normal of the vertex order).
+__device__ __forceinline__ void hat_curl(const double *V, const int32_t *tris, const double *area, int32_t t, int64_t z,
+                                         double g[3])
+{
+    const int32_t *tv = tris + 3 * (int64_t)t;
+    const int k = tv[0] == z ? 0 : (tv[1] == z ? 1 : 2);
+    const double *p1 = V + 3 * (int64_t)tv[(k + 1) % 3], *p2 = V + 3 * (int64_t)tv[(k + 2) % 3];
+    const double s = 1.0 / (2.0 * area[t]);
+    for (int c = 0; c < 3; ++c) g[c] = (p1[c] - p2[c]) * s;
+}
+
+// D^reg[i][j] = sum_{T at i} sum_{T' at j} (curl phi_i|T . curl phi_j|T') V^T[T][T'] +
+// a_i a_j, j >= i, mirrored, stored FP32.  One CTA row i: its star and curls in
+// shared memory; one thread per column j.
+constexpr int kMaxStar = 32;
+
+__global__ void k_hypersingular(const double *V, const int32_t *tris, const int32_t *v2t_off, const int32_t *v2t,
+                                const double *area, const double *__restrict__ VT, int64_t N, const double *a_int,
+                                int64_t M, float *Dm, int64_t ldd, int *bad)
+{
+    __shared__ int32_t st[kMaxStar];
+    __shared__ double sg[kMaxStar][3];
+    __shared__ int s_n;
+    for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int n = v2t_off[i + 1] - v2t_off[i];
+            if (n > kMaxStar) atomicExch(bad, 1);
+            s_n = n < kMaxStar ? n : kMaxStar;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < s_n) {
+            const int32_t t = v2t[v2t_off[i] + threadIdx.x];
+            st[threadIdx.x] = t;
+            hat_curl(V, tris, area, t, i, sg[threadIdx.x]);
+        }
+        __syncthreads();
+        const int64_t j = i + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        if (j >= M) continue;
+        double acc = 0.0;
+        const int nj = min(v2t_off[j + 1] - v2t_off[j], kMaxStar);
+        for (int q = 0; q < nj; ++q) {
+            const int32_t tj = v2t[v2t_off[j] + q];
+            double g[3];
+            hat_curl(V, tris, area, tj, j, g);
+            for (int p = 0; p < s_n; ++p) {
+                const double dot = (sg[p][0] * g[0] + sg[p][1] * g[1]) + sg[p][2] * g[2];
+                acc += dot * __ldg(VT + (int64_t)st[p] * N + tj);
+            }
+        }
+        const float v = __double2float_rn(acc + a_int[i] * a_int[j]);
+        Dm[i * ldd + j] = v;
+        Dm[j * ldd + i] = v;
+    }
+}
+
+// 1 / diag of the mass matrix M[i][j] = int phi_j chi_i^dual: M_ii = sum_{T at i} 22 |T| / 108.
+__global__ void k_mass_dinv(const int32_t *v2t_off, const int32_t *v2t, const double *area, int64_t M, double *dinv)
+{
+    const int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (z >= M) return;
+    double s = 0.0;
+    for (int32_t p = v2t_off[z]; p < v2t_off[z + 1]; ++p) s += area[v2t[p]];
+    dinv[z] = 108.0 / (22.0 * s);
+}
+
+static bem_status calderon_setup(bem_operator *ob, bem_mesh *pm, bem_operator *op, int *bad)
+{
+    bem_ctx *ctx = pm->ctx;
+    cudaStream_t s = ctx->stream;
+    const int64_t N = pm->N, M = pm->M;
+    Allocs tmp;
+    double *VT = nullptr;
+    bem_status st = dalloc(ctx, op->allocs, (void **)&op->cal_D, sizeof(float) * (size_t)M * (size_t)op->ld, true);
+    if (!st) st = dalloc(ctx, op->allocs, (void **)&op->cal_tris, sizeof(int32_t) * (3 * N + M + 1 + 3 * N), false);
+    if (!st) st = dalloc(ctx, op->allocs, (void **)&op->cal_area, sizeof(double) * (N + M), false);
+    if (!st) st = dalloc(ctx, tmp, (void **)&VT, sizeof(double) * (size_t)N * (size_t)N, false);
+    if (st) {
+        dfree_all(ctx, tmp);
+        return st;
+    }
+    op->cal_N = N;
+    op->cal_v2t_off = op->cal_tris + 3 * N;
+    op->cal_v2t = op->cal_v2t_off + M + 1;
+    op->cal_mdinv = op->cal_area + N;
+    cudaError_t e = cudaMemcpyAsync(op->cal_tris, pm->tris, sizeof(int32_t) * 3 * N, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(op->cal_v2t_off, pm->v2t_off, sizeof(int32_t) * (M + 1), cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(op->cal_v2t, pm->v2t, sizeof(int32_t) * 3 * N, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(op->cal_area, pm->area, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+        dfree_all(ctx, tmp);
+        return cuda_error(ctx, e, "preconditioner tables");
+    }
+    k_mass_dinv<<<nblk(M, 256), 256, 0, s>>>(pm->v2t_off, pm->v2t, pm->area, M, op->cal_mdinv); BEM_COUNT(ctx);
+    const dim3 gc((unsigned)nblk(N, 128), (unsigned)std::min<int64_t>(N, 65535));
+    if (ob->precision == BEM_PREC_F64)
+        { k_contract_children<double><<<gc, 128, 0, s>>>((const double *)ob->V, ob->ld, N, VT); BEM_COUNT(ctx); }
+    else if (ob->precision == BEM_PREC_DF64)
+        { k_contract_children<float2><<<gc, 128, 0, s>>>((const float2 *)ob->V, ob->ld, N, VT); BEM_COUNT(ctx); }
+    else
+        { k_contract_children<float><<<gc, 128, 0, s>>>((const float *)ob->V, ob->ld, N, VT); BEM_COUNT(ctx); }
+    const dim3 gh((unsigned)nblk(M, 128), (unsigned)std::min<int64_t>(M, 65535));
+    k_hypersingular<<<gh, 128, 0, s>>>(pm->verts, pm->tris, pm->v2t_off, pm->v2t, pm->area, VT, N,
+                                       op->mesh->area, M, op->cal_D, op->ld, bad); BEM_COUNT(ctx);
+    e = cudaGetLastError();
+    dfree_all(ctx, tmp);  // stream-ordered: freed after the kernels that read it
+    return e == cudaSuccess ? BEM_OK : cuda_error(ctx, e, "preconditioner kernels");
+}
+
 // The dual operator of primal mesh pm from the operator of its barycentric refinement:
 // an M x M operator (DF64, or F64 for an F64 barycentric operator) over a cells mesh
 // (N = M cells: dual areas as |T|, the vertices as centroids) owned by the operator.
@@ -778,6 +909,7 @@ bem_status dual_operator(bem_operator *ob, bem_mesh *pm, bem_operator **out)
             { k_dual_operator<float, float2><<<grid, 128, 0, s>>>((const float *)ob->V, ob->ld, pm->tris, pm->v2t_off, pm->v2t, M, (float2 *)op->V, op->ld, bad); BEM_COUNT(ctx); }
     }
     if (!st) st = operator_diag(op);
+    if (!st) st = calderon_setup(ob, pm, op, bad);
     if (!st) {
         cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

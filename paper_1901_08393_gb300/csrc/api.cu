@@ -571,6 +571,18 @@ bem_status bem_zz_estimate_dual(bem_mesh *mesh, const double *x, int32_t h_mode,
     return dev_out_end(ctx, eta2_out, de);
 }
 
+bem_status bem_operator_preconditioner(const bem_operator *op, float *dst)
+{
+    if (!op) return BEM_ERR_INVALID;
+    bem_ctx *ctx = op->ctx;
+    CHECK_ARG(ctx, dst != nullptr, "null destination");
+    CHECK_ARG(ctx, op->cal_D != nullptr, "the operator carries no preconditioner (not a dual operator)");
+    cudaError_t e = cudaMemcpy2DAsync(dst, sizeof(float) * op->N, op->cal_D, sizeof(float) * op->ld,
+                                      sizeof(float) * op->N, op->N, cudaMemcpyDefault, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    return e == cudaSuccess ? BEM_OK : cuda_error(ctx, e, "preconditioner read");
+}
+
 bem_status bem_operator_info(const bem_operator *op, int64_t *N, int32_t *precision)
 {
     if (!op) return BEM_ERR_INVALID;
@@ -688,7 +700,7 @@ bem_status bem_solve_capacity(bem_operator *op, const bem_solve_opts *opts, cons
     bem_ctx *ctx = op->mesh->ctx;
     CHECK_ARG(ctx, cap_out != nullptr, "null cap_out");
     const bem_solve_opts o = opts ? *opts : default_solve_opts();
-    CHECK_ARG(ctx, o.precond >= BEM_PRECOND_NONE && o.precond <= BEM_PRECOND_BLOCK, "unknown preconditioner");
+    CHECK_ARG(ctx, o.precond >= BEM_PRECOND_NONE && o.precond <= BEM_PRECOND_CALDERON, "unknown preconditioner");
     CHECK_ARG(ctx, !(o.tol < 0), "negative tolerance");
     const size_t vb = sizeof(double) * op->N;
     DevBuf dx0, dphi;
@@ -810,6 +822,7 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
     CHECK_ARG(ctx, opts->basis == BEM_BASIS_P0 || opts->basis == BEM_BASIS_DUAL, "unknown basis");
     const bool dual = opts->basis == BEM_BASIS_DUAL;
     CHECK_ARG(ctx, !(dual && opts->solve.inexact_lambda > 0.0), "the inexact stopping rule needs the P0 basis");
+    CHECK_ARG(ctx, dual || opts->solve.precond != BEM_PRECOND_CALDERON, "BEM_PRECOND_CALDERON needs the dual basis");
     if (final_mesh) *final_mesh = nullptr;
     *n_levels = 0;
     cudaStream_t s = ctx->stream;

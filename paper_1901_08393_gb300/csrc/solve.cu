@@ -911,7 +911,21 @@ struct PcgArgs {
     const double *area, *hdiam;  // hdiam: diam(T), or null for h_T = |T|^1/2
     double *u;                   // M nodal values
     int64_t M;
+    // operator preconditioning (Sec. 2.6): packed FP32 upper triangle of D^reg (the
+    // tiles of vp), primal mesh of the dual cells for the mass matrix, 4 x ld work
+    const float *dvp;
+    const int32_t *mtris, *mv2t_off, *mv2t;
+    const double *marea, *mdinv;
+    double *cw;
 };
+
+// Chebyshev iteration for the mass matrix M[i][j] = int phi_j chi_i^dual with Jacobi
+// scaling: per triangle M_T = (|T| / 108) (15 I + 7 J) against diag 22 |T| / 108, so the
+// spectrum of D^-1 M lies in [15/22, 36/22] on every mesh; theta and delta are the
+// centre and half-width of that interval, kChebSteps the degree (error factor
+// 2 ((sqrt(2.4) - 1) / (sqrt(2.4) + 1))^6 = 2e-4).
+constexpr double kChebTheta = 51.0 / 44.0, kChebDelta = 21.0 / 44.0;
+constexpr int kChebSteps = 6;
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int G)
 {
@@ -980,6 +994,9 @@ __device__ __forceinline__ double grid_total(const double *slot, int G)
     return res;
 }
 
+// kCal: the build with the operator preconditioner (BEM_PRECOND_CALDERON), kept out of
+// the other solvers' kernels (its Chebyshev and D^reg phases cost registers).
+template <bool kCal>
 __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const int cta)
 {
     extern __shared__ float2 sm[];
@@ -988,6 +1005,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     double *pA = a.part, *pB = a.part + G, *pC = a.part + 2 * G;
     const bool mixed = a.vp != nullptr;
     const bool blockpc = a.precond == BEM_PRECOND_BLOCK, jacobi = a.precond == BEM_PRECOND_JACOBI;
+    const bool calpc = kCal && a.precond == BEM_PRECOND_CALDERON;
+    const bool zlocal = !blockpc && !calpc;  // z_i from r_i alone
     float2 *const xsw = sm + (threadIdx.x >> 5) * 2 * kSB;
     __shared__ double rs[kBJ];
     const int lane = threadIdx.x & 31, q4 = lane & 3;
@@ -1008,6 +1027,66 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         }
         return grid_barrier(a.bar, a.err, G);
     };
+    // dst = S src: kChebSteps steps of Chebyshev iteration on the Jacobi-scaled mass
+    // matrix (rows i0 + k stride; the directions double-buffered, so one grid barrier
+    // per step separates a direction's writes from its neighbours' reads)
+    auto cheb = [&](const double *src, double *dst) -> bool {
+        double *res = a.cw, *dc = a.cw + a.ld, *dn = a.cw + 2 * a.ld;
+        double rho = kChebDelta / kChebTheta;
+        for (int64_t i = i0; i < a.N; i += stride) {
+            const double ri = src[i];
+            const double di = ri * a.mdinv[i] / kChebTheta;
+            res[i] = ri;
+            dc[i] = di;
+            dst[i] = di;
+        }
+        for (int k = 1; k < kChebSteps; ++k) {
+            if (!grid_barrier(a.bar, a.err, G)) return false;
+            const double rn = 1.0 / (2.0 * (kChebTheta / kChebDelta) - rho);
+            for (int64_t i = i0; i < a.N; i += stride) {
+                const double di = dc[i];
+                double md = 0.0;
+                for (int32_t q = a.mv2t_off[i]; q < a.mv2t_off[i + 1]; ++q) {
+                    const int32_t t = a.mv2t[q];
+                    double o = 0.0;
+                    for (int c = 0; c < 3; ++c) {
+                        const int32_t v = a.mtris[3 * (int64_t)t + c];
+                        if (v != i) o += __ldcg(dc + v);  // other CTAs' rows: L2
+                    }
+                    md += a.marea[t] * (22.0 * di + 7.0 * o);
+                }
+                const double ri = res[i] - md / 108.0;
+                res[i] = ri;
+                const double dni = rn * rho * di + (2.0 * rn / kChebDelta) * ri * a.mdinv[i];
+                dn[i] = dni;
+                dst[i] += dni;
+            }
+            rho = rn;
+            double *tmp = dc;
+            dc = dn;
+            dn = tmp;
+        }
+        return true;
+    };
+    // z = S D^reg S r (operator preconditioning, Sec. 2.6): Chebyshev, the product with
+    // the packed FP32 D^reg (exact products, double-float sums), Chebyshev
+    auto calderon = [&]() -> bool {
+        double *t = a.cw + 3 * a.ld;
+        if (!cheb(a.r, t)) return false;
+        for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(t[i]) : make_float2(0.f, 0.f);
+        if (!grid_barrier(a.bar, a.err, G)) return false;
+        symv_hi_tiles(a.dvp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
+        tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+        if (!grid_barrier(a.bar, a.err, G)) return false;
+        for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
+            const int64_t i = ib + (lane >> 2);
+            const bool valid = i < a.N;
+            const double ti = symv_row4(a.prow, a.pcol, a.nb, valid ? i : a.N - 1, q4);
+            if (valid && q4 == 0) t[i] = ti;
+        }
+        if (!grid_barrier(a.bar, a.err, G)) return false;
+        return cheb(t, a.z);
+    };
     // r = b - V x0 (or b), z = M^-1 r, p = z
     const bool prod0 = a.has_x0 || mixed;
     if (prod0 && !df64_product(mixed)) return;
@@ -1017,7 +1096,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
             const double ri = a.b[i] - (a.has_x0 ? symv_row(a.prow, a.pcol, a.nb, i) : 0.0);
             a.r[i] = ri;
             bb_l += a.b[i] * a.b[i];
-            if (!blockpc) {
+            if (zlocal) {
                 const double zi = jacobi ? ri / a.d[i] : ri;
                 a.z[i] = zi;
                 a.p[i] = zi;
@@ -1033,6 +1112,16 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         if (!grid_barrier(a.bar, a.err, G)) return;
         for (int blk = cta; blk < a.nbj; blk += G)
             block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, true, rs, rz_l, rr_l);
+    }
+    if (calpc) {  // rows of r are this thread's own: no barrier before the first Chebyshev step
+        if (!calderon()) return;
+        for (int64_t i = i0; i < a.N; i += stride) {
+            const double ri = a.r[i], zi = a.z[i];
+            a.p[i] = zi;
+            a.pdf[i] = df_from_double(zi);
+            rz_l += ri * zi;
+            rr_l += ri * ri;
+        }
     }
     cta_partial(rz_l, pA, cta);
     cta_partial(rr_l, pB, cta);
@@ -1075,6 +1164,15 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         if (blockpc) {
             for (int blk = cta; blk < a.nbj; blk += G)
                 block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, alpha, true, false, rs, rz_n, rr_l);
+        } else if (calpc) {
+            for (int64_t i = i0; i < a.N; i += stride) {
+                a.x[i] += alpha * a.p[i];
+                const double ri = a.r[i] - alpha * a.q[i];
+                a.r[i] = ri;
+                rr_l += ri * ri;
+            }
+            if (!calderon()) return;
+            for (int64_t i = i0; i < a.N; i += stride) rz_n += a.r[i] * a.z[i];
         } else {
             for (int64_t i = i0; i < a.N; i += stride) {
                 a.x[i] += alpha * a.p[i];
@@ -1134,7 +1232,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 if (valid && q4 == 0) {
                     const double ri = a.b[i] - vi;
                     a.r[i] = ri;
-                    if (!blockpc) {
+                    if (zlocal) {
                         const double zi = jacobi ? ri / a.d[i] : ri;
                         a.z[i] = zi;
                         rz_n += ri * zi;
@@ -1147,6 +1245,13 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 for (int blk = cta; blk < a.nbj; blk += G)
                     block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, false, rs, rz_n,
                                 rr_l);
+            } else if (calpc) {  // r was written in the row-pass layout: barrier first
+                if (!grid_barrier(a.bar, a.err, G)) return;
+                if (!calderon()) return;
+                for (int64_t i = i0; i < a.N; i += stride) {
+                    rz_n += a.r[i] * a.z[i];
+                    rr_l += a.r[i] * a.r[i];
+                }
             }
             cta_partial(rz_n, pB, cta);
             cta_partial(rr_l, pC, cta);
@@ -1178,7 +1283,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     }
 }
 
-__global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a) { pcg_body(a, gridDim.x, blockIdx.x); }
+__global__ void __launch_bounds__(kSymThreads, 3) k_pcg_df(PcgArgs a) { pcg_body<false>(a, gridDim.x, blockIdx.x); }
+__global__ void __launch_bounds__(kSymThreads, 3) k_pcg_cal(PcgArgs a) { pcg_body<true>(a, gridDim.x, blockIdx.x); }
 
 // Independent solves in one cooperative launch: problem p owns the CTAs
 // [begin[p], begin[p + 1]) and runs the same solver on them, with its own grid
@@ -1204,7 +1310,7 @@ __global__ void __launch_bounds__(kSymThreads, 3) k_pcg_batch(const PcgArgs *__r
     const int p = s_p;
     const int b0 = begin[p], b1 = begin[p + 1];
     if ((int)blockIdx.x >= b1) return;  // CTAs past the last group
-    pcg_body(sa, b1 - b0, (int)blockIdx.x - b0);
+    pcg_body<false>(sa, b1 - b0, (int)blockIdx.x - b0);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1468,8 +1574,9 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     BEM_CK(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
     if (!coop || !W.tiles) return BEM_OK;
     if (f32op) delta = 1.0;  // a packed copy is needed; residuals are replaced only at convergence
-    BEM_CK(ctx, cudaFuncSetAttribute(k_pcg_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
-    BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_df, kSymThreads, kSymSmem));
+    const void *kern = precond == BEM_PRECOND_CALDERON ? (const void *)k_pcg_cal : (const void *)k_pcg_df;
+    BEM_CK(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
+    BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSymThreads, kSymSmem));
     if (per_sm < 1) return BEM_OK;
     const int nb_ = (int)(op->ld / kSB), nt_ = nb_ * (nb_ + 1) / 2;
     Allocs tmp;
@@ -1481,6 +1588,18 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
             if ((st = dalloc(ctx, tmp, (void **)&vp, vbytes, false))) return st;
     }
     if (f32op && !vp) return BEM_OK;  // no room for the packed copy: host-driven refinement
+    const bool calpc = precond == BEM_PRECOND_CALDERON;
+    float *dvp = nullptr;
+    double *cw = nullptr;
+    if (calpc) {  // packed D^reg (the tiles of the operator's packed copy) and Chebyshev work
+        if ((st = dalloc(ctx, tmp, (void **)&dvp, (size_t)nt_ * kTileF * sizeof(float), false)) ||
+            (st = dalloc(ctx, tmp, (void **)&cw, sizeof(double) * 4 * op->ld, true))) {
+            dfree_all(ctx, tmp);
+            return st;
+        }
+        k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt_ * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256, 0,
+                     ctx->stream>>>(op->cal_D, op->ld, op->N, W.tiles, nt_, dvp); BEM_COUNT(ctx);
+    }
     if (f32op) {
         k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt_ * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256, 0,
                      ctx->stream>>>((const float *)op->V, op->ld, op->N, W.tiles, nt_, vp); BEM_COUNT(ctx);
@@ -1553,9 +1672,16 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.max_it = max_it;
     a.precond = precond;
     a.has_x0 = has_x0 ? 1 : 0;
+    a.dvp = dvp;
+    a.mtris = op->cal_tris;
+    a.mv2t_off = op->cal_v2t_off;
+    a.mv2t = op->cal_v2t;
+    a.marea = op->cal_area;
+    a.mdinv = op->cal_mdinv;
+    a.cw = cw;
     void *args[] = {&a};
     const int prof = prof_start(ctx, BEM_KERNEL_MATVEC, 0.0);
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_pcg_df, dim3(G), dim3(kSymThreads), args, kSymSmem,
+    cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(kSymThreads), args, kSymSmem,
                                                 ctx->stream);
     BEM_COUNT(ctx);
     prof_stop(ctx, prof);
@@ -1584,9 +1710,11 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
             // (8 bytes x N^2 / 2); a mixed-mode iteration reads the packed FP32 upper
             // triangle (4 x N^2 / 2), written once by the first product
             const double n2 = (double)op->N * (double)op->N;
-            const double bytes = f32op ? 2.0 * n2 * (h[2] + h[3])
-                                 : vp  ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
-                                       : 4.0 * n2 * (h[2] + h[3]);
+            // (+ the packed FP32 D^reg once per preconditioner application)
+            const double bytes = (f32op ? 2.0 * n2 * (h[2] + h[3])
+                                  : vp  ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
+                                        : 4.0 * n2 * (h[2] + h[3])) +
+                                 (calpc ? 2.0 * n2 * (h[2] + h[3]) : 0.0);
             prof_set_units(ctx, prof, bytes);
             // Lanczos tridiagonal matrix of the CG coefficients
             const int k = std::min((int)h[2] - (h[4] != 0.0 ? 1 : 0), lcap);  // an inexact stop records no beta
@@ -1627,8 +1755,12 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     bem_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
     const int64_t N = op->N, L = op->ld;
-    if (o->precond < BEM_PRECOND_NONE || o->precond > BEM_PRECOND_BLOCK)
+    if (o->precond < BEM_PRECOND_NONE || o->precond > BEM_PRECOND_CALDERON)
         return set_error(ctx, BEM_ERR_INVALID, "unknown preconditioner %d", o->precond);
+    if (o->precond == BEM_PRECOND_CALDERON &&
+        (!op->cal_D || op->precision == BEM_PREC_F64 || !ctx->persistent_solver))
+        return set_error(ctx, BEM_ERR_INVALID,
+                         "BEM_PRECOND_CALDERON needs a DF64 dual operator (bem_operator_dual) and the persistent solver");
     if (o->inexact_lambda > 0.0 && m->cells_only)
         return set_error(ctx, BEM_ERR_INVALID, "the inexact stopping rule needs a triangle mesh (not a dual operator)");
     if (o->precond == BEM_PRECOND_BLOCK && (op->precision == BEM_PREC_F64 || !ctx->persistent_solver))
@@ -1697,8 +1829,8 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
             st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, bperm,
                                 binv, nbj, o->inexact_lambda, o->h_mode, &its, &outer, &rel, &ran, &lam_min, &lam_max,
                                 &inexact);
-        if (!st && !ran && precond == BEM_PRECOND_BLOCK)
-            st = set_error(ctx, BEM_ERR_CUDA, "BEM_PRECOND_BLOCK: the persistent solver could not be launched");
+        if (!st && !ran && (precond == BEM_PRECOND_BLOCK || precond == BEM_PRECOND_CALDERON))
+            st = set_error(ctx, BEM_ERR_CUDA, "this preconditioner needs the persistent solver, which could not be launched");
         if (st) goto out;
     }
     if (ran) {
@@ -1875,7 +2007,7 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
         return set_error(ctx, BEM_ERR_INVALID, "a batch needs BEM_PREC_DF64 or BEM_PREC_F32 operators");
     const int precond = sopts ? sopts->precond : BEM_PRECOND_JACOBI;
     if (precond < BEM_PRECOND_NONE || precond > BEM_PRECOND_BLOCK)
-        return set_error(ctx, BEM_ERR_INVALID, "unknown preconditioner %d", precond);
+        return set_error(ctx, BEM_ERR_INVALID, "preconditioner %d: a batch takes NONE, JACOBI or BLOCK", precond);
     for (int p = 0; p < count; ++p)
         if (!meshes[p] || meshes[p]->ctx != ctx) return set_error(ctx, BEM_ERR_INVALID, "mesh %d is not of this context", p);
     int coop = 0, per_sm = 0;
