@@ -157,6 +157,52 @@ def reference_arm(args):
     return 0
 
 
+def roofline(prec, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src, mv_kernel=None):
+    """Roofline object of the dominant kernel (far field or solver) from the library's
+    CUDA-event profiler: per-launch algorithmic work over the average launch time."""
+    if far_ms >= mv_ms and prec == 1:
+        rs = far_units * 49 / max(far_n, 1)
+        avg_s = far_ms / max(far_n, 1) / 1e3
+        achieved = rs / avg_s / 1e12
+        peak = 152 * 16 * 2.07e9 / 1e12
+        roof = {"kernel": "k_far_f32", "bound": "alu", "achieved": achieved, "peak": peak,
+                "unit": "T rsqrt/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "MUFU reciprocal-square-root issue peak from unit counts and clock "
+                               "(152 SMs x 16 per clock x 2.07 GHz); 49 per entry",
+                "launches": far_n}
+    elif far_ms >= mv_ms and prec == 2:
+        ops = far_units * DF_FAR_OPS_PER_ENTRY / max(far_n, 1)
+        avg_s = far_ms / max(far_n, 1) / 1e3
+        achieved = ops / avg_s / 1e12
+        roof = {"kernel": "k_far_df", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS,
+                "unit": "T FP32 op/s", "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
+                "peak_source": "FP32 issue peak derived from unit counts and clock (152 SMs x 128 x 2.07 GHz)",
+                "launches": far_n}
+    elif far_ms >= mv_ms:
+        flops = far_units * FAR_FLOPS_PER_ENTRY / max(far_n, 1)
+        avg_s = far_ms / max(far_n, 1) / 1e3
+        achieved = flops / avg_s / 1e12
+        roof = {"kernel": "k_far_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "peak_source": "nominal FP64 rate of the recipe table (no measured FP64 peak)",
+                "launches": far_n}
+    else:
+        bytes_ = mv_units / max(mv_n, 1)
+        avg_s = mv_ms / max(mv_n, 1) / 1e3
+        achieved = bytes_ / avg_s / 1e9
+        # DRAM bytes (read + write) over algorithmic bytes of one ncu capture of k_pcg_df
+        # (adaptive polycube level N = 12,558: 18.04 GB measured, 18.29 GB algorithmic);
+        # traffic scales with the bytes of the products, so the ratio carries to full size
+        traffic = PCG_TRAFFIC_RATIO * bytes_ if prec == 2 else None
+        roof = {"kernel": {0: "k_matvec<double>", 1: "k_matvec<float>",
+                           2: "k_pcg_df (persistent mixed-precision PCG: packed FP32 hi-part tile products, "
+                              "DF64 residual replacement)"}[prec] if mv_kernel is None else mv_kernel,
+                "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
+                "peak_source": f"{peak_src} hbm_gbs", "launches": mv_n}
+    return roof
+
+
 def _pct(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, max(0, math.ceil(q * len(xs)) - 1))]
@@ -238,6 +284,7 @@ def dual_workload(args):
         flush.fill_(1)
         run(mesh, bem.BASIS_DUAL)
     clocks = Clocks(torch.cuda.current_device())
+    ctx.profile(True)
     launches0 = ctx.launch_count()
     torch.cuda.synchronize()
     clocks.start()
@@ -253,6 +300,14 @@ def dual_workload(args):
     launches = ctx.launch_count() - launches0
     step_ms = [ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(args.steps)]
     total_ms = sum(step_ms)
+    far_n, far_ms, far_units = ctx.profile_read(bem.KERNEL_FAR)
+    mv_n, mv_ms, mv_units = ctx.profile_read(bem.KERNEL_MATVEC)
+    ctx.profile(False)
+    peaks, peak_src = _peaks()
+    roof = roofline(bem.PREC_DF64, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src)
+    roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / total_ms
+    if roof["bound"] == "alu":
+        roof["note"] = "far field of the barycentric operators (6 N triangles per level)"
 
     # end to end: host mesh in, level records out, through the public API
     import ctypes
@@ -304,6 +359,8 @@ def dual_workload(args):
             "e2e": {"value": args.steps / sum(e2e_t) if e2e_t else None, "unit": "adaptive runs/s",
                     "h2d_bytes_per_step": cube.verts.nbytes + cube.tris.nbytes,
                     "d2h_bytes_per_step": len(recs) * ctypes.sizeof(bem.LevelRecord)},
+            "roofline": roof, "assembly_gpairs_per_s": sum(36 * r["N"] ** 2 for r in recs) /
+                                                       (sum(r["ms_assemble"] for r in recs) / 1e3) / 1e9,
             "gpu_launches": launches, "clocks": clk, "results": results}
     if not args.no_cpu_baseline:
         import oracle
@@ -407,6 +464,20 @@ def batch_workload(args):
     launches = ctx.launch_count() - launches0
     info = b.info()
     b.close()
+    # roofline: one direct (not replayed) run of the same batch with the profiler on
+    bp = bem.Batch(ctx, meshes, precision=bem.PREC_F32, precond=pc, tol=TOL, max_it=5000, use_graph=False)
+    bp.run()
+    ctx.profile(True)
+    bp.run()
+    far_n, far_ms, far_units = ctx.profile_read(bem.KERNEL_FAR)
+    mv_n, mv_ms, mv_units = ctx.profile_read(bem.KERNEL_MATVEC)
+    ctx.profile(False)
+    bp.close()
+    peaks, peak_src = _peaks()
+    roof = roofline(bem.PREC_F32, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src,
+                    mv_kernel="k_pcg_batch (all problems' persistent PCGs in one cooperative launch, packed FP32 products)")
+    roof["share_of_run"] = (far_ms if roof["bound"] == "alu" else mv_ms) / (1e3 * sum(times) / len(times))
+    roof["note"] = "from one direct run of the batch with the library's event profiler (the timed runs replay a graph)"
     e2e = []
     h2d = sum(m.verts.nbytes + m.tris.nbytes for m in ms)
     for _ in range(0 if args.no_e2e else args.steps):
@@ -433,7 +504,7 @@ def batch_workload(args):
                    "l2": "V of the batch (tens of GB) exceeds L2"},
         "p50_latency_ms": lat[len(lat) // 2], "p99_latency_ms": lat[-1],
         "caps_converged": all(r["converged"] for r in res), "max_iterations": max(r["iterations"] for r in res),
-        "clocks": clk, "roofline": None, "cpu_baseline": None, "gpu_launches": launches,
+        "clocks": clk, "roofline": roof, "cpu_baseline": None, "gpu_launches": launches,
         "e2e": {"value": e2e_val, "unit": "capacity solves/s (meshes)", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": len(ms) * 32},
     }
@@ -688,45 +759,7 @@ def main():
     adapt_ms = sum(r["ms_adapt"] for r in recs)
 
     # dominant kernel roofline
-    if far_ms >= mv_ms and PREC == 1:
-        rs = far_units * 49 / max(far_n, 1)
-        avg_s = far_ms / max(far_n, 1) / 1e3
-        achieved = rs / avg_s / 1e12
-        peak = 152 * 16 * 2.07e9 / 1e12
-        roof = {"kernel": "k_far_f32", "bound": "alu", "achieved": achieved, "peak": peak,
-                "unit": "T rsqrt/s", "frac": achieved / peak, "traffic": None,
-                "peak_source": "MUFU reciprocal-square-root issue peak from unit counts and clock "
-                               "(152 SMs x 16 per clock x 2.07 GHz); 49 per entry",
-                "launches": far_n}
-    elif far_ms >= mv_ms and PREC == 2:
-        ops = far_units * DF_FAR_OPS_PER_ENTRY / max(far_n, 1)
-        avg_s = far_ms / max(far_n, 1) / 1e3
-        achieved = ops / avg_s / 1e12
-        roof = {"kernel": "k_far_df", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS,
-                "unit": "T FP32 op/s", "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
-                "peak_source": "FP32 issue peak derived from unit counts and clock (152 SMs x 128 x 2.07 GHz)",
-                "launches": far_n}
-    elif far_ms >= mv_ms:
-        flops = far_units * FAR_FLOPS_PER_ENTRY / max(far_n, 1)
-        avg_s = far_ms / max(far_n, 1) / 1e3
-        achieved = flops / avg_s / 1e12
-        roof = {"kernel": "k_far_f64", "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal FP64 rate of the recipe table (no measured FP64 peak)",
-                "launches": far_n}
-    else:
-        bytes_ = mv_units / max(mv_n, 1)
-        avg_s = mv_ms / max(mv_n, 1) / 1e3
-        achieved = bytes_ / avg_s / 1e9
-        # DRAM bytes (read + write) over algorithmic bytes of one ncu capture of k_pcg_df
-        # (adaptive polycube level N = 12,558: 18.04 GB measured, 18.29 GB algorithmic);
-        # traffic scales with the bytes of the products, so the ratio carries to full size
-        traffic = PCG_TRAFFIC_RATIO * bytes_ if PREC == 2 else None
-        roof = {"kernel": {0: "k_matvec<double>", 1: "k_matvec<float>",
-                           2: "k_pcg_df (persistent mixed-precision PCG: packed FP32 hi-part tile products, "
-                              "DF64 residual replacement)"}[PREC], "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
-                "peak_source": f"{peak_src} hbm_gbs", "launches": mv_n}
+    roof = roofline(PREC, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src)
     roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / total_ms
 
     # end to end through the public API with host buffers
@@ -763,6 +796,10 @@ def main():
                    "precision": args.precision, "preconditioner": PC_LABEL[pc_name],
                    "final_N": recs[-1]["N"], "levels": len(recs),
                    "cap_final": recs[-1]["cap"], "parallelism": f"replicas x{ws}",
+                   "far_tiles_autotuned": dict(zip(("N<1024", "N<4096", "N<16384", "larger"),
+                                                   [[(32, 256), (16, 256), (64, 256), (8, 128), (16, 128),
+                                                     (32, 128)][v - 1] if v else None
+                                                    for v in ctx.far_tiles()[PREC]])),
                    "l2": "256 MB buffer written before every step; V (up to 3.2 GB) exceeds L2"},
         "p50_latency_ms": lat_ms[len(lat_ms) // 2], "p99_latency_ms": lat_ms[min(len(lat_ms) - 1,
                                                                                    math.ceil(0.99 * len(lat_ms)) - 1)],

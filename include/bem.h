@@ -65,7 +65,14 @@ typedef struct {
     int32_t ss_order;  /* Gauss-Legendre points per variable for touching pairs (2..16, default 4;
                           the radial variables are integrated exactly, which equals the
                           n-point rule in them for n >= 2) */
+    int32_t tile;      /* far-field pair tile (no counterpart in the paper; V is bit-identical
+                          for every choice): 0 = autotuned -- the first assembly of each size
+                          class (N < 1,024, < 4,096, < 16,384, larger) and precision in a
+                          context times every variant on its own far-field block and the
+                          context keeps the fastest; k = 1..BEM_FAR_TILE_VARIANTS: variant k,
+                          rows x columns per CTA 32x256, 16x256, 64x256, 8x128, 16x128, 32x128 */
 } bem_assembly_opts;
+#define BEM_FAR_TILE_VARIANTS 6
 
 #define BEM_PRECOND_NONE 0
 #define BEM_PRECOND_JACOBI 1
@@ -129,6 +136,9 @@ bem_status bem_context_destroy(bem_ctx *ctx);
 const char *bem_last_error(const bem_ctx *ctx);
 /* Device bytes currently held by handles of this context. */
 bem_status bem_context_memory(const bem_ctx *ctx, int64_t *bytes_in_use);
+/* The autotuned far-field tiles of the context: out[4 p + c] for precision p (BEM_PREC_*)
+ * and size class c, the variant 1..BEM_FAR_TILE_VARIANTS, or 0 while not yet timed. */
+bem_status bem_far_tiles(const bem_ctx *ctx, int32_t out[12]);
 
 /* ---------------------------------------------------------------- mesh */
 /* Upload a triangulation T_l of Gamma into N flat triangles with M vertices

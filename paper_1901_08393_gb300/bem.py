@@ -29,6 +29,7 @@ PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_BLOCK = 2
 PRECOND_CALDERON = 3
+FAR_TILE_VARIANTS = 6
 REFINE_BISEC3 = 1
 BASIS_P0 = 0
 BASIS_DUAL = 1
@@ -43,6 +44,7 @@ EXPORTS = [
     "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
     "bem_batch_create", "bem_batch_run", "bem_batch_info", "bem_batch_destroy",
     "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual", "bem_operator_preconditioner",
+    "bem_far_tiles",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -50,7 +52,7 @@ KERNEL_MATVEC = 2
 
 
 class AssemblyOpts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("ss_order", C.c_int32)]
+    _fields_ = [("precision", C.c_int32), ("ss_order", C.c_int32), ("tile", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -158,6 +160,7 @@ def lib():
         "bem_operator_dual": [vp, vp, P(vp)],
         "bem_zz_estimate_dual": [vp, vp, i32, vp, vp],
         "bem_operator_preconditioner": [vp, vp],
+        "bem_far_tiles": [vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -229,6 +232,12 @@ class Context:
 
     def set_persistent(self, on: bool):
         self.check(self.L.bem_context_set_persistent(self.h, int(on)))
+
+    def far_tiles(self):
+        """Autotuned far-field tile variant per (precision, size class); 0 = not yet timed."""
+        out = (C.c_int32 * 12)()
+        self.check(self.L.bem_far_tiles(self.h, out))
+        return [list(out[4 * p:4 * p + 4]) for p in range(3)]
 
     def launch_count(self) -> int:
         n = C.c_int64()
@@ -318,8 +327,8 @@ class Operator:
         self.mesh, self.ctx, self.h = mesh, mesh.ctx, handle
 
     @classmethod
-    def assemble(cls, mesh: Mesh, precision=PREC_F64, ss_order=4):
-        o = AssemblyOpts(precision, ss_order)
+    def assemble(cls, mesh: Mesh, precision=PREC_F64, ss_order=4, tile=0):
+        o = AssemblyOpts(precision, ss_order, tile)
         h = C.c_void_p()
         mesh.ctx.check(mesh.ctx.L.bem_assemble_V(mesh.h, C.byref(o), C.byref(h)))
         return cls(mesh, h)

@@ -340,6 +340,14 @@ bem_status bem_context_destroy(bem_ctx *ctx)
 
 const char *bem_last_error(const bem_ctx *ctx) { return ctx ? ctx->err : "null context"; }
 
+bem_status bem_far_tiles(const bem_ctx *ctx, int32_t out[12])
+{
+    if (!ctx || !out) return BEM_ERR_INVALID;
+    for (int p = 0; p < 3; ++p)
+        for (int c = 0; c < 4; ++c) out[4 * p + c] = ctx->far_tile[p][c] + 1;
+    return BEM_OK;
+}
+
 bem_status bem_context_memory(const bem_ctx *ctx, int64_t *bytes_in_use)
 {
     if (!ctx || !bytes_in_use) return BEM_ERR_INVALID;
@@ -449,12 +457,15 @@ static bem_status operator_alloc(bem_mesh *mesh, const bem_assembly_opts *opts, 
     const int ss = (opts && opts->ss_order > 0) ? opts->ss_order : 4;
     CHECK_ARG(ctx, prec == BEM_PREC_F64 || prec == BEM_PREC_F32 || prec == BEM_PREC_DF64, "unknown precision");
     CHECK_ARG(ctx, ss >= 2 && ss <= kMaxSS, "ss_order outside 2..16");
+    const int tile = opts ? opts->tile : 0;
+    CHECK_ARG(ctx, tile >= 0 && tile <= BEM_FAR_TILE_VARIANTS, "tile outside 0..BEM_FAR_TILE_VARIANTS");
     bem_operator *op = new (std::nothrow) bem_operator();
     if (!op) return set_error(ctx, BEM_ERR_OOM, "host allocation");
     op->mesh = mesh;
     op->ctx = mesh->ctx;
     op->precision = prec;
     op->ss_order = ss;
+    op->tile = tile;
     op->N = mesh->N;
     op->ld = padded_ld(mesh->N);
     const size_t es = prec == BEM_PREC_F32 ? 4 : 8;
@@ -499,7 +510,7 @@ bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse, con
     CHECK_ARG(ctx, !coarse->mesh->cells_only, "a dual operator has no incremental update");
     CHECK_ARG(ctx, fine->parent != nullptr && fine->src_N == coarse->N,
               "mesh was not refined from the operator's mesh");
-    bem_assembly_opts o{coarse->precision, coarse->ss_order};
+    bem_assembly_opts o{coarse->precision, coarse->ss_order, opts ? opts->tile : coarse->tile};
     if (opts) {
         CHECK_ARG(ctx, opts->precision == coarse->precision, "precision differs from the coarse operator");
         CHECK_ARG(ctx, (opts->ss_order > 0 ? opts->ss_order : 4) == coarse->ss_order,

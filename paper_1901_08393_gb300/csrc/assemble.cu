@@ -3,8 +3,9 @@
 //
 //  * Far field (no common vertex): 7 x 7 product of Radon's degree-5 rule,
 //      V_ij = |Ti||Tj|/(4pi) sum_a w_a sum_b w_b / |x_a - y_b|.
-//    One thread per column j holds its 7 points in registers; the CTA stages 32
-//    row triangles in shared memory and walks them (broadcast reads).  Only
+//    One thread per column j holds its 7 points in registers; the CTA stages R
+//    row triangles in shared memory and walks them (broadcast reads; R x C tile
+//    variants, chosen per size class by timing them).  Only
 //    entries with i <= j are computed; the strict lower triangle is mirrored, so
 //    V is exactly symmetric and an incremental re-assembly reproduces the full
 //    one bit for bit.  Three arithmetic variants:
@@ -116,18 +117,25 @@ template <> struct Elem<float2> {
 };
 
 // ------------------------------------------------------------------ far field
-constexpr int kFarCols = 256;  // threads (columns) per CTA
-constexpr int kFarRows = 32;   // row triangles staged per CTA
+// Pair tiles: a CTA of C threads (one column each) walks R row triangles staged in
+// shared memory.  Every variant computes each entry with the same operations, so V
+// is bit-identical whichever is used; the fastest depends on N (small meshes want
+// more, smaller CTAs) and on the arithmetic, and is chosen by timing (autotune).
+struct FarTile {
+    int rows, cols;
+};
+constexpr FarTile kFarTiles[kFarTileVariants] = {{32, 256}, {16, 256}, {64, 256}, {8, 128}, {16, 128}, {32, 128}};
 
-__global__ void __launch_bounds__(kFarCols) k_far_f64(const double *__restrict__ q64, double *__restrict__ V,
+template <int R, int C>
+__global__ void __launch_bounds__(C) k_far_f64(const double *__restrict__ q64, double *__restrict__ V,
                                                       int64_t ld, int64_t r0, int64_t r1, int64_t c0,
                                                       int64_t c1)
 {
-    __shared__ double sx[kFarRows][22];
-    const int64_t cbase = c0 + (int64_t)blockIdx.x * kFarCols;
-    const int64_t i0 = r0 + (int64_t)blockIdx.y * kFarRows;
-    if (i0 > cbase + kFarCols - 1 || i0 >= r1) return;  // tile strictly below the diagonal
-    for (int k = threadIdx.x; k < kFarRows * 22; k += kFarCols) {
+    __shared__ double sx[R][22];
+    const int64_t cbase = c0 + (int64_t)blockIdx.x * C;
+    const int64_t i0 = r0 + (int64_t)blockIdx.y * R;
+    if (i0 > cbase + C - 1 || i0 >= r1) return;  // tile strictly below the diagonal
+    for (int k = threadIdx.x; k < R * 22; k += C) {
         const int r = k / 22, c = k % 22;
         const int64_t i = i0 + r;
         sx[r][c] = (i < r1) ? q64[i * kQ64Stride + c] : 0.0;
@@ -139,7 +147,7 @@ __global__ void __launch_bounds__(kFarCols) k_far_f64(const double *__restrict__
 #pragma unroll
     for (int c = 0; c < 3 * kQ; ++c) y[c] = q64[j * kQ64Stride + c];
     const double Aj = q64[j * kQ64Stride + 21] * kInv4Pi;
-    const int rows = (int)((r1 - i0) < kFarRows ? (r1 - i0) : kFarRows);
+    const int rows = (int)((r1 - i0) < R ? (r1 - i0) : R);
     for (int r = 0; r < rows; ++r) {
         const int64_t i = i0 + r;
         if (i > j) break;
@@ -159,7 +167,8 @@ __global__ void __launch_bounds__(kFarCols) k_far_f64(const double *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ q32,
+template <int R, int C>
+__global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
                                                       const double *__restrict__ cent, float *__restrict__ V,
                                                       int64_t ld, int64_t r0, int64_t r1, int64_t c0,
                                                       int64_t c1)
@@ -167,17 +176,17 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
     // FP32 only in the pair loop: centroids as hi + lo floats, so that the centroid
     // difference (hi_i - hi_j) + (lo_i - lo_j) keeps FP32 relative accuracy for
     // distant pairs; weights and areas rounded to FP32 once
-    __shared__ float so[kFarRows][3 * kQ];
-    __shared__ float sc[kFarRows][7];  // centroid hi (3), lo (3), area
-    const int64_t cbase = c0 + (int64_t)blockIdx.x * kFarCols;
-    const int64_t i0 = r0 + (int64_t)blockIdx.y * kFarRows;
-    if (i0 > cbase + kFarCols - 1 || i0 >= r1) return;
-    for (int k = threadIdx.x; k < kFarRows * 3 * kQ; k += kFarCols) {
+    __shared__ float so[R][3 * kQ];
+    __shared__ float sc[R][7];  // centroid hi (3), lo (3), area
+    const int64_t cbase = c0 + (int64_t)blockIdx.x * C;
+    const int64_t i0 = r0 + (int64_t)blockIdx.y * R;
+    if (i0 > cbase + C - 1 || i0 >= r1) return;
+    for (int k = threadIdx.x; k < R * 3 * kQ; k += C) {
         const int r = k / (3 * kQ), c = k % (3 * kQ);
         const int64_t i = i0 + r;
         so[r][c] = (i < r1) ? q32[i * kQ32Stride + c] : 0.0f;
     }
-    for (int k = threadIdx.x; k < kFarRows * 4; k += kFarCols) {
+    for (int k = threadIdx.x; k < R * 4; k += C) {
         const int r = k / 4, c = k % 4;
         const int64_t i = i0 + r;
         const double v = (i < r1) ? cent[i * 4 + c] : 0.0;
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
     float wf[kQ];  // the weights rounded to FP32 once (c_w7df[.].x = nearest float)
 #pragma unroll
     for (int a = 0; a < kQ; ++a) wf[a] = c_w7df[a].x;
-    const int rows = (int)((r1 - i0) < kFarRows ? (r1 - i0) : kFarRows);
+    const int rows = (int)((r1 - i0) < R ? (r1 - i0) : R);
     for (int r = 0; r < rows; ++r) {
         const int64_t i = i0 + r;
         if (i > j) break;
@@ -230,14 +239,15 @@ __global__ void __launch_bounds__(kFarCols) k_far_f32(const float *__restrict__ 
 }
 
 // Double-float far field: see the file comment.
-__global__ void __launch_bounds__(kFarCols) k_far_df(const float *__restrict__ qdf, float2 *__restrict__ V,
+template <int R, int C>
+__global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, float2 *__restrict__ V,
                                                      int64_t ld, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
-    __shared__ float sq[kFarRows][53];
-    const int64_t cbase = c0 + (int64_t)blockIdx.x * kFarCols;
-    const int64_t i0 = r0 + (int64_t)blockIdx.y * kFarRows;
-    if (i0 > cbase + kFarCols - 1 || i0 >= r1) return;
-    for (int k = threadIdx.x; k < kFarRows * 53; k += kFarCols) {
+    __shared__ float sq[R][53];
+    const int64_t cbase = c0 + (int64_t)blockIdx.x * C;
+    const int64_t i0 = r0 + (int64_t)blockIdx.y * R;
+    if (i0 > cbase + C - 1 || i0 >= r1) return;
+    for (int k = threadIdx.x; k < R * 53; k += C) {
         const int r = k / 53, c = k % 53;
         const int64_t i = i0 + r;
         sq[r][c] = (i < r1) ? qdf[i * kQdfStride + c] : 0.0f;
@@ -255,7 +265,7 @@ __global__ void __launch_bounds__(kFarCols) k_far_df(const float *__restrict__ q
 #pragma unroll
     for (int k = 0; k < 9; ++k) cj[k] = qj[42 + k];
     const float2 Aj = df_mul(make_float2(qj[51], qj[52]), c_inv4pi_df);
-    const int rows = (int)((r1 - i0) < kFarRows ? (r1 - i0) : kFarRows);
+    const int rows = (int)((r1 - i0) < R ? (r1 - i0) : R);
     for (int r = 0; r < rows; ++r) {
         const int64_t i = i0 + r;
         if (i > j) break;
@@ -544,19 +554,35 @@ __global__ void k_diag(const T *V, int64_t ld, int64_t N, double *d)
 }
 
 // ------------------------------------------------------------------ drivers
+template <typename T, int R, int C>
+static void far_kernel(bem_operator *op, dim3 grid, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+{
+    bem_mesh *m = op->mesh;
+    cudaStream_t s = m->ctx->stream;
+    if (op->precision == BEM_PREC_F64)
+        k_far_f64<R, C><<<grid, C, 0, s>>>(m->q64, (double *)op->V, op->ld, r0, r1, c0, c1);
+    else if (op->precision == BEM_PREC_DF64)
+        k_far_df<R, C><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
+    else
+        k_far_f32<R, C><<<grid, C, 0, s>>>(m->q32, m->cent, (float *)op->V, op->ld, r0, r1, c0, c1);
+}
+
+// Far-field entries i <= j of the block [r0, r1) x [c0, c1) with tile variant v.
 template <typename T>
-static bem_status launch_far(bem_operator *op, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+static bem_status launch_far(bem_operator *op, int v, int64_t r0, int64_t r1, int64_t c0, int64_t c1,
+                             bool profile = true)
 {
     if (r1 <= r0 || c1 <= c0) return BEM_OK;
     bem_mesh *m = op->mesh;
     bem_ctx *ctx = m->ctx;
-    const int64_t gx = (c1 - c0 + kFarCols - 1) / kFarCols;
-    const int64_t gy = (r1 - r0 + kFarRows - 1) / kFarRows;
+    const int R = kFarTiles[v].rows, C = kFarTiles[v].cols;
+    const int64_t gx = (c1 - c0 + C - 1) / C;
+    const int64_t gy = (r1 - r0 + R - 1) / R;
     if (gy > 65535) {
         // split rows into chunks that fit the grid's y limit
-        for (int64_t rs = r0; rs < r1; rs += 65535LL * kFarRows) {
-            const int64_t re = rs + 65535LL * kFarRows < r1 ? rs + 65535LL * kFarRows : r1;
-            bem_status st = launch_far<T>(op, rs, re, c0, c1);
+        for (int64_t rs = r0; rs < r1; rs += 65535LL * R) {
+            const int64_t re = rs + 65535LL * R < r1 ? rs + 65535LL * R : r1;
+            bem_status st = launch_far<T>(op, v, rs, re, c0, c1, profile);
             if (st) return st;
         }
         return BEM_OK;
@@ -567,16 +593,71 @@ static bem_status launch_far(bem_operator *op, int64_t r0, int64_t r1, int64_t c
         const int64_t lo = i > c0 ? i : c0;
         if (c1 > lo) units += (double)(c1 - lo);
     }
-    const int prof = prof_start(ctx, BEM_KERNEL_FAR, units);
-    if (op->precision == BEM_PREC_F64)
-        { k_far_f64<<<grid, kFarCols, 0, ctx->stream>>>(m->q64, (double *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
-    else if (op->precision == BEM_PREC_DF64)
-        { k_far_df<<<grid, kFarCols, 0, ctx->stream>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
-    else
-        { k_far_f32<<<grid, kFarCols, 0, ctx->stream>>>(m->q32, m->cent, (float *)op->V, op->ld, r0, r1, c0, c1); BEM_COUNT(ctx); }
-    prof_stop(ctx, prof);
+    const int prof = profile ? prof_start(ctx, BEM_KERNEL_FAR, units) : -1;
+    switch (v) {
+    case 0: far_kernel<T, 32, 256>(op, grid, r0, r1, c0, c1); break;
+    case 1: far_kernel<T, 16, 256>(op, grid, r0, r1, c0, c1); break;
+    case 2: far_kernel<T, 64, 256>(op, grid, r0, r1, c0, c1); break;
+    case 3: far_kernel<T, 8, 128>(op, grid, r0, r1, c0, c1); break;
+    case 4: far_kernel<T, 16, 128>(op, grid, r0, r1, c0, c1); break;
+    default: far_kernel<T, 32, 128>(op, grid, r0, r1, c0, c1); break;
+    }
+    BEM_COUNT(ctx);
+    if (profile) prof_stop(ctx, prof);
     BEM_CK_LAUNCH(ctx);
     return BEM_OK;
+}
+
+// Size classes of the tile cache: N < 1,024, < 4,096, < 16,384, larger.
+static int far_bucket(int64_t N) { return N < 1024 ? 0 : N < 4096 ? 1 : N < 16384 ? 2 : 3; }
+
+// The tile variant of this assembly: the requested one, else the context's choice
+// for (precision, size class), timed now on this assembly's own far-field block if
+// the class has none yet -- every variant once to load its module, then once timed,
+// the fastest kept.  No timing while the stream is being captured into a graph (the
+// variant is then the cached one, or variant 0).
+template <typename T>
+static bem_status far_variant(bem_operator *op, int64_t K, int64_t N, int *v_out)
+{
+    bem_ctx *ctx = op->mesh->ctx;
+    if (op->tile > 0) {
+        *v_out = op->tile - 1;
+        return BEM_OK;
+    }
+    int8_t &slot = ctx->far_tile[op->precision][far_bucket(N)];
+    *v_out = slot >= 0 ? slot : 0;
+    if (slot >= 0 || N - K <= 0) return BEM_OK;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BEM_CK(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return BEM_OK;
+    float best = 0.0f;
+    int bv = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int v = 0; v < kFarTileVariants; ++v) {
+            BEM_CK(ctx, cudaEventRecord(ctx->ev[4], ctx->stream));
+            bem_status st = launch_far<T>(op, v, K, N, K, N, false);
+            if (st) return st;
+            BEM_CK(ctx, cudaEventRecord(ctx->ev[5], ctx->stream));
+            BEM_CK(ctx, cudaEventSynchronize(ctx->ev[5]));
+            float ms = 0.0f;
+            BEM_CK(ctx, cudaEventElapsedTime(&ms, ctx->ev[4], ctx->ev[5]));
+            if (pass == 1 && (v == 0 || ms < best)) {
+                best = ms;
+                bv = v;
+            }
+        }
+    slot = (int8_t)bv;
+    *v_out = bv;
+    return BEM_OK;
+}
+
+bem_status far_tune(bem_operator *op)
+{
+    int v = 0;
+    const int64_t N = op->mesh->N;
+    if (op->precision == BEM_PREC_F64) return far_variant<double>(op, 0, N, &v);
+    if (op->precision == BEM_PREC_DF64) return far_variant<float2>(op, 0, N, &v);
+    return far_variant<float>(op, 0, N, &v);
 }
 
 template <typename T>
@@ -633,9 +714,11 @@ static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
                                                             (T *)op->V, op->ld); BEM_COUNT(ctx);
             BEM_CK_LAUNCH(ctx);
         }
-        if ((st = launch_far<T>(op, 0, K, K, N))) return st;
     }
-    if ((st = launch_far<T>(op, K, N, K, N))) return st;
+    int v = 0;
+    if ((st = far_variant<T>(op, K, N, &v))) return st;
+    if (K > 0 && (st = launch_far<T>(op, v, 0, K, K, N))) return st;
+    if ((st = launch_far<T>(op, v, K, N, K, N))) return st;
     if ((st = launch_mirror<T>(op, K > 0 ? K : 0, N))) return st;
     if ((st = launch_near<T>(op, K))) return st;
     k_diag<T><<<nblk(N, 256), 256, 0, ctx->stream>>>((const T *)op->V, op->ld, N, op->diag); BEM_COUNT(ctx);

@@ -21,6 +21,7 @@ constexpr int kQdfStride = 56;     // floats per triangle in the double-float ta
 constexpr int kMaxSS = 16;         // largest Sauter-Schwab order accepted
 constexpr int kMaxValence = 96;    // triangles per vertex accepted by the pair builder
 constexpr double kInv4Pi = 0.079577471545947668;  // 1 / (4 pi)
+constexpr int kFarTileVariants = BEM_FAR_TILE_VARIANTS;  // far-field pair tile shapes
 
 // Row stride of the dense operator: N rounded up to 64 elements so that every row
 // starts on a 256-byte boundary (vector loads) and whole 64 x 64 tiles fit (the
@@ -61,6 +62,7 @@ struct bem_ctx {
     char err[1024] = {0};
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory for scalar readbacks
     cudaEvent_t ev[8] = {};
+    int8_t far_tile[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // autotuned variant
 };
 
 struct bem_mesh {
@@ -94,6 +96,7 @@ struct bem_operator {
     bem_ctx *ctx = nullptr;  // kept apart from mesh: an operator may be destroyed after its mesh
     int32_t precision = BEM_PREC_F64;
     int32_t ss_order = 4;
+    int32_t tile = 0;       // requested far-field tile variant (1-based), 0: autotuned
     int64_t N = 0, ld = 0;
     void *V = nullptr;      // N x ld, row-major: double (F64), float2 hi/lo (DF64), float (F32)
     double *diag = nullptr; // N, FP64 diagonal
@@ -157,6 +160,7 @@ bem_status assemble_full(bem_operator *op);
 // Operator handle with V (uninitialised) and diag allocated for mesh (api.cu).
 bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out);
 bem_status assembly_prepare(bem_ctx *ctx);  // constant tables on the device (once)
+bem_status far_tune(bem_operator *op);       // time the far-field tile variants for op's size class
 bem_status assemble_update(bem_operator *op, const bem_operator *coarse);
 bem_status operator_diag(bem_operator *op);
 

@@ -1929,6 +1929,7 @@ struct bem_batch {
     int P = 0, use_graph = 1, graph_used = 0, G = 0, precond = BEM_PRECOND_JACOBI;
     double tol = 1e-10;
     int64_t launches_per_run = 0;
+    int prof_solve = -1;  // profiler record of the solver launch (direct runs with profiling on)
     std::vector<bem::BatchProblem> prob;
     std::vector<bem::PcgArgs> args;
     std::vector<int> begin;
@@ -1979,9 +1980,11 @@ static bem_status batch_enqueue(bem_batch *bt)
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
+        bt->prof_solve = prof_start(ctx, BEM_KERNEL_MATVEC, 0.0);  // bytes set once the counts are read
         BEM_CK(ctx, cudaLaunchKernelEx(&cfg, k_pcg_batch, (const PcgArgs *)bt->d_args, (const int *)bt->d_begin,
                                        bt->P));
         BEM_COUNT(ctx);
+        prof_stop(ctx, bt->prof_solve);
     }
     for (int p = 0; p < bt->P; ++p) {
         bem_operator *op = bt->prob[p].op;
@@ -2065,6 +2068,8 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
         st = new_operator(meshes[p], aopts, &pr.op);
         if (st) break;
         bem_operator *op = pr.op;
+        // far-field tiles of this size class timed now: a run may be captured as a graph
+        if ((st = far_tune(op))) break;
         const int64_t N = op->N, L = op->ld;
         const int nb = (int)(L / kSB), nt = nb * (nb + 1) / 2;
         double *vec = nullptr;
@@ -2155,7 +2160,8 @@ bem_status bem_batch_run(bem_batch *bt, bem_batch_result *results)
     cudaStream_t saved = ctx->stream;
     const int saved_profile = ctx->profile;
     ctx->stream = bt->stream;  // the batch's work runs on its own (capturable) stream
-    ctx->profile = 0;
+    ctx->profile = 0;          // no profiler events inside a captured graph
+    bt->prof_solve = -1;
     bem_status st = BEM_OK;
     cudaError_t e = cudaSuccess;
     if (bt->use_graph && !bt->exec) {
@@ -2190,6 +2196,7 @@ bem_status bem_batch_run(bem_batch *bt, bem_batch_result *results)
         bt->graph_used = 1;
     } else {
         bt->graph_used = 0;
+        ctx->profile = saved_profile;
         st = batch_enqueue(bt);
     }
     if (!st && e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
@@ -2198,8 +2205,12 @@ bem_status bem_batch_run(bem_batch *bt, bem_batch_result *results)
     if (!st && e != cudaSuccess) st = cuda_error(ctx, e, "batch run");
     if (st) return st;
     bool timeout = false, unconverged = false;
+    double bytes = 0.0;  // algorithmic bytes of the solver launch, as for a single solve
     for (int p = 0; p < bt->P; ++p) {
         const double *r = bt->h_res + kBatchRes * p;
+        const double n2 = (double)bt->prob[p].op->N * (double)bt->prob[p].op->N;
+        bytes += bt->prob[p].op->precision == BEM_PREC_F32 ? 2.0 * n2 * (r[2] + r[3])
+                                                           : 4.0 * n2 * r[3] + 2.0 * n2 * (r[2] + 1.0);
         const int err = *reinterpret_cast<const int *>(r + 6);
         const double rel = std::sqrt(r[0] / (r[1] > 0.0 ? r[1] : 1.0));
         timeout |= err != 0;
@@ -2214,6 +2225,7 @@ bem_status bem_batch_run(bem_batch *bt, bem_batch_result *results)
             o.status = err ? BEM_ERR_CUDA : (rel <= bt->tol ? BEM_OK : BEM_ERR_NOT_CONVERGED);
         }
     }
+    prof_set_units(ctx, bt->prof_solve, bytes);
     if (timeout) return set_error(ctx, BEM_ERR_CUDA, "batch solve: a grid barrier timed out");
     if (unconverged) return set_error(ctx, BEM_ERR_NOT_CONVERGED, "batch solve: a problem did not reach the tolerance");
     return BEM_OK;
