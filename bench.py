@@ -797,8 +797,10 @@ def main():
                    "final_N": recs[-1]["N"], "levels": len(recs),
                    "cap_final": recs[-1]["cap"], "parallelism": f"replicas x{ws}",
                    "far_tiles_autotuned": dict(zip(("N<1024", "N<4096", "N<16384", "larger"),
-                                                   [[(32, 256), (16, 256), (64, 256), (8, 128), (16, 128),
-                                                     (32, 128)][v - 1] if v else None
+                                                   [["32x256", "16x256", "64x256", "8x128", "16x128", "32x128",
+                                                     "8x128 shared m8", "16x128 shared m8", "32x128 shared m8",
+                                                     "8x128 shared m9", "8x64 shared m16", "8x64 shared m18"][v - 1]
+                                                    if v else None
                                                     for v in ctx.far_tiles()[PREC]])),
                    "l2": "256 MB buffer written before every step; V (up to 3.2 GB) exceeds L2"},
         "p50_latency_ms": lat_ms[len(lat_ms) // 2], "p99_latency_ms": lat_ms[min(len(lat_ms) - 1,

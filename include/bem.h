@@ -70,9 +70,12 @@ typedef struct {
                           class (N < 1,024, < 4,096, < 16,384, larger) and precision in a
                           context times every variant on its own far-field block and the
                           context keeps the fastest; k = 1..BEM_FAR_TILE_VARIANTS: variant k,
-                          rows x columns per CTA 32x256, 16x256, 64x256, 8x128, 16x128, 32x128 */
+                          rows x columns per CTA 32x256, 16x256, 64x256, 8x128, 16x128, 32x128,
+                          and (DF64: column points in shared memory instead of registers, at
+                          least m CTAs per SM) 8x128 m8, 16x128 m8, 32x128 m8, 8x128 m9,
+                          8x64 m16, 8x64 m18 */
 } bem_assembly_opts;
-#define BEM_FAR_TILE_VARIANTS 6
+#define BEM_FAR_TILE_VARIANTS 12
 
 #define BEM_PRECOND_NONE 0
 #define BEM_PRECOND_JACOBI 1

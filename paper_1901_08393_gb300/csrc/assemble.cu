@@ -121,10 +121,14 @@ template <> struct Elem<float2> {
 // shared memory.  Every variant computes each entry with the same operations, so V
 // is bit-identical whichever is used; the fastest depends on N (small meshes want
 // more, smaller CTAs) and on the arithmetic, and is chosen by timing (autotune).
-struct FarTile {
+struct FarTileS {
     int rows, cols;
+    int min_ctas;  // DF64: > 0 -- column offsets in shared memory, this many CTAs per SM
+                   // requested (the other arithmetics use their register form)
 };
-constexpr FarTile kFarTiles[kFarTileVariants] = {{32, 256}, {16, 256}, {64, 256}, {8, 128}, {16, 128}, {32, 128}};
+constexpr FarTileS kFarTiles[kFarTileVariants] = {
+    {32, 256, 0}, {16, 256, 0}, {64, 256, 0}, {8, 128, 0}, {16, 128, 0}, {32, 128, 0},
+    {8, 128, 8},  {16, 128, 8}, {32, 128, 8}, {8, 128, 9}, {8, 64, 16},  {8, 64, 18}};
 
 template <int R, int C>
 __global__ void __launch_bounds__(C) k_far_f64(const double *__restrict__ q64, double *__restrict__ V,
@@ -239,11 +243,17 @@ __global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
 }
 
 // Double-float far field: see the file comment.
-template <int R, int C>
-__global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, float2 *__restrict__ V,
-                                                     int64_t ld, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+// MB > 0: the column triangle's 21 offsets staged in shared memory as (hi, lo) pairs,
+// thread-major (conflict-free), instead of 42 registers, the point loops not unrolled,
+// and MB CTAs per SM requested (registers capped to fit) -- more resident warps for
+// the same work.  MB = 0: offsets in registers, loops unrolled.
+template <int R, int C, int MB>
+__device__ __forceinline__ void far_df_body(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
+                                            int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
+    constexpr bool S = MB > 0;
     __shared__ float sq[R][53];
+    __shared__ float2 scol[S ? 3 * kQ * C : 1];
     const int64_t cbase = c0 + (int64_t)blockIdx.x * C;
     const int64_t i0 = r0 + (int64_t)blockIdx.y * R;
     if (i0 > cbase + C - 1 || i0 >= r1) return;
@@ -256,12 +266,22 @@ __global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, flo
     const int64_t j = cbase + threadIdx.x;
     if (j >= c1) return;
     const float *qj = qdf + j * kQdfStride;
-    float oh[3 * kQ], ol[3 * kQ], cj[9];
+    float oh[S ? 1 : 3 * kQ], ol[S ? 1 : 3 * kQ], cj[9];
+    if constexpr (S) {
 #pragma unroll
-    for (int k = 0; k < 3 * kQ; ++k) {
-        oh[k] = qj[2 * k];
-        ol[k] = qj[2 * k + 1];
+        for (int k = 0; k < 3 * kQ; ++k)  // this thread's own column
+            scol[k * C + threadIdx.x] = make_float2(qj[2 * k], qj[2 * k + 1]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3 * kQ; ++k) {
+            oh[k] = qj[2 * k];
+            ol[k] = qj[2 * k + 1];
+        }
     }
+    auto OF = [&](int k) -> float2 {
+        if constexpr (S) return scol[k * C + threadIdx.x];
+        else return make_float2(oh[k], ol[k]);
+    };
 #pragma unroll
     for (int k = 0; k < 9; ++k) cj[k] = qj[42 + k];
     const float2 Aj = df_mul(make_float2(qj[51], qj[52]), c_inv4pi_df);
@@ -283,7 +303,7 @@ __global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, flo
             fast_two_sum(h, l, Dh[c], Dl[c]);
         }
         float acc_h = 0.0f, acc_l = 0.0f;
-#pragma unroll
+#pragma unroll(S ? 1 : kQ)
         for (int a = 0; a < kQ; ++a) {
             float eh[3], el[3];
 #pragma unroll
@@ -294,15 +314,16 @@ __global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, flo
                 fast_two_sum(s, e, eh[c], el[c]);
             }
             float sh = 0.0f, sl = 0.0f;
-#pragma unroll
+#pragma unroll(S ? 1 : kQ)
             for (int b = 0; b < kQ; ++b) {
                 // d = e_a - o_b; |d|^2 = sum h^2 + 2 h l (two-product, two-sum)
                 float Sh = 0.0f, Sl = 0.0f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     float h, e;
-                    two_sum(eh[c], -oh[3 * b + c], h, e);
-                    const float l = __fadd_rn(e, __fsub_rn(el[c], ol[3 * b + c]));
+                    const float2 o = OF(3 * b + c);
+                    two_sum(eh[c], -o.x, h, e);
+                    const float l = __fadd_rn(e, __fsub_rn(el[c], o.y));
                     float p, pe;
                     two_prod(h, h, p, pe);
                     pe = __fmaf_rn(__fmul_rn(2.0f, h), l, pe);
@@ -347,6 +368,20 @@ __global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, flo
         fast_two_sum(acc_h, acc_l, h, l);
         V[i * ld + j] = df_mul(df_mul(make_float2(qi[51], qi[52]), Aj), make_float2(h, l));
     }
+}
+
+template <int R, int C>
+__global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
+                                              int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+{
+    far_df_body<R, C, 0>(qdf, V, ld, r0, r1, c0, c1);
+}
+
+template <int R, int C, int MB>
+__global__ void __launch_bounds__(C, MB) k_far_df_s(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
+                                                    int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+{
+    far_df_body<R, C, MB>(qdf, V, ld, r0, r1, c0, c1);
 }
 
 // Mirror the strict lower triangle of rows [r0, r1): V[i][j] = V[j][i], j < i,
@@ -554,7 +589,7 @@ __global__ void k_diag(const T *V, int64_t ld, int64_t N, double *d)
 }
 
 // ------------------------------------------------------------------ drivers
-template <typename T, int R, int C>
+template <typename T, int R, int C, int MB = 0>
 static void far_kernel(bem_operator *op, dim3 grid, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
     bem_mesh *m = op->mesh;
@@ -562,7 +597,12 @@ static void far_kernel(bem_operator *op, dim3 grid, int64_t r0, int64_t r1, int6
     if (op->precision == BEM_PREC_F64)
         k_far_f64<R, C><<<grid, C, 0, s>>>(m->q64, (double *)op->V, op->ld, r0, r1, c0, c1);
     else if (op->precision == BEM_PREC_DF64)
-        k_far_df<R, C><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
+    {
+        if constexpr (MB > 0)
+            k_far_df_s<R, C, MB><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
+        else
+            k_far_df<R, C><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
+    }
     else
         k_far_f32<R, C><<<grid, C, 0, s>>>(m->q32, m->cent, (float *)op->V, op->ld, r0, r1, c0, c1);
 }
@@ -600,7 +640,13 @@ static bem_status launch_far(bem_operator *op, int v, int64_t r0, int64_t r1, in
     case 2: far_kernel<T, 64, 256>(op, grid, r0, r1, c0, c1); break;
     case 3: far_kernel<T, 8, 128>(op, grid, r0, r1, c0, c1); break;
     case 4: far_kernel<T, 16, 128>(op, grid, r0, r1, c0, c1); break;
-    default: far_kernel<T, 32, 128>(op, grid, r0, r1, c0, c1); break;
+    case 5: far_kernel<T, 32, 128>(op, grid, r0, r1, c0, c1); break;
+    case 6: far_kernel<T, 8, 128, 8>(op, grid, r0, r1, c0, c1); break;
+    case 7: far_kernel<T, 16, 128, 8>(op, grid, r0, r1, c0, c1); break;
+    case 8: far_kernel<T, 32, 128, 8>(op, grid, r0, r1, c0, c1); break;
+    case 9: far_kernel<T, 8, 128, 9>(op, grid, r0, r1, c0, c1); break;
+    case 10: far_kernel<T, 8, 64, 16>(op, grid, r0, r1, c0, c1); break;
+    default: far_kernel<T, 8, 64, 18>(op, grid, r0, r1, c0, c1); break;
     }
     BEM_COUNT(ctx);
     if (profile) prof_stop(ctx, prof);
