@@ -647,6 +647,9 @@ def main():
     ap.add_argument("--inexact", type=float, default=0.0,
                     help="adaptive workload: stop each solve by the rule of the Remark after Alg. 1 (i), "
                          "|||x_k - x_(k-1)||| <= LAMBDA eta(x_k) (the paper uses ~1e-3); 0: PCG to 1e-10")
+    ap.add_argument("--far-tile", type=int, default=0,
+                    help="adaptive workload: far-field tile variant 1..12 instead of the autotuned one "
+                         "(no timing launches: for profiling captures)")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
@@ -709,7 +712,7 @@ def main():
         if graded:
             return step_graded(mesh)
         recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC,
-                                   inexact_lambda=args.inexact)
+                                   inexact_lambda=args.inexact, tile=args.far_tile)
         return recs
 
     for _ in range(max(args.warmup, 0)):
@@ -777,7 +780,7 @@ def main():
             r2 = step_graded(mh)
         else:
             r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC,
-                                     inexact_lambda=args.inexact)
+                                     inexact_lambda=args.inexact, tile=args.far_tile)
         cap_final = r2[-1]["cap"]
         mh.close()
         torch.cuda.synchronize()

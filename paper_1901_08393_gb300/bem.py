@@ -462,9 +462,9 @@ def mark_refine(mesh: Mesh, eta2, theta=0.5, bisec3=False):
 def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, precision=PREC_F64,
                  ss_order=4, tol=1e-12, max_it=20000, precond=PRECOND_JACOBI, incremental=True,
                  max_outer=20, inner_tol=1e-5, want_final=False, reliable_delta=0.0, inexact_lambda=0.0,
-                 basis=BASIS_P0):
+                 basis=BASIS_P0, tile=0):
     """Alg. 1 in the library's native loop; returns (records, final Mesh or None)."""
-    o = AdaptiveOpts(theta, max_N, max_levels, h_mode, AssemblyOpts(precision, ss_order),
+    o = AdaptiveOpts(theta, max_N, max_levels, h_mode, AssemblyOpts(precision, ss_order, tile),
                      SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode),
                      int(incremental), int(basis))
     recs = (LevelRecord * max_levels)()
