@@ -279,10 +279,11 @@ typedef struct {
 
 /* Discrete space of the adaptive loop.  P0: piecewise constants on the triangles
  * (Eq. 2.5).  DUAL: piecewise constants on the dual cells (Sec. 2.1, 2.6): each level
- * builds the barycentric refinement, assembles its operator (assembly options), forms
- * V^dual (bem_operator_dual), solves from zero, estimates with bem_zz_estimate_dual and
- * marks and refines the primal mesh; incremental and the warm start do not apply, and
- * solve.inexact_lambda must be 0. */
+ * builds the barycentric refinement, assembles its operator (assembly options; with
+ * incremental, the children of unrefined primal triangles keep their entries from the
+ * previous level's barycentric operator), forms V^dual (bem_operator_dual), solves
+ * from zero, estimates with bem_zz_estimate_dual and marks and refines the primal
+ * mesh; the warm start does not apply, and solve.inexact_lambda must be 0. */
 #define BEM_BASIS_P0 0
 #define BEM_BASIS_DUAL 1
 

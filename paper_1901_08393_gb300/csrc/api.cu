@@ -808,17 +808,62 @@ static float elapsed(cudaEvent_t a, cudaEvent_t b)
     return ms;
 }
 
-// Operator of one level of the dual-basis loop: barycentric refinement, its
-// operator, V^dual; the refinement and its operator are released again.
-static bem_status dual_level_operator(bem_mesh *cur, const bem_assembly_opts *aopts, bem_operator **out)
+// Children 6t .. 6t+5 of the kept primal triangles t < K keep their parent's children
+// 6 parent[t] .. 6 parent[t] + 5: the parent map of the barycentric refinement.
+__global__ void k_bary_parent(const int32_t *parent, int64_t K, int32_t *out)
 {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 6 * K) out[i] = 6 * parent[i / 6] + (int32_t)(i % 6);
+}
+
+// The barycentric refinement and its operator of the previous level, kept for the
+// incremental assembly of the next one.
+struct BaryLevel {
+    bem_mesh *mesh = nullptr;
+    bem_operator *op = nullptr;
+    void release()
+    {
+        if (op) bem_operator_destroy(op);
+        if (mesh) bem_mesh_destroy(mesh);
+        op = nullptr;
+        mesh = nullptr;
+    }
+};
+
+// Operator of one level of the dual-basis loop: barycentric refinement, its operator,
+// V^dual.  With incremental, the children of the kept primal triangles (the first 6K
+// barycentric triangles, geometry and adjacency unchanged under conforming NVB) take
+// their entries from the previous level's barycentric operator (bem_assemble_V_update);
+// the refinement and its operator are then kept for the next level.
+static bem_status dual_level_operator(bem_mesh *cur, const bem_assembly_opts *aopts, bool incremental,
+                                      BaryLevel &prev, bem_operator **out)
+{
+    bem_ctx *ctx = cur->ctx;
     bem_mesh *b = nullptr;
     bem_operator *ob = nullptr;
     bem_status st = barycentric(cur, &b);
-    if (!st) st = bem_assemble_V(b, aopts, &ob);
+    const bool inc = incremental && prev.op && cur->parent && cur->n_kept > 0 && prev.op->N == 6 * cur->src_N;
+    if (!st && inc) {
+        st = dalloc(ctx, b->allocs, (void **)&b->parent, sizeof(int32_t) * (size_t)b->N, false);
+        if (!st) {
+            k_bary_parent<<<nblk(6 * cur->n_kept, 256), 256, 0, ctx->stream>>>(cur->parent, cur->n_kept, b->parent);
+            BEM_COUNT(ctx);
+            b->n_kept = 6 * cur->n_kept;
+            b->src_N = prev.op->N;
+            st = bem_assemble_V_update(b, prev.op, aopts, &ob);
+        }
+    } else if (!st) {
+        st = bem_assemble_V(b, aopts, &ob);
+    }
+    prev.release();
     if (!st) st = dual_operator(ob, cur, out);
-    if (ob) bem_operator_destroy(ob);
-    if (b) bem_mesh_destroy(b);
+    if (!st && incremental) {
+        prev.mesh = b;
+        prev.op = ob;
+    } else {
+        if (ob) bem_operator_destroy(ob);
+        if (b) bem_mesh_destroy(b);
+    }
     return st;
 }
 
@@ -840,6 +885,7 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
     bem_mesh *cur = mesh;
     bem_mesh *prev_mesh = nullptr;  // mesh of op_prev, destroyed after op_prev
     bem_operator *op_prev = nullptr;
+    BaryLevel bary_prev;  // dual basis: the previous level's barycentric operator
     Allocs xprev_alloc;
     double *x_prev = nullptr;
     bem_status st = BEM_OK;
@@ -851,7 +897,7 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         cudaEventRecord(ctx->ev[0], s);
         bem_operator *op = nullptr;
         if (dual)
-            st = dual_level_operator(cur, &opts->assembly, &op);
+            st = dual_level_operator(cur, &opts->assembly, opts->incremental != 0, bary_prev, &op);
         else if (op_prev && opts->incremental && cur->parent)
             st = bem_assemble_V_update(cur, op_prev, &opts->assembly, &op);
         else
@@ -937,6 +983,7 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
     }
     if (op_prev) bem_operator_destroy(op_prev);
     if (prev_mesh && prev_mesh != mesh) bem_mesh_destroy(prev_mesh);
+    bary_prev.release();
     dfree_all(ctx, xprev_alloc);
     if (final_mesh && cur != mesh && !st) {
         *final_mesh = cur;

@@ -66,9 +66,10 @@ namespace {
 // level the request can reach -- the first with N >= max_N, which Doerfler marking
 // can overshoot by about 1.5x, or N0 grown by at most 2.2x per level (bisection of
 // every element plus closure) -- plus per-triangle tables and solver vectors.  The
-// dual basis holds, at its largest level, the operator of the barycentric refinement
-// (6 n triangles: 36 times the bytes of a level operator; no incremental assembly)
-// and V^dual (about n / 2 vertices, DF64 plus the packed copy: 2.5 n^2 bytes).
+// dual basis holds, at its largest level, the operators of the barycentric refinements
+// of two consecutive levels (6 n triangles: 36 times the bytes of a level operator,
+// the coarse one read by the incremental assembly of the fine one) and V^dual with its
+// preconditioner (about n / 2 vertices: DF64, packed copies, FP32 D^reg, 4 n^2 bytes).
 int64_t estimate_bytes(int64_t N0, int64_t max_N, int32_t levels, int precision, int basis)
 {
     const double es = precision == BEM_PREC_F32 ? 4.0 : 8.0;
@@ -76,7 +77,7 @@ int64_t estimate_bytes(int64_t N0, int64_t max_N, int32_t levels, int precision,
     const double grown = (double)N0 * std::pow(2.2, (double)(levels - 1));
     if (grown < reach) reach = grown;
     const double n = (levels <= 1 ? (double)N0 : reach) + 64.0;
-    if (basis == BEM_BASIS_DUAL) return (int64_t)((36.0 * es + 2.5) * n * n + 6.0 * 4096.0 * n) + (64ll << 20);
+    if (basis == BEM_BASIS_DUAL) return (int64_t)((72.0 * es + 4.0) * n * n + 6.0 * 4096.0 * n) + (64ll << 20);
     const double ops = levels <= 1 ? (precision == BEM_PREC_DF64 ? 1.25 : precision == BEM_PREC_F32 ? 1.5 : 1.0) : 2.0;
     return (int64_t)(ops * es * n * n + 4096.0 * n) + (64ll << 20);
 }

@@ -123,6 +123,19 @@ def test_dual_adaptive_loop_matches_oracle(ctx, prec):
     assert np.array_equal(v, hist[-1]["verts"]) and np.array_equal(t, hist[-1]["tris"])
 
 
+def test_incremental_barycentric_assembly_is_exact(ctx):
+    """The dual loop's incremental assembly (children of unrefined primal triangles keep
+    their entries) reproduces the from-scratch loop bit for bit."""
+    m = inputs.workload_polycube_adaptive()
+    a, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), max_N=2500, tol=1e-12, precision=bem.PREC_DF64,
+                            basis=bem.BASIS_DUAL, incremental=True)
+    b, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), max_N=2500, tol=1e-12, precision=bem.PREC_DF64,
+                            basis=bem.BASIS_DUAL, incremental=False)
+    assert [(r["N"], r["cap"], r["iterations"], r["eta2_total"]) for r in a] == \
+        [(r["N"], r["cap"], r["iterations"], r["eta2_total"]) for r in b]
+    assert sum(r["ms_assemble"] for r in a[1:]) < sum(r["ms_assemble"] for r in b[1:])
+
+
 def test_dual_levels_match_oracle_levelwise_on_a_symmetric_mesh(ctx):
     """On the cube the indicators come in symmetric groups whose order is decided by
     rounding, so each level is compared with the oracle on the library's own mesh."""
