@@ -174,7 +174,7 @@ def roofline(prec, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_
         ops = far_units * DF_FAR_OPS_PER_ENTRY / max(far_n, 1)
         avg_s = far_ms / max(far_n, 1) / 1e3
         achieved = ops / avg_s / 1e12
-        roof = {"kernel": "k_far_df", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS,
+        roof = {"kernel": "k_far_df / k_far_df_s (DF64 far field, autotuned tile variant)", "bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TOPS,
                 "unit": "T FP32 op/s", "frac": achieved / FP32_PEAK_TOPS, "traffic": None,
                 "peak_source": "FP32 issue peak derived from unit counts and clock (152 SMs x 128 x 2.07 GHz)",
                 "launches": far_n}
