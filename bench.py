@@ -642,8 +642,9 @@ def main():
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
     ap.add_argument("--precond", default="auto", choices=["auto", "block", "jacobi", "calderon"],
                     help="PCG preconditioner (block: DF64 and FP32 operators, FP64 runs Jacobi); auto: "
-                         "block, except jacobi on the graded cube (its V has indefinite diagonal blocks); "
-                         "calderon: the operator preconditioner of Sec. 2.6 (dual workload only)")
+                         "block, except jacobi on the graded cube (its V has indefinite diagonal blocks) and "
+                         "calderon for the dual workload; calderon: the operator preconditioner of Sec. 2.6 "
+                         "(dual workload only)")
     ap.add_argument("--inexact", type=float, default=0.0,
                     help="adaptive workload: stop each solve by the rule of the Remark after Alg. 1 (i), "
                          "|||x_k - x_(k-1)||| <= LAMBDA eta(x_k) (the paper uses ~1e-3); 0: PCG to 1e-10")
@@ -656,7 +657,7 @@ def main():
     if args.impl == "reference":
         return reference_arm(args)
     if args.precond == "auto":
-        args.precond = "jacobi" if args.workload == "graded60k" else "block"
+        args.precond = {"graded60k": "jacobi", "dual": "calderon"}.get(args.workload, "block")
     if args.precond == "calderon" and args.workload != "dual":
         ap.error("--precond calderon needs --workload dual")
     if args.workload == "batch":

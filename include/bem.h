@@ -88,7 +88,8 @@ typedef struct {
  * for dual operators (bem_operator_dual): C = S D^reg S with D^reg = sum_m Q_m^T V^bary
  * Q_m + a a^T and S the degree-6 Chebyshev approximation of M^-1 (M the mass matrix of
  * hats against dual cells, Jacobi-scaled spectrum in [15/22, 36/22]; S agrees with M^-1
- * to 2e-4 relative).  C is SPD, so CG on V^dual x = f with C has the spectrum of the
+ * to 2e-4 relative), formed once with the operator (FP32, M x M) and applied as one
+ * product per iteration.  C is SPD, so CG on V^dual x = f with C has the spectrum of the
  * paper's M^-T V^dual M^-1 D^reg (solved there by GMRES) and reaches the same x.
  * DF64 dual operators, persistent solver, not in a batch. */
 #define BEM_PRECOND_CALDERON 3
@@ -304,8 +305,8 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
  * triangle summed), D_ij = sum over T at i, T' at j of (curl phi_i|T . curl phi_j|T')
  * V^T[T][T'] with curl phi_k = (p_(k+1) - p_(k+2)) / (2 |T|) on T (the surface curl
  * n x grad of the hat of local vertex k), plus a_i a_j, a_i = |T_i^dual| = the integral
- * of the hat; stored in FP32 (4 M^2 bytes) with the operator, beside copies of the
- * primal mesh's triangles, vertex-to-triangle table and areas for the mass matrix. */
+ * of the hat; then C = S D^reg S (S applied to the columns of D^reg, then to the columns
+ * of the transpose); both stored in FP32 (8 M^2 bytes) with the operator. */
 /* The paper's own discretisation (Sec. 2.1-2.6): piecewise constants on the dual mesh.
  * bem_mesh_barycentric: the barycentric refinement T^bary of the (stored, rotated)
  * mesh (Sec. 2.1): each triangle (v0, v1, v2) becomes (v0, m01, c), (m01, v1, c),
@@ -329,9 +330,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
 bem_status bem_mesh_barycentric(bem_mesh *mesh, bem_mesh **out);
 bem_status bem_operator_dual(bem_operator *bary_op, bem_mesh *mesh, bem_operator **out);
 bem_status bem_zz_estimate_dual(bem_mesh *mesh, const double *x, int32_t h_mode, double *eta2_out, double *totals);
-/* The FP32 D^reg of a dual operator, M x M row-major into dst (host or device);
- * BEM_ERR_INVALID for an operator without it. */
-bem_status bem_operator_preconditioner(const bem_operator *op, float *dst);
+/* The FP32 D^reg (which = 0) or C = S D^reg S (which = 1) of a dual operator, M x M
+ * row-major into dst (host or device); BEM_ERR_INVALID for an operator without them. */
+bem_status bem_operator_preconditioner(const bem_operator *op, int32_t which, float *dst);
 
 /* ---------------------------------------------------------------- batch */
 /* Many independent capacity problems assembled and solved together (the paper has

@@ -327,3 +327,26 @@ def calderon_extremes(Vd, Dreg, Mm):
     L = np.linalg.cholesky(Vd)
     ev = np.linalg.eigvalsh(L.T @ C @ L)
     return float(ev[0]), float(ev[-1])
+
+
+def chebyshev_inverse(Mm, K=6, lo=15.0 / 22.0, hi=36.0 / 22.0):
+    """S_K ~ M^-1: K steps of Chebyshev iteration for M s = r from s = 0, Jacobi-scaled,
+    with the spectral interval [lo, hi] of D^-1 M (per triangle the mass matrix is
+    (|T|/108)(15 I + 7 J) against the diagonal 22 |T|/108, so [15/22, 36/22] holds on
+    every mesh), applied to the columns of the identity.  Not the paper's (it factors
+    M): the GPU's operator preconditioner uses this polynomial, C = S_K D^reg S_K."""
+    A = np.asarray(Mm, dtype=np.float64)
+    dinv = 1.0 / np.diag(A)
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    sigma = theta / delta
+    res = np.eye(A.shape[0])
+    d = (dinv[:, None] * res) / theta
+    S = d.copy()
+    rho = 1.0 / sigma
+    for _ in range(1, K):
+        res = res - A @ d
+        rn = 1.0 / (2.0 * sigma - rho)
+        d = rn * rho * d + (2.0 * rn / delta) * (dinv[:, None] * res)
+        S = S + d
+        rho = rn
+    return S

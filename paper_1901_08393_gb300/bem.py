@@ -159,7 +159,7 @@ def lib():
         "bem_mesh_barycentric": [vp, P(vp)],
         "bem_operator_dual": [vp, vp, P(vp)],
         "bem_zz_estimate_dual": [vp, vp, i32, vp, vp],
-        "bem_operator_preconditioner": [vp, vp],
+        "bem_operator_preconditioner": [vp, i32, vp],
         "bem_far_tiles": [vp, vp],
     }
     for name, args in sig.items():
@@ -367,11 +367,11 @@ class Operator:
         self.ctx.check(self.ctx.L.bem_operator_entries(self.h, pI, pJ, int(Ia.shape[0]), out.ctypes.data))
         return out
 
-    def preconditioner(self):
-        """D^reg of a dual operator (Sec. 2.6), FP32, M x M."""
+    def preconditioner(self, which=0):
+        """D^reg (which=0) or C = S D^reg S (which=1) of a dual operator (Sec. 2.6), FP32, M x M."""
         N = self.info()[0]
         out = np.zeros((N, N), dtype=np.float32)
-        self.ctx.check(self.ctx.L.bem_operator_preconditioner(self.h, out.ctypes.data))
+        self.ctx.check(self.ctx.L.bem_operator_preconditioner(self.h, which, out.ctypes.data))
         return out
 
     def matvec(self, x):

@@ -811,44 +811,133 @@ __global__ void k_hypersingular(const double *V, const int32_t *tris, const int3
 }
 
 // 1 / diag of the mass matrix M[i][j] = int phi_j chi_i^dual: M_ii = sum_{T at i} 22 |T| / 108.
-__global__ void k_mass_dinv(const int32_t *v2t_off, const int32_t *v2t, const double *area, int64_t M, double *dinv)
+__global__ void k_mass_dinv(const int32_t *v2t_off, const int32_t *v2t, const double *area, int64_t M, float *dinv)
 {
     const int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (z >= M) return;
     double s = 0.0;
     for (int32_t p = v2t_off[z]; p < v2t_off[z + 1]; ++p) s += area[v2t[p]];
-    dinv[z] = 108.0 / (22.0 * s);
+    dinv[z] = (float)(108.0 / (22.0 * s));
 }
 
+// S ~ M^-1 applied to every column of B (M x ld, FP32): kChebSteps steps of Chebyshev
+// iteration on the Jacobi-scaled mass matrix, whose spectrum lies in [15/22, 36/22] on
+// every mesh (per triangle M_T = (|T| / 108)(15 I + 7 J) against diag 22 |T| / 108);
+// theta and delta are the interval's centre and half-width.  One thread per (row i,
+// column j), columns fastest: (M X)_ij = sum_{T at i} |T| / 108 (22 X_ij + 7 (X_kj + X_lj)).
+constexpr double kChebTheta = 51.0 / 44.0, kChebDelta = 21.0 / 44.0;
+constexpr int kChebSteps = 6;  // error factor 2 ((sqrt(2.4) - 1) / (sqrt(2.4) + 1))^6 = 2e-4
+
+__global__ void k_cheb_cols(const int32_t *tris, const int32_t *v2t_off, const int32_t *v2t, const double *area,
+                            const float *dinv, int64_t M, int64_t ld, const float *B, const float *dc, float *dn,
+                            float *res, float *out, float c_old, float c_res, int first)
+{
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    for (int64_t i = blockIdx.y; i < M; i += gridDim.y) {
+        const int64_t o = i * ld + j;
+        if (first) {  // res = B, d = D^-1 B / theta, out = d
+            const float b = B[o];
+            const float d = b * dinv[i] * (float)(1.0 / kChebTheta);
+            res[o] = b;
+            dn[o] = d;
+            out[o] = d;
+            continue;
+        }
+        const float di = dc[o];
+        float md = 0.0f;
+        for (int32_t q = v2t_off[i]; q < v2t_off[i + 1]; ++q) {
+            const int32_t t = v2t[q];
+            float nb = 0.0f;
+            for (int c = 0; c < 3; ++c) {
+                const int32_t v = tris[3 * (int64_t)t + c];
+                if (v != i) nb += dc[(int64_t)v * ld + j];
+            }
+            md += (float)area[t] * (22.0f * di + 7.0f * nb);
+        }
+        const float r = res[o] - md * (1.0f / 108.0f);
+        res[o] = r;
+        const float d = c_old * di + c_res * r * dinv[i];
+        dn[o] = d;
+        out[o] += d;
+    }
+}
+
+// out[j][i] = in[i][j] over 32 x 32 tiles (M x ld, FP32).
+__global__ void k_transpose_f32(const float *in, int64_t M, int64_t ld, float *out)
+{
+    __shared__ float t[32][33];
+    const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = by + r, j = bx + threadIdx.x;
+        t[r][threadIdx.x] = (i < M && j < M) ? in[i * ld + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = bx + r, j = by + threadIdx.x;
+        if (i < M && j < M) out[i * ld + j] = t[threadIdx.x][r];
+    }
+}
+
+// C[i][j] = C[j][i] for i > j through 32 x 32 tiles: the rounded S W^T made exactly
+// symmetric (the packed product reads both halves of the diagonal tiles).
+__global__ void k_mirror_upper_f32(float *C, int64_t M, int64_t ld)
+{
+    __shared__ float t[32][33];
+    const int64_t bi = blockIdx.y, bj = blockIdx.x;
+    if (bj > bi) return;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {  // upper block (bj, bi)
+        const int64_t i = bj * 32 + r, j = bi * 32 + threadIdx.x;
+        t[r][threadIdx.x] = (i < M && j < M) ? C[i * ld + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {  // lower block (bi, bj)
+        const int64_t i = bi * 32 + r, j = bj * 32 + threadIdx.x;
+        if (i < M && j < M && i > j) C[i * ld + j] = t[threadIdx.x][r];
+    }
+}
+
+static bem_status cheb_cols(bem_ctx *ctx, bem_mesh *pm, const float *dinv, int64_t ld, const float *B, float *out,
+                            float *w)
+{
+    const int64_t M = pm->M;
+    float *res = w, *dA = w + M * ld, *dB = w + 2 * M * ld;
+    const dim3 grid((unsigned)nblk(M, 128), (unsigned)std::min<int64_t>(M, 65535));
+    k_cheb_cols<<<grid, 128, 0, ctx->stream>>>(pm->tris, pm->v2t_off, pm->v2t, pm->area, dinv, M, ld, B, nullptr, dA,
+                                               res, out, 0.f, 0.f, 1); BEM_COUNT(ctx);
+    double rho = kChebDelta / kChebTheta;
+    for (int k = 1; k < kChebSteps; ++k) {
+        const double rn = 1.0 / (2.0 * (kChebTheta / kChebDelta) - rho);
+        k_cheb_cols<<<grid, 128, 0, ctx->stream>>>(pm->tris, pm->v2t_off, pm->v2t, pm->area, dinv, M, ld, B, dA, dB,
+                                                   res, out, (float)(rn * rho), (float)(2.0 * rn / kChebDelta), 0);
+        BEM_COUNT(ctx);
+        rho = rn;
+        float *t = dA;
+        dA = dB;
+        dB = t;
+    }
+    BEM_CK_LAUNCH(ctx);
+    return BEM_OK;
+}
+
+// The operator preconditioner of Sec. 2.6 for CG on V^dual: D^reg (FP32, from V^bary),
+// then C = S D^reg S with S the Chebyshev approximation of M^-1 (W = S D^reg by
+// columns, C = S W^T, which equals S D^reg S since it is symmetric), stored FP32.
 static bem_status calderon_setup(bem_operator *ob, bem_mesh *pm, bem_operator *op, int *bad)
 {
     bem_ctx *ctx = pm->ctx;
     cudaStream_t s = ctx->stream;
-    const int64_t N = pm->N, M = pm->M;
+    const int64_t N = pm->N, M = pm->M, ld = op->ld;
     Allocs tmp;
     double *VT = nullptr;
-    bem_status st = dalloc(ctx, op->allocs, (void **)&op->cal_D, sizeof(float) * (size_t)M * (size_t)op->ld, true);
-    if (!st) st = dalloc(ctx, op->allocs, (void **)&op->cal_tris, sizeof(int32_t) * (3 * N + M + 1 + 3 * N), false);
-    if (!st) st = dalloc(ctx, op->allocs, (void **)&op->cal_area, sizeof(double) * (N + M), false);
+    float *W = nullptr, *work = nullptr, *dinv = nullptr;
+    bem_status st = dalloc(ctx, op->allocs, (void **)&op->cal_D, sizeof(float) * (size_t)M * (size_t)ld, true);
+    if (!st) st = dalloc(ctx, op->allocs, (void **)&op->cal_C, sizeof(float) * (size_t)M * (size_t)ld, true);
     if (!st) st = dalloc(ctx, tmp, (void **)&VT, sizeof(double) * (size_t)N * (size_t)N, false);
     if (st) {
         dfree_all(ctx, tmp);
         return st;
     }
-    op->cal_N = N;
-    op->cal_v2t_off = op->cal_tris + 3 * N;
-    op->cal_v2t = op->cal_v2t_off + M + 1;
-    op->cal_mdinv = op->cal_area + N;
-    cudaError_t e = cudaMemcpyAsync(op->cal_tris, pm->tris, sizeof(int32_t) * 3 * N, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(op->cal_v2t_off, pm->v2t_off, sizeof(int32_t) * (M + 1), cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(op->cal_v2t, pm->v2t, sizeof(int32_t) * 3 * N, cudaMemcpyDeviceToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(op->cal_area, pm->area, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) {
-        dfree_all(ctx, tmp);
-        return cuda_error(ctx, e, "preconditioner tables");
-    }
-    k_mass_dinv<<<nblk(M, 256), 256, 0, s>>>(pm->v2t_off, pm->v2t, pm->area, M, op->cal_mdinv); BEM_COUNT(ctx);
     const dim3 gc((unsigned)nblk(N, 128), (unsigned)std::min<int64_t>(N, 65535));
     if (ob->precision == BEM_PREC_F64)
         { k_contract_children<double><<<gc, 128, 0, s>>>((const double *)ob->V, ob->ld, N, VT); BEM_COUNT(ctx); }
@@ -858,9 +947,25 @@ static bem_status calderon_setup(bem_operator *ob, bem_mesh *pm, bem_operator *o
         { k_contract_children<float><<<gc, 128, 0, s>>>((const float *)ob->V, ob->ld, N, VT); BEM_COUNT(ctx); }
     const dim3 gh((unsigned)nblk(M, 128), (unsigned)std::min<int64_t>(M, 65535));
     k_hypersingular<<<gh, 128, 0, s>>>(pm->verts, pm->tris, pm->v2t_off, pm->v2t, pm->area, VT, N,
-                                       op->mesh->area, M, op->cal_D, op->ld, bad); BEM_COUNT(ctx);
-    e = cudaGetLastError();
-    dfree_all(ctx, tmp);  // stream-ordered: freed after the kernels that read it
+                                       op->mesh->area, M, op->cal_D, ld, bad); BEM_COUNT(ctx);
+    dfree_all(ctx, tmp);  // stream-ordered: V^T is freed after the kernel that reads it
+    // C = S D^reg S: W = S D^reg, then S W^T (all buffers zeroed: padding columns stay 0)
+    st = dalloc(ctx, tmp, (void **)&W, sizeof(float) * ((size_t)M * (size_t)ld * 5 + (size_t)M), true);
+    if (st) return st;
+    float *Wt = W + M * ld;
+    work = W + 2 * M * ld;  // residuals and two directions
+    dinv = W + 5 * M * ld;
+    k_mass_dinv<<<nblk(M, 256), 256, 0, s>>>(pm->v2t_off, pm->v2t, pm->area, M, dinv); BEM_COUNT(ctx);
+    if (!(st = cheb_cols(ctx, pm, dinv, ld, op->cal_D, W, work))) {
+        k_transpose_f32<<<dim3(nblk(M, 32), nblk(M, 32)), dim3(32, 8), 0, s>>>(W, M, ld, Wt); BEM_COUNT(ctx);
+        st = cheb_cols(ctx, pm, dinv, ld, Wt, op->cal_C, work);
+    }
+    if (!st) {
+        k_mirror_upper_f32<<<dim3(nblk(M, 32), nblk(M, 32)), dim3(32, 8), 0, s>>>(op->cal_C, M, ld); BEM_COUNT(ctx);
+    }
+    cudaError_t e = cudaGetLastError();
+    dfree_all(ctx, tmp);
+    if (st) return st;
     return e == cudaSuccess ? BEM_OK : cuda_error(ctx, e, "preconditioner kernels");
 }
 

@@ -582,13 +582,14 @@ bem_status bem_zz_estimate_dual(bem_mesh *mesh, const double *x, int32_t h_mode,
     return dev_out_end(ctx, eta2_out, de);
 }
 
-bem_status bem_operator_preconditioner(const bem_operator *op, float *dst)
+bem_status bem_operator_preconditioner(const bem_operator *op, int32_t which, float *dst)
 {
     if (!op) return BEM_ERR_INVALID;
     bem_ctx *ctx = op->ctx;
     CHECK_ARG(ctx, dst != nullptr, "null destination");
+    CHECK_ARG(ctx, which == 0 || which == 1, "which must be 0 (D^reg) or 1 (C)");
     CHECK_ARG(ctx, op->cal_D != nullptr, "the operator carries no preconditioner (not a dual operator)");
-    cudaError_t e = cudaMemcpy2DAsync(dst, sizeof(float) * op->N, op->cal_D, sizeof(float) * op->ld,
+    cudaError_t e = cudaMemcpy2DAsync(dst, sizeof(float) * op->N, which ? op->cal_C : op->cal_D, sizeof(float) * op->ld,
                                       sizeof(float) * op->N, op->N, cudaMemcpyDefault, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     return e == cudaSuccess ? BEM_OK : cuda_error(ctx, e, "preconditioner read");

@@ -101,12 +101,9 @@ struct bem_operator {
     void *V = nullptr;      // N x ld, row-major: double (F64), float2 hi/lo (DF64), float (F32)
     double *diag = nullptr; // N, FP64 diagonal
     int owns_mesh = 0;      // 1: mesh is a cells mesh freed with the operator
-    // dual operators: the operator preconditioner (D^reg in FP32, N x ld) and the
-    // primal mesh of the dual cells for the mass matrix
-    float *cal_D = nullptr;
-    int64_t cal_N = 0;      // primal triangles
-    int32_t *cal_tris = nullptr, *cal_v2t_off = nullptr, *cal_v2t = nullptr;
-    double *cal_area = nullptr, *cal_mdinv = nullptr;  // primal areas; 1 / diag(mass matrix)
+    // dual operators: the regularised hypersingular operator D^reg and the operator
+    // preconditioner C = S D^reg S (both FP32, N x ld)
+    float *cal_D = nullptr, *cal_C = nullptr;
     bem::Allocs allocs;
 };
 

@@ -911,21 +911,10 @@ struct PcgArgs {
     const double *area, *hdiam;  // hdiam: diam(T), or null for h_T = |T|^1/2
     double *u;                   // M nodal values
     int64_t M;
-    // operator preconditioning (Sec. 2.6): packed FP32 upper triangle of D^reg (the
-    // tiles of vp), primal mesh of the dual cells for the mass matrix, 4 x ld work
+    // operator preconditioning (Sec. 2.6): packed FP32 upper triangle of the
+    // preconditioner C = S D^reg S (the tiles of vp)
     const float *dvp;
-    const int32_t *mtris, *mv2t_off, *mv2t;
-    const double *marea, *mdinv;
-    double *cw;
 };
-
-// Chebyshev iteration for the mass matrix M[i][j] = int phi_j chi_i^dual with Jacobi
-// scaling: per triangle M_T = (|T| / 108) (15 I + 7 J) against diag 22 |T| / 108, so the
-// spectrum of D^-1 M lies in [15/22, 36/22] on every mesh; theta and delta are the
-// centre and half-width of that interval, kChebSteps the degree (error factor
-// 2 ((sqrt(2.4) - 1) / (sqrt(2.4) + 1))^6 = 2e-4).
-constexpr double kChebTheta = 51.0 / 44.0, kChebDelta = 21.0 / 44.0;
-constexpr int kChebSteps = 6;
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int G)
 {
@@ -1027,53 +1016,11 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         }
         return grid_barrier(a.bar, a.err, G);
     };
-    // dst = S src: kChebSteps steps of Chebyshev iteration on the Jacobi-scaled mass
-    // matrix (rows i0 + k stride; the directions double-buffered, so one grid barrier
-    // per step separates a direction's writes from its neighbours' reads)
-    auto cheb = [&](const double *src, double *dst) -> bool {
-        double *res = a.cw, *dc = a.cw + a.ld, *dn = a.cw + 2 * a.ld;
-        double rho = kChebDelta / kChebTheta;
-        for (int64_t i = i0; i < a.N; i += stride) {
-            const double ri = src[i];
-            const double di = ri * a.mdinv[i] / kChebTheta;
-            res[i] = ri;
-            dc[i] = di;
-            dst[i] = di;
-        }
-        for (int k = 1; k < kChebSteps; ++k) {
-            if (!grid_barrier(a.bar, a.err, G)) return false;
-            const double rn = 1.0 / (2.0 * (kChebTheta / kChebDelta) - rho);
-            for (int64_t i = i0; i < a.N; i += stride) {
-                const double di = dc[i];
-                double md = 0.0;
-                for (int32_t q = a.mv2t_off[i]; q < a.mv2t_off[i + 1]; ++q) {
-                    const int32_t t = a.mv2t[q];
-                    double o = 0.0;
-                    for (int c = 0; c < 3; ++c) {
-                        const int32_t v = a.mtris[3 * (int64_t)t + c];
-                        if (v != i) o += __ldcg(dc + v);  // other CTAs' rows: L2
-                    }
-                    md += a.marea[t] * (22.0 * di + 7.0 * o);
-                }
-                const double ri = res[i] - md / 108.0;
-                res[i] = ri;
-                const double dni = rn * rho * di + (2.0 * rn / kChebDelta) * ri * a.mdinv[i];
-                dn[i] = dni;
-                dst[i] += dni;
-            }
-            rho = rn;
-            double *tmp = dc;
-            dc = dn;
-            dn = tmp;
-        }
-        return true;
-    };
-    // z = S D^reg S r (operator preconditioning, Sec. 2.6): Chebyshev, the product with
-    // the packed FP32 D^reg (exact products, double-float sums), Chebyshev
-    auto calderon = [&]() -> bool {
-        double *t = a.cw + 3 * a.ld;
-        if (!cheb(a.r, t)) return false;
-        for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(t[i]) : make_float2(0.f, 0.f);
+    // z = C r (operator preconditioning, Sec. 2.6): the product with the packed FP32 C
+    // (exact products, double-float sums); its row pass also forms the partial of r.z,
+    // and with init p = z
+    auto calderon = [&](bool init, double &rz_part) -> bool {
+        for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.r[i]) : make_float2(0.f, 0.f);
         if (!grid_barrier(a.bar, a.err, G)) return false;
         symv_hi_tiles(a.dvp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
         tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
@@ -1081,11 +1028,17 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
             const int64_t i = ib + (lane >> 2);
             const bool valid = i < a.N;
-            const double ti = symv_row4(a.prow, a.pcol, a.nb, valid ? i : a.N - 1, q4);
-            if (valid && q4 == 0) t[i] = ti;
+            const double zi = symv_row4(a.prow, a.pcol, a.nb, valid ? i : a.N - 1, q4);
+            if (valid && q4 == 0) {
+                a.z[i] = zi;
+                rz_part += __ldcg(a.r + i) * zi;  // r of other threads' rows: L2
+                if (init) {
+                    a.p[i] = zi;
+                    a.pdf[i] = df_from_double(zi);
+                }
+            }
         }
-        if (!grid_barrier(a.bar, a.err, G)) return false;
-        return cheb(t, a.z);
+        return true;
     };
     // r = b - V x0 (or b), z = M^-1 r, p = z
     const bool prod0 = a.has_x0 || mixed;
@@ -1113,15 +1066,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         for (int blk = cta; blk < a.nbj; blk += G)
             block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, true, rs, rz_l, rr_l);
     }
-    if (calpc) {  // rows of r are this thread's own: no barrier before the first Chebyshev step
-        if (!calderon()) return;
-        for (int64_t i = i0; i < a.N; i += stride) {
-            const double ri = a.r[i], zi = a.z[i];
-            a.p[i] = zi;
-            a.pdf[i] = df_from_double(zi);
-            rz_l += ri * zi;
-            rr_l += ri * ri;
-        }
+    if (calpc) {  // r.r of this thread's rows, then z = C r (r written by its own rows)
+        for (int64_t i = i0; i < a.N; i += stride) rr_l += a.r[i] * a.r[i];
+        if (!calderon(true, rz_l)) return;
     }
     cta_partial(rz_l, pA, cta);
     cta_partial(rr_l, pB, cta);
@@ -1171,8 +1118,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 a.r[i] = ri;
                 rr_l += ri * ri;
             }
-            if (!calderon()) return;
-            for (int64_t i = i0; i < a.N; i += stride) rz_n += a.r[i] * a.z[i];
+            if (!calderon(false, rz_n)) return;
         } else {
             for (int64_t i = i0; i < a.N; i += stride) {
                 a.x[i] += alpha * a.p[i];
@@ -1247,11 +1193,8 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                                 rr_l);
             } else if (calpc) {  // r was written in the row-pass layout: barrier first
                 if (!grid_barrier(a.bar, a.err, G)) return;
-                if (!calderon()) return;
-                for (int64_t i = i0; i < a.N; i += stride) {
-                    rz_n += a.r[i] * a.z[i];
-                    rr_l += a.r[i] * a.r[i];
-                }
+                for (int64_t i = i0; i < a.N; i += stride) rr_l += a.r[i] * a.r[i];
+                if (!calderon(false, rz_n)) return;
             }
             cta_partial(rz_n, pB, cta);
             cta_partial(rr_l, pC, cta);
@@ -1590,15 +1533,13 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     if (f32op && !vp) return BEM_OK;  // no room for the packed copy: host-driven refinement
     const bool calpc = precond == BEM_PRECOND_CALDERON;
     float *dvp = nullptr;
-    double *cw = nullptr;
-    if (calpc) {  // packed D^reg (the tiles of the operator's packed copy) and Chebyshev work
-        if ((st = dalloc(ctx, tmp, (void **)&dvp, (size_t)nt_ * kTileF * sizeof(float), false)) ||
-            (st = dalloc(ctx, tmp, (void **)&cw, sizeof(double) * 4 * op->ld, true))) {
+    if (calpc) {  // packed C (the tiles of the operator's packed copy)
+        if ((st = dalloc(ctx, tmp, (void **)&dvp, (size_t)nt_ * kTileF * sizeof(float), false))) {
             dfree_all(ctx, tmp);
             return st;
         }
         k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt_ * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256, 0,
-                     ctx->stream>>>(op->cal_D, op->ld, op->N, W.tiles, nt_, dvp); BEM_COUNT(ctx);
+                     ctx->stream>>>(op->cal_C, op->ld, op->N, W.tiles, nt_, dvp); BEM_COUNT(ctx);
     }
     if (f32op) {
         k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt_ * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256, 0,
@@ -1673,12 +1614,6 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.precond = precond;
     a.has_x0 = has_x0 ? 1 : 0;
     a.dvp = dvp;
-    a.mtris = op->cal_tris;
-    a.mv2t_off = op->cal_v2t_off;
-    a.mv2t = op->cal_v2t;
-    a.marea = op->cal_area;
-    a.mdinv = op->cal_mdinv;
-    a.cw = cw;
     void *args[] = {&a};
     const int prof = prof_start(ctx, BEM_KERNEL_MATVEC, 0.0);
     cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(kSymThreads), args, kSymSmem,
@@ -1710,7 +1645,7 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
             // (8 bytes x N^2 / 2); a mixed-mode iteration reads the packed FP32 upper
             // triangle (4 x N^2 / 2), written once by the first product
             const double n2 = (double)op->N * (double)op->N;
-            // (+ the packed FP32 D^reg once per preconditioner application)
+            // (+ the packed FP32 C once per preconditioner application)
             const double bytes = (f32op ? 2.0 * n2 * (h[2] + h[3])
                                   : vp  ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
                                         : 4.0 * n2 * (h[2] + h[3])) +
@@ -1758,7 +1693,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
     if (o->precond < BEM_PRECOND_NONE || o->precond > BEM_PRECOND_CALDERON)
         return set_error(ctx, BEM_ERR_INVALID, "unknown preconditioner %d", o->precond);
     if (o->precond == BEM_PRECOND_CALDERON &&
-        (!op->cal_D || op->precision == BEM_PREC_F64 || !ctx->persistent_solver))
+        (!op->cal_C || op->precision == BEM_PREC_F64 || !ctx->persistent_solver))
         return set_error(ctx, BEM_ERR_INVALID,
                          "BEM_PRECOND_CALDERON needs a DF64 dual operator (bem_operator_dual) and the persistent solver");
     if (o->inexact_lambda > 0.0 && m->cells_only)

@@ -208,9 +208,17 @@ def test_hypersingular_preconditioner_matches_oracle(ctx, m):
     mesh, v, t = _upload(ctx, m)
     bop = bem.Operator.assemble(mesh.barycentric(), precision=bem.PREC_F64)
     dop = bem.Operator.dual(bop, mesh)
-    Dg = dop.preconditioner().astype(np.float64)
+    Dg = dop.preconditioner(0).astype(np.float64)
     _, ref = D.hypersingular(v, t, bop.read())
     assert np.all(np.abs(Dg - ref) <= 1.2e-7 * np.abs(ref) + 1e-11 * np.max(np.abs(ref)))
+    # C = S D^reg S with the degree-6 Chebyshev S (FP32 throughout: 1e-5 of the largest entry)
+    S = D.chebyshev_inverse(D.mass_dual(v, t), 6)
+    C_ref = S @ ref @ S
+    Cg = dop.preconditioner(1).astype(np.float64)
+    assert np.max(np.abs(Cg - C_ref)) <= 1e-5 * np.max(np.abs(C_ref))
+    assert np.array_equal(Cg, Cg.T)
+    Minv = np.linalg.inv(D.mass_dual(v, t))
+    assert np.max(np.abs(C_ref - Minv @ ref @ Minv)) <= 1e-3 * np.max(np.abs(C_ref))
 
 
 @pytest.mark.parametrize("m", SMALL + [inputs.workload_polycube_adaptive()], ids=lambda m: m.name)
@@ -218,8 +226,9 @@ def test_calderon_solve_matches_oracle(ctx, m):
     """PCG with C = S D^reg S reaches the Galerkin solution of V^dual x = f (the paper's
     GMRES system has the same solution); its iterations are those of CG with the exact
     C = M^-1 D^reg M^-T (within 2 + 10%: S is the degree-6 Chebyshev approximation of
-    M^-1, and the products use the FP32 hi parts with DF64 residual replacements, each of
-    which restarts the recurrence's superlinear phase); the Lanczos extremes from the CG coefficients bracket like Ritz
+    M^-1 and C is stored in FP32, and the products use the FP32 hi parts with DF64
+    residual replacements, each of which restarts the recurrence's superlinear phase);
+    the Lanczos extremes from the CG coefficients bracket like Ritz
     values: lambda_max within 2% of that of the exact C V^dual, lambda_min above its
     smallest eigenvalue (S moves the spectrum by ~4e-4) and within 1.5x of it."""
     mesh, v, t = _upload(ctx, m)
@@ -287,6 +296,9 @@ def test_calderon_errors_are_reported(ctx):
     assert e.value.code == bem.BEM_ERR_INVALID
     with pytest.raises(bem.BemError) as e:
         bem.Operator.assemble(mesh).preconditioner()
+    assert e.value.code == bem.BEM_ERR_INVALID
+    with pytest.raises(bem.BemError) as e:
+        dop64.preconditioner(2)
     assert e.value.code == bem.BEM_ERR_INVALID
     with pytest.raises(bem.BemError) as e:
         bem.adaptive_run(mesh, max_N=100, precond=bem.PRECOND_CALDERON)

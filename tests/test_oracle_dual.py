@@ -215,3 +215,21 @@ def test_operator_preconditioned_adaptive_iterations():
     assert its[0] == 4 and max(its) <= 13, its
     caps = [h["cap"] for h in hist]
     assert all(b > a for a, b in zip(caps, caps[1:]))
+
+
+def test_chebyshev_inverse_of_the_mass_matrix():
+    """S_K is the degree-K Chebyshev polynomial in D^-1 M times D^-1: symmetric, and the
+    eigenvalues of S_K M lie within 2 q^K of 1, q = (sqrt(k) - 1)/(sqrt(k) + 1) for the
+    interval's k = 36/15 -- the bound that fixes K = 6 at 2e-4."""
+    v, t = _mesh(inputs.workload_polycube_adaptive())
+    Mm = D.mass_dual(v, t)
+    d = np.diag(Mm)
+    ev = np.linalg.eigvalsh(Mm / np.sqrt(np.outer(d, d)))
+    assert ev[0] >= 15 / 22 - 1e-12 and ev[-1] <= 36 / 22 + 1e-12
+    q = (np.sqrt(2.4) - 1) / (np.sqrt(2.4) + 1)
+    for K in (2, 4, 6):
+        S = D.chebyshev_inverse(Mm, K)
+        assert np.allclose(S, S.T, rtol=0, atol=1e-14 * np.max(np.abs(S)))
+        e = np.linalg.eigvals(S @ Mm).real
+        assert np.max(np.abs(e - 1)) <= 2 * q ** K * (1 + 1e-9), (K, np.max(np.abs(e - 1)))
+    assert 2 * q ** 6 < 2.2e-4
