@@ -252,8 +252,9 @@ def rates_workload(args):
 def dual_workload(args):
     """The paper's own discretisation (Sec. 2.1-2.6): piecewise constants on the dual
     mesh.  One step = one adaptive run on the unit cube (12 triangles) in the dual
-    basis: per level the barycentric refinement, its operator (DF64), V^dual = P^T V^bary P,
-    block-Jacobi PCG to 1e-10, the ZZ estimate of Eq. 1.6 on the dual density, Doerfler
+    basis: per level the barycentric refinement, its operator (DF64; the children of
+    unrefined triangles keep their entries), V^dual = P^T V^bary P, PCG to 1e-10 with the
+    operator preconditioner of Sec. 2.6 (--precond), the ZZ estimate of Eq. 1.6 on the dual density, Doerfler
     (theta = 0.5) and NVB of the primal mesh, until N >= --max-n (default 5,000 here:
     the barycentric operator at that level has 30,000^2 entries).  Untimed beside it:
     the Fichera cube in the dual basis and both geometries in the P0 basis to the same N,
@@ -278,7 +279,7 @@ def dual_workload(args):
         if basis == bem.BASIS_P0 and pc == "calderon":
             pc = "block"
         return bem.adaptive_run(msh, theta=THETA, max_N=n, max_levels=200, tol=TOL, precision=bem.PREC_DF64,
-                                precond=pcs[pc], basis=basis)[0]
+                                precond=pcs[pc], basis=basis, tile=args.far_tile)[0]
 
     for _ in range(max(args.warmup, 0)):
         flush.fill_(1)
@@ -649,8 +650,8 @@ def main():
                     help="adaptive workload: stop each solve by the rule of the Remark after Alg. 1 (i), "
                          "|||x_k - x_(k-1)||| <= LAMBDA eta(x_k) (the paper uses ~1e-3); 0: PCG to 1e-10")
     ap.add_argument("--far-tile", type=int, default=0,
-                    help="adaptive workload: far-field tile variant 1..12 instead of the autotuned one "
-                         "(no timing launches: for profiling captures)")
+                    help="adaptive and dual workloads: far-field tile variant 1..12 instead of the autotuned "
+                         "one (no timing launches: for profiling captures)")
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
