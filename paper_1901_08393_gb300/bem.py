@@ -521,11 +521,11 @@ class Server:
 
     def __init__(self, slots=4, hbm_budget_bytes=64 << 30, theta=0.5, precision=PREC_F32, tol=1e-10,
                  max_it=20000, h_mode=0, ss_order=4, incremental=True, max_outer=20, inner_tol=1e-5,
-                 reliable_delta=0.0, precond=PRECOND_JACOBI):
+                 reliable_delta=0.0, precond=PRECOND_JACOBI, basis=BASIS_P0):
         self.L = lib()
         o = AdaptiveOpts(theta, 0, 1, h_mode, AssemblyOpts(precision, ss_order),
                          SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta),
-                         int(incremental))
+                         int(incremental), int(basis))
         h = C.c_void_p()
         st = self.L.bem_server_create(slots, int(hbm_budget_bytes), C.byref(o), C.byref(h))
         if st != BEM_OK:

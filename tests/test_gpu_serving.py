@@ -77,3 +77,19 @@ def test_admission_budget_and_bad_request(cuda):
     # served one after another, in arrival order of the fitting requests
     starts = sorted((r["t_start"], r["t_done"]) for r in res)
     assert all(b[0] >= a[1] - 1e-6 for a, b in zip(starts, starts[1:]))
+
+
+def test_dual_basis_requests(cuda):
+    """The paper's dual basis with its operator preconditioner through the server: each
+    request's Cap history is the same alone, in the mix and through bem_adaptive_run."""
+    reqs = [(inputs.cube_mesh(1), 8, 600), (inputs.fichera_mesh(1), 6, 600), (inputs.tetra_mesh(3), 6, 500)]
+    kw = dict(precision=bem.PREC_DF64, precond=bem.PRECOND_CALDERON, basis=bem.BASIS_DUAL)
+    srv = bem.Server(slots=3, hbm_budget_bytes=16 << 30, **kw)
+    ids = [srv.submit(m.verts, m.tris, lv, mx) for m, lv, mx in reqs]
+    mixed = [srv.wait(i) for i in ids]
+    srv.close()
+    ctx = bem.Context()
+    for (m, lv, mx), r in zip(reqs, mixed):
+        assert r["status"] == 0, r["message"]
+        recs, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), max_N=mx, max_levels=lv, tol=1e-10, **kw)
+        assert [x["cap"] for x in recs] == r["caps"] and [x["N"] for x in recs] == r["Ns"]
