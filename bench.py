@@ -804,7 +804,8 @@ def main():
                    "far_tiles_autotuned": dict(zip(("N<1024", "N<4096", "N<16384", "larger"),
                                                    [["32x256", "16x256", "64x256", "8x128", "16x128", "32x128",
                                                      "8x128 shared m8", "16x128 shared m8", "32x128 shared m8",
-                                                     "8x128 shared m9", "8x64 shared m16", "8x64 shared m18"][v - 1]
+                                                     "8x128 shared m9", "8x64 shared m16", "8x64 shared m18",
+                                                     "8x128 shared m6 unrolled", "32x128 shared m6 unrolled"][v - 1]
                                                     if v else None
                                                     for v in ctx.far_tiles()[PREC]])),
                    "l2": "256 MB buffer written before every step; V (up to 3.2 GB) exceeds L2"},

@@ -73,9 +73,10 @@ typedef struct {
                           rows x columns per CTA 32x256, 16x256, 64x256, 8x128, 16x128, 32x128,
                           and (DF64: column points in shared memory instead of registers, at
                           least m CTAs per SM) 8x128 m8, 16x128 m8, 32x128 m8, 8x128 m9,
-                          8x64 m16, 8x64 m18 */
+                          8x64 m16, 8x64 m18, and with the point loop unrolled 8x128 m6,
+                          32x128 m6 */
 } bem_assembly_opts;
-#define BEM_FAR_TILE_VARIANTS 12
+#define BEM_FAR_TILE_VARIANTS 14
 
 #define BEM_PRECOND_NONE 0
 #define BEM_PRECOND_JACOBI 1

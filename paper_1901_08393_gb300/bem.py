@@ -29,7 +29,7 @@ PRECOND_NONE = 0
 PRECOND_JACOBI = 1
 PRECOND_BLOCK = 2
 PRECOND_CALDERON = 3
-FAR_TILE_VARIANTS = 12
+FAR_TILE_VARIANTS = 14
 REFINE_BISEC3 = 1
 BASIS_P0 = 0
 BASIS_DUAL = 1

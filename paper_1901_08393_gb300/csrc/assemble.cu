@@ -127,8 +127,8 @@ struct FarTileS {
                    // requested (the other arithmetics use their register form)
 };
 constexpr FarTileS kFarTiles[kFarTileVariants] = {
-    {32, 256, 0}, {16, 256, 0}, {64, 256, 0}, {8, 128, 0}, {16, 128, 0}, {32, 128, 0},
-    {8, 128, 8},  {16, 128, 8}, {32, 128, 8}, {8, 128, 9}, {8, 64, 16},  {8, 64, 18}};
+    {32, 256, 0}, {16, 256, 0}, {64, 256, 0}, {8, 128, 0}, {16, 128, 0}, {32, 128, 0}, {8, 128, 8},
+    {16, 128, 8}, {32, 128, 8}, {8, 128, 9},  {8, 64, 16},  {8, 64, 18},  {8, 128, 6}, {32, 128, 6}};
 
 template <int R, int C>
 __global__ void __launch_bounds__(C) k_far_f64(const double *__restrict__ q64, double *__restrict__ V,
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
 // thread-major (conflict-free), instead of 42 registers, the point loops not unrolled,
 // and MB CTAs per SM requested (registers capped to fit) -- more resident warps for
 // the same work.  MB = 0: offsets in registers, loops unrolled.
-template <int R, int C, int MB>
+template <int R, int C, int MB, bool UB = false>
 __device__ __forceinline__ void far_df_body(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
                                             int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
@@ -314,7 +314,7 @@ __device__ __forceinline__ void far_df_body(const float *__restrict__ qdf, float
                 fast_two_sum(s, e, eh[c], el[c]);
             }
             float sh = 0.0f, sl = 0.0f;
-#pragma unroll(S ? 1 : kQ)
+#pragma unroll((S && !UB) ? 1 : kQ)
             for (int b = 0; b < kQ; ++b) {
                 // d = e_a - o_b; |d|^2 = sum h^2 + 2 h l (two-product, two-sum)
                 float Sh = 0.0f, Sl = 0.0f;
@@ -377,11 +377,12 @@ __global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, flo
     far_df_body<R, C, 0>(qdf, V, ld, r0, r1, c0, c1);
 }
 
-template <int R, int C, int MB>
+// UB: the inner point loop unrolled (more registers: fewer CTAs per SM requested)
+template <int R, int C, int MB, bool UB = false>
 __global__ void __launch_bounds__(C, MB) k_far_df_s(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
                                                     int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
-    far_df_body<R, C, MB>(qdf, V, ld, r0, r1, c0, c1);
+    far_df_body<R, C, MB, UB>(qdf, V, ld, r0, r1, c0, c1);
 }
 
 // Mirror the strict lower triangle of rows [r0, r1): V[i][j] = V[j][i], j < i,
@@ -589,7 +590,7 @@ __global__ void k_diag(const T *V, int64_t ld, int64_t N, double *d)
 }
 
 // ------------------------------------------------------------------ drivers
-template <typename T, int R, int C, int MB = 0>
+template <typename T, int R, int C, int MB = 0, bool UB = false>
 static void far_kernel(bem_operator *op, dim3 grid, int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
     bem_mesh *m = op->mesh;
@@ -599,7 +600,7 @@ static void far_kernel(bem_operator *op, dim3 grid, int64_t r0, int64_t r1, int6
     else if (op->precision == BEM_PREC_DF64)
     {
         if constexpr (MB > 0)
-            k_far_df_s<R, C, MB><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
+            k_far_df_s<R, C, MB, UB><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
         else
             k_far_df<R, C><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
     }
@@ -646,7 +647,9 @@ static bem_status launch_far(bem_operator *op, int v, int64_t r0, int64_t r1, in
     case 8: far_kernel<T, 32, 128, 8>(op, grid, r0, r1, c0, c1); break;
     case 9: far_kernel<T, 8, 128, 9>(op, grid, r0, r1, c0, c1); break;
     case 10: far_kernel<T, 8, 64, 16>(op, grid, r0, r1, c0, c1); break;
-    default: far_kernel<T, 8, 64, 18>(op, grid, r0, r1, c0, c1); break;
+    case 11: far_kernel<T, 8, 64, 18>(op, grid, r0, r1, c0, c1); break;
+    case 12: far_kernel<T, 8, 128, 6, true>(op, grid, r0, r1, c0, c1); break;
+    default: far_kernel<T, 32, 128, 6, true>(op, grid, r0, r1, c0, c1); break;
     }
     BEM_COUNT(ctx);
     if (profile) prof_stop(ctx, prof);
