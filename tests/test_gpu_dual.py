@@ -303,3 +303,16 @@ def test_calderon_errors_are_reported(ctx):
     with pytest.raises(bem.BemError) as e:
         bem.adaptive_run(mesh, max_N=100, precond=bem.PRECOND_CALDERON)
     assert e.value.code == bem.BEM_ERR_INVALID
+
+
+def test_dual_loop_with_fp32_barycentric_operator(ctx):
+    """An FP32 barycentric operator (V^dual then holds FP64 sums of FP32 entries, ~1e-7
+    relative): the same meshes as the DF64 loop on the polycube, whose indicators are
+    well separated at the Doerfler cut, and Cap within 1e-6."""
+    m = inputs.workload_polycube_adaptive()
+    kw = dict(max_N=1500, tol=1e-10, basis=bem.BASIS_DUAL, precond=bem.PRECOND_CALDERON)
+    r32, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), precision=bem.PREC_F32, **kw)
+    r64, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), precision=bem.PREC_DF64, **kw)
+    assert [r["N"] for r in r32] == [r["N"] for r in r64]
+    for a, b in zip(r32, r64):
+        assert abs(a["cap"] / b["cap"] - 1) < 1e-6, (a["cap"], b["cap"])
