@@ -32,8 +32,8 @@ def _upload(ctx, m):
     return mesh, v, t
 
 
-SMALL = [inputs.cube_mesh(1), inputs.cube_mesh(2), inputs.tetra_mesh(2), inputs.fichera_mesh(1),
-         inputs.icosphere_mesh(1)]
+SMALL = [inputs.tetra_mesh(1), inputs.cube_mesh(1), inputs.cube_mesh(2), inputs.tetra_mesh(2),
+         inputs.fichera_mesh(1), inputs.icosphere_mesh(1)]
 MESHES = SMALL + [inputs.cube_mesh(4), inputs.workload_polycube_adaptive(), inputs.fichera_mesh(2)]
 
 
@@ -316,3 +316,20 @@ def test_dual_loop_with_fp32_barycentric_operator(ctx):
     assert [r["N"] for r in r32] == [r["N"] for r in r64]
     for a, b in zip(r32, r64):
         assert abs(a["cap"] / b["cap"] - 1) < 1e-6, (a["cap"], b["cap"])
+
+
+def test_dual_loop_on_the_smallest_mesh(ctx):
+    """The regular tetrahedron (4 triangles, 4 unknowns, one padded 64 x 64 tile): its
+    indicators are tiny (~1e-10: the quadrature's orientation breaks the symmetry at
+    1e-5 in x) yet well above the vanishing-estimator threshold; the first two levels,
+    marks included, equal the oracle's with both preconditioners."""
+    m = inputs.tetra_mesh(1)
+    hist = D.adaptive_run_dual(m.verts, m.tris, max_N=60, max_levels=2, tol=1e-12)
+    for pc in (bem.PRECOND_JACOBI, bem.PRECOND_CALDERON):
+        recs, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), max_N=60, max_levels=2, tol=1e-12,
+                                   precision=bem.PREC_DF64, basis=bem.BASIS_DUAL, precond=pc)
+        assert len(recs) == len(hist) == 2
+        assert recs[0]["n_marked"] == int(hist[0]["marked"].sum())
+        for r, h in zip(recs, hist):
+            assert r["N"] == h["N"] and r["M"] == h["M"]
+            assert abs(r["cap"] / h["cap"] - 1) < 1e-9
