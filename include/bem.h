@@ -289,9 +289,10 @@ typedef struct {
 #define BEM_BASIS_P0 0
 #define BEM_BASIS_DUAL 1
 
-/* Alg. 1 on the primal P0 space: solve -> estimate -> mark -> refine, starting
- * from the uploaded mesh, until N >= max_N or max_levels.  The previous level's
- * solution copied to the children starts each solve.  When every indicator
+/* Alg. 1: solve -> estimate -> mark -> refine, starting from the uploaded mesh, until
+ * N >= max_N or max_levels, in the basis opts->basis (P0 on the triangles, or the
+ * dual basis of Sec. 2.6, see BEM_BASIS_DUAL).  P0: the previous level's solution
+ * copied to the children starts each solve.  When every indicator
  * vanishes up to rounding (sum eta^2 <= 1e-20 sum h|T|phi^2/12, a symmetric mesh
  * with a constant solution) Eq. 2.6 holds for the empty set and the level is
  * refined uniformly instead.  records: caller array of max_levels entries;
