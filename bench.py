@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -66,7 +67,7 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -427,7 +428,7 @@ def condition_workload(args):
 
 
 def batch_workload(args):
-    """Batching (BASELINE config 4) through bem_batch_*: inputs.batch_meshes (seed 4:
+    """Batching form through bem_batch_*: inputs.batch_meshes (seed 4:
     polycubes g in 3..10, p in [0.3, 0.7], uniform meshes, log-uniform 500..30,000
     triangles), FP32 V, PCG to 1e-10 with FP64-accurate residuals.  One step = one
     bem_batch_run: every V assembled, all systems solved by ONE cooperative launch of
@@ -517,7 +518,7 @@ def batch_workload(args):
 
 
 def server_workload(args):
-    """Serving (BASELINE config 5) and batching (config 4) through bem_server_*.
+    """Serving form (and the batching form's meshes) through bem_server_*.
 
     serve: requests of inputs.serving_requests (seed 5, Poisson 50 req/s: polycubes,
     rotated/scaled cubes, tetrahedra, 100..2000 triangles, 3..6 adaptive levels capped

@@ -220,7 +220,7 @@ extern "C" {
 // One stream-ordered memory pool per device for all contexts of the library.  Its
 // release threshold keeps freed blocks reserved, so that the operators of successive
 // adaptive levels (up to several GB each) reuse mapped memory instead of returning
-// it to the driver at every synchronisation; the pool is trimmed when the last
+// it to the CUDA driver at every synchronisation; the pool is trimmed when the last
 // context of the device is destroyed.
 namespace {
 std::mutex g_pool_mu;
