@@ -35,3 +35,27 @@ def test_library_exports_every_symbol():
 def test_no_torch_types_in_header():
     src = open(os.path.join(ROOT, "include", "bem.h")).read()
     assert "torch" not in src.lower().replace("pytorch", "") and "at::" not in src
+
+
+def _prototypes():
+    """{name: parameter count} of every entry point declared in include/bem.h."""
+    src = open(os.path.join(ROOT, "include", "bem.h")).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"(?:bem_status|const char \*)\s*(bem_\w+)\s*\(([^)]*)\)\s*;", src):
+        params = [p for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+        out[m.group(1)] = len(params)
+    return out
+
+
+def test_binding_argument_counts_match_the_header():
+    """The ctypes signature of every entry point has as many arguments as its C
+    prototype (a changed signature cannot go unnoticed by the binding)."""
+    from paper_1901_08393_gb300 import build
+
+    build.build()
+    L = bem.lib()
+    protos = _prototypes()
+    assert set(protos) == set(_declared())
+    for name, n in protos.items():
+        assert len(getattr(L, name).argtypes) == n, (name, n, len(getattr(L, name).argtypes))
