@@ -126,6 +126,30 @@ def run_oracle(max_n=MAX_N):
     return time.perf_counter() - t, hist
 
 
+def oracle_baseline(max_n=MAX_N, max_n_1t=3000):
+    """cpu_baseline of the default workload: the FP64 oracle's complete adaptive run on
+    all host cores, and a bounded sample (the same loop to N >= max_n_1t) timed at one
+    thread and at all cores."""
+    import oracle
+
+    oracle.build()
+    dt, hist = run_oracle(max_n)
+    cores = oracle.num_threads()
+    t_all, h_small = run_oracle(max_n_1t)
+    oracle.set_num_threads(1)
+    try:
+        t_one, _ = run_oracle(max_n_1t)
+    finally:
+        oracle.set_num_threads(0)
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one complete adaptive run of the workload ({len(hist)} levels, final N={hist[-1]['N']}), "
+                      "FP64 C/OpenMP oracle",
+            "cap_final": hist[-1]["cap"],
+            "threads": {"sample": f"the same loop to N >= {max_n_1t} ({len(h_small)} levels)",
+                        "one_thread_runs_per_s": 1.0 / t_one, "all_cores_runs_per_s": 1.0 / t_all,
+                        "speedup": t_one / t_all}}
+
+
 def reference_arm(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -835,14 +859,7 @@ def main():
         args.no_cpu_baseline = True
         line["cpu_baseline"] = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        import oracle
-
-        oracle.build()
-        dt, hist = run_oracle()
-        line["cpu_baseline"] = {"value": 1.0 / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                                "sample": f"one complete adaptive run of the workload ({len(hist)} levels, "
-                                          f"final N={hist[-1]['N']}), FP64 C/OpenMP oracle",
-                                "cap_final": hist[-1]["cap"]}
+        line["cpu_baseline"] = oracle_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

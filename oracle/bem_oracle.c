@@ -733,3 +733,14 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* Threads of the following parallel regions (n <= 0: all processors).  Timing only:
+ * every reduction of the oracle is sequential, so results do not depend on it. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
+#else
+    (void)n;
+#endif
+}

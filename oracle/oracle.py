@@ -25,7 +25,7 @@ __all__ = [
     "build", "lib", "gauss_legendre01", "radon7", "geometry", "pair_far", "pair_identical",
     "pair_edge", "pair_vertex", "pair_type", "entry", "entries", "assemble", "pcg",
     "solve_cholesky", "capacity", "zz", "dorfler", "canonical", "refine", "num_threads",
-    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "cluster_order", "block_jacobi_inverses", "block_jacobi_pcg", "cg_lanczos_extremes", "pcg_inexact",
+    "solve_capacity", "adaptive_run", "mark", "VANISHING_ETA", "set_num_threads", "cluster_order", "block_jacobi_inverses", "block_jacobi_pcg", "cg_lanczos_extremes", "pcg_inexact",
     "preconditioned_extremes",
 ]
 
@@ -75,6 +75,8 @@ def lib():
             L.orc_canonical.argtypes = [vp, vp, i64, vp, vp]
             L.orc_refine.argtypes = [vp, i64, vp, i64, vp, i32, vp, vp, vp, vp, vp, vp]
             L.orc_num_threads.restype = i32
+            L.orc_set_num_threads.argtypes = [i32]
+            L.orc_set_num_threads.restype = None
             _lib = L
     return _lib
 
@@ -93,6 +95,11 @@ def _i32(a):
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (n <= 0: all processors); timing only."""
+    lib().orc_set_num_threads(int(n))
 
 
 def gauss_legendre01(n: int):

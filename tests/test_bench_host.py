@@ -67,3 +67,27 @@ def test_clock_samples_and_throttle_reasons(bench, tmp_path):
     out = c.stop()
     assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
     assert out["reasons"] == ["sw_power_cap"] and out["power_w_max"] == 1390.0
+
+
+def test_oracle_baseline_threads(bench):
+    """The cpu_baseline leg on a tiny case: all cores and one thread run the same oracle
+    (the oracle's reductions are sequential, so the Cap does not depend on threads)."""
+    import oracle
+
+    b = bench.oracle_baseline(max_n=700, max_n_1t=700)
+    assert b["kind"] == "oracle" and b["cores"] >= 1 and b["value"] > 0
+    assert b["threads"]["one_thread_runs_per_s"] > 0 and b["threads"]["all_cores_runs_per_s"] > 0
+    assert oracle.num_threads() == b["cores"]  # restored
+    oracle.set_num_threads(1)
+    try:
+        h1 = oracle.adaptive_run(*[getattr(bench_inputs(), k) for k in ("verts", "tris")], max_N=700)
+    finally:
+        oracle.set_num_threads(0)
+    hn = oracle.adaptive_run(*[getattr(bench_inputs(), k) for k in ("verts", "tris")], max_N=700)
+    assert [h["cap"] for h in h1] == [h["cap"] for h in hn]
+
+
+def bench_inputs():
+    from paper_1901_08393_gb300 import inputs
+
+    return inputs.workload_polycube_adaptive()
