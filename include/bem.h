@@ -208,7 +208,9 @@ bem_status bem_operator_matvec(const bem_operator *op, const double *x, double *
  * (cudaGetSymbolAddress), so make that first call before any stream capture.
  * Enqueued on the context's stream without synchronising.  All calls share the
  * one array: calls that overlap on the GPU race.  Larger N, other precisions,
- * host pointers or another current device: BEM_ERR_INVALID with a message. */
+ * host pointers, device memory of another GPU or another current device:
+ * BEM_ERR_INVALID with a message.  The looked-up address is kept for the life of
+ * the process; it does not survive a cudaDeviceReset. */
 bem_status bem_operator_matvec_noalloc(const bem_operator *op, const double *x, double *y);
 
 /* ---------------------------------------------------------------- solve */
@@ -434,6 +436,16 @@ bem_status bem_profile_read(bem_ctx *ctx, int32_t kernel, int64_t *launches, dou
  * as a host-driven loop of kernels (on = 0; also used when a cooperative launch is
  * not possible).  Both give the same iterates up to the order of the reductions. */
 bem_status bem_context_set_persistent(bem_ctx *ctx, int32_t on);
+/* Failure detection of the persistent solvers (the paper has no counterpart: it runs
+ * on one workstation thread).  Their CTAs meet at grid barriers whose wait is bounded
+ * in time; a CTA that waits longer than the limit raises an error flag and returns,
+ * the others give up once they see the flag, and the solve reports BEM_ERR_CUDA
+ * ("grid barrier timed out") with the context still usable.  wait_limit_ns (> 0)
+ * sets that limit for later solves of ctx (<= 0: the default, 2 s); absent_cta >= 0
+ * makes that CTA of later single-problem persistent solves leave at its first
+ * barrier without arriving, as a CTA that stopped would, so that the others' waits
+ * run out (a test of the time-out path that faults nothing); -1 turns it off. */
+bem_status bem_debug_barrier_fault(bem_ctx *ctx, int64_t wait_limit_ns, int32_t absent_cta);
 /* Number of CUDA kernels the context has launched so far. */
 bem_status bem_launch_count(const bem_ctx *ctx, int64_t *n);
 

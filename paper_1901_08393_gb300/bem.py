@@ -44,7 +44,7 @@ EXPORTS = [
     "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
     "bem_batch_create", "bem_batch_run", "bem_batch_info", "bem_batch_destroy",
     "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual", "bem_operator_preconditioner",
-    "bem_far_tiles",
+    "bem_far_tiles", "bem_debug_barrier_fault",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -161,6 +161,7 @@ def lib():
         "bem_zz_estimate_dual": [vp, vp, i32, vp, vp],
         "bem_operator_preconditioner": [vp, i32, vp],
         "bem_far_tiles": [vp, vp],
+        "bem_debug_barrier_fault": [vp, i64, i32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -238,6 +239,11 @@ class Context:
         out = (C.c_int32 * 12)()
         self.check(self.L.bem_far_tiles(self.h, out))
         return [list(out[4 * p:4 * p + 4]) for p in range(3)]
+
+    def barrier_fault(self, wait_limit_ns: int = 0, absent_cta: int = -1):
+        """Failure-detection hook of the persistent solvers: grid-barrier wait limit
+        (0: default 2 s) and a CTA that leaves at its first barrier (-1: none)."""
+        self.check(self.L.bem_debug_barrier_fault(self.h, int(wait_limit_ns), int(absent_cta)))
 
     def launch_count(self) -> int:
         n = C.c_int64()

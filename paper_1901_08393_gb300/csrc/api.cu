@@ -64,14 +64,16 @@ void dfree_all(bem_ctx *ctx, Allocs &a)
     a.bytes = 0;
 }
 
-bool is_device_ptr(const void *p)
+bool is_device_ptr(const void *p, int *device)
 {
+    if (device) *device = -1;
     if (!p) return false;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
+    if (device && at.type == cudaMemoryTypeDevice) *device = at.device;
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
@@ -314,6 +316,15 @@ bem_status bem_context_set_persistent(bem_ctx *ctx, int32_t on)
 {
     if (!ctx) return BEM_ERR_INVALID;
     ctx->persistent_solver = on ? 1 : 0;
+    return BEM_OK;
+}
+
+bem_status bem_debug_barrier_fault(bem_ctx *ctx, int64_t wait_limit_ns, int32_t absent_cta)
+{
+    if (!ctx) return BEM_ERR_INVALID;
+    CHECK_ARG(ctx, absent_cta >= -1, "absent_cta must be -1 or a CTA index");
+    ctx->bar_limit_ns = wait_limit_ns > 0 ? wait_limit_ns : 0;
+    ctx->bar_absent_cta = absent_cta;
     return BEM_OK;
 }
 

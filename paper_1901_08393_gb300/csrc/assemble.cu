@@ -27,6 +27,7 @@
 //    variables use n Gauss-Legendre points each: identical 6 hexagon sectors x n,
 //    common edge 4 sub-regions x n^2, common vertex 2 regions x n^3.  FP64.
 #include <cmath>
+#include <type_traits>
 
 #include "bem_internal.cuh"
 #include "dfloat.cuh"
@@ -130,14 +131,14 @@ constexpr FarTileS kFarTiles[kFarTileVariants] = {
     {32, 256, 0}, {16, 256, 0}, {64, 256, 0}, {8, 128, 0}, {16, 128, 0}, {32, 128, 0}, {8, 128, 8},
     {16, 128, 8}, {32, 128, 8}, {8, 128, 9},  {8, 64, 16},  {8, 64, 18},  {8, 128, 6}, {32, 128, 6}};
 
+// The far-field bodies take the tile origin (first row i0, first column cbase) as
+// arguments: the per-operator kernels derive it from the block index, the batched
+// kernel (several operators in one launch) from its work list.
 template <int R, int C>
-__global__ void __launch_bounds__(C) k_far_f64(const double *__restrict__ q64, double *__restrict__ V,
-                                                      int64_t ld, int64_t r0, int64_t r1, int64_t c0,
-                                                      int64_t c1)
+__device__ __forceinline__ void far_f64_body(const double *__restrict__ q64, double *__restrict__ V, int64_t ld,
+                                             int64_t r1, int64_t c1, int64_t i0, int64_t cbase)
 {
     __shared__ double sx[R][22];
-    const int64_t cbase = c0 + (int64_t)blockIdx.x * C;
-    const int64_t i0 = r0 + (int64_t)blockIdx.y * R;
     if (i0 > cbase + C - 1 || i0 >= r1) return;  // tile strictly below the diagonal
     for (int k = threadIdx.x; k < R * 22; k += C) {
         const int r = k / 22, c = k % 22;
@@ -172,18 +173,23 @@ __global__ void __launch_bounds__(C) k_far_f64(const double *__restrict__ q64, d
 }
 
 template <int R, int C>
-__global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
-                                                      const double *__restrict__ cent, float *__restrict__ V,
+__global__ void __launch_bounds__(C) k_far_f64(const double *__restrict__ q64, double *__restrict__ V,
                                                       int64_t ld, int64_t r0, int64_t r1, int64_t c0,
                                                       int64_t c1)
+{
+    far_f64_body<R, C>(q64, V, ld, r1, c1, r0 + (int64_t)blockIdx.y * R, c0 + (int64_t)blockIdx.x * C);
+}
+
+template <int R, int C>
+__device__ __forceinline__ void far_f32_body(const float *__restrict__ q32, const double *__restrict__ cent,
+                                             float *__restrict__ V, int64_t ld, int64_t r1, int64_t c1,
+                                             int64_t i0, int64_t cbase)
 {
     // FP32 only in the pair loop: centroids as hi + lo floats, so that the centroid
     // difference (hi_i - hi_j) + (lo_i - lo_j) keeps FP32 relative accuracy for
     // distant pairs; weights and areas rounded to FP32 once
     __shared__ float so[R][3 * kQ];
     __shared__ float sc[R][7];  // centroid hi (3), lo (3), area
-    const int64_t cbase = c0 + (int64_t)blockIdx.x * C;
-    const int64_t i0 = r0 + (int64_t)blockIdx.y * R;
     if (i0 > cbase + C - 1 || i0 >= r1) return;
     for (int k = threadIdx.x; k < R * 3 * kQ; k += C) {
         const int r = k / (3 * kQ), c = k % (3 * kQ);
@@ -242,6 +248,15 @@ __global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
     }
 }
 
+template <int R, int C>
+__global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
+                                                      const double *__restrict__ cent, float *__restrict__ V,
+                                                      int64_t ld, int64_t r0, int64_t r1, int64_t c0,
+                                                      int64_t c1)
+{
+    far_f32_body<R, C>(q32, cent, V, ld, r1, c1, r0 + (int64_t)blockIdx.y * R, c0 + (int64_t)blockIdx.x * C);
+}
+
 // Double-float far field: see the file comment.
 // MB > 0: the column triangle's 21 offsets staged in shared memory as (hi, lo) pairs,
 // thread-major (conflict-free), instead of 42 registers, the point loops not unrolled,
@@ -249,13 +264,11 @@ __global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
 // the same work.  MB = 0: offsets in registers, loops unrolled.
 template <int R, int C, int MB, bool UB = false>
 __device__ __forceinline__ void far_df_body(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
-                                            int64_t r0, int64_t r1, int64_t c0, int64_t c1)
+                                            int64_t r1, int64_t c1, int64_t i0, int64_t cbase)
 {
     constexpr bool S = MB > 0;
     __shared__ float sq[R][53];
     __shared__ float2 scol[S ? 3 * kQ * C : 1];
-    const int64_t cbase = c0 + (int64_t)blockIdx.x * C;
-    const int64_t i0 = r0 + (int64_t)blockIdx.y * R;
     if (i0 > cbase + C - 1 || i0 >= r1) return;
     for (int k = threadIdx.x; k < R * 53; k += C) {
         const int r = k / 53, c = k % 53;
@@ -374,7 +387,7 @@ template <int R, int C>
 __global__ void __launch_bounds__(C) k_far_df(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
                                               int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
-    far_df_body<R, C, 0>(qdf, V, ld, r0, r1, c0, c1);
+    far_df_body<R, C, 0>(qdf, V, ld, r1, c1, r0 + (int64_t)blockIdx.y * R, c0 + (int64_t)blockIdx.x * C);
 }
 
 // UB: the inner point loop unrolled (more registers: fewer CTAs per SM requested)
@@ -382,17 +395,15 @@ template <int R, int C, int MB, bool UB = false>
 __global__ void __launch_bounds__(C, MB) k_far_df_s(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
                                                     int64_t r0, int64_t r1, int64_t c0, int64_t c1)
 {
-    far_df_body<R, C, MB, UB>(qdf, V, ld, r0, r1, c0, c1);
+    far_df_body<R, C, MB, UB>(qdf, V, ld, r1, c1, r0 + (int64_t)blockIdx.y * R, c0 + (int64_t)blockIdx.x * C);
 }
 
 // Mirror the strict lower triangle of rows [r0, r1): V[i][j] = V[j][i], j < i,
 // through 32 x 32 shared-memory tiles (coalesced on both sides).
 template <typename T>
-__global__ void k_mirror(T *V, int64_t ld, int64_t r0, int64_t r1)
+__device__ __forceinline__ void mirror_tile(T *V, int64_t ld, int64_t r0, int64_t r1, int64_t bi, int64_t bj)
 {
     __shared__ T tile[32][33];
-    const int64_t bi = (int64_t)blockIdx.y * 32 + (r0 / 32) * 32;  // destination row tile
-    const int64_t bj = (int64_t)blockIdx.x * 32;                   // destination column tile
     if (bj > bi) return;
     const int tx = threadIdx.x, ty = threadIdx.y;
     // load source block rows bj.., cols bi.. (upper part)
@@ -405,6 +416,13 @@ __global__ void k_mirror(T *V, int64_t ld, int64_t r0, int64_t r1)
         const int64_t i = bi + k, j = bj + tx;
         if (i >= r0 && i < r1 && j < i) V[i * ld + j] = tile[tx][k];
     }
+}
+
+template <typename T>
+__global__ void k_mirror(T *V, int64_t ld, int64_t r0, int64_t r1)
+{
+    // destination row tile, destination column tile
+    mirror_tile<T>(V, ld, r0, r1, (int64_t)blockIdx.y * 32 + (r0 / 32) * 32, (int64_t)blockIdx.x * 32);
 }
 
 // ------------------------------------------------------------------ near field
@@ -510,12 +528,10 @@ __device__ __forceinline__ void load_tri(const double *verts, const int32_t *v, 
 // kind 0: identical pairs i = j = K + idx; 1: common-vertex list; 2: common-edge list.
 // Pairs (i < j) with j < K are skipped (their entries are reused).
 template <typename T>
-__global__ void k_near(const double *__restrict__ verts, const int32_t *__restrict__ tris,
-                       const double *__restrict__ area, const int32_t *__restrict__ pairs, int64_t npairs,
-                       int kind, int64_t K, int n, T *V, int64_t ld)
+__device__ __forceinline__ void near_entry(const double *__restrict__ verts, const int32_t *__restrict__ tris,
+                                           const double *__restrict__ area, const int32_t *__restrict__ pairs,
+                                           int64_t idx, int kind, int64_t K, int n, T *V, int64_t ld)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= npairs) return;
     int64_t i, j;
     if (kind == 0) {
         i = j = K + idx;
@@ -568,6 +584,16 @@ __global__ void k_near(const double *__restrict__ verts, const int32_t *__restri
     const T e = Elem<T>::from_double(v);
     V[i * ld + j] = e;
     if (i != j) V[j * ld + i] = e;
+}
+
+template <typename T>
+__global__ void k_near(const double *__restrict__ verts, const int32_t *__restrict__ tris,
+                       const double *__restrict__ area, const int32_t *__restrict__ pairs, int64_t npairs,
+                       int kind, int64_t K, int n, T *V, int64_t ld)
+{
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npairs) return;
+    near_entry<T>(verts, tris, area, pairs, idx, kind, K, n, V, ld);
 }
 
 // ------------------------------------------------------------------ reuse and diagonal
@@ -700,6 +726,8 @@ static bem_status far_variant(bem_operator *op, int64_t K, int64_t N, int *v_out
     return BEM_OK;
 }
 
+int far_cached_variant(const bem_ctx *ctx, int precision, int64_t N) { return ctx->far_tile[precision][far_bucket(N)]; }
+
 bem_status far_tune(bem_operator *op)
 {
     int v = 0;
@@ -773,6 +801,143 @@ static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
     k_diag<T><<<nblk(N, 256), 256, 0, ctx->stream>>>((const T *)op->V, op->ld, N, op->diag); BEM_COUNT(ctx);
     BEM_CK_LAUNCH(ctx);
     return BEM_OK;
+}
+
+// ------------------------------------------------------------------ batched assembly
+// The assembly of every operator of a batch wave in one launch per phase: the far
+// field over a work list of (problem, row tile, column tile) items, the mirror over
+// the 32 x 32 tile pairs of all problems, the near field over the concatenated
+// identical / common-vertex / common-edge lists.  Every entry is computed by the same
+// device code as the per-operator kernels, so the operators are bit-identical to
+// bem_assemble_V's.
+
+// Problem p with prefix[p] <= k < prefix[p + 1] (prefix: P + 1 ascending entries).
+__device__ __forceinline__ int batch_find(const int64_t *__restrict__ prefix, int P, int64_t k)
+{
+    int lo = 0, hi = P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= k)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int R, int C, int MB, bool UB>
+__global__ void __launch_bounds__(C, (MB > 0 ? MB : 1))
+    k_far_batch(const BatchAsmProb *__restrict__ prob, const int4 *__restrict__ items)
+{
+    const int4 it = items[blockIdx.x];
+    const BatchAsmProb *pb = prob + it.x;
+    const int64_t N = pb->N, ld = pb->ld;
+    if constexpr (std::is_same<T, double>::value)
+        far_f64_body<R, C>(pb->q64, (double *)pb->V, ld, N, N, it.y, it.z);
+    else if constexpr (std::is_same<T, float2>::value)
+        far_df_body<R, C, MB, UB>(pb->qdf, (float2 *)pb->V, ld, N, N, it.y, it.z);
+    else
+        far_f32_body<R, C>(pb->q32, pb->cent, (float *)pb->V, ld, N, N, it.y, it.z);
+}
+
+// Tile pair t of a problem: row tile bi >= column tile bj, t = bi (bi + 1) / 2 + bj.
+template <typename T>
+__global__ void k_mirror_batch(const BatchAsmProb *__restrict__ prob, const int64_t *__restrict__ pref, int P)
+{
+    const int64_t k = blockIdx.x;
+    const int p = batch_find(pref, P, k);
+    const int64_t t = k - pref[p];
+    int64_t bi = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+    while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
+    while (bi * (bi + 1) / 2 > t) --bi;
+    const int64_t bj = t - bi * (bi + 1) / 2;
+    const BatchAsmProb *pb = prob + p;
+    mirror_tile<T>((T *)pb->V, pb->ld, 0, pb->N, 32 * bi, 32 * bj);
+}
+
+// Item k of a problem: identical pairs [0, N), common-vertex pairs, common-edge pairs.
+template <typename T>
+__global__ void k_near_batch(const BatchAsmProb *__restrict__ prob, const int64_t *__restrict__ pref, int P,
+                             int64_t total, int n)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= total) return;
+    const int p = batch_find(pref, P, k);
+    const BatchAsmProb *pb = prob + p;
+    int64_t idx = k - pref[p];
+    const int64_t N = pb->N;
+    if (idx < N) {
+        near_entry<T>(pb->verts, pb->tris, pb->area, nullptr, idx, 0, 0, n, (T *)pb->V, pb->ld);
+    } else if ((idx -= N) < pb->n_vert) {
+        near_entry<T>(pb->verts, pb->tris, pb->area, pb->vert_pairs, idx, 1, 0, n, (T *)pb->V, pb->ld);
+    } else {
+        idx -= pb->n_vert;
+        near_entry<T>(pb->verts, pb->tris, pb->area, pb->edge_pairs, idx, 2, 0, n, (T *)pb->V, pb->ld);
+    }
+}
+
+int far_variant_rows(int v) { return kFarTiles[v].rows; }
+int far_variant_cols(int v) { return kFarTiles[v].cols; }
+
+void batch_far_items(int v, int p, int64_t N, std::vector<int4> &items)
+{
+    const int64_t R = kFarTiles[v].rows, C = kFarTiles[v].cols;
+    for (int64_t i0 = 0; i0 < N; i0 += R)
+        for (int64_t c = (i0 / C) * C; c < N; c += C)  // tiles reaching the diagonal or above
+            if (i0 <= c + C - 1) items.push_back(make_int4(p, (int)i0, (int)c, 0));
+}
+
+template <typename T, int R, int C, int MB = 0, bool UB = false>
+static void far_batch_launch(const BatchAsm &b, cudaStream_t s)
+{
+    k_far_batch<T, R, C, MB, UB><<<(unsigned)b.n_far, C, 0, s>>>(b.prob, b.far_items);
+}
+
+template <typename T>
+static bem_status batch_assemble_t(bem_ctx *ctx, const BatchAsm &b)
+{
+    cudaStream_t s = ctx->stream;
+    if (b.n_far > 0) {
+        const int prof = prof_start(ctx, BEM_KERNEL_FAR, b.far_entries);
+        switch (b.variant) {
+        case 0: far_batch_launch<T, 32, 256>(b, s); break;
+        case 1: far_batch_launch<T, 16, 256>(b, s); break;
+        case 2: far_batch_launch<T, 64, 256>(b, s); break;
+        case 3: far_batch_launch<T, 8, 128>(b, s); break;
+        case 4: far_batch_launch<T, 16, 128>(b, s); break;
+        case 5: far_batch_launch<T, 32, 128>(b, s); break;
+        case 6: far_batch_launch<T, 8, 128, 8>(b, s); break;
+        case 7: far_batch_launch<T, 16, 128, 8>(b, s); break;
+        case 8: far_batch_launch<T, 32, 128, 8>(b, s); break;
+        case 9: far_batch_launch<T, 8, 128, 9>(b, s); break;
+        case 10: far_batch_launch<T, 8, 64, 16>(b, s); break;
+        case 11: far_batch_launch<T, 8, 64, 18>(b, s); break;
+        case 12: far_batch_launch<T, 8, 128, 6, true>(b, s); break;
+        default: far_batch_launch<T, 32, 128, 6, true>(b, s); break;
+        }
+        BEM_COUNT(ctx);
+        prof_stop(ctx, prof);
+        BEM_CK_LAUNCH(ctx);
+    }
+    if (b.n_mirror > 0) {
+        k_mirror_batch<T><<<(unsigned)b.n_mirror, dim3(32, 8), 0, s>>>(b.prob, b.mirror_pref, b.P); BEM_COUNT(ctx);
+        BEM_CK_LAUNCH(ctx);
+    }
+    if (b.n_near > 0) {
+        const int prof = prof_start(ctx, BEM_KERNEL_NEAR, (double)b.n_near);
+        k_near_batch<T><<<nblk(b.n_near, 128), 128, 0, s>>>(b.prob, b.near_pref, b.P, b.n_near, b.ss_order);
+        BEM_COUNT(ctx);
+        prof_stop(ctx, prof);
+        BEM_CK_LAUNCH(ctx);
+    }
+    return BEM_OK;
+}
+
+bem_status batch_assemble(bem_ctx *ctx, const BatchAsm &b)
+{
+    if (b.precision == BEM_PREC_F64) return batch_assemble_t<double>(ctx, b);
+    if (b.precision == BEM_PREC_DF64) return batch_assemble_t<float2>(ctx, b);
+    return batch_assemble_t<float>(ctx, b);
 }
 
 bem_status assembly_prepare(bem_ctx *ctx) { return assembly_constants(ctx); }

@@ -63,6 +63,8 @@ struct bem_ctx {
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory for scalar readbacks
     cudaEvent_t ev[8] = {};
     int8_t far_tile[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // autotuned variant
+    int64_t bar_limit_ns = 0;   // persistent solver: grid-barrier wait limit (0: default)
+    int32_t bar_absent_cta = -1;  // failure-detection tests: CTA that leaves at its first barrier
 };
 
 struct bem_mesh {
@@ -114,7 +116,9 @@ bem_status set_error(bem_ctx *ctx, bem_status code, const char *fmt, ...);
 bem_status cuda_error(bem_ctx *ctx, cudaError_t e, const char *what);
 bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero);
 void dfree_all(bem_ctx *ctx, Allocs &a);
-bool is_device_ptr(const void *p);
+// True for device or managed memory; device (nullable) receives the device that holds
+// plain device memory (-1 for managed or host memory).
+bool is_device_ptr(const void *p, int *device = nullptr);
 
 #define BEM_CK(ctx, call)                                              \
     do {                                                               \
@@ -160,6 +164,42 @@ bem_status assembly_prepare(bem_ctx *ctx);  // constant tables on the device (on
 bem_status far_tune(bem_operator *op);       // time the far-field tile variants for op's size class
 bem_status assemble_update(bem_operator *op, const bem_operator *coarse);
 bem_status operator_diag(bem_operator *op);
+
+// ----------------------------------------------------------------- batched assembly (assemble.cu)
+// One problem of a batch wave as the batched assembly kernels see it.
+struct BatchAsmProb {
+    const double *q64;
+    const float *q32;
+    const double *cent;
+    const float *qdf;
+    const double *verts;
+    const int32_t *tris;
+    const double *area;
+    const int32_t *edge_pairs, *vert_pairs;
+    int64_t n_edge, n_vert;
+    void *V;
+    int64_t ld, N;
+};
+// The batched assembly of one wave: device arrays owned by the batch.
+struct BatchAsm {
+    int P = 0, precision = 0, variant = 0, ss_order = 4;
+    const BatchAsmProb *prob = nullptr;    // P entries
+    const int4 *far_items = nullptr;       // (problem, first row, first column, 0) per far-field tile
+    int64_t n_far = 0;
+    const int64_t *mirror_pref = nullptr;  // P + 1: prefix of the 32 x 32 tile pairs (row tile >= column tile)
+    int64_t n_mirror = 0;
+    const int64_t *near_pref = nullptr;    // P + 1: prefix of N + touching pairs
+    int64_t n_near = 0;
+    double far_entries = 0.0;              // entries i <= j (profiler units)
+};
+int far_variant_rows(int v);
+int far_variant_cols(int v);
+// Host: append the far-field tiles (i <= j part) of problem p of size N for tile variant v.
+void batch_far_items(int v, int p, int64_t N, std::vector<int4> &items);
+// Enqueue the far field, the mirror and the near field of every problem of b.
+bem_status batch_assemble(bem_ctx *ctx, const BatchAsm &b);
+// The autotuned far-field variant of (precision, N) in ctx, or -1 while not timed.
+int far_cached_variant(const bem_ctx *ctx, int precision, int64_t N);
 
 // ----------------------------------------------------------------- solve (solve.cu)
 bem_status matvec_f64(bem_operator *op, const double *x, double *y);

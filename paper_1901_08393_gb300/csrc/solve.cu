@@ -12,6 +12,7 @@
 // N = 60k) would sit at the inner tolerance, and the product is HBM-bound either way.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <vector>
 
 #include "bem_internal.cuh"
@@ -891,7 +892,7 @@ struct PcgArgs {
     double *x, *r, *z, *p, *q;
     const double *d, *b;
     double *part;             // 3 x G per-CTA partials
-    unsigned *bar;            // [0] arrivals, [1] generation
+    unsigned *bar;            // [0] grid-barrier arrival counter (zero at launch)
     unsigned long long *ctr;  // tile counter (never decreases)
     int *err;
     double *out;              // [0] r.r, [1] b.b, [2] iterations, [3] DF64 residuals
@@ -914,34 +915,71 @@ struct PcgArgs {
     // operator preconditioning (Sec. 2.6): packed FP32 upper triangle of the
     // preconditioner C = S D^reg S (the tiles of vp)
     const float *dvp;
+    long long bar_limit_ns;   // grid-barrier wait limit (ns)
+    int absent_cta;           // failure-detection tests: this CTA leaves at its first barrier (-1: none)
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err, int G)
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
+{
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid barrier of the persistent solvers: one arrival counter that only grows
+// (thread 0 of each CTA adds 1 with release semantics, then polls with acquire
+// loads until the counter reaches G times the number of barriers passed), so a
+// barrier costs one fire-and-forget add and the polls.  The wait is bounded in
+// time: after limit_ns (%globaltimer) the CTA raises err and the call returns
+// false, so the kernel ends with an error status instead of hanging; a CTA that
+// sees err raised by another one gives up as well.  absent: this CTA leaves at the
+// barrier without arriving (failure-detection tests: the others must time out).
+constexpr long long kBarrierLimitNs = 2000000000ll;  // default wait limit: 2 s
+struct GridBar {
+    unsigned *cnt;
+    int *err;
+    unsigned target;
+    long long limit_ns;
+    bool absent;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBar &b, int G)
 {
     __shared__ int s_ok;
     __syncthreads();
+    b.target += (unsigned)G;
     if (threadIdx.x == 0) {
         int ok = 1;
-        volatile unsigned *gen = bar + 1;
-        const unsigned g = *gen;
-        __threadfence();
-        if (atomicAdd(bar, 1u) + 1u == (unsigned)G) {
-            atomicExch(bar, 0u);
-            __threadfence();
-            atomicAdd(bar + 1, 1u);
+        if (b.absent) {
+            ok = 0;
         } else {
-            long long spins = 0;
-            while (*gen == g) {
-                if (++spins > (1ll << 24)) {
-                    atomicExch(err, 1);
-                    ok = 0;
-                    break;
+            red_release_add_u32(b.cnt, 1u);
+            unsigned long long t0 = 0;
+            for (unsigned polls = 1; (int)(ld_acquire_u32(b.cnt) - b.target) < 0; ++polls) {
+                if ((polls & 31) == 0) {
+                    const unsigned long long t = global_ns();
+                    if (t0 == 0) {
+                        t0 = t;
+                    } else if ((long long)(t - t0) > b.limit_ns || *(volatile int *)b.err) {
+                        atomicExch(b.err, 1);
+                        ok = 0;
+                        break;
+                    }
                 }
-                __nanosleep(100);
             }
+            if (ok && *(volatile int *)b.err) ok = 0;
         }
-        __threadfence();
-        s_ok = ok && *(volatile int *)err == 0;
+        s_ok = ok;
     }
     __syncthreads();
     return s_ok != 0;
@@ -1001,11 +1039,12 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     const int lane = threadIdx.x & 31, q4 = lane & 3;
     const int64_t warp_g = ((int64_t)cta * kSymThreads + threadIdx.x) >> 5, nwarps = stride >> 5;
     unsigned long long tbase = 0ull;
+    GridBar gb{a.bar, a.err, 0u, a.bar_limit_ns > 0 ? a.bar_limit_ns : kBarrierLimitNs, a.absent_cta == cta};
     // DF64 product V x into the tile partials (x = the FP64 iterate); the first one
     // of the mixed mode also packs the hi parts
     auto df64_product = [&](bool pack) -> bool {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.x[i]) : make_float2(0.f, 0.f);
-        if (!grid_barrier(a.bar, a.err, G)) return false;
+        if (!grid_barrier(gb, G)) return false;
         if (a.f32op) {  // the stored operator is the packed copy itself
             symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
             tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
@@ -1014,17 +1053,17 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                        pack ? a.vp : nullptr);
             tbase += (unsigned long long)(a.ntiles + G);
         }
-        return grid_barrier(a.bar, a.err, G);
+        return grid_barrier(gb, G);
     };
     // z = C r (operator preconditioning, Sec. 2.6): the product with the packed FP32 C
     // (exact products, double-float sums); its row pass also forms the partial of r.z,
     // and with init p = z
     auto calderon = [&](bool init, double &rz_part) -> bool {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.r[i]) : make_float2(0.f, 0.f);
-        if (!grid_barrier(a.bar, a.err, G)) return false;
+        if (!grid_barrier(gb, G)) return false;
         symv_hi_tiles(a.dvp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
         tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
-        if (!grid_barrier(a.bar, a.err, G)) return false;
+        if (!grid_barrier(gb, G)) return false;
         for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
             const int64_t i = ib + (lane >> 2);
             const bool valid = i < a.N;
@@ -1062,7 +1101,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         }
     }
     if (blockpc) {  // z = M^-1 r over whole clusters: every r written first
-        if (!grid_barrier(a.bar, a.err, G)) return;
+        if (!grid_barrier(gb, G)) return;
         for (int blk = cta; blk < a.nbj; blk += G)
             block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, true, rs, rz_l, rr_l);
     }
@@ -1073,13 +1112,13 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     cta_partial(rz_l, pA, cta);
     cta_partial(rr_l, pB, cta);
     cta_partial(bb_l, pC, cta);
-    if (!grid_barrier(a.bar, a.err, G)) return;
+    if (!grid_barrier(gb, G)) return;
     double rz = grid_total(pA, G), rr = grid_total(pB, G);
     const double bb = grid_total(pC, G);
     const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
     double rr_true = rr;  // r.r at the last residual formed with the DF64 product
     int it = 0, ndf = prod0 ? 1 : 0, inexact_stop = 0;
-    if (!grid_barrier(a.bar, a.err, G)) return;  // partial slots are reused below
+    if (!grid_barrier(gb, G)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
         if (mixed) {
             symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
@@ -1088,7 +1127,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
             symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase);
             tbase += (unsigned long long)(a.ntiles + G);
         }
-        if (!grid_barrier(a.bar, a.err, G)) return;
+        if (!grid_barrier(gb, G)) return;
         double pq_l = 0.0;
         // 8 rows per warp and pass, 4 threads per row; the loop is uniform across the
         // warp (rows past N recompute row N-1 and are discarded) because the row sum
@@ -1104,7 +1143,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
             }
         }
         cta_partial(pq_l, pA, cta);
-        if (!grid_barrier(a.bar, a.err, G)) return;
+        if (!grid_barrier(gb, G)) return;
         const double alpha = rz / grid_total(pA, G);
         double rz_n = 0.0;
         rr_l = 0.0;
@@ -1132,7 +1171,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         }
         cta_partial(rz_n, pB, cta);
         cta_partial(rr_l, pC, cta);
-        if (!grid_barrier(a.bar, a.err, G)) return;
+        if (!grid_barrier(gb, G)) return;
         double rz_new = grid_total(pB, G);
         rr = grid_total(pC, G);
         ++it;
@@ -1148,7 +1187,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 }
                 a.u[z] = den > 0.0 ? num / den : 0.0;
             }
-            if (!grid_barrier(a.bar, a.err, G)) return;
+            if (!grid_barrier(gb, G)) return;
             double el = 0.0;
             for (int64_t t = i0; t < a.N; t += stride) {
                 double d[3];
@@ -1159,7 +1198,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 el += (h * a.area[t]) / 12.0 * (s2 + s1 * s1);
             }
             cta_partial(el, pA, cta);
-            if (!grid_barrier(a.bar, a.err, G)) return;
+            if (!grid_barrier(gb, G)) return;
             if (upd2 <= a.lam2 * grid_total(pA, G)) {
                 inexact_stop = 1;
                 break;
@@ -1187,18 +1226,18 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 }
             }
             if (blockpc) {
-                if (!grid_barrier(a.bar, a.err, G)) return;
+                if (!grid_barrier(gb, G)) return;
                 for (int blk = cta; blk < a.nbj; blk += G)
                     block_apply(a.bperm, a.binv, blk, a.x, a.r, a.z, a.p, a.q, a.pdf, 0.0, false, false, rs, rz_n,
                                 rr_l);
             } else if (calpc) {  // r was written in the row-pass layout: barrier first
-                if (!grid_barrier(a.bar, a.err, G)) return;
+                if (!grid_barrier(gb, G)) return;
                 for (int64_t i = i0; i < a.N; i += stride) rr_l += a.r[i] * a.r[i];
                 if (!calderon(false, rz_n)) return;
             }
             cta_partial(rz_n, pB, cta);
             cta_partial(rr_l, pC, cta);
-            if (!grid_barrier(a.bar, a.err, G)) return;
+            if (!grid_barrier(gb, G)) return;
             rz_new = grid_total(pB, G);
             rr = grid_total(pC, G);
             rr_true = rr;
@@ -1215,7 +1254,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
             a.p[i] = pi;
             a.pdf[i] = df_from_double(pi);
         }
-        if (!grid_barrier(a.bar, a.err, G)) return;
+        if (!grid_barrier(gb, G)) return;
     }
     if (cta == 0 && threadIdx.x == 0) {
         a.out[0] = rr;
@@ -1571,7 +1610,7 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
         dfree_all(ctx, tmp);
         return st;
     }
-    PcgArgs a;
+    PcgArgs a{};
     a.V = (const float2 *)op->V;
     a.ld = op->ld;
     a.N = op->N;
@@ -1614,6 +1653,8 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.precond = precond;
     a.has_x0 = has_x0 ? 1 : 0;
     a.dvp = dvp;
+    a.bar_limit_ns = ctx->bar_limit_ns;
+    a.absent_cta = ctx->bar_absent_cta < G ? ctx->bar_absent_cta : -1;
     void *args[] = {&a};
     const int prof = prof_start(ctx, BEM_KERNEL_MATVEC, 0.0);
     cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(G), dim3(kSymThreads), args, kSymSmem,
@@ -2059,6 +2100,12 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
         a.max_it = max_it;
         a.precond = precond;
         a.has_x0 = 0;
+        a.bar_limit_ns = ctx->bar_limit_ns;
+        a.absent_cta = -1;
+        a.dvp = nullptr;
+        a.lanczos = nullptr;
+        a.lanczos_cap = 0;
+        a.lam2 = 0.0;
         if (!a.f32op && delta <= 0.0) a.vp = nullptr;  // DF64 products only
     }
     if (!st) st = dalloc(ctx, bt->allocs, (void **)&bt->d_res, sizeof(double) * kBatchRes * count, true);
@@ -2206,6 +2253,10 @@ bem_status bem_batch_destroy(bem_batch *bt)
 namespace bem {
 
 constexpr int64_t kNoAllocMaxN = 4096;  // largest operator accepted
+// padded_ld(N) <= kNoAllocMaxN for every N <= kNoAllocMaxN only if the limit is a
+// whole number of tiles (rows are padded to 64 entries, one tile side)
+static_assert(kNoAllocMaxN % kSB == 0, "the no-allocation limit must be a multiple of the tile side");
+static_assert(kSB == 64, "rows are padded to 64 entries (padded_ld): one tile side");
 constexpr int kNoAllocNb = (int)(kNoAllocMaxN / kSB);
 constexpr int64_t kNoAllocTiles = (int64_t)kNoAllocNb * (kNoAllocNb + 1) / 2;
 constexpr size_t kNoAllocXBytes = (size_t)kNoAllocMaxN * sizeof(float2);           // x as hi/lo pairs
@@ -2217,7 +2268,14 @@ constexpr size_t kNoAllocBytes = kNoAllocXBytes + 2 * kNoAllocPartBytes + kNoAll
 // that overlap on the GPU (other streams, other threads) share it and race.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-static void *g_noalloc_addr[64] = {nullptr};  // device address of the array, per device
+// Device address of the array, per device: looked up once per device under
+// std::call_once (slot threads of a server may make their first calls at once).
+// A device reset (cudaDeviceReset) invalidates the cached address: the library
+// does not support calls after one.
+constexpr int kNoAllocDevices = 64;
+static std::once_flag g_noalloc_once[kNoAllocDevices];
+static void *g_noalloc_addr[kNoAllocDevices] = {nullptr};
+static cudaError_t g_noalloc_err[kNoAllocDevices] = {cudaSuccess};
 
 }  // namespace bem
 
@@ -2232,21 +2290,32 @@ extern "C" bem_status bem_operator_matvec_noalloc(const bem_operator *op, const 
         return set_error(ctx, BEM_ERR_INVALID,
                          "operator size N = %lld exceeds the no-allocation limit N <= %lld; use bem_operator_matvec",
                          (long long)op->N, (long long)kNoAllocMaxN);
-    if (!x || !y || !is_device_ptr(x) || !is_device_ptr(y))
+    if (op->ld > kNoAllocMaxN)
+        return set_error(ctx, BEM_ERR_INVALID, "padded row length %lld exceeds the no-allocation limit %lld",
+                         (long long)op->ld, (long long)kNoAllocMaxN);
+    int xdev = -1, ydev = -1;
+    if (!x || !y || !is_device_ptr(x, &xdev) || !is_device_ptr(y, &ydev))
         return set_error(ctx, BEM_ERR_INVALID,
                          "x and y must be device pointers (host arrays would need staging buffers)");
+    // plain device memory must sit on the context's device (a peer pointer would be
+    // read by the kernels directly, without a copy); managed memory is reachable
+    if ((xdev >= 0 && xdev != ctx->device) || (ydev >= 0 && ydev != ctx->device))
+        return set_error(ctx, BEM_ERR_INVALID, "x and y must be memory of the context's device (%d)", ctx->device);
     int dev = -1;
     BEM_CK(ctx, cudaGetDevice(&dev));
-    if (dev != ctx->device || dev < 0 || dev >= 64)
+    if (dev != ctx->device || dev < 0 || dev >= kNoAllocDevices)
         return set_error(ctx, BEM_ERR_INVALID, "call with the context's device (%d) current", ctx->device);
-    if (!g_noalloc_addr[dev]) {
-        // set-up on the first call on this device: the host-side name of the array
-        // is not a device address, so ask the runtime for it
+    // set-up on the first call on this device: the host-side name of the array is
+    // not a device address, so ask the runtime for it (with this device current)
+    std::call_once(g_noalloc_once[dev], [dev] {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_error(ctx, e, "cudaGetSymbolAddress of the no-allocation scratch");
-        g_noalloc_addr[dev] = p;
-    }
+        g_noalloc_err[dev] = (e == cudaSuccess && !p) ? cudaErrorInvalidSymbol : e;
+        if (e != cudaSuccess) cudaGetLastError();
+        g_noalloc_addr[dev] = e == cudaSuccess ? p : nullptr;
+    });
+    if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_addr[dev])
+        return cuda_error(ctx, g_noalloc_err[dev], "cudaGetSymbolAddress of the no-allocation scratch");
     unsigned char *base = static_cast<unsigned char *>(g_noalloc_addr[dev]);
     float2 *xdf = reinterpret_cast<float2 *>(base);
     float2 *prow = reinterpret_cast<float2 *>(base + kNoAllocXBytes);
