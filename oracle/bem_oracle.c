@@ -548,11 +548,20 @@ static int kv_cmp(const void *a, const void *b)
 
 /*
  * Eq. 2.6 / Alg. 1 (iii): order the elements by decreasing indicator (compared
- * in single precision, ties by index), accumulate eta^2 in that order in FP64,
- * mark the shortest prefix whose sum reaches theta * total (total = the same
- * ordered sum), then extend it over elements whose single-precision indicator
- * equals the last marked one.
+ * in single precision, ties by index), form the running sums of eta^2 in that
+ * order in FP64, mark the shortest prefix whose running sum reaches
+ * theta * total (total = the last running sum), then extend it over elements
+ * whose single-precision indicator equals the last marked one.
+ *
+ * Summation order of the running sums (the paper fixes none; Eq. 2.6 is an
+ * inequality between exact sums): the sorted sequence is cut into blocks of
+ * ORC_DORFLER_BLOCK consecutive elements; l = the running sum inside a block
+ * (from 0, left to right), o_b = the offset of block b (o_0 = 0,
+ * o_(b+1) = o_b + the block's full sum l), and the running sum at an element of
+ * block b is o_b + l.  For N <= ORC_DORFLER_BLOCK this is the plain left-to-right
+ * sum.  Every addition is one IEEE-754 double addition in this order.
  */
+#define ORC_DORFLER_BLOCK 128
 int orc_dorfler(const double *eta2, int64_t N, double theta, uint8_t *marked, int64_t *n_marked)
 {
     orc_kv *kv = malloc((N ? N : 1) * sizeof(orc_kv));
@@ -561,15 +570,22 @@ int orc_dorfler(const double *eta2, int64_t N, double theta, uint8_t *marked, in
         kv[i].idx = i;
     }
     qsort(kv, N, sizeof(orc_kv), kv_cmp);
-    double total = 0.0;
-    for (int64_t k = 0; k < N; ++k) total += eta2[kv[k].idx];
-    double thr = theta * total;
-    double acc = 0.0;
-    int64_t k = 0;
-    while (k < N && acc < thr) {
-        acc += eta2[kv[k].idx];
-        ++k;
+    /* running sums in the two-level order */
+    double *run = malloc((N ? N : 1) * sizeof(double));
+    double off = 0.0;
+    for (int64_t b0 = 0; b0 < N; b0 += ORC_DORFLER_BLOCK) {
+        double l = 0.0;
+        for (int64_t k = b0; k < N && k < b0 + ORC_DORFLER_BLOCK; ++k) {
+            l = l + eta2[kv[k].idx];
+            run[k] = off + l;
+        }
+        off = off + l;
     }
+    const double total = N > 0 ? run[N - 1] : 0.0;
+    const double thr = theta * total;
+    int64_t k = 0;
+    while (k < N && (k == 0 ? 0.0 : run[k - 1]) < thr) ++k;
+    free(run);
     while (k > 0 && k < N && kv[k].key == kv[k - 1].key) ++k;
     if (N > 0) memset(marked, 0, (size_t)N);
     for (int64_t i = 0; i < k; ++i) marked[kv[i].idx] = 1;

@@ -166,56 +166,59 @@ __global__ void k_bitonic_shared(unsigned long long *keys, int64_t n2, int64_t k
     for (int q = threadIdx.x; q < chunk; q += blockDim.x) keys[base + q] = sk[q];
 }
 
-// Running FP64 sums of eta2 in key order, sequentially: prefix[k] = (((v_0 + v_1) +
-// v_2) + ... + v_k).  One CTA: warps 1..7 gather the values of the next chunk of
-// keys into shared memory while thread 0 of warp 0 adds the current chunk (a single
-// dependent chain of FP64 additions, issued by one lane so that the narrow FP64 pipe
-// is not occupied by 31 redundant copies).
-constexpr int kPrefixChunk = 2048;
+// Running FP64 sums of eta2 in key order, in a fixed two-level order: the sorted
+// sequence is cut into blocks of kDorflerBlock; l = the running sum inside a block
+// (from 0, left to right), o_b = the offset of block b (o_0 = 0, o_(b+1) = o_b +
+// the block's full sum), and prefix[k] = o_b + l for k in block b.  The marking
+// rule (Eq. 2.6) fixes no order; this one is the oracle's, addition for addition, and
+// its chains are 128 (blocks, in parallel) plus N / 128 (offsets) additions long
+// instead of N.
+constexpr int kDorflerBlock = 128;
 
-__global__ void __launch_bounds__(256) k_dorfler_prefix(const unsigned long long *keys, const double *eta2, int64_t N,
-                                                        double *prefix)
+// One thread per block: the running sums inside the block and the block's sum.
+__global__ void k_dorfler_blocks(const unsigned long long *__restrict__ keys, const double *__restrict__ eta2,
+                                 int64_t N, double *__restrict__ prefix, double *__restrict__ bsum)
 {
-    __shared__ double vals[2][kPrefixChunk];
-    const int t = threadIdx.x;
-    const int64_t nchunks = (N + kPrefixChunk - 1) / kPrefixChunk;
-    for (int q = t; q < kPrefixChunk; q += blockDim.x) {
-        const int64_t k = q;
-        vals[0][q] = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
-    }
-    __syncthreads();
-    double acc = 0.0;
-    for (int64_t c = 0; c < nchunks; ++c) {
-        const int cur = (int)(c & 1);
-        if (t >= 32) {  // gather chunk c + 1
-            const int64_t base = (c + 1) * kPrefixChunk;
-            for (int q = t - 32; q < kPrefixChunk; q += blockDim.x - 32) {
-                const int64_t k = base + q;
-                vals[cur ^ 1][q] = k < N ? eta2[keys[k] & 0xFFFFFFFFull] : 0.0;
-            }
-        } else if (t == 0) {
-            const int64_t base = c * kPrefixChunk;
-            const int n = (int)((N - base) < kPrefixChunk ? (N - base) : kPrefixChunk);
-            const double *v = vals[cur];
-            double *out = prefix + base;
-            int q = 0;
-            for (; q + 16 <= n; q += 16) {  // loads of a group issued before its additions
-                double r[16];
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b0 = b * kDorflerBlock;
+    if (b0 >= N) return;
+    const int n = (int)((N - b0) < kDorflerBlock ? (N - b0) : kDorflerBlock);
+    double l = 0.0;
+    int q = 0;
+    for (; q + 16 <= n; q += 16) {  // loads of a group issued before its additions
+        double r[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) r[u] = v[q + u];
+        for (int u = 0; u < 16; ++u) r[u] = eta2[keys[b0 + q + u] & 0xFFFFFFFFull];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) {
-                    acc = acc + r[u];
-                    out[q + u] = acc;
-                }
-            }
-            for (; q < n; ++q) {
-                acc = acc + v[q];
-                out[q] = acc;
-            }
+        for (int u = 0; u < 16; ++u) {
+            l = l + r[u];
+            prefix[b0 + q + u] = l;
         }
-        __syncthreads();
     }
+    for (; q < n; ++q) {
+        l = l + eta2[keys[b0 + q] & 0xFFFFFFFFull];
+        prefix[b0 + q] = l;
+    }
+    bsum[b] = l;
+}
+
+// The block offsets, by one thread: off[0] = 0, off[b + 1] = off[b] + bsum[b].
+__global__ void k_dorfler_offsets(const double *__restrict__ bsum, int64_t nb, double *__restrict__ off)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double o = 0.0;
+    off[0] = 0.0;
+    for (int64_t b = 0; b < nb; ++b) {
+        o = o + bsum[b];
+        off[b + 1] = o;
+    }
+}
+
+// prefix[k] = off[block of k] + (running sum inside the block).
+__global__ void k_dorfler_finish(const double *__restrict__ off, int64_t N, double *__restrict__ prefix)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < N) prefix[k] = off[k / kDorflerBlock] + prefix[k];
 }
 
 // The shortest prefix whose running sum reaches theta * total (total = prefix[N-1];
@@ -276,13 +279,18 @@ bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, 
     if (n2 < 2) n2 = 2;
     Allocs tmp;
     unsigned long long *keys = nullptr;
-    bem_status st = dalloc(ctx, tmp, (void **)&keys, sizeof(unsigned long long) * n2 + sizeof(double) * N + 64, false);
+    const int64_t nb = (N + kDorflerBlock - 1) / kDorflerBlock;
+    bem_status st = dalloc(ctx, tmp, (void **)&keys,
+                           sizeof(unsigned long long) * n2 + sizeof(double) * (N + 2 * nb + 1) + 64, false);
     if (st) return st;
     double *prefix = reinterpret_cast<double *>(keys + n2);
-    long long *dK = reinterpret_cast<long long *>(prefix + N);
+    double *bsum = prefix + N, *off = bsum + nb;
+    long long *dK = reinterpret_cast<long long *>(off + nb + 1);
     k_keys<<<nblk(n2, 256), 256, 0, s>>>(d_eta2, N, n2, keys); BEM_COUNT(ctx);
     sort_u64(ctx, keys, n2);
-    k_dorfler_prefix<<<1, 256, 0, s>>>(keys, d_eta2, N, prefix); BEM_COUNT(ctx);
+    k_dorfler_blocks<<<nblk(nb, 64), 64, 0, s>>>(keys, d_eta2, N, prefix, bsum); BEM_COUNT(ctx);
+    k_dorfler_offsets<<<1, 32, 0, s>>>(bsum, nb, off); BEM_COUNT(ctx);
+    k_dorfler_finish<<<nblk(N, 256), 256, 0, s>>>(off, N, prefix); BEM_COUNT(ctx);
     k_dorfler_select<<<1, 1, 0, s>>>(keys, prefix, N, theta, dK); BEM_COUNT(ctx);
     k_mark<<<nblk(N, 256), 256, 0, s>>>(keys, N, dK, d_marked); BEM_COUNT(ctx);
     cudaError_t e = cudaGetLastError();

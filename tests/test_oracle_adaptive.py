@@ -206,3 +206,23 @@ def test_adaptive_loop_monotone():
     adaptive = [h for h in hist[:-1] if h["eta2_total"] > 1e-10]
     assert adaptive and all(h["marked"].sum() > 0 for h in adaptive)
     assert any(h["marked"].sum() < h["N"] for h in adaptive)  # symmetric tie groups may be whole
+
+
+def test_dorfler_large_sets_meet_eq_2_6_minimally():
+    """Beyond one summation block (128 sorted elements): the marked set satisfies
+    theta * sum(eta^2) <= sum over the set with exact sums, and dropping its last
+    tie group of single-precision keys breaks the inequality (minimality up to the
+    rounding of the running sums)."""
+    rng = np.random.default_rng(17)
+    for N in (129, 1000, 5000):
+        for theta in (0.2, 0.5, 0.9):
+            eta2 = rng.random(N) ** 4
+            eta2[: N // 7] = eta2[N // 7]  # exact ties across block boundaries
+            m = O.dorfler(eta2, theta).astype(bool)
+            tot = math.fsum(eta2)
+            assert math.fsum(eta2[m]) >= theta * tot * (1 - 1e-12)
+            key = eta2.astype(np.float32)
+            cut = key[m].min()
+            assert not np.any(key[~m] > cut) and not np.any(key[~m] == cut)  # upward closed, ties closed
+            rest = m & (key > cut)
+            assert math.fsum(eta2[rest]) < theta * tot * (1 + 1e-12)
