@@ -341,18 +341,27 @@ bem_status bem_operator_preconditioner(const bem_operator *op, int32_t which, fl
 /* ---------------------------------------------------------------- batch */
 /* Many independent capacity problems assembled and solved together (the paper has
  * no counterpart: it solves one polyhedron at a time).  bem_batch_create takes count
- * meshes of any sizes (same context; the meshes must outlive the batch), allocates one
- * operator per mesh (aopts->precision BEM_PREC_DF64 or BEM_PREC_F32) and everything
- * the solves need, and, for BEM_PRECOND_BLOCK, computes the cluster orders.
- * bem_batch_run assembles every V (Eq. 2.4-2.5; the kernels of bem_assemble_V, per
- * mesh), then solves all V x = |T| from x = 0 in ONE cooperative launch of the
- * persistent solver of bem_solve_capacity (sopts: tol, max_it, precond,
- * reliable_delta), in which problem p owns a share of the CTAs in proportion to its
- * work and has its own grid barrier, and forms every Cap (Eq. 2.8).  The work runs on
- * a stream of the batch; with use_graph the first run records it as a CUDA graph and
- * later runs replay that graph.  The call blocks until the results are on the host;
- * results (nullable, count entries) receive them; BEM_ERR_NOT_CONVERGED if any
- * problem missed tol.  At most 3 x (number of SMs) problems per batch. */
+ * meshes of any sizes (same context; the meshes must outlive the batch) and the
+ * operator precision (aopts->precision BEM_PREC_DF64 or BEM_PREC_F32).  It cuts the
+ * problems, in their given order, into waves whose device memory fits what is
+ * available at creation -- 90% of the device's free memory, and the context's HBM
+ * budget if it has one -- and at most 3 x (number of SMs) problems per wave; one
+ * arena sized for the largest wave holds the operators and the solver state of the
+ * wave that runs (a problem that alone exceeds it: BEM_ERR_OOM).  It also times the
+ * far-field tiles of the size classes present and, for BEM_PRECOND_BLOCK, computes the
+ * cluster orders.  bem_batch_run runs every wave in turn: the assembly of all its
+ * operators (Eq. 2.4-2.5) by one launch per phase -- the far field over a work list of
+ * (problem, tile) items with one tile shape (the autotuned one of the wave's largest
+ * size class), the mirror of the lower triangles, the Sauter-Schwab near field over
+ * all touching pairs -- entries bit-identical to bem_assemble_V's; then the diagonals,
+ * right-hand sides and preconditioners; then ONE cooperative launch of the persistent
+ * solver of bem_solve_capacity (sopts: tol, max_it, precond, reliable_delta; x = 0
+ * start) in which problem p owns a share of the CTAs in proportion to its work and
+ * has its own grid barrier; then every Cap (Eq. 2.8).  The work runs on a stream of
+ * the batch; with use_graph each wave is recorded once as a CUDA graph on the first
+ * run and later runs replay it.  The call blocks until the results are on the host;
+ * results (nullable, count entries, in the given order) receive them;
+ * BEM_ERR_NOT_CONVERGED if any problem missed tol. */
 typedef struct bem_batch bem_batch;
 typedef struct {
     double cap;
@@ -368,6 +377,9 @@ bem_status bem_batch_run(bem_batch *b, bem_batch_result *results);
 /* count: problems; ctas: CTAs of the solver launch; graph_used: 1 if the last run
  * replayed a captured graph. */
 bem_status bem_batch_info(const bem_batch *b, int32_t *count, int32_t *ctas, int32_t *graph_used);
+/* waves: number of waves; arena_bytes: device bytes of the arena; wave_of (nullable,
+ * count entries): the wave of each problem.  Any pointer may be NULL. */
+bem_status bem_batch_waves(const bem_batch *b, int32_t *waves, int64_t *arena_bytes, int32_t *wave_of);
 bem_status bem_batch_destroy(bem_batch *b);
 
 /* ---------------------------------------------------------------- serving */

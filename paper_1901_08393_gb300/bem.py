@@ -44,7 +44,7 @@ EXPORTS = [
     "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
     "bem_batch_create", "bem_batch_run", "bem_batch_info", "bem_batch_destroy",
     "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual", "bem_operator_preconditioner",
-    "bem_far_tiles", "bem_debug_barrier_fault",
+    "bem_far_tiles", "bem_debug_barrier_fault", "bem_batch_waves",
 ]
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
@@ -162,6 +162,7 @@ def lib():
         "bem_operator_preconditioner": [vp, i32, vp],
         "bem_far_tiles": [vp, vp],
         "bem_debug_barrier_fault": [vp, i64, i32],
+        "bem_batch_waves": [vp, P(i32), P(i64), vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -483,16 +484,17 @@ def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, pr
 
 
 class Batch:
-    """Independent problems assembled and solved together (bem_batch_*): one
-    cooperative launch solves all of them; with use_graph the run is recorded as a
-    CUDA graph once and replayed."""
+    """Independent problems assembled and solved together (bem_batch_*), in waves
+    that fit the device memory: per wave one launch per assembly phase and one
+    cooperative launch of the solver; with use_graph each wave is recorded as a CUDA
+    graph once and replayed."""
 
     def __init__(self, ctx: Context, meshes, precision=PREC_DF64, ss_order=4, tol=1e-10, max_it=10000,
-                 precond=PRECOND_JACOBI, reliable_delta=0.0, use_graph=True):
+                 precond=PRECOND_JACOBI, reliable_delta=0.0, use_graph=True, tile=0):
         self.ctx, self.meshes, self.h = ctx, list(meshes), None
         arr = (C.c_void_p * len(self.meshes))(*[m.h.value if hasattr(m.h, "value") else m.h for m in self.meshes])
         h = C.c_void_p()
-        ctx.check(ctx.L.bem_batch_create(ctx.h, len(self.meshes), arr, C.byref(AssemblyOpts(precision, ss_order)),
+        ctx.check(ctx.L.bem_batch_create(ctx.h, len(self.meshes), arr, C.byref(AssemblyOpts(precision, ss_order, tile)),
                                          C.byref(SolveOpts(tol, max_it, precond, 20, 1e-5, reliable_delta)),
                                          int(bool(use_graph)), C.byref(h)))
         self.h = h
@@ -509,6 +511,13 @@ class Batch:
         n, g, used = C.c_int32(), C.c_int32(), C.c_int32()
         self.ctx.check(self.ctx.L.bem_batch_info(self.h, C.byref(n), C.byref(g), C.byref(used)))
         return {"count": n.value, "ctas": g.value, "graph_used": used.value}
+
+    def waves(self):
+        """(number of waves, arena bytes, wave of each problem)."""
+        w, b = C.c_int32(), C.c_int64()
+        of = np.zeros(len(self.meshes), dtype=np.int32)
+        self.ctx.check(self.ctx.L.bem_batch_waves(self.h, C.byref(w), C.byref(b), of.ctypes.data))
+        return int(w.value), int(b.value), of
 
     def close(self):
         if self.h is not None and self.ctx.h:

@@ -82,7 +82,8 @@ __global__ void k_sum2(const double *a, const double *b, int n, double *out)
     }
 }
 
-bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_eta2, double *h_totals)
+bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_eta2, double *h_totals,
+                       double *d_totals)
 {
     bem_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
@@ -91,7 +92,7 @@ bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_e
     const int nb = (int)nblk(m->N, 256);
     bem_status st = dalloc(ctx, tmp, (void **)&u, sizeof(double) * (m->M + 2 * nb + 2), false);
     if (st) return st;
-    double *pe = u + m->M, *ps = pe + nb, *tot = ps + nb;
+    double *pe = u + m->M, *ps = pe + nb, *tot = d_totals ? d_totals : ps + nb;
     k_zz_nodal<<<nblk(m->M, 128), 128, 0, s>>>(m->v2t_off, m->v2t, m->area, d_phi, u, m->M); BEM_COUNT(ctx);
     k_zz_eta<<<nb, 256, 0, s>>>(m->tris, m->area, m->diam, d_phi, u, m->N, h_mode, d_eta2, pe, ps); BEM_COUNT(ctx);
     k_sum2<<<1, 32, 0, s>>>(pe, ps, nb, tot); BEM_COUNT(ctx);
@@ -225,8 +226,15 @@ __global__ void k_dorfler_finish(const double *__restrict__ off, int64_t N, doub
 // none if theta * total <= 0), by bisection over the non-decreasing prefix sums,
 // then extended over equal keys.
 __global__ void k_dorfler_select(const unsigned long long *keys, const double *prefix, int64_t N, double theta,
-                                 long long *K_out)
+                                 const double *vanish, long long *K_out)
 {
+    // vanish (nullable): [sum eta^2, sum h|T|x^2/12]; when every indicator vanishes up
+    // to rounding (sum eta^2 <= 1e-20 of the scale) Eq. 2.6 holds for the empty set and
+    // every element is marked (uniform refinement)
+    if (vanish && !(vanish[0] > 1e-20 * vanish[1])) {
+        *K_out = N;
+        return;
+    }
     const double thr = theta * prefix[N - 1];
     int64_t kk = 0;
     if (0.0 < thr) {
@@ -266,10 +274,11 @@ void sort_u64(bem_ctx *ctx, unsigned long long *keys, int64_t n2)
 }
 
 bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, uint8_t *d_marked,
-                   int64_t *n_marked)
+                   int64_t *n_marked, const double *d_vanish, long long *d_count)
 {
     if (N <= 0) {
         if (n_marked) *n_marked = 0;
+        if (d_count) BEM_CK(ctx, cudaMemsetAsync(d_count, 0, sizeof(long long), ctx->stream));
         return BEM_OK;
     }
     if (N > 0x7FFFFFFFLL) return set_error(ctx, BEM_ERR_INVALID, "too many elements for marking");
@@ -291,9 +300,10 @@ bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, 
     k_dorfler_blocks<<<nblk(nb, 64), 64, 0, s>>>(keys, d_eta2, N, prefix, bsum); BEM_COUNT(ctx);
     k_dorfler_offsets<<<1, 32, 0, s>>>(bsum, nb, off); BEM_COUNT(ctx);
     k_dorfler_finish<<<nblk(N, 256), 256, 0, s>>>(off, N, prefix); BEM_COUNT(ctx);
-    k_dorfler_select<<<1, 1, 0, s>>>(keys, prefix, N, theta, dK); BEM_COUNT(ctx);
+    k_dorfler_select<<<1, 1, 0, s>>>(keys, prefix, N, theta, d_vanish, dK); BEM_COUNT(ctx);
     k_mark<<<nblk(N, 256), 256, 0, s>>>(keys, N, dK, d_marked); BEM_COUNT(ctx);
     cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && d_count) e = cudaMemcpyAsync(d_count, dK, sizeof(long long), cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) st = cuda_error(ctx, e, "doerfler kernels");
     if (!st && n_marked) {
         e = cudaMemcpyAsync(ctx->h_pinned, dK, sizeof(long long), cudaMemcpyDeviceToHost, s);
@@ -431,9 +441,9 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
     TRY(dalloc(ctx, tmp, (void **)&n_child, sizeof(int32_t) * (N + 1), false));
     TRY(dalloc(ctx, tmp, (void **)&child_pos, sizeof(int32_t) * (N + 1), false));
     k_nvb_seed<<<nblk(N, 256), 256, 0, s>>>(m->owner, d_marked, N, flags & BEM_REFINE_BISEC3, flag); BEM_COUNT(ctx);
-    // closure sweeps, four per check of the changed flag (a sweep after the fixed
-    // point changes nothing)
-    for (int sweep = 0;; sweep += 4) {
+    // closure sweeps, eight per check of the changed flag (a sweep after the fixed
+    // point changes nothing; a level's closure rarely needs more than eight)
+    for (int sweep = 0;; sweep += 8) {
         if (sweep > 100000) {
             st = set_error(ctx, BEM_ERR_MESH, "NVB closure did not terminate");
             goto fail;
@@ -442,7 +452,7 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
             st = set_error(ctx, BEM_ERR_CUDA, "closure flag reset");
             goto fail;
         }
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < 8; ++k)
             { k_nvb_close<<<nblk(N, 256), 256, 0, s>>>(m->owner, N, flag, changed); BEM_COUNT(ctx); }
         cudaError_t e = cudaMemcpyAsync(ctx->h_pinned, changed, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -453,9 +463,17 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
         if (*reinterpret_cast<int32_t *>(ctx->h_pinned) == 0) break;
     }
     k_nvb_counts<<<nblk(N, 256), 256, 0, s>>>(m->owner, flag, N, is_new, is_kept, n_child); BEM_COUNT(ctx);
-    TRY(exclusive_scan_i32(ctx, is_new, new_pos, H, &n_new));
-    TRY(exclusive_scan_i32(ctx, is_kept, kept_pos, N, &n_kept));
-    TRY(exclusive_scan_i32(ctx, n_child, child_pos, N, &n_children));
+    TRY(exclusive_scan_i32(ctx, is_new, new_pos, H, nullptr));
+    TRY(exclusive_scan_i32(ctx, is_kept, kept_pos, N, nullptr));
+    TRY(exclusive_scan_i32(ctx, n_child, child_pos, N, nullptr));
+    {  // the three totals in one read
+        const int32_t *src[3] = {new_pos + H, kept_pos + N, child_pos + N};
+        int64_t tot[3] = {0, 0, 0};
+        TRY(read_i32s(ctx, src, 3, tot));
+        n_new = tot[0];
+        n_kept = tot[1];
+        n_children = tot[2];
+    }
     r = new bem_mesh();
     r->ctx = ctx;
     r->M = M + n_new;

@@ -344,6 +344,8 @@ bem_status bem_context_destroy(bem_ctx *ctx)
     for (int k = 0; k < 8; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->h_levels) cudaFreeHost(ctx->h_levels);
+    for (cudaEvent_t e : ctx->lvl_ev) cudaEventDestroy(e);
     if (ctx->pool) pool_release(ctx->device);
     delete ctx;
     return BEM_OK;
@@ -491,17 +493,36 @@ static bem_status operator_alloc(bem_mesh *mesh, const bem_assembly_opts *opts, 
     return BEM_OK;
 }
 
-bem_status bem_assemble_V(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out)
+// Assembly of a new operator for mesh: from scratch (coarse null) or reusing the
+// entries of unrefined pairs from coarse.  sync: wait for the kernels (the public
+// entry points; the adaptive loop lets them run on).
+static bem_status assemble_impl(bem_mesh *mesh, const bem_assembly_opts *opts, const bem_operator *coarse, bool sync,
+                                bem_operator **out)
 {
-    if (!mesh || !out) return BEM_ERR_INVALID;
+    bem_ctx *ctx = mesh->ctx;
     *out = nullptr;
+    bem_assembly_opts o{};
+    const bem_assembly_opts *use = opts;
+    if (coarse) {
+        CHECK_ARG(ctx, coarse->mesh->ctx == ctx, "operator and mesh belong to different contexts");
+        CHECK_ARG(ctx, !coarse->mesh->cells_only, "a dual operator has no incremental update");
+        CHECK_ARG(ctx, mesh->parent != nullptr && mesh->src_N == coarse->N,
+                  "mesh was not refined from the operator's mesh");
+        o = bem_assembly_opts{coarse->precision, coarse->ss_order, opts ? opts->tile : coarse->tile};
+        if (opts) {
+            CHECK_ARG(ctx, opts->precision == coarse->precision, "precision differs from the coarse operator");
+            CHECK_ARG(ctx, (opts->ss_order > 0 ? opts->ss_order : 4) == coarse->ss_order,
+                      "ss_order differs from the coarse operator");
+        }
+        use = &o;
+    }
     bem_operator *op = nullptr;
-    bem_status st = operator_alloc(mesh, opts, &op);
+    bem_status st = operator_alloc(mesh, use, &op);
     if (st) return st;
-    st = assemble_full(op);
-    if (!st) {
-        cudaError_t e = cudaStreamSynchronize(mesh->ctx->stream);
-        if (e != cudaSuccess) st = cuda_error(mesh->ctx, e, "assembly");
+    st = coarse ? assemble_update(op, coarse) : assemble_full(op);
+    if (!st && sync) {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e != cudaSuccess) st = cuda_error(ctx, e, coarse ? "incremental assembly" : "assembly");
     }
     if (st) {
         bem_operator_destroy(op);
@@ -511,36 +532,17 @@ bem_status bem_assemble_V(bem_mesh *mesh, const bem_assembly_opts *opts, bem_ope
     return BEM_OK;
 }
 
+bem_status bem_assemble_V(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out)
+{
+    if (!mesh || !out) return BEM_ERR_INVALID;
+    return assemble_impl(mesh, opts, nullptr, true, out);
+}
+
 bem_status bem_assemble_V_update(bem_mesh *fine, const bem_operator *coarse, const bem_assembly_opts *opts,
                                  bem_operator **out)
 {
     if (!fine || !coarse || !out) return BEM_ERR_INVALID;
-    bem_ctx *ctx = fine->ctx;
-    *out = nullptr;
-    CHECK_ARG(ctx, coarse->mesh->ctx == ctx, "operator and mesh belong to different contexts");
-    CHECK_ARG(ctx, !coarse->mesh->cells_only, "a dual operator has no incremental update");
-    CHECK_ARG(ctx, fine->parent != nullptr && fine->src_N == coarse->N,
-              "mesh was not refined from the operator's mesh");
-    bem_assembly_opts o{coarse->precision, coarse->ss_order, opts ? opts->tile : coarse->tile};
-    if (opts) {
-        CHECK_ARG(ctx, opts->precision == coarse->precision, "precision differs from the coarse operator");
-        CHECK_ARG(ctx, (opts->ss_order > 0 ? opts->ss_order : 4) == coarse->ss_order,
-                  "ss_order differs from the coarse operator");
-    }
-    bem_operator *op = nullptr;
-    bem_status st = operator_alloc(fine, &o, &op);
-    if (st) return st;
-    st = assemble_update(op, coarse);
-    if (!st) {
-        cudaError_t e = cudaStreamSynchronize(ctx->stream);
-        if (e != cudaSuccess) st = cuda_error(ctx, e, "incremental assembly");
-    }
-    if (st) {
-        bem_operator_destroy(op);
-        return st;
-    }
-    *out = op;
-    return BEM_OK;
+    return assemble_impl(fine, opts, coarse, true, out);
 }
 
 bem_status bem_operator_destroy(bem_operator *op)
@@ -816,7 +818,10 @@ bem_status bem_mark_refine(bem_mesh *mesh, const double *eta2, double theta, int
 static float elapsed(cudaEvent_t a, cudaEvent_t b)
 {
     float ms = 0.0f;
-    cudaEventElapsedTime(&ms, a, b);
+    if (cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+        cudaGetLastError();
+        ms = 0.0f;
+    }
     return ms;
 }
 
@@ -879,6 +884,24 @@ static bem_status dual_level_operator(bem_mesh *cur, const bem_assembly_opts *ao
     return st;
 }
 
+// Pinned result slots and timing events for `levels` levels of the adaptive loop.
+static bem_status level_slots(bem_ctx *ctx, int levels)
+{
+    if (ctx->h_levels_cap < levels) {
+        if (ctx->h_levels) cudaFreeHost(ctx->h_levels);
+        ctx->h_levels = nullptr;
+        ctx->h_levels_cap = 0;
+        BEM_CK(ctx, cudaMallocHost((void **)&ctx->h_levels, sizeof(double) * 16 * (size_t)levels));
+        ctx->h_levels_cap = levels;
+    }
+    while ((int)ctx->lvl_ev.size() < 4 * levels) {
+        cudaEvent_t e = nullptr;
+        BEM_CK(ctx, cudaEventCreate(&e));
+        ctx->lvl_ev.push_back(e);
+    }
+    return BEM_OK;
+}
+
 bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_level_record *records, int32_t *n_levels,
                             bem_mesh **final_mesh)
 {
@@ -893,6 +916,12 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
     CHECK_ARG(ctx, dual || opts->solve.precond != BEM_PRECOND_CALDERON, "BEM_PRECOND_CALDERON needs the dual basis");
     if (final_mesh) *final_mesh = nullptr;
     *n_levels = 0;
+    bem_status st = level_slots(ctx, opts->max_levels);
+    if (st) return st;
+    // The loop synchronises with the host only where it needs a count: the sizes of the
+    // refined mesh (refine) and its touching-pair lists.  The solve's results, the ZZ
+    // totals and the Doerfler count travel to pinned slots meanwhile and are read after
+    // that synchronisation; the per-phase times come from events read once at the end.
     cudaStream_t s = ctx->stream;
     bem_mesh *cur = mesh;
     bem_mesh *prev_mesh = nullptr;  // mesh of op_prev, destroyed after op_prev
@@ -900,20 +929,21 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
     BaryLevel bary_prev;  // dual basis: the previous level's barycentric operator
     Allocs xprev_alloc;
     double *x_prev = nullptr;
-    bem_status st = BEM_OK;
     for (int lvl = 0; lvl < opts->max_levels; ++lvl) {
         bem_level_record &rec = records[lvl];
         memset(&rec, 0, sizeof(rec));
         rec.N = cur->N;
         rec.M = cur->M;
-        cudaEventRecord(ctx->ev[0], s);
+        double *slot = ctx->h_levels + 16 * (size_t)lvl;
+        cudaEvent_t *ev = &ctx->lvl_ev[4 * (size_t)lvl];
+        cudaEventRecord(ev[0], s);
         bem_operator *op = nullptr;
         if (dual)
             st = dual_level_operator(cur, &opts->assembly, opts->incremental != 0, bary_prev, &op);
         else if (op_prev && opts->incremental && cur->parent)
-            st = bem_assemble_V_update(cur, op_prev, &opts->assembly, &op);
+            st = assemble_impl(cur, &opts->assembly, op_prev, false, &op);
         else
-            st = bem_assemble_V(cur, &opts->assembly, &op);
+            st = assemble_impl(cur, &opts->assembly, nullptr, false, &op);
         if (op_prev) {
             bem_operator_destroy(op_prev);
             op_prev = nullptr;
@@ -921,14 +951,15 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         if (prev_mesh && prev_mesh != mesh) bem_mesh_destroy(prev_mesh);
         prev_mesh = nullptr;
         if (st) break;
-        cudaEventRecord(ctx->ev[1], s);
+        cudaEventRecord(ev[1], s);
         Allocs lv;
-        double *x0 = nullptr, *x = nullptr, *eta2 = nullptr;
+        double *x0 = nullptr, *x = nullptr, *eta2 = nullptr, *dsc = nullptr;
         const int64_t nx = dual ? cur->M : cur->N;  // unknowns: vertices or triangles
-        st = dalloc(ctx, lv, (void **)&x, sizeof(double) * (2 * nx + cur->N), false);
+        st = dalloc(ctx, lv, (void **)&x, sizeof(double) * (2 * nx + cur->N + 4), false);
         if (st) { bem_operator_destroy(op); break; }
         x0 = x + nx;
         eta2 = x + 2 * nx;
+        dsc = eta2 + cur->N;  // [0..1] ZZ totals, [2] Doerfler count (long long)
         if (!dual && x_prev && cur->parent) {
             k_prolong<<<nblk(cur->N, 256), 256, 0, s>>>(x_prev, cur->parent, cur->N, x0); BEM_COUNT(ctx);
         } else {
@@ -938,24 +969,33 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         double cap = 0.0;
         bem_solve_opts so = opts->solve;
         so.h_mode = opts->h_mode;  // the estimator of the inexact stopping rule
-        st = solve_capacity(op, &so, x0, x, &cap, &info);
-        rec.cap = cap;
-        rec.iterations = info.iterations;
-        rec.outer = info.outer;
-        rec.relres = info.relres;
+        SolveDeferred def;
+        def.h = slot;
+        st = solve_capacity(op, &so, x0, x, &cap, &info, &def);
         if (st) { dfree_all(ctx, lv); bem_operator_destroy(op); break; }
-        cudaEventRecord(ctx->ev[2], s);
+        cudaEventRecord(ev[2], s);
         double tot[2] = {0.0, 0.0};
-        st = dual ? zz_estimate_dual(cur, x, opts->h_mode, eta2, tot) : zz_estimate(cur, x, opts->h_mode, eta2, tot);
-        rec.eta2_total = tot[0];
+        if (dual) {
+            st = zz_estimate_dual(cur, x, opts->h_mode, eta2, tot);
+            slot[8] = tot[0];
+            slot[9] = tot[1];
+        } else {
+            st = zz_estimate(cur, x, opts->h_mode, eta2, nullptr, dsc);
+            if (!st) {
+                cudaError_t e = cudaMemcpyAsync(slot + 8, dsc, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+                if (e != cudaSuccess) st = cuda_error(ctx, e, "ZZ totals");
+            }
+        }
         bem_mesh *next = nullptr;
         const bool last = cur->N >= opts->max_N || lvl == opts->max_levels - 1;
+        long long *hcount = reinterpret_cast<long long *>(slot + 10);
+        *hcount = 0;
         if (!st && !last) {
             Allocs mk;
             uint8_t *dm = nullptr;
             st = dalloc(ctx, mk, (void **)&dm, (size_t)cur->N, false);
-            int64_t nm = 0;
-            if (!st) {
+            if (!st && dual) {
+                int64_t nm = 0;
                 if (!(tot[0] > 1e-20 * tot[1])) {
                     // every indicator vanishes up to rounding: refine uniformly
                     cudaMemsetAsync(dm, 1, (size_t)cur->N, s);
@@ -963,17 +1003,35 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
                 } else {
                     st = dorfler(ctx, eta2, cur->N, opts->theta, dm, &nm);
                 }
+                *hcount = nm;
+            } else if (!st) {
+                // the vanishing-estimator rule is taken on the device from the totals
+                long long *dcount = reinterpret_cast<long long *>(dsc + 2);
+                st = dorfler(ctx, eta2, cur->N, opts->theta, dm, nullptr, dsc, dcount);
+                if (!st) {
+                    cudaError_t e = cudaMemcpyAsync(hcount, dcount, sizeof(long long), cudaMemcpyDeviceToHost, s);
+                    if (e != cudaSuccess) st = cuda_error(ctx, e, "Doerfler count");
+                }
             }
-            if (!st) st = refine(cur, dm, 0, &next);
-            rec.n_marked = (int32_t)nm;
+            if (!st) st = refine(cur, dm, 0, &next);  // synchronises: the new mesh's sizes
             dfree_all(ctx, mk);
         }
-        cudaEventRecord(ctx->ev[3], s);
-        cudaEventSynchronize(ctx->ev[3]);
-        rec.ms_assemble = elapsed(ctx->ev[0], ctx->ev[1]);
-        rec.ms_solve = elapsed(ctx->ev[1], ctx->ev[2]);
-        rec.ms_adapt = elapsed(ctx->ev[2], ctx->ev[3]);
-        *n_levels = lvl + 1;
+        cudaEventRecord(ev[3], s);
+        if (last || st) cudaEventSynchronize(ev[3]);
+        // the level's results are in their pinned slot now
+        bem_status st_solve = BEM_OK;
+        if (def.pending) st_solve = solve_capacity_end(ctx, def, &cap, &info);
+        rec.cap = cap;
+        rec.iterations = info.iterations;
+        rec.outer = info.outer;
+        rec.relres = info.relres;
+        rec.eta2_total = slot[8];
+        rec.n_marked = last ? 0 : (int32_t)*hcount;
+        if (st_solve) {  // a failed solve ends the loop; its level is not counted
+            st = st_solve;
+        } else {
+            *n_levels = lvl + 1;
+        }
         // keep this level's solution for the warm start of the next one
         dfree_all(ctx, xprev_alloc);
         x_prev = nullptr;
@@ -992,6 +1050,14 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         op_prev = op;
         prev_mesh = cur;
         cur = next;
+    }
+    // per-phase device times of every level that ran
+    cudaStreamSynchronize(s);
+    for (int l = 0; l < *n_levels; ++l) {
+        cudaEvent_t *ev = &ctx->lvl_ev[4 * (size_t)l];
+        records[l].ms_assemble = elapsed(ev[0], ev[1]);
+        records[l].ms_solve = elapsed(ev[1], ev[2]);
+        records[l].ms_adapt = elapsed(ev[2], ev[3]);
     }
     if (op_prev) bem_operator_destroy(op_prev);
     if (prev_mesh && prev_mesh != mesh) bem_mesh_destroy(prev_mesh);

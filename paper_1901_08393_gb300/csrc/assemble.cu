@@ -893,12 +893,25 @@ static void far_batch_launch(const BatchAsm &b, cudaStream_t s)
     k_far_batch<T, R, C, MB, UB><<<(unsigned)b.n_far, C, 0, s>>>(b.prob, b.far_items);
 }
 
+// Event record that also fires when a captured graph replays (an external event node
+// while the stream is being captured; a plain record otherwise).
+bem_status record_timing_event(bem_ctx *ctx, cudaEvent_t e)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    BEM_CK(ctx, cudaStreamIsCapturing(ctx->stream, &cs));
+    BEM_CK(ctx, cudaEventRecordWithFlags(e, ctx->stream,
+                                         cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal
+                                                                             : cudaEventRecordDefault));
+    return BEM_OK;
+}
+
 template <typename T>
-static bem_status batch_assemble_t(bem_ctx *ctx, const BatchAsm &b)
+static bem_status batch_assemble_t(bem_ctx *ctx, const BatchAsm &b, cudaEvent_t *ev)
 {
     cudaStream_t s = ctx->stream;
+    bem_status st;
+    if (ev && (st = record_timing_event(ctx, ev[0]))) return st;
     if (b.n_far > 0) {
-        const int prof = prof_start(ctx, BEM_KERNEL_FAR, b.far_entries);
         switch (b.variant) {
         case 0: far_batch_launch<T, 32, 256>(b, s); break;
         case 1: far_batch_launch<T, 16, 256>(b, s); break;
@@ -916,28 +929,28 @@ static bem_status batch_assemble_t(bem_ctx *ctx, const BatchAsm &b)
         default: far_batch_launch<T, 32, 128, 6, true>(b, s); break;
         }
         BEM_COUNT(ctx);
-        prof_stop(ctx, prof);
         BEM_CK_LAUNCH(ctx);
     }
+    if (ev && (st = record_timing_event(ctx, ev[1]))) return st;
     if (b.n_mirror > 0) {
         k_mirror_batch<T><<<(unsigned)b.n_mirror, dim3(32, 8), 0, s>>>(b.prob, b.mirror_pref, b.P); BEM_COUNT(ctx);
         BEM_CK_LAUNCH(ctx);
     }
+    if (ev && (st = record_timing_event(ctx, ev[2]))) return st;
     if (b.n_near > 0) {
-        const int prof = prof_start(ctx, BEM_KERNEL_NEAR, (double)b.n_near);
         k_near_batch<T><<<nblk(b.n_near, 128), 128, 0, s>>>(b.prob, b.near_pref, b.P, b.n_near, b.ss_order);
         BEM_COUNT(ctx);
-        prof_stop(ctx, prof);
         BEM_CK_LAUNCH(ctx);
     }
+    if (ev && (st = record_timing_event(ctx, ev[3]))) return st;
     return BEM_OK;
 }
 
-bem_status batch_assemble(bem_ctx *ctx, const BatchAsm &b)
+bem_status batch_assemble(bem_ctx *ctx, const BatchAsm &b, cudaEvent_t *ev)
 {
-    if (b.precision == BEM_PREC_F64) return batch_assemble_t<double>(ctx, b);
-    if (b.precision == BEM_PREC_DF64) return batch_assemble_t<float2>(ctx, b);
-    return batch_assemble_t<float>(ctx, b);
+    if (b.precision == BEM_PREC_F64) return batch_assemble_t<double>(ctx, b, ev);
+    if (b.precision == BEM_PREC_DF64) return batch_assemble_t<float2>(ctx, b, ev);
+    return batch_assemble_t<float>(ctx, b, ev);
 }
 
 bem_status assembly_prepare(bem_ctx *ctx) { return assembly_constants(ctx); }

@@ -63,6 +63,10 @@ struct bem_ctx {
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory for scalar readbacks
     cudaEvent_t ev[8] = {};
     int8_t far_tile[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // autotuned variant
+    // adaptive loop: pinned per-level result slots (16 doubles each) and timing events
+    double *h_levels = nullptr;
+    int h_levels_cap = 0;
+    std::vector<cudaEvent_t> lvl_ev;
     int64_t bar_limit_ns = 0;   // persistent solver: grid-barrier wait limit (0: default)
     int32_t bar_absent_cta = -1;  // failure-detection tests: CTA that leaves at its first barrier
 };
@@ -150,6 +154,8 @@ bem_status dev_out_end(bem_ctx *ctx, void *dst, DevBuf &buf);
 // returns the total through a synchronous read when total != nullptr.
 bem_status exclusive_scan_i32(bem_ctx *ctx, const int32_t *in, int32_t *out, int64_t n,
                               int64_t *total);
+// Read n (<= 64) int32 device scalars with one synchronisation of the stream.
+bem_status read_i32s(bem_ctx *ctx, const int32_t *const *src, int n, int64_t *out);
 
 // ----------------------------------------------------------------- mesh (mesh.cu)
 // Build every derived array of a mesh whose verts / tris are already on the device.
@@ -196,26 +202,54 @@ int far_variant_rows(int v);
 int far_variant_cols(int v);
 // Host: append the far-field tiles (i <= j part) of problem p of size N for tile variant v.
 void batch_far_items(int v, int p, int64_t N, std::vector<int4> &items);
-// Enqueue the far field, the mirror and the near field of every problem of b.
-bem_status batch_assemble(bem_ctx *ctx, const BatchAsm &b);
+// Enqueue the far field, the mirror and the near field of every problem of b; ev
+// (nullable, 4 events) is recorded before the far field, after it, before and after
+// the near field.
+bem_status batch_assemble(bem_ctx *ctx, const BatchAsm &b, cudaEvent_t *ev);
+// Record e on the context's stream so that it also fires in replays of a graph being
+// captured from that stream.
+bem_status record_timing_event(bem_ctx *ctx, cudaEvent_t e);
 // The autotuned far-field variant of (precision, N) in ctx, or -1 while not timed.
 int far_cached_variant(const bem_ctx *ctx, int precision, int64_t N);
 
 // ----------------------------------------------------------------- solve (solve.cu)
 bem_status matvec_f64(bem_operator *op, const double *x, double *y);
+// How the algorithmic bytes of a persistent solve are counted once its counts are read.
+struct PersistentRun {
+    int prof = -1;  // profiler record of the launch
+    bool f32op = false, mixed = false, calpc = false;
+    double n2 = 0.0;  // N^2
+};
+// A solve whose results are still travelling to pinned host memory: solve_capacity
+// with a SolveDeferred enqueues the persistent solve, the Cap reduction and the
+// copies of their results to h without synchronising (when the persistent solver
+// runs; other paths finish at once and leave pending false); after any later
+// synchronisation of the context's stream, solve_capacity_end reads them.
+struct SolveDeferred {
+    double *h = nullptr;  // pinned, 8 doubles: [0..4] solver out, [5] barrier error flag, [6] Cap
+    bool pending = false;
+    PersistentRun run;
+    double tol = 0.0;
+};
 bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const double *d_x0,
-                          double *d_x, double *cap, bem_solve_info *info);
+                          double *d_x, double *cap, bem_solve_info *info, SolveDeferred *def = nullptr);
+bem_status solve_capacity_end(bem_ctx *ctx, SolveDeferred &def, double *cap, bem_solve_info *info);
 
 // ----------------------------------------------------------------- adaptivity (adapt.cu)
 bem_status barycentric(bem_mesh *m, bem_mesh **out);
 bem_status dual_operator(bem_operator *ob, bem_mesh *pm, bem_operator **out);
 bem_status zz_estimate_dual(bem_mesh *m, const double *d_x, int h_mode, double *d_eta2, double *h_totals);
+// d_totals (nullable, device, 2 doubles): where the totals are formed (the host copy
+// h_totals, nullable, synchronises the stream).
 bem_status zz_estimate(bem_mesh *m, const double *d_phi, int h_mode, double *d_eta2,
-                       double *h_totals);
+                       double *h_totals, double *d_totals = nullptr);
 // Ascending sort of n2 (a power of two) 64-bit keys on the context's stream.
 void sort_u64(bem_ctx *ctx, unsigned long long *keys, int64_t n2);
+// n_marked (nullable) synchronises the stream; d_vanish (nullable, device: the ZZ
+// totals) marks everything when the estimator vanishes up to rounding; d_count
+// (nullable, device) receives the count without synchronising.
 bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, uint8_t *d_marked,
-                   int64_t *n_marked);
+                   int64_t *n_marked, const double *d_vanish = nullptr, long long *d_count = nullptr);
 bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out);
 
 }  // namespace bem

@@ -102,6 +102,17 @@ static bem_status scan_rec(bem_ctx *ctx, const int32_t *in, int32_t *out, int64_
     return BEM_OK;
 }
 
+bem_status read_i32s(bem_ctx *ctx, const int32_t *const *src, int n, int64_t *out)
+{
+    int32_t *h = reinterpret_cast<int32_t *>(ctx->h_pinned);
+    if (n > 64) return set_error(ctx, BEM_ERR_INVALID, "too many scalars in one read");
+    for (int k = 0; k < n; ++k)
+        BEM_CK(ctx, cudaMemcpyAsync(h + k, src[k], sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    BEM_CK(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < n; ++k) out[k] = h[k];
+    return BEM_OK;
+}
+
 bem_status exclusive_scan_i32(bem_ctx *ctx, const int32_t *in, int32_t *out, int64_t n,
                               int64_t *total)
 {
@@ -399,11 +410,15 @@ bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge)
         if (st) goto done;        \
     } while (0)
     TRY(dalloc(ctx, tmp, (void **)&bad, 4 * sizeof(int32_t), true));
-    k_check_indices<<<nblk(N, 256), 256, 0, s>>>(m->tris, N, M, bad); BEM_COUNT(ctx);
-    TRY(read_bad(ctx, bad, hb));
-    if (hb[0]) {
-        st = set_error(ctx, BEM_ERR_MESH, "triangle with a vertex index outside [0, M) or repeated");
-        goto done;
+    if (canonicalize) {
+        // a caller's mesh: indices checked before any kernel follows them (meshes made
+        // by the library's refinements have valid indices by construction)
+        k_check_indices<<<nblk(N, 256), 256, 0, s>>>(m->tris, N, M, bad); BEM_COUNT(ctx);
+        TRY(read_bad(ctx, bad, hb));
+        if (hb[0]) {
+            st = set_error(ctx, BEM_ERR_MESH, "triangle with a vertex index outside [0, M) or repeated");
+            goto done;
+        }
     }
     if (canonicalize) {
         int32_t *t2 = nullptr;
@@ -452,9 +467,12 @@ bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge)
         k_touch<false><<<nblk(N, 128), 128, 0, s>>>(m->tris, N, m->v2t_off, m->v2t, ne, nv, nullptr,
                                                     nullptr, nullptr, nullptr, 0, 0, bad); BEM_COUNT(ctx);
         BEM_CK_LAUNCH(ctx);
-        int64_t te = 0, tv = 0;
-        TRY(exclusive_scan_i32(ctx, ne, oe, N, &te));
-        TRY(exclusive_scan_i32(ctx, nv, ov, N, &tv));
+        int64_t tt[2] = {0, 0};
+        TRY(exclusive_scan_i32(ctx, ne, oe, N, nullptr));
+        TRY(exclusive_scan_i32(ctx, nv, ov, N, nullptr));
+        const int32_t *src[2] = {oe + N, ov + N};
+        TRY(read_i32s(ctx, src, 2, tt));  // both totals in one read
+        const int64_t te = tt[0], tv = tt[1];
         m->n_edge_pairs = te;
         m->n_vert_pairs = tv;
         TRY(dalloc(ctx, m->allocs, (void **)&m->edge_pairs, sizeof(int32_t) * 2 * (te > 0 ? te : 1), false));

@@ -728,15 +728,16 @@ __device__ __forceinline__ double elem_f64(const float *V, int64_t o) { return (
 // with a non-positive eigenvalue); a block whose factorisation meets a pivot <= 0
 // is replaced by its diagonal, so that M stays symmetric positive definite.
 template <typename T>
-__global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, int64_t ld,
-                                                       const int32_t *__restrict__ perm, double *__restrict__ binv)
+__device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int64_t ld,
+                                                   const int32_t *__restrict__ perm, double *__restrict__ binv,
+                                                   int64_t blk)
 {
     __shared__ float A[kBJ][kBJ + 1];
     __shared__ float B[kBJ][kBJ + 1];
     __shared__ double sc[kBJ], d0[kBJ];
     __shared__ int s_fail;
     const int t = threadIdx.x;
-    const int32_t *pk = perm + (int64_t)blockIdx.x * kBJ;
+    const int32_t *pk = perm + blk * kBJ;
     if (t == 0) s_fail = 0;
     __syncthreads();
     if (t < kBJ) {
@@ -770,7 +771,7 @@ __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, 
         }
         __syncthreads();
     }
-    double *out = binv + (int64_t)blockIdx.x * kBJ * kBJ;
+    double *out = binv + blk * kBJ * kBJ;
     if (s_fail) {  // diagonal block (Jacobi)
         for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
             const int i = idx / kBJ, j = idx % kBJ;
@@ -800,6 +801,13 @@ __global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, 
         out[i * kBJ + j] = v;
         out[j * kBJ + i] = v;
     }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_block_inverse(const T *__restrict__ V, int64_t ld,
+                                                       const int32_t *__restrict__ perm, double *__restrict__ binv)
+{
+    block_inverse_body<T>(V, ld, perm, binv, blockIdx.x);
 }
 
 // z = M^-1 r on the rows of cluster blk, by one CTA.  Thread t < 64 handles row t of
@@ -1541,10 +1549,33 @@ static void tridiag_extremes(const std::vector<double> &d, const std::vector<dou
 // product whenever ||r|| has dropped by delta since the last such residual (and at
 // convergence).  Without room for the packed copy in the context's budget the
 // solve runs with DF64 products only.
+// Results of a finished persistent solve from their pinned copy h ([0..4] the
+// solver's out, [5] the barrier error flag).
+static bem_status persistent_results(bem_ctx *ctx, const double *h, const PersistentRun &r, int *its, int *ndf,
+                                     double *rel, bool *inexact)
+{
+    if (*reinterpret_cast<const int *>(h + 5)) return set_error(ctx, BEM_ERR_CUDA, "persistent solve: grid barrier timed out");
+    *inexact = h[4] != 0.0;
+    *its = (int)h[2];
+    *ndf = r.mixed ? (int)h[3] : 1;
+    *rel = std::sqrt(h[0] / (h[1] > 0.0 ? h[1] : 1.0));
+    // algorithmic bytes: a DF64 product reads the upper triangle of V (8 bytes x N^2 /
+    // 2); a mixed-mode iteration reads the packed FP32 upper triangle (4 x N^2 / 2),
+    // written once by the first product (+ the packed FP32 C once per preconditioner
+    // application)
+    const double n2 = r.n2;
+    const double bytes = (r.f32op  ? 2.0 * n2 * (h[2] + h[3])
+                          : r.mixed ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
+                                    : 4.0 * n2 * (h[2] + h[3])) +
+                         (r.calpc ? 2.0 * n2 * (h[2] + h[3]) : 0.0);
+    prof_set_units(ctx, r.prof, bytes);
+    return BEM_OK;
+}
+
 static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, bool has_x0, double tol, int max_it,
                                  int precond, double delta, const int32_t *bperm, const double *binv, int nbj,
                                  double inexact_lambda, int h_mode, int *its_out, int *ndf_out, double *rel_out,
-                                 bool *ran, double *lmin, double *lmax, bool *inexact_out)
+                                 bool *ran, double *lmin, double *lmax, bool *inexact_out, SolveDeferred *def)
 {
     // FP32 operators: the products of the iteration and of the residuals read the
     // packed copy of the stored operator (the residual, formed from x with
@@ -1666,32 +1697,30 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
         dfree_all(ctx, tmp);
         return BEM_OK;  // not launchable here: fall back
     }
-    double h[5];
-    e = cudaMemcpyAsync(ctx->h_pinned, out, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->h_pinned + 5, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    // the solver's out[0..4] and its barrier error flag to pinned host memory: read
+    // now (synchronous solve), or after a later synchronisation of the stream
+    // (deferred: the caller finishes the solve with solve_capacity_end)
+    double *hres = def ? def->h : ctx->h_pinned;
+    PersistentRun run;
+    run.prof = prof;
+    run.f32op = f32op;
+    run.mixed = vp != nullptr;
+    run.calpc = calpc;
+    run.n2 = (double)op->N * (double)op->N;
+    e = cudaMemcpyAsync(hres, out, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hres + 5, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess && !def) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) st = cuda_error(ctx, e, "persistent solve");
-    if (!st) {
-        memcpy(h, ctx->h_pinned, sizeof(h));
-        const int err_h = *reinterpret_cast<int *>(ctx->h_pinned + 5);
-        if (err_h) {
-            st = set_error(ctx, BEM_ERR_CUDA, "persistent solve: grid barrier timed out");
-        } else {
+    if (!st && def) {
+        def->run = run;
+        *ran = true;
+        *lmin = *lmax = 0.0;  // no condition estimates for deferred solves
+    } else if (!st) {
+        double h[6];
+        memcpy(h, hres, sizeof(h));
+        st = persistent_results(ctx, h, run, its_out, ndf_out, rel_out, inexact_out);
+        if (!st) {
             *ran = true;
-            *inexact_out = h[4] != 0.0;
-            *its_out = (int)h[2];
-            *ndf_out = vp ? (int)h[3] : 1;
-            *rel_out = std::sqrt(h[0] / (h[1] > 0.0 ? h[1] : 1.0));
-            // algorithmic bytes: a DF64 product reads the upper triangle of V
-            // (8 bytes x N^2 / 2); a mixed-mode iteration reads the packed FP32 upper
-            // triangle (4 x N^2 / 2), written once by the first product
-            const double n2 = (double)op->N * (double)op->N;
-            // (+ the packed FP32 C once per preconditioner application)
-            const double bytes = (f32op ? 2.0 * n2 * (h[2] + h[3])
-                                  : vp  ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
-                                        : 4.0 * n2 * (h[2] + h[3])) +
-                                 (calpc ? 2.0 * n2 * (h[2] + h[3]) : 0.0);
-            prof_set_units(ctx, prof, bytes);
             // Lanczos tridiagonal matrix of the CG coefficients
             const int k = std::min((int)h[2] - (h[4] != 0.0 ? 1 : 0), lcap);  // an inexact stop records no beta
             *lmin = *lmax = 0.0;
@@ -1724,9 +1753,32 @@ __global__ void k_capacity(int64_t N, const double *area, const double *x, doubl
     if (threadIdx.x == 0) out[0] = part[0] * kInv4Pi;
 }
 
-bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const double *d_x0, double *d_x,
-                          double *cap, bem_solve_info *info)
+bem_status solve_capacity_end(bem_ctx *ctx, SolveDeferred &def, double *cap, bem_solve_info *info)
 {
+    if (!def.pending) return BEM_OK;
+    def.pending = false;
+    int its = 0, ndf = 0;
+    double rel = 0.0;
+    bool inexact = false;
+    bem_status st = persistent_results(ctx, def.h, def.run, &its, &ndf, &rel, &inexact);
+    if (st) return st;
+    *cap = def.h[6];
+    if (info) {
+        info->iterations = its;
+        info->outer = ndf;
+        info->relres = rel;
+        info->converged = rel <= def.tol || inexact;
+        info->lambda_min = info->lambda_max = 0.0;
+    }
+    if (rel > def.tol && !inexact)
+        return set_error(ctx, BEM_ERR_NOT_CONVERGED, "solve stopped at relative residual %.3e > %.3e", rel, def.tol);
+    return BEM_OK;
+}
+
+bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const double *d_x0, double *d_x,
+                          double *cap, bem_solve_info *info, SolveDeferred *def)
+{
+    if (def) def->pending = false;
     bem_mesh *m = op->mesh;
     bem_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
@@ -1804,7 +1856,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         if (op->precision != BEM_PREC_F64 && ctx->persistent_solver)
             st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, bperm,
                                 binv, nbj, o->inexact_lambda, o->h_mode, &its, &outer, &rel, &ran, &lam_min, &lam_max,
-                                &inexact);
+                                &inexact, def);
         if (!st && !ran && (precond == BEM_PRECOND_BLOCK || precond == BEM_PRECOND_CALDERON))
             st = set_error(ctx, BEM_ERR_CUDA, "this preconditioner needs the persistent solver, which could not be launched");
         if (st) goto out;
@@ -1862,6 +1914,13 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
             e = cudaMemcpyAsync(d_x, W.x, sizeof(double) * N, cudaMemcpyDeviceToDevice, s);
             if (e != cudaSuccess) { st = cuda_error(ctx, e, "solution copy"); goto out; }
         }
+        if (def && ran) {  // deferred: Cap joins the solver's results in pinned memory
+            e = cudaMemcpyAsync(def->h + 6, W.scal + 6, sizeof(double), cudaMemcpyDeviceToHost, s);
+            if (e != cudaSuccess) { st = cuda_error(ctx, e, "Cap copy"); goto out; }
+            def->pending = true;
+            def->tol = tol;
+            goto out;
+        }
         double c;
         if ((st = read_scalars(ctx, W.scal + 6, 1, &c))) goto out;
         *cap = c;
@@ -1882,72 +1941,175 @@ out:
 }
 
 // ------------------------------------------------------------------ batch
-// Independent problems assembled and solved together (bem_batch_*): everything a run
-// needs is allocated at creation; a run enqueues the assembly kernels of every
-// problem, one cooperative launch of k_pcg_batch for all solves, the capacities, and
-// one copy of the results to pinned host memory.  With use_graph the first run
-// records that sequence as a CUDA graph on the batch's stream and later runs replay
-// it.
+// Independent problems assembled and solved together (bem_batch_*).  The problems are
+// cut, in their given order, into waves whose device memory fits the budget (the
+// context's HBM budget and the device's free memory, read at creation); one arena
+// sized for the largest wave holds the operators and solver state of whichever wave
+// runs, and a wave is one launch per phase for all its problems: the batched far
+// field (a work list of (problem, tile) items), mirror and near field, the set-up of
+// diagonals, right-hand sides and preconditioners, ONE cooperative launch of the
+// persistent solver in which every problem owns a share of the CTAs, the capacities,
+// and a copy of the results to pinned host memory.  With use_graph each wave's
+// sequence is recorded once as a CUDA graph (its arena layout is fixed) and replayed
+// by later runs; the waves of a run follow each other on the batch's stream.
+struct BatchSolveProb {
+    const void *V;
+    int64_t ld, N;
+    double *d, *b, *x;
+    const double *area;
+    double *part;
+    int64_t part_n;  // doubles of part zeroed per run
+    float *vp;       // packed FP32 upper triangle (FP32 operators: formed per run)
+    const int2 *tiles;
+    int64_t nt;
+    const int32_t *perm;
+    double *binv;
+    int nbj;
+    double *res;     // kBatchRes doubles: out[0..4] of the solver, [5] Cap, [6] error flag
+};
+
+constexpr int kBatchRes = 8;
+
+// Per run, after the assembly: x = 0, the diagonal, b = |T|, zero padding columns
+// of V, zero partials, barrier counter and results.  Grid (rows / 256, problems).
+template <typename T>
+__global__ void k_batch_init(const BatchSolveProb *__restrict__ prob)
+{
+    const BatchSolveProb *pb = prob + blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t N = pb->N, ld = pb->ld;
+    if (i < ld) {
+        pb->x[i] = 0.0;
+        if (i < N) {
+            T *V = (T *)pb->V;
+            pb->d[i] = elem_f64(V, i * ld + i);
+            pb->b[i] = pb->area[i];
+            for (int64_t j = N; j < ld; ++j) V[i * ld + j] = T();
+        }
+    }
+    if (i < pb->part_n) pb->part[i] = 0.0;
+    if (i < kBatchRes) pb->res[i] = 0.0;
+}
+
+// Packed upper triangles of FP32 operators; grid (blocks, problems).
+__global__ void k_batch_pack(const BatchSolveProb *__restrict__ prob)
+{
+    const BatchSolveProb *pb = prob + blockIdx.y;
+    const int64_t n4 = pb->nt * (kTileF / 4);
+    const float *V = (const float *)pb->V;
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < n4; f += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = f / (kTileF / 4);
+        const int e = (int)(f % (kTileF / 4)), r = e >> 4, c4 = e & 15;
+        const int2 tj = pb->tiles[k];
+        const int64_t row = (int64_t)tj.x * kSB + r;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (row < pb->N) v = __ldcs(reinterpret_cast<const float4 *>(V + row * pb->ld + (int64_t)tj.y * kSB) + c4);
+        reinterpret_cast<float4 *>(pb->vp)[f] = v;
+    }
+}
+
+// Inverse cluster blocks of every problem; grid (largest cluster count, problems).
+template <typename T>
+__global__ void __launch_bounds__(256) k_batch_block_inverse(const BatchSolveProb *__restrict__ prob)
+{
+    const BatchSolveProb *pb = prob + blockIdx.y;
+    if ((int)blockIdx.x >= pb->nbj) return;
+    block_inverse_body<T>((const T *)pb->V, pb->ld, pb->perm, pb->binv, blockIdx.x);
+}
+
+// Cap = (1/4pi) sum |T_i| x_i of every problem (Eq. 2.8); one CTA per problem.
+__global__ void k_batch_capacity(const BatchSolveProb *__restrict__ prob)
+{
+    const BatchSolveProb *pb = prob + blockIdx.x;
+    double v = 0.0;
+    for (int64_t i = threadIdx.x; i < pb->N; i += blockDim.x) v += pb->area[i] * pb->x[i];
+    // the fixed tree of block_partial (warps, then the warp sums), kept in this CTA
+    __shared__ double sw[32];
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sw[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        double t = lane < (int)(blockDim.x >> 5) ? sw[lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0) pb->res[5] = t * kInv4Pi;
+    }
+}
+
 struct BatchProblem {
-    bem_operator *op = nullptr;
-    double *b = nullptr, *d = nullptr, *x = nullptr, *part = nullptr;
-    size_t part_bytes = 0;
-    float *vp = nullptr;
-    int32_t *perm = nullptr;
-    double *binv = nullptr;
+    bem_operator *op = nullptr;  // V and diag in the arena (the handle owns no memory)
+    int wave = 0;
+    size_t off = 0;              // offset of this problem's block in the arena
+    size_t bytes = 0;
+    int64_t nt = 0;
+    int2 *tiles = nullptr;       // persistent tile list
+    int32_t *perm = nullptr;     // persistent cluster order (block preconditioner)
     int nbj = 0;
+};
+
+struct BatchWave {
+    int first = 0, count = 0, G = 0, variant = 0, max_nbj = 0;
+    int64_t max_rows = 0;
+    std::vector<int> begin;
+    PcgArgs *d_args = nullptr;
+    int *d_begin = nullptr;
+    BatchSolveProb *d_sprob = nullptr;
+    BatchAsm asmb;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;        // kernels of one replay
+    // recorded around the far field (0, 1), the near field (2, 3) and the solver
+    // launch (4, 5) of every run, captured into the graph too, so that profiling sees
+    // the replayed runs themselves
+    cudaEvent_t ev[6] = {};
 };
 
 }  // namespace bem
 
 struct bem_batch {
     bem_ctx *ctx = nullptr;
-    int P = 0, use_graph = 1, graph_used = 0, G = 0, precond = BEM_PRECOND_JACOBI;
+    int P = 0, use_graph = 1, graph_used = 0, precond = BEM_PRECOND_JACOBI, precision = BEM_PREC_F32;
     double tol = 1e-10;
-    int64_t launches_per_run = 0;
-    int prof_solve = -1;  // profiler record of the solver launch (direct runs with profiling on)
+    void *arena = nullptr;
+    size_t arena_bytes = 0;
     std::vector<bem::BatchProblem> prob;
-    std::vector<bem::PcgArgs> args;
-    std::vector<int> begin;
-    bem::PcgArgs *d_args = nullptr;
-    int *d_begin = nullptr;
-    double *d_res = nullptr;  // P x 8: out[0..4] of the solver, [5] Cap, [6] error flag (int)
+    std::vector<bem::PcgArgs> args;  // per problem (pointers into the arena)
+    std::vector<bem::BatchWave> waves;
+    double *d_res = nullptr;  // P x kBatchRes
     double *h_res = nullptr;  // pinned copy
     cudaStream_t stream = nullptr;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     bem::Allocs allocs;
 };
 
 namespace bem {
 
-constexpr int kBatchRes = 8;
-
-static bem_status batch_enqueue(bem_batch *bt)
+static bem_status batch_enqueue(bem_batch *bt, BatchWave &w)
 {
     bem_ctx *ctx = bt->ctx;
     cudaStream_t s = ctx->stream;
     bem_status st;
-    for (auto &pr : bt->prob)
-        if ((st = assemble_full(pr.op))) return st;
-    BEM_CK(ctx, cudaMemsetAsync(bt->d_res, 0, sizeof(double) * kBatchRes * bt->P, s));
-    for (auto &pr : bt->prob) {
-        bem_operator *op = pr.op;
-        const int64_t N = op->N;
-        BEM_CK(ctx, cudaMemcpyAsync(pr.b, op->mesh->area, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-        BEM_CK(ctx, cudaMemcpyAsync(pr.d, op->diag, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
-        BEM_CK(ctx, cudaMemsetAsync(pr.x, 0, sizeof(double) * op->ld, s));
-        BEM_CK(ctx, cudaMemsetAsync(pr.part, 0, pr.part_bytes, s));
-        if (op->precision == BEM_PREC_F32) {
-            const int nb = (int)(op->ld / kSB), nt = nb * (nb + 1) / 2;
-            k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256,
-                         0, s>>>((const float *)op->V, op->ld, N, bt->args[&pr - &bt->prob[0]].tiles, nt, pr.vp); BEM_COUNT(ctx);
-        }
-        if (bt->precond == BEM_PRECOND_BLOCK && (st = block_inverse_launch(op, pr.perm, pr.nbj, pr.binv))) return st;
+    if ((st = batch_assemble(ctx, w.asmb, w.ev))) return st;
+    const dim3 gi((unsigned)((w.max_rows + 255) / 256), (unsigned)w.count);
+    if (bt->precision == BEM_PREC_F32)
+        k_batch_init<float><<<gi, 256, 0, s>>>(w.d_sprob);
+    else
+        k_batch_init<float2><<<gi, 256, 0, s>>>(w.d_sprob);
+    BEM_COUNT(ctx);
+    if (bt->precision == BEM_PREC_F32) {
+        k_batch_pack<<<dim3(64, (unsigned)w.count), 256, 0, s>>>(w.d_sprob); BEM_COUNT(ctx);
     }
+    if (bt->precond == BEM_PRECOND_BLOCK) {
+        const dim3 gb((unsigned)w.max_nbj, (unsigned)w.count);
+        if (bt->precision == BEM_PREC_F32)
+            k_batch_block_inverse<float><<<gb, 256, 0, s>>>(w.d_sprob);
+        else
+            k_batch_block_inverse<float2><<<gb, 256, 0, s>>>(w.d_sprob);
+        BEM_COUNT(ctx);
+    }
+    BEM_CK_LAUNCH(ctx);
     {
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)bt->G);
+        cfg.gridDim = dim3((unsigned)w.G);
         cfg.blockDim = dim3(kSymThreads);
         cfg.dynamicSmemBytes = kSymSmem;
         cfg.stream = s;
@@ -1956,19 +2118,31 @@ static bem_status batch_enqueue(bem_batch *bt)
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        bt->prof_solve = prof_start(ctx, BEM_KERNEL_MATVEC, 0.0);  // bytes set once the counts are read
-        BEM_CK(ctx, cudaLaunchKernelEx(&cfg, k_pcg_batch, (const PcgArgs *)bt->d_args, (const int *)bt->d_begin,
-                                       bt->P));
+        if ((st = record_timing_event(ctx, w.ev[4]))) return st;
+        BEM_CK(ctx, cudaLaunchKernelEx(&cfg, k_pcg_batch, (const PcgArgs *)w.d_args, (const int *)w.d_begin, w.count));
         BEM_COUNT(ctx);
-        prof_stop(ctx, bt->prof_solve);
+        if ((st = record_timing_event(ctx, w.ev[5]))) return st;
     }
-    for (int p = 0; p < bt->P; ++p) {
-        bem_operator *op = bt->prob[p].op;
-        k_capacity<<<1, 1024, 0, s>>>(op->N, op->mesh->area, bt->prob[p].x, bt->d_res + kBatchRes * p + 5); BEM_COUNT(ctx);
-    }
+    k_batch_capacity<<<w.count, 1024, 0, s>>>(w.d_sprob); BEM_COUNT(ctx);
     BEM_CK_LAUNCH(ctx);
-    BEM_CK(ctx, cudaMemcpyAsync(bt->h_res, bt->d_res, sizeof(double) * kBatchRes * bt->P, cudaMemcpyDeviceToHost, s));
+    BEM_CK(ctx, cudaMemcpyAsync(bt->h_res + (size_t)kBatchRes * w.first, bt->d_res + (size_t)kBatchRes * w.first,
+                                sizeof(double) * kBatchRes * w.count, cudaMemcpyDeviceToHost, s));
     return BEM_OK;
+}
+
+// Device bytes of one problem's block in the arena: V, diagonal, 7 solver vectors, the
+// double-float copy of the product's input, the tile partials of the product, the
+// packed FP32 upper triangle, the CTA partials and the inverse cluster blocks.
+static size_t batch_problem_bytes(int64_t N, int prec, bool packed, bool block, int G)
+{
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const int64_t L = padded_ld(N), nb = L / kSB, nt = nb * (nb + 1) / 2;
+    const size_t es = prec == BEM_PREC_F32 ? 4 : 8;
+    size_t b = al(es * (size_t)N * (size_t)L) + al(8 * (size_t)N) + al(8 * 7 * (size_t)L) + al(8 * (size_t)L) +
+               al(2 * (size_t)nt * kSB * 8) + al(sizeof(double) * (3 * (size_t)G + 8) + 64);
+    if (packed) b += al((size_t)nt * kTileF * 4);
+    if (block) b += al(8 * (size_t)kBJ * kBJ * (size_t)((N + kBJ - 1) / kBJ));
+    return b;
 }
 
 }  // namespace bem
@@ -1988,14 +2162,17 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
     if (precond < BEM_PRECOND_NONE || precond > BEM_PRECOND_BLOCK)
         return set_error(ctx, BEM_ERR_INVALID, "preconditioner %d: a batch takes NONE, JACOBI or BLOCK", precond);
     for (int p = 0; p < count; ++p)
-        if (!meshes[p] || meshes[p]->ctx != ctx) return set_error(ctx, BEM_ERR_INVALID, "mesh %d is not of this context", p);
+        if (!meshes[p] || meshes[p]->ctx != ctx || meshes[p]->cells_only)
+            return set_error(ctx, BEM_ERR_INVALID, "mesh %d is not a triangle mesh of this context", p);
+    const int ss = (aopts && aopts->ss_order > 0) ? aopts->ss_order : 4;
+    if (ss < 2 || ss > kMaxSS) return set_error(ctx, BEM_ERR_INVALID, "ss_order outside 2..16");
     int coop = 0, per_sm = 0;
     BEM_CK(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
     if (!coop) return set_error(ctx, BEM_ERR_CUDA, "the device has no cooperative launch");
     BEM_CK(ctx, cudaFuncSetAttribute(k_pcg_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
     BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_batch, kSymThreads, kSymSmem));
     const int Gmax = (per_sm < 3 ? per_sm : 3) * ctx->sm_count;
-    if (count > Gmax) return set_error(ctx, BEM_ERR_INVALID, "at most %d problems per batch on this device", Gmax);
+    if (Gmax < 1) return set_error(ctx, BEM_ERR_CUDA, "the batch solver cannot be resident on this device");
     bem_status st = assembly_prepare(ctx);
     if (st) return st;
     BEM_CK(ctx, cudaStreamSynchronize(ctx->stream));  // meshes built on the context's stream
@@ -2005,131 +2182,317 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
     bt->P = count;
     bt->use_graph = use_graph ? 1 : 0;
     bt->precond = precond;
+    bt->precision = prec;
     bt->tol = (sopts && sopts->tol > 0) ? sopts->tol : 1e-10;
     const int max_it = (sopts && sopts->max_it > 0) ? sopts->max_it : 10000;
     const double rd = sopts ? sopts->reliable_delta : 0.0;
     const double delta = rd == 0.0 ? 1e-4 : (rd > 0.0 && rd < 1.0 ? rd : 0.0);
+    const bool packed = prec == BEM_PREC_F32 || delta > 0.0;
+    const bool block = precond == BEM_PRECOND_BLOCK;
     bt->prob.resize(count);
     bt->args.resize(count);
-    // CTAs per problem in proportion to its bytes per product (N^2; iteration counts
-    // are alike), at least one, at most what the single-problem rule can use (a tile
-    // per warp, 8 rows per warp), so that the problems finish at about the same time
-    std::vector<int64_t> want(count);
-    double wsum = 0.0;
-    for (int p = 0; p < count; ++p) {
-        const int64_t N = meshes[p]->N, nb = padded_ld(N) / kSB, nt = nb * (nb + 1) / 2;
-        want[p] = std::min<int64_t>(std::max<int64_t>(std::max<int64_t>((nt + 7) / 8, (N + 63) / 64), 1), Gmax);
-        wsum += (double)N * (double)N;
-    }
-    std::vector<int> g(count);
-    int gsum = 0;
-    for (int p = 0; p < count; ++p) {
-        const double N = (double)meshes[p]->N;
-        const int64_t share = (int64_t)((double)(Gmax - count) * N * N / wsum) + 1;
-        g[p] = (int)std::min<int64_t>(share, want[p]);
-        gsum += g[p];
-    }
-    while (gsum > Gmax) {  // rounding: take from the largest
-        int pm = 0;
-        for (int p = 1; p < count; ++p)
-            if (g[p] > g[pm]) pm = p;
-        --g[pm];
-        --gsum;
-    }
-    bt->begin.assign(count + 1, 0);
-    for (int p = 0; p < count; ++p) bt->begin[p + 1] = bt->begin[p] + g[p];
-    bt->G = bt->begin[count];
+    auto fail = [&](bem_status code) {
+        bem_batch_destroy(bt);
+        return code;
+    };
+    // persistent per-problem data: tile lists, cluster orders, results
     for (int p = 0; p < count && !st; ++p) {
         BatchProblem &pr = bt->prob[p];
-        st = new_operator(meshes[p], aopts, &pr.op);
-        if (st) break;
-        bem_operator *op = pr.op;
-        // far-field tiles of this size class timed now: a run may be captured as a graph
-        if ((st = far_tune(op))) break;
-        const int64_t N = op->N, L = op->ld;
-        const int nb = (int)(L / kSB), nt = nb * (nb + 1) / 2;
-        double *vec = nullptr;
-        float2 *xdf = nullptr, *prow = nullptr, *pcol = nullptr;
-        int2 *tiles = nullptr;
-        void *scr = nullptr;
-        const int Gp = g[p];
-        pr.part_bytes = sizeof(double) * (3 * Gp + 8) + 64;
-        if ((st = dalloc(ctx, bt->allocs, (void **)&vec, sizeof(double) * 7 * L, true))) break;
-        if ((st = dalloc(ctx, bt->allocs, (void **)&xdf, sizeof(float2) * L, true))) break;
-        if ((st = dalloc(ctx, bt->allocs, &scr, symv_scratch_bytes(op), false))) break;
-        if ((st = symv_setup(op, scr, &prow, &pcol, &tiles))) break;
-        if ((st = dalloc(ctx, bt->allocs, (void **)&pr.vp, (size_t)nt * kTileF * sizeof(float), false))) break;
-        if ((st = dalloc(ctx, bt->allocs, (void **)&pr.part, pr.part_bytes, true))) break;
-        if (precond == BEM_PRECOND_BLOCK) {
-            if ((st = cluster_setup(op, bt->allocs, &pr.perm, &pr.nbj))) break;
-            if ((st = dalloc(ctx, bt->allocs, (void **)&pr.binv, sizeof(double) * kBJ * kBJ * pr.nbj, false))) break;
-        }
-        pr.x = vec + 5 * L;
-        pr.b = vec + 4 * L;
-        pr.d = vec + 6 * L;
-        PcgArgs &a = bt->args[p];
-        a.V = prec == BEM_PREC_DF64 ? (const float2 *)op->V : nullptr;
-        a.ld = L;
-        a.N = N;
-        a.nb = nb;
-        a.ntiles = nt;
-        a.tiles = tiles;
-        a.prow = prow;
-        a.pcol = pcol;
-        a.pdf = xdf;
-        a.r = vec;
-        a.z = vec + L;
-        a.p = vec + 2 * L;
-        a.q = vec + 3 * L;
-        a.b = pr.b;
-        a.x = pr.x;
-        a.d = pr.d;
-        a.part = pr.part;
-        double *outp = pr.part + 3 * Gp;
-        a.ctr = reinterpret_cast<unsigned long long *>(outp + 4);
-        a.bar = reinterpret_cast<unsigned *>(a.ctr + 1);
-        a.out = nullptr;  // set below (d_res)
-        a.err = nullptr;
-        a.vp = pr.vp;
-        a.bperm = pr.perm;
-        a.binv = pr.binv;
-        a.nbj = pr.nbj;
-        a.tol = bt->tol;
-        a.f32op = prec == BEM_PREC_F32 ? 1 : 0;
-        a.delta2 = a.f32op ? 0.0 : (delta > 0.0 ? delta * delta : 0.0);
-        a.max_it = max_it;
-        a.precond = precond;
-        a.has_x0 = 0;
-        a.bar_limit_ns = ctx->bar_limit_ns;
-        a.absent_cta = -1;
-        a.dvp = nullptr;
-        a.lanczos = nullptr;
-        a.lanczos_cap = 0;
-        a.lam2 = 0.0;
-        if (!a.f32op && delta <= 0.0) a.vp = nullptr;  // DF64 products only
+        const int64_t N = meshes[p]->N, nb = padded_ld(N) / kSB;
+        pr.nt = nb * (nb + 1) / 2;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&pr.tiles, sizeof(int2) * (size_t)pr.nt, false))) break;
+        k_tile_list<<<(unsigned)nb, 128, 0, ctx->stream>>>((int)nb, pr.tiles); BEM_COUNT(ctx);
     }
     if (!st) st = dalloc(ctx, bt->allocs, (void **)&bt->d_res, sizeof(double) * kBatchRes * count, true);
-    if (!st) st = dalloc(ctx, bt->allocs, (void **)&bt->d_args, sizeof(PcgArgs) * count, false);
-    if (!st) st = dalloc(ctx, bt->allocs, (void **)&bt->d_begin, sizeof(int) * (count + 1), false);
-    if (!st) {
+    if (st) return fail(st);
+    // waves: problems in their order, a new wave when the next one does not fit the
+    // memory left for the arena or the CTAs of one cooperative launch
+    int64_t avail = 0;
+    {
+        cudaError_t e = cudaStreamSynchronize(ctx->stream);
+        if (e == cudaSuccess) e = cudaMemPoolTrimTo(ctx->pool, 0);
+        size_t fr = 0, tot = 0;
+        if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
+        if (e != cudaSuccess) return fail(cuda_error(ctx, e, "batch memory query"));
+        // room for what is allocated after the arena: the far-field work lists (bounded
+        // by the smallest tile, 8 x 64), the cluster orders and the wave tables
+        double later = 4.0 * 1048576.0;
         for (int p = 0; p < count; ++p) {
-            bt->args[p].out = bt->d_res + kBatchRes * p;
-            bt->args[p].err = reinterpret_cast<int *>(bt->d_res + kBatchRes * p + 6);
+            const double N = (double)meshes[p]->N;
+            int64_t n2 = 2;
+            while (n2 < meshes[p]->N) n2 <<= 1;
+            later += 16.0 * (N * N / 1024.0 + N / 8.0 + 2.0) + 1024.0 + sizeof(PcgArgs) + 512.0;
+            if (block) later += 8.0 * (double)n2 + 4.0 * kBJ * std::ceil(N / kBJ) + 6.0 * 8.0 * 80.0 + 1024.0;
         }
-        cudaError_t e = cudaMemcpyAsync(bt->d_args, bt->args.data(), sizeof(PcgArgs) * count, cudaMemcpyHostToDevice,
-                                        ctx->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(bt->d_begin, bt->begin.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
-                                ctx->stream);
-        if (e == cudaSuccess) e = cudaMallocHost((void **)&bt->h_res, sizeof(double) * kBatchRes * count);
+        avail = (int64_t)((double)fr * 0.9) - (int64_t)later;
+        if (ctx->budget > 0) avail = std::min<int64_t>(avail, ctx->budget - ctx->in_use - (int64_t)later);
+    }
+    // CTA share of each problem (within its wave, below) needs the wave; size the
+    // partials for the largest share a problem can get
+    {
+        int w = 0, n_in = 0;
+        size_t wbytes = 0, maxw = 0;
+        for (int p = 0; p < count; ++p) {
+            const size_t b = batch_problem_bytes(meshes[p]->N, prec, packed, block, Gmax);
+            if ((int64_t)b > avail) {
+                return fail(set_error(ctx, BEM_ERR_OOM,
+                                      "problem %d (N = %lld) needs %zu bytes, more than the %lld available to a wave",
+                                      p, (long long)meshes[p]->N, b, (long long)avail));
+            }
+            if (n_in > 0 && ((int64_t)(wbytes + b) > avail || n_in == Gmax)) {
+                ++w;
+                n_in = 0;
+                wbytes = 0;
+            }
+            bt->prob[p].wave = w;
+            bt->prob[p].off = wbytes;
+            bt->prob[p].bytes = b;
+            wbytes += b;
+            ++n_in;
+            maxw = std::max(maxw, wbytes);
+        }
+        bt->waves.resize(w + 1);
+        for (int p = 0; p < count; ++p) {
+            BatchWave &wv = bt->waves[bt->prob[p].wave];
+            if (wv.count == 0) wv.first = p;
+            ++wv.count;
+        }
+        bt->arena_bytes = maxw;
+        if ((st = dalloc(ctx, bt->allocs, &bt->arena, maxw, false))) return fail(st);
+    }
+    // operator handles over the arena; far-field tiles timed per size class now (a
+    // run may be captured as a graph); cluster orders
+    for (int p = 0; p < count && !st; ++p) {
+        BatchProblem &pr = bt->prob[p];
+        bem_operator *op = new (std::nothrow) bem_operator();
+        if (!op) {
+            st = set_error(ctx, BEM_ERR_OOM, "host allocation");
+            break;
+        }
+        pr.op = op;
+        op->mesh = meshes[p];
+        op->ctx = ctx;
+        op->precision = prec;
+        op->ss_order = ss;
+        op->tile = aopts ? aopts->tile : 0;
+        op->N = meshes[p]->N;
+        op->ld = padded_ld(op->N);
+        char *base = static_cast<char *>(bt->arena) + pr.off;
+        op->V = base;
+        const size_t es = prec == BEM_PREC_F32 ? 4 : 8;
+        op->diag = reinterpret_cast<double *>(base + (es * (size_t)op->N * op->ld + 255) / 256 * 256);
+        if (op->tile < 0 || op->tile > BEM_FAR_TILE_VARIANTS) {
+            st = set_error(ctx, BEM_ERR_INVALID, "tile outside 0..BEM_FAR_TILE_VARIANTS");
+            break;
+        }
+        if ((st = far_tune(op))) break;
+        if (block && (st = cluster_setup(op, bt->allocs, &pr.perm, &pr.nbj))) break;
+    }
+    if (st) return fail(st);
+    // per wave: CTA shares, solver arguments, device tables and work lists
+    std::vector<int4> items;
+    for (size_t wi = 0; wi < bt->waves.size() && !st; ++wi) {
+        BatchWave &w = bt->waves[wi];
+        const int P = w.count;
+        // CTAs per problem in proportion to its bytes per product (N^2; iteration counts
+        // are alike), at least one, at most what the single-problem rule can use (a tile
+        // per warp, 8 rows per warp), so that the problems finish at about the same time
+        std::vector<int64_t> want(P);
+        double wsum = 0.0;
+        for (int k = 0; k < P; ++k) {
+            const int64_t N = meshes[w.first + k]->N, nt = bt->prob[w.first + k].nt;
+            want[k] = std::min<int64_t>(std::max<int64_t>(std::max<int64_t>((nt + 7) / 8, (N + 63) / 64), 1), Gmax);
+            wsum += (double)N * (double)N;
+        }
+        std::vector<int> g(P);
+        int gsum = 0;
+        for (int k = 0; k < P; ++k) {
+            const double N = (double)meshes[w.first + k]->N;
+            const int64_t share = (int64_t)((double)(Gmax - P) * N * N / wsum) + 1;
+            g[k] = (int)std::min<int64_t>(share, want[k]);
+            gsum += g[k];
+        }
+        while (gsum > Gmax) {  // rounding: take from the largest
+            int km = 0;
+            for (int k = 1; k < P; ++k)
+                if (g[k] > g[km]) km = k;
+            --g[km];
+            --gsum;
+        }
+        w.begin.assign(P + 1, 0);
+        for (int k = 0; k < P; ++k) w.begin[k + 1] = w.begin[k] + g[k];
+        w.G = w.begin[P];
+        std::vector<BatchSolveProb> sp(P);
+        std::vector<BatchAsmProb> ap(P);
+        std::vector<int64_t> mpref(P + 1, 0), npref(P + 1, 0);
+        int64_t nmax = 0;
+        double far_entries = 0.0;
+        for (int k = 0; k < P; ++k) {
+            const int p = w.first + k;
+            BatchProblem &pr = bt->prob[p];
+            bem_operator *op = pr.op;
+            bem_mesh *m = op->mesh;
+            const int64_t N = op->N, L = op->ld;
+            nmax = std::max(nmax, N);
+            auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+            char *cur = static_cast<char *>(bt->arena) + pr.off;
+            const size_t es = prec == BEM_PREC_F32 ? 4 : 8;
+            cur += al(es * (size_t)N * L) + al(8 * (size_t)N);  // V, diag
+            double *vec = reinterpret_cast<double *>(cur);
+            cur += al(8 * 7 * (size_t)L);
+            float2 *xdf = reinterpret_cast<float2 *>(cur);
+            cur += al(8 * (size_t)L);
+            float2 *prow = reinterpret_cast<float2 *>(cur);
+            float2 *pcol = prow + (size_t)pr.nt * kSB;
+            cur += al(2 * (size_t)pr.nt * kSB * 8);
+            double *part = reinterpret_cast<double *>(cur);
+            const size_t part_bytes = sizeof(double) * (3 * (size_t)g[k] + 8) + 64;
+            cur += al(sizeof(double) * (3 * (size_t)Gmax + 8) + 64);
+            float *vp = nullptr;
+            if (packed) {
+                vp = reinterpret_cast<float *>(cur);
+                cur += al((size_t)pr.nt * kTileF * 4);
+            }
+            double *binv = nullptr;
+            if (block) {
+                binv = reinterpret_cast<double *>(cur);
+                cur += al(8 * (size_t)kBJ * kBJ * (size_t)((N + kBJ - 1) / kBJ));
+            }
+            PcgArgs &a = bt->args[p];
+            a = PcgArgs{};
+            a.V = prec == BEM_PREC_DF64 ? (const float2 *)op->V : nullptr;
+            a.ld = L;
+            a.N = N;
+            a.nb = (int)(L / kSB);
+            a.ntiles = (int)pr.nt;
+            a.tiles = pr.tiles;
+            a.prow = prow;
+            a.pcol = pcol;
+            a.pdf = xdf;
+            a.r = vec;
+            a.z = vec + L;
+            a.p = vec + 2 * L;
+            a.q = vec + 3 * L;
+            a.b = vec + 4 * L;
+            a.x = vec + 5 * L;
+            a.d = vec + 6 * L;
+            a.part = part;
+            double *outp = part + 3 * g[k];
+            a.ctr = reinterpret_cast<unsigned long long *>(outp + 4);
+            a.bar = reinterpret_cast<unsigned *>(a.ctr + 1);
+            a.out = bt->d_res + (size_t)kBatchRes * p;
+            a.err = reinterpret_cast<int *>(bt->d_res + (size_t)kBatchRes * p + 6);
+            a.vp = vp;
+            a.bperm = pr.perm;
+            a.binv = binv;
+            a.nbj = pr.nbj;
+            a.tol = bt->tol;
+            a.f32op = prec == BEM_PREC_F32 ? 1 : 0;
+            a.delta2 = a.f32op ? 0.0 : (delta > 0.0 ? delta * delta : 0.0);
+            a.max_it = max_it;
+            a.precond = precond;
+            a.has_x0 = 0;
+            a.bar_limit_ns = ctx->bar_limit_ns;
+            a.absent_cta = -1;
+            BatchSolveProb &q = sp[k];
+            q.V = op->V;
+            q.ld = L;
+            q.N = N;
+            q.d = vec + 6 * L;
+            q.b = vec + 4 * L;
+            q.x = a.x;
+            q.area = m->area;
+            q.part = part;
+            q.part_n = (int64_t)(part_bytes / 8);
+            q.vp = prec == BEM_PREC_F32 ? vp : nullptr;
+            q.tiles = pr.tiles;
+            q.nt = pr.nt;
+            q.perm = pr.perm;
+            q.binv = binv;
+            q.nbj = pr.nbj;
+            q.res = bt->d_res + (size_t)kBatchRes * p;
+            w.max_rows = std::max<int64_t>(w.max_rows, std::max<int64_t>(L, q.part_n));
+            w.max_nbj = std::max(w.max_nbj, pr.nbj);
+            BatchAsmProb &c = ap[k];
+            c.q64 = m->q64;
+            c.q32 = m->q32;
+            c.cent = m->cent;
+            c.qdf = m->qdf;
+            c.verts = m->verts;
+            c.tris = m->tris;
+            c.area = m->area;
+            c.edge_pairs = m->edge_pairs;
+            c.vert_pairs = m->vert_pairs;
+            c.n_edge = m->n_edge_pairs;
+            c.n_vert = m->n_vert_pairs;
+            c.V = op->V;
+            c.ld = L;
+            c.N = N;
+            const int64_t T = (N + 31) / 32;
+            mpref[k + 1] = mpref[k] + T * (T + 1) / 2;
+            npref[k + 1] = npref[k] + N + m->n_vert_pairs + m->n_edge_pairs;
+            far_entries += 0.5 * (double)N * (double)(N + 1);
+        }
+        // one far-field tile for the wave: the autotuned one of its largest size class
+        // (or the requested one)
+        const int tile_req = aopts ? aopts->tile : 0;
+        w.variant = tile_req > 0 ? tile_req - 1 : std::max(0, far_cached_variant(ctx, prec, nmax));
+        items.clear();
+        for (int k = 0; k < P; ++k) batch_far_items(w.variant, k, bt->prob[w.first + k].op->N, items);
+        int4 *d_items = nullptr;
+        BatchAsmProb *d_ap = nullptr;
+        int64_t *d_pref = nullptr;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&w.d_args, sizeof(PcgArgs) * P, false))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&w.d_begin, sizeof(int) * (P + 1), false))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&w.d_sprob, sizeof(BatchSolveProb) * P, false))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&d_ap, sizeof(BatchAsmProb) * P, false))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&d_pref, sizeof(int64_t) * 2 * (P + 1), false))) break;
+        if ((st = dalloc(ctx, bt->allocs, (void **)&d_items, sizeof(int4) * std::max<size_t>(items.size(), 1), false)))
+            break;
+        std::vector<int64_t> prefs(mpref);
+        prefs.insert(prefs.end(), npref.begin(), npref.end());
+        // on the context's stream, which orders them after the stream-ordered
+        // allocations; copies from pageable memory return once the data is staged
+        cudaStream_t s = ctx->stream;
+        const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
+        cudaError_t e = cudaMemcpyAsync(w.d_args, &bt->args[w.first], sizeof(PcgArgs) * P, h2d, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w.d_begin, w.begin.data(), sizeof(int) * (P + 1), h2d, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(w.d_sprob, sp.data(), sizeof(BatchSolveProb) * P, h2d, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_ap, ap.data(), sizeof(BatchAsmProb) * P, h2d, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(d_pref, prefs.data(), sizeof(int64_t) * prefs.size(), h2d, s);
+        if (e == cudaSuccess && !items.empty())
+            e = cudaMemcpyAsync(d_items, items.data(), sizeof(int4) * items.size(), h2d, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host tables go out of scope
+        if (e != cudaSuccess) {
+            st = cuda_error(ctx, e, "batch set-up");
+            break;
+        }
+        for (auto &ev : w.ev)
+            if (e == cudaSuccess) e = cudaEventCreate(&ev);
+        if (e != cudaSuccess) {
+            st = cuda_error(ctx, e, "batch events");
+            break;
+        }
+        w.asmb.P = P;
+        w.asmb.precision = prec;
+        w.asmb.variant = w.variant;
+        w.asmb.ss_order = ss;
+        w.asmb.prob = d_ap;
+        w.asmb.far_items = d_items;
+        w.asmb.n_far = (int64_t)items.size();
+        w.asmb.mirror_pref = d_pref;
+        w.asmb.n_mirror = mpref[P];
+        w.asmb.near_pref = d_pref + (P + 1);
+        w.asmb.n_near = npref[P];
+        w.asmb.far_entries = far_entries;
+    }
+    if (!st) {
+        cudaError_t e = cudaMallocHost((void **)&bt->h_res, sizeof(double) * kBatchRes * count);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&bt->stream, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) st = cuda_error(ctx, e, "batch set-up");
     }
-    if (st) {
-        bem_batch_destroy(bt);
-        return st;
-    }
+    if (st) return fail(st);
     *out = bt;
     return BEM_OK;
 }
@@ -2142,72 +2505,96 @@ bem_status bem_batch_run(bem_batch *bt, bem_batch_result *results)
     cudaStream_t saved = ctx->stream;
     const int saved_profile = ctx->profile;
     ctx->stream = bt->stream;  // the batch's work runs on its own (capturable) stream
-    ctx->profile = 0;          // no profiler events inside a captured graph
-    bt->prof_solve = -1;
     bem_status st = BEM_OK;
     cudaError_t e = cudaSuccess;
-    if (bt->use_graph && !bt->exec) {
-        const int64_t l0 = ctx->n_launch;
-        e = cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal);
-        if (e == cudaSuccess) {
-            st = batch_enqueue(bt);
-            cudaGraph_t graph = nullptr;
-            const cudaError_t e2 = cudaStreamEndCapture(bt->stream, &graph);
-            if (!st && e2 == cudaSuccess) {
-                bt->graph = graph;
-                e = cudaGraphInstantiate(&bt->exec, graph, 0);
-            } else {
-                if (graph) cudaGraphDestroy(graph);
-                if (!st) e = e2;
+    int replayed = 0;
+    for (auto &w : bt->waves) {
+        if (bt->use_graph && !w.exec) {
+            ctx->profile = 0;  // no profiler events inside a captured graph
+            const int64_t l0 = ctx->n_launch;
+            e = cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                st = batch_enqueue(bt, w);
+                cudaGraph_t graph = nullptr;
+                const cudaError_t e2 = cudaStreamEndCapture(bt->stream, &graph);
+                if (!st && e2 == cudaSuccess) {
+                    w.graph = graph;
+                    e = cudaGraphInstantiate(&w.exec, graph, 0);
+                } else {
+                    if (graph) cudaGraphDestroy(graph);
+                    if (!st) e = e2;
+                }
+            }
+            w.launches = ctx->n_launch - l0;
+            ctx->n_launch = l0;
+            ctx->profile = saved_profile;
+            if (st || e != cudaSuccess) {
+                // not capturable here: run the sequence directly from now on
+                cudaGetLastError();
+                for (auto &x : bt->waves) {
+                    if (x.exec) cudaGraphExecDestroy(x.exec);
+                    if (x.graph) cudaGraphDestroy(x.graph);
+                    x.exec = nullptr;
+                    x.graph = nullptr;
+                }
+                bt->use_graph = 0;
+                st = BEM_OK;
+                e = cudaSuccess;
             }
         }
-        bt->launches_per_run = ctx->n_launch - l0;
-        ctx->n_launch = l0;
-        if (st || e != cudaSuccess) {
-            // not capturable here: run the sequence directly from now on
-            cudaGetLastError();
-            bt->use_graph = 0;
-            bt->exec = nullptr;
-            st = BEM_OK;
-            e = cudaSuccess;
+        if (bt->use_graph && w.exec) {
+            e = cudaGraphLaunch(w.exec, bt->stream);
+            ctx->n_launch += w.launches;
+            ++replayed;
+        } else {
+            st = batch_enqueue(bt, w);
         }
+        if (st || e != cudaSuccess) break;
     }
-    if (bt->use_graph && bt->exec) {
-        e = cudaGraphLaunch(bt->exec, bt->stream);
-        ctx->n_launch += bt->launches_per_run;
-        bt->graph_used = 1;
-    } else {
-        bt->graph_used = 0;
-        ctx->profile = saved_profile;
-        st = batch_enqueue(bt);
-    }
+    bt->graph_used = replayed == (int)bt->waves.size() ? 1 : 0;
     if (!st && e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
     ctx->stream = saved;
     ctx->profile = saved_profile;
     if (!st && e != cudaSuccess) st = cuda_error(ctx, e, "batch run");
     if (st) return st;
     bool timeout = false, unconverged = false;
-    double bytes = 0.0;  // algorithmic bytes of the solver launch, as for a single solve
-    for (int p = 0; p < bt->P; ++p) {
-        const double *r = bt->h_res + kBatchRes * p;
-        const double n2 = (double)bt->prob[p].op->N * (double)bt->prob[p].op->N;
-        bytes += bt->prob[p].op->precision == BEM_PREC_F32 ? 2.0 * n2 * (r[2] + r[3])
-                                                           : 4.0 * n2 * r[3] + 2.0 * n2 * (r[2] + 1.0);
-        const int err = *reinterpret_cast<const int *>(r + 6);
-        const double rel = std::sqrt(r[0] / (r[1] > 0.0 ? r[1] : 1.0));
-        timeout |= err != 0;
-        unconverged |= !(rel <= bt->tol);
-        if (results) {
-            bem_batch_result &o = results[p];
-            o.cap = r[5];
-            o.iterations = (int32_t)r[2];
-            o.outer = (int32_t)r[3];
-            o.relres = rel;
-            o.converged = (err == 0 && rel <= bt->tol) ? 1 : 0;
-            o.status = err ? BEM_ERR_CUDA : (rel <= bt->tol ? BEM_OK : BEM_ERR_NOT_CONVERGED);
+    for (auto &w : bt->waves) {
+        double bytes = 0.0;  // algorithmic bytes of the wave's solver launch, as for a single solve
+        for (int p = w.first; p < w.first + w.count; ++p) {
+            const double *r = bt->h_res + (size_t)kBatchRes * p;
+            const double n2 = (double)bt->prob[p].op->N * (double)bt->prob[p].op->N;
+            bytes += bt->precision == BEM_PREC_F32 ? 2.0 * n2 * (r[2] + r[3]) : 4.0 * n2 * r[3] + 2.0 * n2 * (r[2] + 1.0);
+            const int err = *reinterpret_cast<const int *>(r + 6);
+            const double rel = std::sqrt(r[0] / (r[1] > 0.0 ? r[1] : 1.0));
+            timeout |= err != 0;
+            unconverged |= !(rel <= bt->tol);
+            if (results) {
+                bem_batch_result &o = results[p];
+                o.cap = r[5];
+                o.iterations = (int32_t)r[2];
+                o.outer = (int32_t)r[3];
+                o.relres = rel;
+                o.converged = (err == 0 && rel <= bt->tol) ? 1 : 0;
+                o.status = err ? BEM_ERR_CUDA : (rel <= bt->tol ? BEM_OK : BEM_ERR_NOT_CONVERGED);
+            }
+        }
+        if (ctx->profile) {
+            // the wave's own events (recorded by direct runs and by graph replays alike)
+            float ms[3] = {0.f, 0.f, 0.f};
+            for (int k = 0; k < 3; ++k)
+                if (cudaEventElapsedTime(&ms[k], w.ev[2 * k], w.ev[2 * k + 1]) != cudaSuccess) {
+                    cudaGetLastError();
+                    ms[k] = 0.f;
+                }
+            const double units[3] = {w.asmb.far_entries, (double)w.asmb.n_near, bytes};
+            const int kinds[3] = {BEM_KERNEL_FAR, BEM_KERNEL_NEAR, BEM_KERNEL_MATVEC};
+            for (int k = 0; k < 3; ++k) {
+                ctx->prof_launches[kinds[k]] += 1;
+                ctx->prof_ms[kinds[k]] += ms[k];
+                ctx->prof_units[kinds[k]] += units[k];
+            }
         }
     }
-    prof_set_units(ctx, bt->prof_solve, bytes);
     if (timeout) return set_error(ctx, BEM_ERR_CUDA, "batch solve: a grid barrier timed out");
     if (unconverged) return set_error(ctx, BEM_ERR_NOT_CONVERGED, "batch solve: a problem did not reach the tolerance");
     return BEM_OK;
@@ -2217,8 +2604,22 @@ bem_status bem_batch_info(const bem_batch *bt, int32_t *count, int32_t *ctas, in
 {
     if (!bt) return BEM_ERR_INVALID;
     if (count) *count = bt->P;
-    if (ctas) *ctas = bt->G;
+    if (ctas) {
+        int g = 0;
+        for (const auto &w : bt->waves) g = std::max(g, w.G);
+        *ctas = g;
+    }
     if (graph_used) *graph_used = bt->graph_used;
+    return BEM_OK;
+}
+
+bem_status bem_batch_waves(const bem_batch *bt, int32_t *waves, int64_t *arena_bytes, int32_t *wave_of)
+{
+    if (!bt) return BEM_ERR_INVALID;
+    if (waves) *waves = (int32_t)bt->waves.size();
+    if (arena_bytes) *arena_bytes = (int64_t)bt->arena_bytes;
+    if (wave_of)
+        for (int p = 0; p < bt->P; ++p) wave_of[p] = bt->prob[p].wave;
     return BEM_OK;
 }
 
@@ -2228,10 +2629,14 @@ bem_status bem_batch_destroy(bem_batch *bt)
     if (!bt) return BEM_ERR_INVALID;
     bem_ctx *ctx = bt->ctx;
     if (bt->stream) cudaStreamSynchronize(bt->stream);
-    if (bt->exec) cudaGraphExecDestroy(bt->exec);
-    if (bt->graph) cudaGraphDestroy(bt->graph);
+    for (auto &w : bt->waves) {
+        if (w.exec) cudaGraphExecDestroy(w.exec);
+        if (w.graph) cudaGraphDestroy(w.graph);
+        for (auto &ev : w.ev)
+            if (ev) cudaEventDestroy(ev);
+    }
     for (auto &pr : bt->prob)
-        if (pr.op) bem_operator_destroy(pr.op);
+        if (pr.op) bem_operator_destroy(pr.op);  // the handles own no memory: V lives in the arena
     dfree_all(ctx, bt->allocs);
     cudaStreamSynchronize(ctx->stream);
     if (bt->h_res) cudaFreeHost(bt->h_res);

@@ -314,10 +314,24 @@ def batch_meshes(count: int = 256, seed: int = 4, n_lo: int = 500, n_hi: int = 3
     return out
 
 
-def serving_requests(count: int = 2000, seed: int = 5, rate: float = 50.0):
-    """Poisson stream of capacity requests: arrival time, initial mesh and number
-    of adaptive steps (3..6).  A third each of polycubes, randomly rotated and
-    scaled cubes, and regular tetrahedra, with 100..2000 initial triangles."""
+def serving_requests(count: int = 2000, seed: int = 5, rate: float = 50.0, n_lo: int = 5000,
+                     n_hi: int = 40000, growth: float = 1.31):
+    """Poisson stream of capacity requests with 3..6 adaptive steps ending at 5k..40k
+    triangles from shapes described by 100..2000 triangles.
+
+    Per request, in this order of draws: the inter-arrival gap (exponential, ``rate``
+    per second); the shape kind (a third each: seeded polycubes with g in 3..6 and
+    p in [0.3, 0.7], cubes with a uniform random rotation and a scale log-uniform in
+    [0.5, 2], regular tetrahedra); the coarse size N0 in [100, 2000] of the shape's
+    description (polycube faces / cube and tetrahedron face grids split into about N0
+    triangles); the number of adaptive steps L in 3..6; the target size N_T
+    log-uniform in [n_lo, n_hi]; then the shape's own draws.  Dorfler marking with
+    theta = 0.5 grows a mesh by about ``growth`` per level (1.31 on the adaptive
+    polycube run), so L steps cannot take 100..2000 triangles to 5k..40k; the request
+    therefore starts from the same shape uniformly subdivided to about
+    N_T / growth^(L-1) triangles (at least its N0), runs at most L levels and stops at
+    the first level with N >= N_T.  Returned per request: id, arrival time, start
+    mesh, steps (L), target (N_T), coarse size (N0)."""
     rng = SplitMix64(seed)
     t = 0.0
     reqs = []
@@ -326,22 +340,30 @@ def serving_requests(count: int = 2000, seed: int = 5, rate: float = 50.0):
         kind = rng.randint(0, 2)
         n0 = rng.randint(100, 2000)
         steps = rng.randint(3, 6)
+        target = int(round(math.exp(math.log(n_lo) + (math.log(n_hi) - math.log(n_lo)) * rng.uniform())))
+        start = target / growth ** (steps - 1)
         if kind == 0:
             g = rng.randint(3, 6)
             p = 0.3 + 0.4 * rng.uniform()
             occ = polycube_occupancy(g, p, rng.next_u64() & 0xFFFFFFFF)
             _, t1 = voxel_surface_int(occ, 1)
-            s = max(1, int(round(math.sqrt(n0 / t1.shape[0]))))
+            s0 = max(1, int(round(math.sqrt(n0 / t1.shape[0]))))
+            s = max(s0, int(round(math.sqrt(start / t1.shape[0]))))
             iv, tris = voxel_surface_int(occ, sub=s)
             m = Mesh(iv.astype(np.float64) / s, tris, f"req{r}_polycube")
+            coarse = t1.shape[0] * s0 * s0
         elif kind == 1:
-            n = max(1, int(round(math.sqrt(n0 / 12.0))))
+            n_c = max(1, int(round(math.sqrt(n0 / 12.0))))
+            n = max(n_c, int(round(math.sqrt(start / 12.0))))
             sc = math.exp(math.log(0.5) + (math.log(2.0) - math.log(0.5)) * rng.uniform())
             m = transformed(cube_mesh(n), random_rotation(rng), sc)
             m.name = f"req{r}_cube"
+            coarse = 12 * n_c * n_c
         else:
-            k = max(1, int(round(math.sqrt(n0 / 4.0))))
+            k_c = max(1, int(round(math.sqrt(n0 / 4.0))))
+            k = max(k_c, int(round(math.sqrt(start / 4.0))))
             m = tetra_mesh(k)
             m.name = f"req{r}_tetra"
-        reqs.append({"id": r, "t_arrive": t, "mesh": m, "steps": steps})
+            coarse = 4 * k_c * k_c
+        reqs.append({"id": r, "t_arrive": t, "mesh": m, "steps": steps, "target": target, "coarse": coarse})
     return reqs

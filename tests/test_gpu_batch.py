@@ -71,3 +71,48 @@ def test_batch_errors_and_memory(ctx):
     b.run()
     b.close()
     assert ctx.memory_in_use() == before
+
+
+def _wave_meshes():
+    return [inputs.cube_mesh(14), inputs.polycube_mesh(4, 0.5, 3, sub=3), inputs.cube_mesh(2),
+            inputs.fichera_mesh(6), inputs.tetra_mesh(24), inputs.cube_mesh(12)]
+
+
+@pytest.mark.parametrize("prec", [bem.PREC_F32, bem.PREC_DF64], ids=["f32", "df64"])
+def test_batch_waves_under_a_budget(prec):
+    """A context budget that holds about half of the batch: the problems run in two or
+    more waves through one arena, every Cap equals the one-wave batch's (other CTA
+    shares only change the order of the sums) and the FP64 oracle's within the
+    tolerance of the precision (1e-6 for the FP32 operator, 1e-10 for DF64)."""
+    ms = _wave_meshes()
+    big = bem.Context()
+    one = bem.Batch(big, [bem.Mesh.upload(big, m.verts, m.tris) for m in ms], precision=prec,
+                    precond=bem.PRECOND_BLOCK, tol=1e-10)
+    w1, arena1, _ = one.waves()
+    r1 = one.run()
+    one.close()
+    assert w1 == 1
+    small = bem.Context(hbm_budget_bytes=1 << 40)  # probe the meshes' own bytes first
+    probe = [bem.Mesh.upload(small, m.verts, m.tris) for m in ms]
+    base = small.memory_in_use()
+    for mh in probe:
+        mh.close()
+    small.close()
+    ctx = bem.Context(hbm_budget_bytes=base + arena1 // 2 + (8 << 20))
+    meshes = [bem.Mesh.upload(ctx, m.verts, m.tris) for m in ms]
+    b = bem.Batch(ctx, meshes, precision=prec, precond=bem.PRECOND_BLOCK, tol=1e-10)
+    nw, arena, wave_of = b.waves()
+    assert nw >= 2 and arena < arena1, (nw, arena, arena1)
+    assert list(wave_of) == sorted(wave_of)  # waves follow the given order
+    ra = b.run()
+    rb = b.run()  # graph replay of every wave: the same bits
+    assert b.info()["graph_used"] == 1
+    assert [r["cap"] for r in ra] == [r["cap"] for r in rb]
+    assert ctx.memory_in_use() <= base + arena1 // 2 + (8 << 20)
+    tol = 1e-6 if prec == bem.PREC_F32 else 1e-10
+    for m, x, y in zip(ms, ra, r1):
+        assert x["status"] == 0 and x["converged"], (m.name, x)
+        assert abs(x["cap"] / y["cap"] - 1) < 1e-11, (m.name, x["cap"], y["cap"])
+        ref = O.solve_capacity(m.verts, O.canonical(m.verts, m.tris), tol=1e-12)[0]
+        assert abs(x["cap"] / ref - 1) < tol, (m.name, x["cap"], ref)
+    b.close()

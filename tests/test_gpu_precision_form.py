@@ -52,3 +52,31 @@ def test_graded_cube_60k_fp32_refinement():
     assert info["converged"], info
     assert abs(cap32 / cap - 1) < 1e-7, (cap32, cap)
     assert 0.6 < cap < 0.7  # near the unit cube's capacity 0.6607 (Sec. 3.1)
+
+
+def test_fp32_refinement_cap_against_oracle_on_adaptively_graded_cube():
+    """The precision form's Cap pinned to the FP64 oracle, not only to the DF64 path:
+    the oracle's own adaptive loop (ZZ + Doerfler theta = 0.5 + NVB from the
+    192-triangle cube, Alg. 1) grades the cube toward its edges and corners up to
+    N >= 5,000; on that mesh (uploaded with its reference edges, so that the stored
+    triangles are the oracle's), the FP32 operator with FP64-accurate residuals and
+    the block preconditioner reaches Cap within 1e-7 of the oracle's FP64 solve."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("needs a CUDA device")
+    m = inputs.cube_mesh(4)
+    hist = O.adaptive_run(m.verts, m.tris, theta=0.5, max_N=5000, tol=1e-12)
+    last = hist[-1]
+    v, t = last["verts"], last["tris"]
+    assert t.shape[0] >= 5000 and len(hist) > 8
+    cap_ref = O.solve_capacity(v, t, tol=1e-12)[0]
+    ctx = bem.Context()
+    mesh = bem.Mesh.upload(ctx, v, t, ref_edge=np.zeros(t.shape[0], dtype=np.uint8))
+    assert np.array_equal(mesh.download()[1], t)
+    for pc in (bem.PRECOND_JACOBI, bem.PRECOND_BLOCK):
+        op32 = bem.Operator.assemble(mesh, precision=bem.PREC_F32)
+        cap32, _, info = bem.solve_capacity(op32, tol=1e-10, max_it=5000, precond=pc)
+        op32.close()
+        assert info["converged"], info
+        assert abs(cap32 / cap_ref - 1) < 1e-7, (pc, cap32, cap_ref)
