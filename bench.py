@@ -633,10 +633,10 @@ def server_workload(args):
     serve: requests of inputs.serving_requests (seed 5, Poisson 50 req/s; a third each
     polycubes, rotated/scaled cubes, tetrahedra described by 100..2000 triangles;
     3..6 adaptive ZZ/Doerfler/NVB levels ending at 5k..40k triangles: the start mesh
-    is the shape subdivided toward target / 1.31^(levels - 1)) are submitted on their
+    is the shape subdivided toward target / 1.13^(levels - 1)) are submitted on their
     arrival clock; one step = one stream of --requests requests; value = completed
     requests per second of the step, latency = completion - submission.  A second pass
-    submits the same stream at once (saturation throughput).  Accuracy: for every 16th
+    submits the same stream at once (saturation throughput).  Accuracy: for every 25th
     request, the run alone (bem_adaptive_run, bit-identical to the served one) gives
     the final mesh, on which the FP64 oracle solves; cap_rel_err_max compares the
     served Cap with it (the oracle's time for those solves is cpu_baseline).
@@ -664,7 +664,7 @@ def server_workload(args):
         jobs = [(r["mesh"], r["steps"], r["target"], r["t_arrive"]) for r in reqs]
         label = ("serving: Poisson 50 req/s, polycubes / rotated+scaled cubes / tetrahedra described by 100..2000 "
                  "triangles, 3..6 adaptive ZZ/Doerfler/NVB levels (theta 0.5) ending at targets log-uniform in "
-                 "5k..40k triangles (start mesh subdivided toward target / 1.31^(levels-1)), FP32 V + FP64 "
+                 "5k..40k triangles (start mesh subdivided toward target / 1.13^(levels-1)), FP32 V + FP64 "
                  f"refinement to 1e-10, {args.slots} slots, HBM budget {budget >> 30} GiB")
     else:
         ms = inputs.batch_meshes(count=args.batch, seed=4 + rank)
@@ -740,7 +740,7 @@ def server_workload(args):
 
         oracle.build()
         ctx = bem.Context()
-        sample = list(range(0, len(jobs), 16))
+        sample = list(range(0, len(jobs), 25))
         errs, same, t_or, ns = [], True, 0.0, []
         for i in sample:
             m, lv, mx, _ = jobs[i]
@@ -759,12 +759,12 @@ def server_workload(args):
                 fin.close()
             mh.close()
         line["cap_rel_err_max"] = max(errs)
-        line["cap_check"] = {"sample": f"requests {sample} (every 16th); final N {ns}", "errors": errs,
+        line["cap_check"] = {"sample": f"requests {sample} (every 25th); final N {ns}", "errors": errs,
                              "served_equals_alone": bool(same),
                              "reference": "FP64 oracle on the request's final mesh, Jacobi PCG to 1e-10"}
         line["cpu_baseline"] = {"value": len(sample) / t_or, "unit": "capacity solves/s", "cores": oracle.num_threads(),
                                 "kind": "oracle", "sample": f"FP64 oracle solve (assembly + Jacobi PCG) on the final "
-                                                            f"mesh of {len(sample)} requests (every 16th)"}
+                                                            f"mesh of {len(sample)} requests (every 25th)"}
         if not args.no_compare:
             forms = {"df64_single_block": (bem.PREC_DF64, bem.PRECOND_BLOCK, 1),
                      "f64_single_jacobi": (bem.PREC_F64, bem.PRECOND_JACOBI, 4)}

@@ -37,6 +37,7 @@ namespace bem {
 __constant__ double c_w7[kQ];
 __constant__ float2 c_w7df[kQ];
 __constant__ float2 c_inv4pi_df;
+__constant__ double c_inv4pi_f32;  // 1 / (4 pi (sum of the FP32 Radon weights)^2)
 __constant__ double c_glx[kMaxSS + 1][kMaxSS];
 __constant__ double c_glw[kMaxSS + 1][kMaxSS];
 
@@ -94,6 +95,10 @@ static bem_status assembly_constants(bem_ctx *ctx)
     const float ih = (float)kInv4Pi;
     const float2 inv4pi = make_float2(ih, (float)(kInv4Pi - (double)ih));
     BEM_CK(ctx, cudaMemcpyToSymbol(c_inv4pi_df, &inv4pi, sizeof(inv4pi)));
+    double wsum = 0.0;  // exact: seven floats of similar size
+    for (int a = 0; a < kQ; ++a) wsum += (double)w7df[a].x;
+    const double inv4pi_f32 = kInv4Pi / (wsum * wsum);
+    BEM_CK(ctx, cudaMemcpyToSymbol(c_inv4pi_f32, &inv4pi_f32, sizeof(inv4pi_f32)));
     BEM_CK(ctx, cudaMemcpyToSymbol(c_glx, X, sizeof(X)));
     BEM_CK(ctx, cudaMemcpyToSymbol(c_glw, W, sizeof(W)));
     if (ctx->device < 64) g_asm_ready[ctx->device] = true;
@@ -221,7 +226,10 @@ __device__ __forceinline__ void far_f32_body(const float *__restrict__ q32, cons
         ch[c] = (float)v;
         cl[c] = (float)(v - (double)ch[c]);
     }
-    const float Aj = (float)(cent[4 * j + 3] * kInv4Pi);
+    // 1/(4pi) with the weights' rounding undone: the FP32 Radon weights all round down
+    // (their sum is 1 - 2.98e-8), which would scale every far entry by (sum w)^2; the
+    // factor 1 / (sum of the FP32 weights)^2 is folded into the column's area term
+    const float Aj = (float)(cent[4 * j + 3] * c_inv4pi_f32);
     float wf[kQ];  // the weights rounded to FP32 once (c_w7df[.].x = nearest float)
 #pragma unroll
     for (int a = 0; a < kQ; ++a) wf[a] = c_w7df[a].x;
@@ -774,13 +782,24 @@ static bem_status launch_near(bem_operator *op, int64_t K)
     return BEM_OK;
 }
 
+// Zero the padding columns [N, ld) of every row (the far field, the mirror, the near
+// field and the reused block write every entry of [0, N) x [0, N)).
+template <typename T>
+__global__ void k_zero_padding(T *V, int64_t ld, int64_t N)
+{
+    const int64_t i = blockIdx.x, j = N + threadIdx.x;
+    if (i < N && j < ld) V[i * ld + j] = T();
+}
+
 template <typename T>
 static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
 {
     bem_mesh *m = op->mesh;
     bem_ctx *ctx = m->ctx;
     const int64_t N = m->N;
-    BEM_CK(ctx, cudaMemsetAsync(op->V, 0, sizeof(T) * N * op->ld, ctx->stream));  // padding columns stay zero
+    if (op->ld > N) {
+        k_zero_padding<T><<<(unsigned)N, 64, 0, ctx->stream>>>((T *)op->V, op->ld, N); BEM_COUNT(ctx);
+    }
     bem_status st;
     int64_t K = 0;
     if (coarse) {

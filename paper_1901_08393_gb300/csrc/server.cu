@@ -82,12 +82,20 @@ int64_t estimate_bytes(int64_t N0, int64_t max_N, int32_t levels, int precision,
     return (int64_t)(ops * es * n * n + 4096.0 * n) + (64ll << 20);
 }
 
-void run_request(bem_server *srv, Request *r, cudaStream_t stream)
+// A request on its slot's context (one per slot, kept across requests: its stream,
+// pinned buffers, events and autotuned far-field tiles are reused), held to the
+// request's admission estimate by the context's HBM budget.
+void run_request(bem_server *srv, Request *r, bem_ctx *ctx)
 {
-    bem_ctx *ctx = nullptr;
     bem_mesh *mesh = nullptr;
     bem_request_result &res = r->res;
-    bem_status st = bem_context_create(stream, r->estimate, &ctx);
+    bem_status st = ctx ? BEM_OK : BEM_ERR_CUDA;
+    if (ctx) {
+        ctx->budget = ctx->in_use + r->estimate;
+        ctx->err[0] = 0;
+    } else {
+        snprintf(res.message, sizeof(res.message), "the slot has no library context");
+    }
     if (!st)
         st = bem_mesh_upload(ctx, r->verts.data(), (int64_t)(r->verts.size() / 3), r->tris.data(),
                              (int64_t)(r->tris.size() / 3), nullptr, &mesh);
@@ -111,7 +119,7 @@ void run_request(bem_server *srv, Request *r, cudaStream_t stream)
     if (st && ctx) snprintf(res.message, sizeof(res.message), "%s", bem_last_error(ctx));
     res.status = st;
     if (mesh) bem_mesh_destroy(mesh);
-    if (ctx) bem_context_destroy(ctx);
+    if (ctx) cudaStreamSynchronize(ctx->stream);  // the request's frees are done before the next one
 }
 
 void worker_main(bem_server *srv)
@@ -122,6 +130,8 @@ void worker_main(bem_server *srv)
         cudaGetLastError();
         stream = nullptr;
     }
+    bem_ctx *ctx = nullptr;
+    if (bem_context_create(stream, 0, &ctx) != BEM_OK) ctx = nullptr;
     for (;;) {
         Request *r = nullptr;
         {
@@ -146,7 +156,7 @@ void worker_main(bem_server *srv)
             if (srv->in_flight > srv->peak_in_flight) srv->peak_in_flight = srv->in_flight;
             r->res.t_start = srv->now();
         }
-        run_request(srv, r, stream);
+        run_request(srv, r, ctx);
         {
             std::lock_guard<std::mutex> lk(srv->mu);
             r->res.t_done = srv->now();
@@ -161,6 +171,7 @@ void worker_main(bem_server *srv)
         srv->cv_work.notify_all();
         srv->cv_done.notify_all();
     }
+    if (ctx) bem_context_destroy(ctx);
     if (stream) cudaStreamDestroy(stream);
 }
 

@@ -452,13 +452,16 @@ __device__ __forceinline__ float2 shfl_df(float2 v, int o)
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
 
+// static_k >= 0: at most one tile per warp, this one (no counter: when there are no
+// more tiles than warps, dynamic grabs only add two L2 atomic round trips)
 __device__ void symv_hi_tiles(const float *__restrict__ vp, const int2 *__restrict__ tiles, int ntiles,
                               const float2 *__restrict__ xdf, float2 *__restrict__ prow, float2 *__restrict__ pcol,
-                              float2 *xsw, unsigned long long *ctr, unsigned long long base)
+                              float2 *xsw, unsigned long long *ctr, unsigned long long base, int static_k = -1)
 {
     const int lane = threadIdx.x & 31, cg = lane & 15, par = lane >> 4;
     const bool b1 = lane & 2, b2 = lane & 4, b3 = lane & 8;
-    for (int k = warp_grab(ctr, base); k < ntiles; k = warp_grab(ctr, base)) {
+    for (int k = static_k >= 0 ? static_k : warp_grab(ctr, base); k < ntiles;
+         k = static_k >= 0 ? ntiles : warp_grab(ctr, base)) {
         const int2 tj = tiles[k];
         __syncwarp();
         // x_I in xsw[0..63] (lanes 0..15), x_J in xsw[64..127] (lanes 16..31)
@@ -1009,6 +1012,30 @@ __device__ __forceinline__ void cta_partial(double v, double *slot, int cta)
     __syncthreads();
 }
 
+// Two values at once, each summed exactly as cta_partial sums it.
+__device__ __forceinline__ void cta_partial2(double v1, double v2, double *slot1, double *slot2, int cta)
+{
+    __shared__ double sw1[kSymThreads / 32], sw2[kSymThreads / 32];
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sw1[w] = v1;
+        sw2[w] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = 0; k < kSymThreads / 32; ++k) {
+            t1 += sw1[k];
+            t2 += sw2[k];
+        }
+        slot1[cta] = t1;
+        slot2[cta] = t2;
+    }
+    __syncthreads();
+}
+
 // Fixed-order sum of the G per-CTA partials (L2 loads: written by other CTAs).
 __device__ __forceinline__ double grid_total(const double *slot, int G)
 {
@@ -1027,6 +1054,38 @@ __device__ __forceinline__ double grid_total(const double *slot, int G)
     }
     __syncthreads();
     return res;
+}
+
+// Two totals at once, each summed exactly as grid_total sums it.
+__device__ __forceinline__ void grid_total2(const double *slot1, const double *slot2, int G, double &r1, double &r2)
+{
+    __shared__ double sw1[kSymThreads / 32], sw2[kSymThreads / 32];
+    __shared__ double res1, res2;
+    double v1 = 0.0, v2 = 0.0;
+    for (int k = threadIdx.x; k < G; k += blockDim.x) {
+        v1 += __ldcg(slot1 + k);
+        v2 += __ldcg(slot2 + k);
+    }
+    v1 = warp_sum(v1);
+    v2 = warp_sum(v2);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) {
+        sw1[w] = v1;
+        sw2[w] = v2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t1 = 0.0, t2 = 0.0;
+        for (int k = 0; k < kSymThreads / 32; ++k) {
+            t1 += sw1[k];
+            t2 += sw2[k];
+        }
+        res1 = t1;
+        res2 = t2;
+    }
+    __syncthreads();
+    r1 = res1;
+    r2 = res2;
 }
 
 // kCal: the build with the operator preconditioner (BEM_PRECOND_CALDERON), kept out of
@@ -1048,14 +1107,19 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     const int64_t warp_g = ((int64_t)cta * kSymThreads + threadIdx.x) >> 5, nwarps = stride >> 5;
     unsigned long long tbase = 0ull;
     GridBar gb{a.bar, a.err, 0u, a.bar_limit_ns > 0 ? a.bar_limit_ns : kBarrierLimitNs, a.absent_cta == cta};
+    // packed products: tiles taken statically when every warp gets one at most
+    const int hi_static = a.ntiles <= nwarps ? (int)warp_g : -1;
+    auto hi_product = [&](const float *packed) {
+        symv_hi_tiles(packed, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase, hi_static);
+        if (hi_static < 0) tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+    };
     // DF64 product V x into the tile partials (x = the FP64 iterate); the first one
     // of the mixed mode also packs the hi parts
     auto df64_product = [&](bool pack) -> bool {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.x[i]) : make_float2(0.f, 0.f);
         if (!grid_barrier(gb, G)) return false;
         if (a.f32op) {  // the stored operator is the packed copy itself
-            symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
-            tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+            hi_product(a.vp);
         } else {
             symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase,
                        pack ? a.vp : nullptr);
@@ -1069,8 +1133,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     auto calderon = [&](bool init, double &rz_part) -> bool {
         for (int64_t i = i0; i < a.ld; i += stride) a.pdf[i] = i < a.N ? df_from_double(a.r[i]) : make_float2(0.f, 0.f);
         if (!grid_barrier(gb, G)) return false;
-        symv_hi_tiles(a.dvp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
-        tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+        hi_product(a.dvp);
         if (!grid_barrier(gb, G)) return false;
         for (int64_t ib = warp_g * 8; ib < a.N; ib += nwarps * 8) {
             const int64_t i = ib + (lane >> 2);
@@ -1129,8 +1192,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     if (!grid_barrier(gb, G)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
         if (mixed) {
-            symv_hi_tiles(a.vp, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase);
-            tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+            hi_product(a.vp);
         } else {
             symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase);
             tbase += (unsigned long long)(a.ntiles + G);
@@ -1177,11 +1239,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 rr_l += ri * ri;
             }
         }
-        cta_partial(rz_n, pB, cta);
-        cta_partial(rr_l, pC, cta);
+        cta_partial2(rz_n, rr_l, pB, pC, cta);
         if (!grid_barrier(gb, G)) return;
-        double rz_new = grid_total(pB, G);
-        rr = grid_total(pC, G);
+        double rz_new;
+        grid_total2(pB, pC, G, rz_new, rr);
         ++it;
         if (a.lam2 > 0.0) {
             // |||alpha p|||^2 = alpha^2 p.Vp = alpha (r.z); ZZ estimator of the iterate
@@ -1243,11 +1304,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 for (int64_t i = i0; i < a.N; i += stride) rr_l += a.r[i] * a.r[i];
                 if (!calderon(false, rz_n)) return;
             }
-            cta_partial(rz_n, pB, cta);
-            cta_partial(rr_l, pC, cta);
+            cta_partial2(rz_n, rr_l, pB, pC, cta);
             if (!grid_barrier(gb, G)) return;
-            rz_new = grid_total(pB, G);
-            rr = grid_total(pC, G);
+            grid_total2(pB, pC, G, rz_new, rr);
             rr_true = rr;
             ++ndf;
         }
@@ -2047,12 +2106,20 @@ struct BatchProblem {
     int nbj = 0;
 };
 
-struct BatchWave {
-    int first = 0, count = 0, G = 0, variant = 0, max_nbj = 0;
-    int64_t max_rows = 0;
-    std::vector<int> begin;
+// Problems of a wave solved by one cooperative launch: similar sizes, CTAs shared in
+// proportion to N^2, so that they finish at about the same time.
+struct BatchGroup {
+    int count = 0, G = 0;
+    std::vector<int> idx;    // problems (batch indices), in launch order
+    std::vector<int> begin;  // CTA ranges
     PcgArgs *d_args = nullptr;
     int *d_begin = nullptr;
+};
+
+struct BatchWave {
+    int first = 0, count = 0, variant = 0, max_nbj = 0;
+    int64_t max_rows = 0;
+    std::vector<BatchGroup> groups;
     BatchSolveProb *d_sprob = nullptr;
     BatchAsm asmb;
     cudaGraph_t graph = nullptr;
@@ -2107,9 +2174,10 @@ static bem_status batch_enqueue(bem_batch *bt, BatchWave &w)
         BEM_COUNT(ctx);
     }
     BEM_CK_LAUNCH(ctx);
-    {
+    if ((st = record_timing_event(ctx, w.ev[4]))) return st;
+    for (const auto &gr : w.groups) {  // one cooperative launch per group of similar sizes
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)w.G);
+        cfg.gridDim = dim3((unsigned)gr.G);
         cfg.blockDim = dim3(kSymThreads);
         cfg.dynamicSmemBytes = kSymSmem;
         cfg.stream = s;
@@ -2118,11 +2186,10 @@ static bem_status batch_enqueue(bem_batch *bt, BatchWave &w)
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        if ((st = record_timing_event(ctx, w.ev[4]))) return st;
-        BEM_CK(ctx, cudaLaunchKernelEx(&cfg, k_pcg_batch, (const PcgArgs *)w.d_args, (const int *)w.d_begin, w.count));
+        BEM_CK(ctx, cudaLaunchKernelEx(&cfg, k_pcg_batch, (const PcgArgs *)gr.d_args, (const int *)gr.d_begin, gr.count));
         BEM_COUNT(ctx);
-        if ((st = record_timing_event(ctx, w.ev[5]))) return st;
     }
+    if ((st = record_timing_event(ctx, w.ev[5]))) return st;
     k_batch_capacity<<<w.count, 1024, 0, s>>>(w.d_sprob); BEM_COUNT(ctx);
     BEM_CK_LAUNCH(ctx);
     BEM_CK(ctx, cudaMemcpyAsync(bt->h_res + (size_t)kBatchRes * w.first, bt->d_res + (size_t)kBatchRes * w.first,
@@ -2211,6 +2278,7 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
     {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e == cudaSuccess) e = cudaMemPoolTrimTo(ctx->pool, 0);
+        if (e == cudaSuccess) e = cudaMemPoolTrimTo(ctx->pool_large, 0);
         size_t fr = 0, tot = 0;
         if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
         if (e != cudaSuccess) return fail(cuda_error(ctx, e, "batch memory query"));
@@ -2294,34 +2362,62 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
     for (size_t wi = 0; wi < bt->waves.size() && !st; ++wi) {
         BatchWave &w = bt->waves[wi];
         const int P = w.count;
-        // CTAs per problem in proportion to its bytes per product (N^2; iteration counts
-        // are alike), at least one, at most what the single-problem rule can use (a tile
-        // per warp, 8 rows per warp), so that the problems finish at about the same time
+        // Groups: the wave's problems by decreasing N, a new group when N^2 falls below
+        // half the group's first or the group has as many problems as CTAs can serve
+        // (8 per problem that can use them, else what it can use).  Within a group, CTAs
+        // per problem in proportion to its bytes per product (N^2; iteration counts are
+        // alike), at least one, at most what the single-problem rule can use (a tile per
+        // warp, 8 rows per warp), so that the group's problems finish at about the same
+        // time; small, latency-bound problems share one launch instead of holding CTAs
+        // that the large ones need.
         std::vector<int64_t> want(P);
-        double wsum = 0.0;
         for (int k = 0; k < P; ++k) {
             const int64_t N = meshes[w.first + k]->N, nt = bt->prob[w.first + k].nt;
             want[k] = std::min<int64_t>(std::max<int64_t>(std::max<int64_t>((nt + 7) / 8, (N + 63) / 64), 1), Gmax);
-            wsum += (double)N * (double)N;
         }
-        std::vector<int> g(P);
-        int gsum = 0;
-        for (int k = 0; k < P; ++k) {
-            const double N = (double)meshes[w.first + k]->N;
-            const int64_t share = (int64_t)((double)(Gmax - P) * N * N / wsum) + 1;
-            g[k] = (int)std::min<int64_t>(share, want[k]);
-            gsum += g[k];
+        std::vector<int> order(P);
+        for (int k = 0; k < P; ++k) order[k] = k;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int a, int b) { return meshes[w.first + a]->N > meshes[w.first + b]->N; });
+        std::vector<int> g(P, 1);
+        w.groups.clear();
+        for (size_t pos = 0; pos < order.size();) {
+            BatchGroup gr;
+            const int k0 = order[pos];
+            const double n0 = (double)meshes[w.first + k0]->N;
+            const int per = (int)std::min<int64_t>(want[k0], 8);
+            const int cap = std::max(1, Gmax / std::max(per, 1));
+            while (pos < order.size() && (int)gr.idx.size() < cap) {
+                const int k = order[pos];
+                const double n = (double)meshes[w.first + k]->N;
+                if (!gr.idx.empty() && 2.0 * n * n < n0 * n0) break;
+                gr.idx.push_back(k);
+                ++pos;
+            }
+            const int Pg = (int)gr.idx.size();
+            double wsum = 0.0;
+            for (int k : gr.idx) wsum += (double)meshes[w.first + k]->N * (double)meshes[w.first + k]->N;
+            int gsum = 0;
+            for (int k : gr.idx) {
+                const double N = (double)meshes[w.first + k]->N;
+                const int64_t share = (int64_t)((double)(Gmax - Pg) * N * N / wsum) + 1;
+                g[k] = (int)std::min<int64_t>(share, want[k]);
+                gsum += g[k];
+            }
+            while (gsum > Gmax) {  // rounding: take from the largest
+                int km = gr.idx[0];
+                for (int k : gr.idx)
+                    if (g[k] > g[km]) km = k;
+                --g[km];
+                --gsum;
+            }
+            gr.count = Pg;
+            gr.begin.assign(Pg + 1, 0);
+            for (int q = 0; q < Pg; ++q) gr.begin[q + 1] = gr.begin[q] + g[gr.idx[q]];
+            gr.G = gr.begin[Pg];
+            for (int &k : gr.idx) k += w.first;  // batch indices from here on
+            w.groups.push_back(std::move(gr));
         }
-        while (gsum > Gmax) {  // rounding: take from the largest
-            int km = 0;
-            for (int k = 1; k < P; ++k)
-                if (g[k] > g[km]) km = k;
-            --g[km];
-            --gsum;
-        }
-        w.begin.assign(P + 1, 0);
-        for (int k = 0; k < P; ++k) w.begin[k + 1] = w.begin[k] + g[k];
-        w.G = w.begin[P];
         std::vector<BatchSolveProb> sp(P);
         std::vector<BatchAsmProb> ap(P);
         std::vector<int64_t> mpref(P + 1, 0), npref(P + 1, 0);
@@ -2442,8 +2538,11 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
         int4 *d_items = nullptr;
         BatchAsmProb *d_ap = nullptr;
         int64_t *d_pref = nullptr;
-        if ((st = dalloc(ctx, bt->allocs, (void **)&w.d_args, sizeof(PcgArgs) * P, false))) break;
-        if ((st = dalloc(ctx, bt->allocs, (void **)&w.d_begin, sizeof(int) * (P + 1), false))) break;
+        for (auto &gr : w.groups) {
+            if ((st = dalloc(ctx, bt->allocs, (void **)&gr.d_args, sizeof(PcgArgs) * gr.count, false))) break;
+            if ((st = dalloc(ctx, bt->allocs, (void **)&gr.d_begin, sizeof(int) * (gr.count + 1), false))) break;
+        }
+        if (st) break;
         if ((st = dalloc(ctx, bt->allocs, (void **)&w.d_sprob, sizeof(BatchSolveProb) * P, false))) break;
         if ((st = dalloc(ctx, bt->allocs, (void **)&d_ap, sizeof(BatchAsmProb) * P, false))) break;
         if ((st = dalloc(ctx, bt->allocs, (void **)&d_pref, sizeof(int64_t) * 2 * (P + 1), false))) break;
@@ -2455,8 +2554,14 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
         // allocations; copies from pageable memory return once the data is staged
         cudaStream_t s = ctx->stream;
         const cudaMemcpyKind h2d = cudaMemcpyHostToDevice;
-        cudaError_t e = cudaMemcpyAsync(w.d_args, &bt->args[w.first], sizeof(PcgArgs) * P, h2d, s);
-        if (e == cudaSuccess) e = cudaMemcpyAsync(w.d_begin, w.begin.data(), sizeof(int) * (P + 1), h2d, s);
+        cudaError_t e = cudaSuccess;
+        std::vector<std::vector<PcgArgs>> gargs(w.groups.size());
+        for (size_t gi = 0; gi < w.groups.size() && e == cudaSuccess; ++gi) {
+            const BatchGroup &gr = w.groups[gi];
+            for (int p : gr.idx) gargs[gi].push_back(bt->args[p]);
+            e = cudaMemcpyAsync(gr.d_args, gargs[gi].data(), sizeof(PcgArgs) * gr.count, h2d, s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(gr.d_begin, gr.begin.data(), sizeof(int) * (gr.count + 1), h2d, s);
+        }
         if (e == cudaSuccess) e = cudaMemcpyAsync(w.d_sprob, sp.data(), sizeof(BatchSolveProb) * P, h2d, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_ap, ap.data(), sizeof(BatchAsmProb) * P, h2d, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(d_pref, prefs.data(), sizeof(int64_t) * prefs.size(), h2d, s);
@@ -2606,7 +2711,8 @@ bem_status bem_batch_info(const bem_batch *bt, int32_t *count, int32_t *ctas, in
     if (count) *count = bt->P;
     if (ctas) {
         int g = 0;
-        for (const auto &w : bt->waves) g = std::max(g, w.G);
+        for (const auto &w : bt->waves)
+            for (const auto &gr : w.groups) g = std::max(g, gr.G);
         *ctas = g;
     }
     if (graph_used) *graph_used = bt->graph_used;

@@ -315,7 +315,7 @@ def batch_meshes(count: int = 256, seed: int = 4, n_lo: int = 500, n_hi: int = 3
 
 
 def serving_requests(count: int = 2000, seed: int = 5, rate: float = 50.0, n_lo: int = 5000,
-                     n_hi: int = 40000, growth: float = 1.31):
+                     n_hi: int = 40000, growth: float = 1.13):
     """Poisson stream of capacity requests with 3..6 adaptive steps ending at 5k..40k
     triangles from shapes described by 100..2000 triangles.
 
@@ -326,8 +326,9 @@ def serving_requests(count: int = 2000, seed: int = 5, rate: float = 50.0, n_lo:
     description (polycube faces / cube and tetrahedron face grids split into about N0
     triangles); the number of adaptive steps L in 3..6; the target size N_T
     log-uniform in [n_lo, n_hi]; then the shape's own draws.  Dorfler marking with
-    theta = 0.5 grows a mesh by about ``growth`` per level (1.31 on the adaptive
-    polycube run), so L steps cannot take 100..2000 triangles to 5k..40k; the request
+    theta = 0.5 grows a uniform start mesh of these shapes by about ``growth`` per
+    level (1.13, measured on this stream: the first levels mark mostly elements at
+    edges and corners), so L steps cannot take 100..2000 triangles to 5k..40k; the request
     therefore starts from the same shape uniformly subdivided to about
     N_T / growth^(L-1) triangles (at least its N0), runs at most L levels and stops at
     the first level with N >= N_T.  Returned per request: id, arrival time, start

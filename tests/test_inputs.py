@@ -63,10 +63,10 @@ def test_batch_and_requests_shapes():
     reqs = inputs.serving_requests(count=6)
     assert all(3 <= r["steps"] <= 6 for r in reqs)
     assert all(5000 <= r["target"] <= 40000 for r in reqs)
-    # the start mesh is the shape subdivided toward target / 1.31^(steps - 1), never
+    # the start mesh is the shape subdivided toward target / 1.13^(steps - 1), never
     # coarser than the shape's description
     for r in reqs:
-        start = r["target"] / 1.31 ** (r["steps"] - 1)
+        start = r["target"] / 1.13 ** (r["steps"] - 1)
         assert r["mesh"].N >= r["coarse"] and 0.4 * start <= r["mesh"].N <= 2.5 * start, r
     assert all(b["t_arrive"] > a["t_arrive"] for a, b in zip(reqs, reqs[1:]))
     assert all(_closed(r["mesh"]) and _volume(r["mesh"]) > 0 for r in reqs)
