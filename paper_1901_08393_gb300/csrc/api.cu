@@ -30,6 +30,35 @@ bem_status cuda_error(bem_ctx *ctx, cudaError_t e, const char *what)
                      cudaGetErrorString(e));
 }
 
+// Freed large blocks kept by contexts without an HBM budget: the stream-ordered pool
+// keeps freed memory mapped but seldom hands an operator's block to the next
+// operator of another size, and mapping new memory cost about 1 ms of host time per
+// GB for every adaptive level while the GPU waited; a block is reused by a request on
+// the same stream that it fits with at most 2x to spare.
+constexpr size_t kCacheMaxBlock = size_t(8) << 30, kCacheMaxTotal = size_t(16) << 30;
+constexpr int kCacheMaxBlocks = 6;
+
+static void cache_put(bem_ctx *ctx, void *p, size_t bytes)
+{
+    ctx->block_cache.push_back(CachedBlock{p, bytes, ctx->stream});
+    ctx->cache_bytes += bytes;
+    while ((int)ctx->block_cache.size() > kCacheMaxBlocks || ctx->cache_bytes > kCacheMaxTotal) {
+        size_t k = 0;  // drop the smallest
+        for (size_t j = 1; j < ctx->block_cache.size(); ++j)
+            if (ctx->block_cache[j].bytes < ctx->block_cache[k].bytes) k = j;
+        cudaFreeAsync(ctx->block_cache[k].p, ctx->block_cache[k].stream);
+        ctx->cache_bytes -= ctx->block_cache[k].bytes;
+        ctx->block_cache.erase(ctx->block_cache.begin() + (std::ptrdiff_t)k);
+    }
+}
+
+void cache_release(bem_ctx *ctx)
+{
+    for (auto &b : ctx->block_cache) cudaFreeAsync(b.p, b.stream);
+    ctx->block_cache.clear();
+    ctx->cache_bytes = 0;
+}
+
 bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero)
 {
     if (bytes == 0) bytes = 16;
@@ -37,6 +66,32 @@ bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero)
     if (ctx->budget > 0 && ctx->in_use + (int64_t)bytes > ctx->budget)
         return set_error(ctx, BEM_ERR_OOM, "HBM budget exceeded: %lld in use + %zu requested > %lld",
                          (long long)ctx->in_use, bytes, (long long)ctx->budget);
+    if (ctx->budget <= 0 && bytes >= kLargeAlloc) {  // a kept block that fits
+        int best = -1;
+        for (int k = 0; k < (int)ctx->block_cache.size(); ++k) {
+            const CachedBlock &b = ctx->block_cache[k];
+            if (b.stream == ctx->stream && b.bytes >= bytes && b.bytes <= 2 * bytes &&
+                (best < 0 || b.bytes < ctx->block_cache[best].bytes))
+                best = k;
+        }
+        if (best >= 0) {
+            const CachedBlock b = ctx->block_cache[best];
+            ctx->block_cache.erase(ctx->block_cache.begin() + best);
+            ctx->cache_bytes -= b.bytes;
+            *p = b.p;
+            if (zero) {
+                const cudaError_t e = cudaMemsetAsync(*p, 0, bytes, ctx->stream);
+                if (e != cudaSuccess) {
+                    cudaFreeAsync(*p, ctx->stream);
+                    return cuda_error(ctx, e, "memset");
+                }
+            }
+            a.list.emplace_back(*p, b.bytes);
+            a.bytes += b.bytes;
+            ctx->in_use += (int64_t)b.bytes;
+            return BEM_OK;
+        }
+    }
     cudaError_t e = cudaMallocFromPoolAsync(p, bytes, bytes >= kLargeAlloc ? ctx->pool_large : ctx->pool, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -58,7 +113,12 @@ bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero)
 
 void dfree_all(bem_ctx *ctx, Allocs &a)
 {
-    for (auto &pb : a.list) cudaFreeAsync(pb.first, ctx->stream);
+    for (auto &pb : a.list) {
+        if (ctx->budget <= 0 && pb.second >= kLargeAlloc && pb.second <= kCacheMaxBlock)
+            cache_put(ctx, pb.first, pb.second);
+        else
+            cudaFreeAsync(pb.first, ctx->stream);
+    }
     ctx->in_use -= (int64_t)a.bytes;
     a.list.clear();
     a.bytes = 0;
@@ -372,6 +432,8 @@ bem_status bem_context_destroy(bem_ctx *ctx)
     for (int k = 0; k < 8; ++k)
         if (ctx->ev[k]) cudaEventDestroy(ctx->ev[k]);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    cache_release(ctx);
+    cudaStreamSynchronize(ctx->stream);
     if (ctx->h_levels) cudaFreeHost(ctx->h_levels);
     for (cudaEvent_t e : ctx->lvl_ev) cudaEventDestroy(e);
     if (ctx->pool) pool_release(ctx->device);
@@ -916,7 +978,9 @@ static bem_status dual_level_operator(bem_mesh *cur, const bem_assembly_opts *ao
 static bem_status level_slots(bem_ctx *ctx, int levels)
 {
     if (ctx->h_levels_cap < levels) {
-        if (ctx->h_levels) cudaFreeHost(ctx->h_levels);
+        cache_release(ctx);
+    cudaStreamSynchronize(ctx->stream);
+    if (ctx->h_levels) cudaFreeHost(ctx->h_levels);
         ctx->h_levels = nullptr;
         ctx->h_levels_cap = 0;
         BEM_CK(ctx, cudaMallocHost((void **)&ctx->h_levels, sizeof(double) * 16 * (size_t)levels));

@@ -38,6 +38,11 @@ struct Allocs {
 }  // namespace bem
 
 namespace bem {
+struct CachedBlock {
+    void *p;
+    size_t bytes;
+    cudaStream_t stream;  // the stream it was freed on (reused only there)
+};
 struct ProfRec {
     int id;
     cudaEvent_t a, b;
@@ -66,6 +71,9 @@ struct bem_ctx {
     double *h_pinned = nullptr;  // 64 doubles of pinned host memory for scalar readbacks
     cudaEvent_t ev[8] = {};
     int8_t far_tile[3][4] = {{-1, -1, -1, -1}, {-1, -1, -1, -1}, {-1, -1, -1, -1}};  // autotuned variant
+    // freed large blocks kept for reuse (contexts without a budget; see dalloc)
+    std::vector<bem::CachedBlock> block_cache;
+    size_t cache_bytes = 0;
     // adaptive loop: pinned per-level result slots (16 doubles each) and timing events
     double *h_levels = nullptr;
     int h_levels_cap = 0;
@@ -123,6 +131,7 @@ bem_status set_error(bem_ctx *ctx, bem_status code, const char *fmt, ...);
 bem_status cuda_error(bem_ctx *ctx, cudaError_t e, const char *what);
 bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero);
 void dfree_all(bem_ctx *ctx, Allocs &a);
+void cache_release(bem_ctx *ctx);  // free the kept blocks (stream-ordered)
 // True for device or managed memory; device (nullable) receives the device that holds
 // plain device memory (-1 for managed or host memory).
 bool is_device_ptr(const void *p, int *device = nullptr);

@@ -1191,6 +1191,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     int it = 0, ndf = prod0 ? 1 : 0, inexact_stop = 0;
     if (!grid_barrier(gb, G)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
+        double alpha, rz_new, rz_n = 0.0;
         if (mixed) {
             hi_product(a.vp);
         } else {
@@ -1214,8 +1215,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         }
         cta_partial(pq_l, pA, cta);
         if (!grid_barrier(gb, G)) return;
-        const double alpha = rz / grid_total(pA, G);
-        double rz_n = 0.0;
+        alpha = rz / grid_total(pA, G);
         rr_l = 0.0;
         if (blockpc) {
             for (int blk = cta; blk < a.nbj; blk += G)
@@ -1241,7 +1241,6 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         }
         cta_partial2(rz_n, rr_l, pB, pC, cta);
         if (!grid_barrier(gb, G)) return;
-        double rz_new;
         grid_total2(pB, pC, G, rz_new, rr);
         ++it;
         if (a.lam2 > 0.0) {
@@ -1646,11 +1645,11 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     BEM_CK(ctx, cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device));
     if (!coop || !W.tiles) return BEM_OK;
     if (f32op) delta = 1.0;  // a packed copy is needed; residuals are replaced only at convergence
+    const int nb_ = (int)(op->ld / kSB), nt_ = nb_ * (nb_ + 1) / 2;
     const void *kern = precond == BEM_PRECOND_CALDERON ? (const void *)k_pcg_cal : (const void *)k_pcg_df;
     BEM_CK(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSymSmem));
     BEM_CK(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kSymThreads, kSymSmem));
     if (per_sm < 1) return BEM_OK;
-    const int nb_ = (int)(op->ld / kSB), nt_ = nb_ * (nb_ + 1) / 2;
     Allocs tmp;
     bem_status st = BEM_OK;
     float *vp = nullptr;
@@ -2276,6 +2275,7 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
     // memory left for the arena or the CTAs of one cooperative launch
     int64_t avail = 0;
     {
+        cache_release(ctx);  // the kept blocks go back to the pool, then to the device
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e == cudaSuccess) e = cudaMemPoolTrimTo(ctx->pool, 0);
         if (e == cudaSuccess) e = cudaMemPoolTrimTo(ctx->pool_large, 0);
