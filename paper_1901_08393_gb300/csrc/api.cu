@@ -92,7 +92,7 @@ bem_status dalloc(bem_ctx *ctx, Allocs &a, void **p, size_t bytes, bool zero)
             return BEM_OK;
         }
     }
-    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, bytes >= kLargeAlloc ? ctx->pool_large : ctx->pool, ctx->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, ctx->pool, ctx->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
@@ -150,8 +150,7 @@ bem_status dev_in(bem_ctx *ctx, const void *src, size_t bytes, DevBuf &buf)
         buf.dptr = const_cast<void *>(src);
         return BEM_OK;
     }
-    BEM_CK(ctx, cudaMallocFromPoolAsync(&buf.owned, bytes ? bytes : 16, bytes >= kLargeAlloc ? ctx->pool_large : ctx->pool,
-                                        ctx->stream));
+    BEM_CK(ctx, cudaMallocFromPoolAsync(&buf.owned, bytes ? bytes : 16, ctx->pool, ctx->stream));
     buf.dptr = buf.owned;
     if (bytes) BEM_CK(ctx, cudaMemcpyAsync(buf.owned, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
     return BEM_OK;
@@ -165,8 +164,7 @@ bem_status dev_out_begin(bem_ctx *ctx, void *dst, size_t bytes, DevBuf &buf)
         buf.dptr = dst;
         return BEM_OK;
     }
-    BEM_CK(ctx, cudaMallocFromPoolAsync(&buf.owned, bytes ? bytes : 16, bytes >= kLargeAlloc ? ctx->pool_large : ctx->pool,
-                                        ctx->stream));
+    BEM_CK(ctx, cudaMallocFromPoolAsync(&buf.owned, bytes ? bytes : 16, ctx->pool, ctx->stream));
     buf.dptr = buf.owned;
     return BEM_OK;
 }
@@ -287,54 +285,31 @@ extern "C" {
 // it to the CUDA driver at every synchronisation; the pool is trimmed when the last
 // context of the device is destroyed.
 namespace {
-// Two pools per device: one for allocations of kLargeAlloc bytes and more (operators,
-// packed copies) and one for the rest.  With one pool, the small allocations of an
-// adaptive level were carved out of the operators' freed blocks, so that every level
-// mapped new memory for its operator (about 1 ms per GB of host time while the GPU
-// waited); kept apart, an operator's block is found again by the next operator.
-struct DevicePools {
-    cudaMemPool_t small = nullptr, large = nullptr;
-    int contexts = 0;
-};
 std::mutex g_pool_mu;
-std::unordered_map<int, DevicePools> g_pools;
+std::unordered_map<int, std::pair<cudaMemPool_t, int>> g_pools;  // device -> (pool, contexts)
 
-cudaError_t make_pool(int device, cudaMemPool_t *out)
-{
-    cudaMemPoolProps props = {};
-    props.allocType = cudaMemAllocationTypePinned;
-    props.location.type = cudaMemLocationTypeDevice;
-    props.location.id = device;
-    cudaMemPool_t pool;
-    cudaError_t e = cudaMemPoolCreate(&pool, &props);
-    if (e != cudaSuccess) return e;
-    unsigned long long keep = ~0ull;
-    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
-    if (e != cudaSuccess) {
-        cudaMemPoolDestroy(pool);
-        return e;
-    }
-    *out = pool;
-    return cudaSuccess;
-}
-
-cudaError_t pool_acquire(int device, cudaMemPool_t *small, cudaMemPool_t *large)
+cudaError_t pool_acquire(int device, cudaMemPool_t *out)
 {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     auto it = g_pools.find(device);
     if (it == g_pools.end()) {
-        DevicePools p;
-        cudaError_t e = make_pool(device, &p.small);
-        if (e == cudaSuccess) e = make_pool(device, &p.large);
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = ~0ull;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
         if (e != cudaSuccess) {
-            if (p.small) cudaMemPoolDestroy(p.small);
+            cudaMemPoolDestroy(pool);
             return e;
         }
-        it = g_pools.emplace(device, p).first;
+        it = g_pools.emplace(device, std::make_pair(pool, 0)).first;
     }
-    it->second.contexts += 1;
-    *small = it->second.small;
-    *large = it->second.large;
+    it->second.second += 1;
+    *out = it->second.first;
     return cudaSuccess;
 }
 
@@ -342,10 +317,7 @@ void pool_release(int device)
 {
     std::lock_guard<std::mutex> lk(g_pool_mu);
     auto it = g_pools.find(device);
-    if (it != g_pools.end() && --it->second.contexts == 0) {
-        cudaMemPoolTrimTo(it->second.small, 0);
-        cudaMemPoolTrimTo(it->second.large, 0);
-    }
+    if (it != g_pools.end() && --it->second.second == 0) cudaMemPoolTrimTo(it->second.first, 0);
 }
 }  // namespace
 
@@ -359,7 +331,7 @@ bem_status bem_context_create(void *cuda_stream, int64_t hbm_budget_bytes, bem_c
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&ctx->h_pinned, 64 * sizeof(double));
     for (int k = 0; k < 8 && e == cudaSuccess; ++k) e = cudaEventCreate(&ctx->ev[k]);
-    if (e == cudaSuccess) e = pool_acquire(ctx->device, &ctx->pool, &ctx->pool_large);
+    if (e == cudaSuccess) e = pool_acquire(ctx->device, &ctx->pool);
     if (e != cudaSuccess) {
         cudaGetLastError();
         for (int k = 0; k < 8; ++k)

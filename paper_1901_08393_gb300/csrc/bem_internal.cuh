@@ -28,7 +28,7 @@ constexpr int kFarTileVariants = BEM_FAR_TILE_VARIANTS;  // far-field pair tile 
 // symmetric matvec); the padding columns are zero.
 inline int64_t padded_ld(int64_t n) { return (n + 63) / 64 * 64; }
 
-constexpr size_t kLargeAlloc = size_t(64) << 20;  // allocations from the large pool
+constexpr size_t kLargeAlloc = size_t(64) << 20;  // blocks from this size up are kept for reuse (dalloc)
 
 struct Allocs {
     std::vector<std::pair<void *, size_t>> list;
@@ -61,8 +61,7 @@ struct bem_ctx {
     double prof_ms[bem::kProfKinds] = {0, 0, 0, 0};
     double prof_units[bem::kProfKinds] = {0, 0, 0, 0};
     cudaStream_t stream = nullptr;
-    cudaMemPool_t pool = nullptr;        // the library's stream-ordered pool of this device
-    cudaMemPool_t pool_large = nullptr;  // its pool for allocations of kLargeAlloc bytes and more
+    cudaMemPool_t pool = nullptr;  // the library's stream-ordered pool of this device
     int device = 0;
     int sm_count = 0;
     int64_t budget = 0;  // <= 0: unlimited

@@ -2278,7 +2278,6 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
         cache_release(ctx);  // the kept blocks go back to the pool, then to the device
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e == cudaSuccess) e = cudaMemPoolTrimTo(ctx->pool, 0);
-        if (e == cudaSuccess) e = cudaMemPoolTrimTo(ctx->pool_large, 0);
         size_t fr = 0, tot = 0;
         if (e == cudaSuccess) e = cudaMemGetInfo(&fr, &tot);
         if (e != cudaSuccess) return fail(cuda_error(ctx, e, "batch memory query"));
