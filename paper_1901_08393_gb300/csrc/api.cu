@@ -280,10 +280,11 @@ using namespace bem;
 extern "C" {
 
 // One stream-ordered memory pool per device for all contexts of the library.  Its
-// release threshold keeps freed blocks reserved, so that the operators of successive
-// adaptive levels (up to several GB each) reuse mapped memory instead of returning
-// it to the CUDA driver at every synchronisation; the pool is trimmed when the last
-// context of the device is destroyed.
+// release threshold keeps freed blocks reserved instead of returning them to the CUDA
+// driver at every synchronisation; the pool is trimmed when the last context of the
+// device is destroyed.  (Operator-sized blocks were seldom handed back by the pool to
+// the next level's operator; contexts without a budget keep those blocks themselves,
+// see dalloc.)
 namespace {
 std::mutex g_pool_mu;
 std::unordered_map<int, std::pair<cudaMemPool_t, int>> g_pools;  // device -> (pool, contexts)
