@@ -167,6 +167,34 @@ __global__ void k_bitonic_shared(unsigned long long *keys, int64_t n2, int64_t k
     for (int q = threadIdx.x; q < chunk; q += blockDim.x) keys[base + q] = sk[q];
 }
 
+// The whole bitonic network of n2 <= kSortBlockMax keys in one CTA's shared memory
+// (one launch instead of one per stage for the arrays of the first adaptive levels);
+// the keys are unique, so the result is the array the per-stage kernels produce.
+constexpr int64_t kSortBlockMax = 16384;  // 128 KB of shared memory
+constexpr int kSortBlockThreads = 1024;
+
+__global__ void __launch_bounds__(kSortBlockThreads) k_bitonic_block(unsigned long long *keys, int64_t n2)
+{
+    extern __shared__ unsigned long long sk[];
+    const int n = (int)n2, half = n / 2;
+    for (int q = threadIdx.x; q < n; q += blockDim.x) sk[q] = keys[q];
+    __syncthreads();
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j >= 1; j >>= 1) {
+            for (int t = threadIdx.x; t < half; t += blockDim.x) {
+                const int i = 2 * j * (t / j) + (t % j);
+                const bool asc = (i & k) == 0;
+                const unsigned long long a = sk[i], b = sk[i + j];
+                if ((a > b) == asc) {
+                    sk[i] = b;
+                    sk[i + j] = a;
+                }
+            }
+            __syncthreads();
+        }
+    for (int q = threadIdx.x; q < n; q += blockDim.x) keys[q] = sk[q];
+}
+
 // Running FP64 sums of eta2 in key order, in a fixed two-level order: the sorted
 // sequence is cut into blocks of kDorflerBlock; l = the running sum inside a block
 // (from 0, left to right), o_b = the offset of block b (o_0 = 0, o_(b+1) = o_b +
@@ -263,6 +291,20 @@ __global__ void k_mark(const unsigned long long *keys, int64_t N, const long lon
 void sort_u64(bem_ctx *ctx, unsigned long long *keys, int64_t n2)
 {
     cudaStream_t s = ctx->stream;
+    if (n2 <= kSortBlockMax) {
+        const size_t smem = sizeof(unsigned long long) * (size_t)n2;
+        bool ok = true;  // shared memory beyond 48 KB needs the opt-in
+        if (smem > 48 * 1024 && cudaFuncSetAttribute(k_bitonic_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     (int)(sizeof(unsigned long long) * kSortBlockMax)) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+        }
+        if (ok) {
+            const int threads = (int)std::min<int64_t>(kSortBlockThreads, std::max<int64_t>(n2 / 2, 32));
+            k_bitonic_block<<<1, threads, smem, s>>>(keys, n2); BEM_COUNT(ctx);
+            return;
+        }
+    }
     const int64_t chunk = n2 < 2048 ? n2 : 2048;
     const int sthreads = (int)(chunk / 2);
     for (int64_t k = 2; k <= n2; k <<= 1) {
@@ -328,6 +370,35 @@ __global__ void k_nvb_seed(const int32_t *owner, const uint8_t *marked, int64_t 
 }
 
 // One closure sweep: a triangle with a marked edge marks its reference edge.
+// The closure to its fixed point in one CTA (meshes up to kCloseBlockMax triangles):
+// sweeps until one changes nothing.  Flags only go from 0 to 1, so the fixed point
+// (the least closed set containing the seeds) does not depend on the order of the
+// updates; each sweep that changes something sets at least one of the 3N flags, so
+// 3N + 1 sweeps always reach it.
+constexpr int64_t kCloseBlockMax = 65536;
+
+__global__ void __launch_bounds__(1024) k_nvb_close_block(const int32_t *owner, int64_t N, uint8_t *flag)
+{
+    __shared__ int changed;
+    for (int64_t sweep = 0; sweep <= 3 * N; ++sweep) {
+        if (threadIdx.x == 0) changed = 0;
+        __syncthreads();
+        int c = 0;
+        for (int64_t t = threadIdx.x; t < N; t += blockDim.x) {
+            const int32_t o0 = owner[3 * t];
+            if (!flag[o0] && (flag[owner[3 * t + 1]] | flag[owner[3 * t + 2]])) {
+                flag[o0] = 1;
+                c = 1;
+            }
+        }
+        if (c) changed = 1;
+        __syncthreads();
+        const int done = !changed;
+        __syncthreads();  // every thread has read changed before thread 0 clears it
+        if (done) return;
+    }
+}
+
 __global__ void k_nvb_close(const int32_t *owner, int64_t N, uint8_t *flag, int32_t *changed)
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -441,9 +512,13 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
     TRY(dalloc(ctx, tmp, (void **)&n_child, sizeof(int32_t) * (N + 1), false));
     TRY(dalloc(ctx, tmp, (void **)&child_pos, sizeof(int32_t) * (N + 1), false));
     k_nvb_seed<<<nblk(N, 256), 256, 0, s>>>(m->owner, d_marked, N, flags & BEM_REFINE_BISEC3, flag); BEM_COUNT(ctx);
-    // closure sweeps, eight per check of the changed flag (a sweep after the fixed
-    // point changes nothing; a level's closure rarely needs more than eight)
-    for (int sweep = 0;; sweep += 8) {
+    // closure: in one CTA for meshes up to kCloseBlockMax triangles; larger ones by
+    // sweeps over the grid, eight per check of the changed flag (a sweep after the
+    // fixed point changes nothing; a level's closure rarely needs more than eight)
+    if (N <= kCloseBlockMax) {
+        k_nvb_close_block<<<1, 1024, 0, s>>>(m->owner, N, flag); BEM_COUNT(ctx);
+    }
+    for (int sweep = 0; N > kCloseBlockMax; sweep += 8) {
         if (sweep > 100000) {
             st = set_error(ctx, BEM_ERR_MESH, "NVB closure did not terminate");
             goto fail;
