@@ -53,6 +53,17 @@ __device__ __forceinline__ float2 df_add(float2 a, float2 b)
     return make_float2(h, l);
 }
 
+// a + b as df_add without the final renormalisation: hi is the rounded sum of the
+// hi parts and lo collects the rest, so |lo| may exceed ulp(hi) / 2 by a few units
+// of the lo parts' rounding.  For intermediate sums whose result goes through
+// df_add (or df_to_double) before it is stored.
+__device__ __forceinline__ float2 df_add_u(float2 a, float2 b)
+{
+    float s, e;
+    two_sum(a.x, b.x, s, e);
+    return make_float2(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+
 // (ah + al) * (bh + bl), renormalised.
 __device__ __forceinline__ float2 df_mul(float2 a, float2 b)
 {

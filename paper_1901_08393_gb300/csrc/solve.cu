@@ -491,22 +491,25 @@ __device__ void symv_hi_tiles(const float *__restrict__ vp, const int2 *__restri
             for (int m = 0; m < 8; ++m) {
                 const float2 xr = xsw[r0 + m];
                 const float e[4] = {v[m].x, v[m].y, v[m].z, v[m].w};
-                float h = 0.f, l = 0.f;
+                // the row sum starts from the first exact product itself (a two-sum
+                // with zero adds nothing)
+                float h, l;
+                two_prod(e[0], xc[0].x, h, l);
+                l = __fmaf_rn(e[0], xc[0].y, l);
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    acc_hi(h, l, e[u], xc[u].x, xc[u].y);
-                    acc_hi(cs[u].x, cs[u].y, e[u], xr.x, xr.y);
-                }
+                for (int u = 1; u < 4; ++u) acc_hi(h, l, e[u], xc[u].x, xc[u].y);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc_hi(cs[u].x, cs[u].y, e[u], xr.x, xr.y);
                 sr[m] = make_float2(h, l);
             }
-            // rows m of this lane: 8 -> 4 (xor 8) -> 2 (xor 4) -> 1 (xor 2), then xor 1;
-            // lane keeps row (l / 2) % 8
+            // rows m of this lane: 8 -> 4 (xor 8) -> 2 (xor 4) -> 1 (xor 2), then xor 1
+            // (renormalised there); lane keeps row (l / 2) % 8
             float2 t4[4], t2[2];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) t4[j] = df_add(b3 ? sr[j + 4] : sr[j], shfl_df(b3 ? sr[j] : sr[j + 4], 8));
+            for (int j = 0; j < 4; ++j) t4[j] = df_add_u(b3 ? sr[j + 4] : sr[j], shfl_df(b3 ? sr[j] : sr[j + 4], 8));
 #pragma unroll
-            for (int j = 0; j < 2; ++j) t2[j] = df_add(b2 ? t4[j + 2] : t4[j], shfl_df(b2 ? t4[j] : t4[j + 2], 4));
-            float2 w = df_add(b1 ? t2[1] : t2[0], shfl_df(b1 ? t2[0] : t2[1], 2));
+            for (int j = 0; j < 2; ++j) t2[j] = df_add_u(b2 ? t4[j + 2] : t4[j], shfl_df(b2 ? t4[j] : t4[j + 2], 4));
+            float2 w = df_add_u(b1 ? t2[1] : t2[0], shfl_df(b1 ? t2[0] : t2[1], 2));
             const float2 o = shfl_df(w, 1);
             w = (lane & 1) ? df_add(o, w) : df_add(w, o);
             if (!(lane & 1)) prow[(int64_t)k * kSB + r0 + ((lane >> 1) & 7)] = w;
