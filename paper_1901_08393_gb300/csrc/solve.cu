@@ -399,6 +399,17 @@ __device__ __forceinline__ double symv_row4(const float2 *__restrict__ prow, con
     const int64_t rbase = tile_pos(I, I, nb) * kSB + r;
     float2 s = make_float2(0.f, 0.f);
     int J = J0;
+    // 16 partials in flight per thread (L2 round trips, not the adds, bound this pass)
+    for (; J + 16 <= J1; J += 16) {
+        float2 v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int j = J + u;
+            v[u] = j < I ? __ldcg(pcol + tile_pos(j, I, nb) * kSB + r) : __ldcg(prow + rbase + (int64_t)(j - I) * kSB);
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) s = df_add(s, v[u]);
+    }
     for (; J + 4 <= J1; J += 4) {
         float2 v[4];
 #pragma unroll
@@ -830,6 +841,13 @@ __device__ __forceinline__ void block_apply(const int32_t *__restrict__ perm, co
 {
     const int t = threadIdx.x;
     const int32_t *pk = perm + (int64_t)blk * kBJ;
+    // this thread's row slice of the inverse block, loaded first: it does not depend
+    // on r, so its latency overlaps the gather below
+    const int i = t >> 2, c = t & 3;
+    const double2 *Mi = reinterpret_cast<const double2 *>(binv + (int64_t)blk * kBJ * kBJ + i * kBJ + 16 * c);
+    double2 m[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) m[u] = Mi[u];
     if (t < kBJ) {
         const int32_t g = pk[t];
         double v = 0.0;
@@ -845,11 +863,6 @@ __device__ __forceinline__ void block_apply(const int32_t *__restrict__ perm, co
         rs[t] = v;
     }
     __syncthreads();
-    const int i = t >> 2, c = t & 3;
-    const double2 *Mi = reinterpret_cast<const double2 *>(binv + (int64_t)blk * kBJ * kBJ + i * kBJ + 16 * c);
-    double2 m[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) m[u] = Mi[u];
     double sacc = 0.0;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
