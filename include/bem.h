@@ -352,12 +352,13 @@ bem_status bem_operator_preconditioner(const bem_operator *op, int32_t which, fl
  * cluster orders.  bem_batch_run runs every wave in turn: the assembly of all its
  * operators (Eq. 2.4-2.5) by one launch per phase -- the far field over a work list of
  * (problem, tile) items with one tile shape (the autotuned one of the wave's largest
- * size class), the mirror of the lower triangles, the Sauter-Schwab near field over
- * all touching pairs -- entries bit-identical to bem_assemble_V's; then the diagonals,
- * right-hand sides and preconditioners; then ONE cooperative launch of the persistent
- * solver of bem_solve_capacity (sopts: tol, max_it, precond, reliable_delta; x = 0
- * start) in which problem p owns a share of the CTAs in proportion to its work and
- * has its own grid barrier; then every Cap (Eq. 2.8).  The work runs on a stream of
+ * size class), the mirror of the diagonal 64 x 64 blocks (the solves read only the
+ * upper triangles), the Sauter-Schwab near field over all touching pairs -- upper
+ * triangles bit-identical to bem_assemble_V's; then the diagonals, right-hand sides and
+ * preconditioners; then the persistent solver of bem_solve_capacity (sopts: tol,
+ * max_it, precond, reliable_delta; x = 0 start), one cooperative launch per group of
+ * problems of similar size, in which problem p owns a share of the CTAs in proportion
+ * to its work and has its own grid barrier; then every Cap (Eq. 2.8).  The work runs on a stream of
  * the batch; with use_graph each wave is recorded once as a CUDA graph on the first
  * run and later runs replay it.  The call blocks until the results are on the host;
  * results (nullable, count entries, in the given order) receive them;

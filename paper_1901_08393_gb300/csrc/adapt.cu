@@ -486,7 +486,7 @@ __global__ void k_nvb_tris(const int32_t *tris, const int32_t *owner, const uint
     }
 }
 
-bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out)
+bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out, bool defer_check)
 {
     bem_ctx *ctx = m->ctx;
     cudaStream_t s = ctx->stream;
@@ -541,10 +541,20 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
     TRY(exclusive_scan_i32(ctx, is_new, new_pos, H, nullptr));
     TRY(exclusive_scan_i32(ctx, is_kept, kept_pos, N, nullptr));
     TRY(exclusive_scan_i32(ctx, n_child, child_pos, N, nullptr));
-    {  // the three totals in one read
-        const int32_t *src[3] = {new_pos + H, kept_pos + N, child_pos + N};
-        int64_t tot[3] = {0, 0, 0};
-        TRY(read_i32s(ctx, src, 3, tot));
+    {  // the three totals in one read, with the source mesh's deferred checks
+        const bool chk = m->bad_pending != 0;
+        const int32_t *src[6] = {new_pos + H, kept_pos + N, child_pos + N, nullptr, nullptr, nullptr};
+        if (chk) {
+            src[3] = m->d_bad + 1;
+            src[4] = m->d_bad + 2;
+            src[5] = m->d_bad + 3;
+        }
+        int64_t tot[6] = {0, 0, 0, 0, 0, 0};
+        TRY(read_i32s(ctx, src, chk ? 6 : 3, tot));
+        if (chk) {
+            m->bad_pending = 0;
+            TRY(mesh_bad_status(ctx, tot + 3));
+        }
         n_new = tot[0];
         n_kept = tot[1];
         n_children = tot[2];
@@ -574,7 +584,7 @@ bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **ou
         st = set_error(ctx, BEM_ERR_CUDA, "refinement kernels");
         goto fail;
     }
-    TRY(mesh_build(r, false, nullptr));
+    TRY(mesh_build(r, false, nullptr, defer_check));
     dfree_all(ctx, tmp);
     *out = r;
     return BEM_OK;

@@ -1078,7 +1078,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
                     if (e != cudaSuccess) st = cuda_error(ctx, e, "Doerfler count");
                 }
             }
-            if (!st) st = refine(cur, dm, 0, &next);  // synchronises: the new mesh's sizes
+            // synchronises: the new mesh's sizes; the new mesh's checks are read with
+            // the next level's sizes (or at the end)
+            if (!st) st = refine(cur, dm, 0, &next, true);
             dfree_all(ctx, mk);
         }
         cudaEventRecord(ev[3], s);
@@ -1116,7 +1118,8 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         prev_mesh = cur;
         cur = next;
     }
-    // per-phase device times of every level that ran
+    // the last mesh's deferred checks, then the per-phase device times of every level
+    if (!st && cur != mesh) st = mesh_check_pending(cur);
     cudaStreamSynchronize(s);
     for (int l = 0; l < *n_levels; ++l) {
         cudaEvent_t *ev = &ctx->lvl_ev[4 * (size_t)l];

@@ -860,16 +860,18 @@ __global__ void __launch_bounds__(C, (MB > 0 ? MB : 1))
 }
 
 // Tile pair t of a problem: row tile bi >= column tile bj, t = bi (bi + 1) / 2 + bj.
+// A batch's operators are read only through their upper triangle (the packed tiles, the
+// DF64 tile products, the symmetric reads of the block preconditioner), so only the
+// 64 x 64 diagonal blocks, whose lower halves those tiles include, are mirrored: 32 x 32
+// tiles (2D, 2D), (2D+1, 2D), (2D+1, 2D+1) of block D, item t = 3 D + (0, 1, 2).
 template <typename T>
 __global__ void k_mirror_batch(const BatchAsmProb *__restrict__ prob, const int64_t *__restrict__ pref, int P)
 {
     const int64_t k = blockIdx.x;
     const int p = batch_find(pref, P, k);
     const int64_t t = k - pref[p];
-    int64_t bi = (int64_t)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
-    while ((bi + 1) * (bi + 2) / 2 <= t) ++bi;
-    while (bi * (bi + 1) / 2 > t) --bi;
-    const int64_t bj = t - bi * (bi + 1) / 2;
+    const int64_t D = t / 3, r = t % 3;
+    const int64_t bi = 2 * D + (r > 0 ? 1 : 0), bj = 2 * D + (r == 2 ? 1 : 0);
     const BatchAsmProb *pb = prob + p;
     mirror_tile<T>((T *)pb->V, pb->ld, 0, pb->N, 32 * bi, 32 * bj);
 }

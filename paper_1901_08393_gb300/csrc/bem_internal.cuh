@@ -104,6 +104,10 @@ struct bem_mesh {
     int64_t n_kept = 0;         // refined meshes: triangles [0, n_kept) are unrefined
     int64_t src_N = 0;          // refined meshes: N of the source mesh
     int cells_only = 0;         // dual cells of an operator from bem_operator_dual: N, area, cent only
+    // checks of a mesh built by the adaptive loop's refinement (degenerate, not closed,
+    // duplicate: flags 1..3 of d_bad), read with the next count the loop needs anyway
+    int32_t *d_bad = nullptr;
+    int bad_pending = 0;
     bem::Allocs allocs;
 };
 
@@ -170,7 +174,9 @@ bem_status read_i32s(bem_ctx *ctx, const int32_t *const *src, int n, int64_t *ou
 
 // ----------------------------------------------------------------- mesh (mesh.cu)
 // Build every derived array of a mesh whose verts / tris are already on the device.
-bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge);
+bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge, bool defer_check = false);
+// the error of the mesh check flags bad[1..3] (BEM_OK if none is raised)
+bem_status mesh_bad_status(bem_ctx *ctx, const int64_t *bad3);
 
 // ----------------------------------------------------------------- assembly (assemble.cu)
 bem_status gauss_legendre_upload(int n);
@@ -203,7 +209,7 @@ struct BatchAsm {
     const BatchAsmProb *prob = nullptr;    // P entries
     const int4 *far_items = nullptr;       // (problem, first row, first column, 0) per far-field tile
     int64_t n_far = 0;
-    const int64_t *mirror_pref = nullptr;  // P + 1: prefix of the 32 x 32 tile pairs (row tile >= column tile)
+    const int64_t *mirror_pref = nullptr;  // P + 1: prefix of the 32 x 32 tiles in the diagonal 64 x 64 blocks
     int64_t n_mirror = 0;
     const int64_t *near_pref = nullptr;    // P + 1: prefix of N + touching pairs
     int64_t n_near = 0;
@@ -261,6 +267,9 @@ void sort_u64(bem_ctx *ctx, unsigned long long *keys, int64_t n2);
 // (nullable, device) receives the count without synchronising.
 bem_status dorfler(bem_ctx *ctx, const double *d_eta2, int64_t N, double theta, uint8_t *d_marked,
                    int64_t *n_marked, const double *d_vanish = nullptr, long long *d_count = nullptr);
-bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out);
+// defer_check: the refined mesh's checks are read by the next refine of it (or by
+// mesh_check_pending) instead of a synchronisation of their own
+bem_status refine(bem_mesh *m, const uint8_t *d_marked, int flags, bem_mesh **out, bool defer_check = false);
+bem_status mesh_check_pending(bem_mesh *m);
 
 }  // namespace bem

@@ -395,7 +395,26 @@ static bem_status read_bad(bem_ctx *ctx, const int32_t *d_bad, int32_t *h_bad)
     return BEM_OK;
 }
 
-bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge)
+bem_status mesh_bad_status(bem_ctx *ctx, const int64_t *bad3)
+{
+    if (bad3[0]) return set_error(ctx, BEM_ERR_MESH, "degenerate triangle (zero area)");
+    if (bad3[1]) return set_error(ctx, BEM_ERR_MESH, "mesh is not closed (an edge is used an odd number of times)");
+    if (bad3[2]) return set_error(ctx, BEM_ERR_MESH, "duplicate triangle");
+    return BEM_OK;
+}
+
+bem_status mesh_check_pending(bem_mesh *m)
+{
+    if (!m->bad_pending) return BEM_OK;
+    const int32_t *src[3] = {m->d_bad + 1, m->d_bad + 2, m->d_bad + 3};
+    int64_t b[3] = {0, 0, 0};
+    bem_status st = read_i32s(m->ctx, src, 3, b);
+    if (st) return st;
+    m->bad_pending = 0;
+    return mesh_bad_status(m->ctx, b);
+}
+
+bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge, bool defer_check)
 {
     bem_ctx *ctx = m->ctx;
     const int64_t N = m->N, M = m->M;
@@ -409,7 +428,7 @@ bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge)
         st = (x);                 \
         if (st) goto done;        \
     } while (0)
-    TRY(dalloc(ctx, tmp, (void **)&bad, 4 * sizeof(int32_t), true));
+    TRY(dalloc(ctx, defer_check ? m->allocs : tmp, (void **)&bad, 4 * sizeof(int32_t), true));
     if (canonicalize) {
         // a caller's mesh: indices checked before any kernel follows them (meshes made
         // by the library's refinements have valid indices by construction)
@@ -481,10 +500,14 @@ bem_status mesh_build(bem_mesh *m, bool canonicalize, const uint8_t *d_ref_edge)
                                                    ov, m->edge_pairs, m->vert_pairs, te, tv, bad); BEM_COUNT(ctx);
         BEM_CK_LAUNCH(ctx);
     }
-    TRY(read_bad(ctx, bad, hb));
-    if (hb[1]) st = set_error(ctx, BEM_ERR_MESH, "degenerate triangle (zero area)");
-    else if (hb[2]) st = set_error(ctx, BEM_ERR_MESH, "mesh is not closed (an edge is used an odd number of times)");
-    else if (hb[3]) st = set_error(ctx, BEM_ERR_MESH, "duplicate triangle");
+    if (defer_check) {
+        m->d_bad = bad;
+        m->bad_pending = 1;
+    } else {
+        TRY(read_bad(ctx, bad, hb));
+        const int64_t b3[3] = {hb[1], hb[2], hb[3]};
+        st = mesh_bad_status(ctx, b3);
+    }
 done:
 #undef TRY
     dfree_all(ctx, tmp);

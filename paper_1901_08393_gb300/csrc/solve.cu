@@ -769,7 +769,10 @@ __device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int6
     for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
         const int i = idx / kBJ, j = idx % kBJ;
         const int32_t gi = pk[i], gj = pk[j];
-        const double a = (gi >= 0 && gj >= 0) ? elem_f64(V, (int64_t)gi * ld + gj) : (i == j ? 1.0 : 0.0);
+        // upper-triangle read: V (i, j) for i <= j (batch operators mirror only their
+        // diagonal blocks; mirrored entries are bit-identical copies)
+        const int64_t lo = gi < gj ? gi : gj, hi = gi < gj ? gj : gi;
+        const double a = (gi >= 0 && gj >= 0) ? elem_f64(V, lo * ld + hi) : (i == j ? 1.0 : 0.0);
         A[i][j] = (float)(a * sc[i] * sc[j]);
     }
     __syncthreads();
@@ -2474,8 +2477,8 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
             c.V = op->V;
             c.ld = L;
             c.N = N;
-            const int64_t T = (N + 31) / 32;
-            mpref[k + 1] = mpref[k] + T * (T + 1) / 2;
+            const int64_t T = (N + 31) / 32;  // 32 x 32 tiles inside the diagonal 64 x 64 blocks
+            mpref[k + 1] = mpref[k] + 3 * (T / 2) + (T % 2);
             npref[k + 1] = npref[k] + N + m->n_vert_pairs + m->n_edge_pairs;
             far_entries += 0.5 * (double)N * (double)(N + 1);
         }
