@@ -78,9 +78,62 @@ __global__ void k_scan_add(int32_t *out, int64_t n, const int32_t *block_offsets
         if (i + k < n) out[i + k] += off;
 }
 
+// Whole scan in one CTA for short inputs (up to kScanSingleMax): chunks of 4096 scanned
+// in turn with a running carry, out[n] = total written by the kernel.  Saves the
+// second-level launches, allocations and the total's copy of the multi-block scan for
+// the per-level tables of the adaptive loop.
+constexpr int64_t kScanSingleMax = 16384;
+__global__ void __launch_bounds__(1024) k_scan_single(const int32_t *in, int32_t *out, int64_t n)
+{
+    __shared__ int32_t wsum[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t carry = 0;
+    for (int64_t c0 = 0; c0 < n; c0 += 4096) {
+        const int64_t base = c0 + threadIdx.x * 4;
+        int32_t v[4], s = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = (base + k < n) ? in[base + k] : 0;
+            s += v[k];
+        }
+        int32_t x = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) wsum[w] = x;
+        __syncthreads();
+        if (w == 0) {
+            int32_t t = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int32_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+            wsum[lane] = t;
+        }
+        __syncthreads();
+        int32_t excl = carry + x - s + (w > 0 ? wsum[w - 1] : 0);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (base + k < n) out[base + k] = excl;
+            excl += v[k];
+        }
+        carry += wsum[31];
+        __syncthreads();  // wsum is rewritten by the next chunk
+    }
+    if (threadIdx.x == 0) out[n] = carry;
+}
+
 static bem_status scan_rec(bem_ctx *ctx, const int32_t *in, int32_t *out, int64_t n, Allocs &tmp)
 {
     // out[0..n) exclusive, out[n] = total
+    if (n <= kScanSingleMax) {
+        k_scan_single<<<1, 1024, 0, ctx->stream>>>(in, out, n); BEM_COUNT(ctx);
+        BEM_CK_LAUNCH(ctx);
+        return BEM_OK;
+    }
     const int64_t nb = (n + 4095) / 4096;
     int32_t *bs = nullptr;
     bem_status st = dalloc(ctx, tmp, (void **)&bs, sizeof(int32_t) * (nb + 1), false);

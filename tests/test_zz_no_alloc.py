@@ -67,3 +67,40 @@ def test_no_alloc_matvec_rejects_what_it_cannot_do():
     xh = np.zeros(small.N)
     st = L.bem_operator_matvec_noalloc(opdf.h, ctypes.c_void_p(xh.ctypes.data), ctypes.c_void_p(y2.data_ptr()))
     assert st == bem.BEM_ERR_INVALID and "device pointers" in ctx.last_error()
+
+
+def test_no_alloc_matvec_inside_graph_capture():
+    """The call recorded into a CUDA graph under global capture mode (which refuses
+    device allocation from any thread while the capture runs), then replayed."""
+    import torch
+
+    s = torch.cuda.Stream()
+    ctx = bem.Context(stream=s.cuda_stream)
+    L = bem.lib()
+    m = inputs.workload_polycube_adaptive()
+    mesh = bem.Mesh.upload(ctx, m.verts, m.tris)
+    op = bem.Operator.assemble(mesh, precision=bem.PREC_DF64)
+    x = np.random.default_rng(7).standard_normal(m.N)
+    y_ref = op.matvec(x)
+    xd = torch.from_numpy(x).cuda()
+    yd = torch.zeros(m.N, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    # the first call outside capture (its one-time set-up may query the runtime)
+    st = L.bem_operator_matvec_noalloc(op.h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()))
+    assert st == bem.BEM_OK, ctx.last_error()
+    torch.cuda.synchronize()
+    held = ctx.memory_in_use()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="global"):
+        st = L.bem_operator_matvec_noalloc(op.h, ctypes.c_void_p(xd.data_ptr()), ctypes.c_void_p(yd.data_ptr()))
+    assert st == bem.BEM_OK, ctx.last_error()
+    for _ in range(2):
+        yd.fill_(float("nan"))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        y = yd.cpu().numpy()
+        assert np.max(np.abs(y - y_ref)) <= 1e-13 * np.max(np.abs(y_ref))
+    assert ctx.memory_in_use() == held
+    op.close()
+    mesh.close()
