@@ -238,7 +238,7 @@ def roofline(prec, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_
         avg_s = mv_ms / max(mv_n, 1) / 1e3
         achieved = bytes_ / avg_s / 1e9
         # DRAM bytes (read + write) over algorithmic bytes of one ncu capture of k_pcg_df
-        # (adaptive polycube level N = 12,558: 18.04 GB measured, 18.29 GB algorithmic);
+        # (adaptive polycube level N = 12,558: 18.07 GB measured, 18.29 GB algorithmic);
         # traffic scales with the bytes of the products, so the ratio carries to full size
         traffic = PCG_TRAFFIC_RATIO * bytes_ if prec == 2 else None
         roof = {"kernel": {0: "k_matvec<double>", 1: "k_matvec<float>",
@@ -698,6 +698,7 @@ def server_workload(args):
     if ws > 1:
         torch.distributed.barrier()
     clocks = Clocks(local)
+    srv.profile(True)  # every slot's hot kernels, from its next request on
     clocks.start()
     lat, tp, spans, fails, solves = [], [], [], 0, 0
     res = None
@@ -710,6 +711,15 @@ def server_workload(args):
         fails += sum(1 for r in res if r["status"] != 0)
         solves += sum(r["levels"] for r in res)
     clk = clocks.stop()
+    # the timed requests' kernels, summed over the slots (the server is idle here)
+    far_n, far_ms, far_units = srv.profile_read(bem.KERNEL_FAR)
+    mv_n, mv_ms, mv_units = srv.profile_read(bem.KERNEL_MATVEC)
+    srv.profile(False)
+    peaks, peak_src = _peaks()
+    roof = roofline(1, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src,
+                    mv_kernel="k_pcg_df (FP32 operator: packed-tile products, residual at convergence)")
+    roof["note"] = ("CUDA events around each slot's launches over the timed requests; the requests run "
+                    "concurrently, so a launch's time includes the kernels of other requests beside it")
     sat = None
     if args.workload == "serve":
         rs = run_stream(False)
@@ -730,7 +740,7 @@ def server_workload(args):
         "final_N": {"min": nf[0], "p10": _pct(nf, 0.1), "p50": _pct(nf, 0.5), "p90": _pct(nf, 0.9), "max": nf[-1]},
         "levels_hist": {str(k): sum(1 for r in res if r["levels"] == k) for k in range(1, 7)},
         "p50_latency_ms": _pct(lat, 0.5), "p99_latency_ms": _pct(lat, 0.99),
-        "saturation_requests_per_s": sat, "clocks": clk, "roofline": None, "cpu_baseline": None,
+        "saturation_requests_per_s": sat, "clocks": clk, "roofline": roof, "cpu_baseline": None,
         "e2e": {"value": value, "unit": "capacity requests/s",
                 "h2d_bytes_per_step": int(sum(m.verts.nbytes + m.tris.nbytes for m, _, _, _ in jobs)),
                 "d2h_bytes_per_step": len(jobs) * 512},

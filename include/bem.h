@@ -426,6 +426,14 @@ bem_status bem_server_submit(bem_server *s, const double *verts, int64_t M, cons
 /* Block until request id has finished, return its result and forget it. */
 bem_status bem_server_wait(bem_server *s, int64_t id, bem_request_result *out);
 bem_status bem_server_stats(bem_server *s, bem_server_stats_t *out);
+/* Profiling of the slots' hot kernels (bem_profile_enable / bem_profile_read on every
+ * slot's context).  bem_server_profile_enable takes effect at each slot's next request
+ * (enabling restarts its counts); bem_server_profile_read returns the sums over the
+ * slots and needs an idle server -- no request queued or running -- else
+ * BEM_ERR_INVALID.  The kernels of concurrent requests share the GPU, so a launch's
+ * event time includes the time other requests' kernels ran beside it. */
+bem_status bem_server_profile_enable(bem_server *s, int32_t on);
+bem_status bem_server_profile_read(bem_server *s, int32_t kernel, int64_t *launches, double *ms, double *units);
 /* Finish every queued request, then stop the slot threads and free the server. */
 bem_status bem_server_destroy(bem_server *s);
 

@@ -42,6 +42,7 @@ EXPORTS = [
     "bem_zz_estimate", "bem_dorfler", "bem_refine", "bem_mark_refine", "bem_adaptive_run",
     "bem_profile_enable", "bem_profile_read", "bem_launch_count", "bem_operator_matvec_noalloc", "bem_context_set_persistent",
     "bem_server_create", "bem_server_submit", "bem_server_wait", "bem_server_stats", "bem_server_destroy",
+    "bem_server_profile_enable", "bem_server_profile_read",
     "bem_batch_create", "bem_batch_run", "bem_batch_info", "bem_batch_destroy",
     "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual", "bem_operator_preconditioner",
     "bem_far_tiles", "bem_debug_barrier_fault", "bem_batch_waves",
@@ -152,6 +153,8 @@ def lib():
         "bem_server_wait": [vp, i64, P(RequestResult)],
         "bem_server_stats": [vp, P(ServerStats)],
         "bem_server_destroy": [vp],
+        "bem_server_profile_enable": [vp, i32],
+        "bem_server_profile_read": [vp, i32, P(i64), P(C.c_double), P(C.c_double)],
         "bem_batch_create": [vp, i32, vp, P(AssemblyOpts), P(SolveOpts), i32, P(vp)],
         "bem_batch_run": [vp, vp],
         "bem_batch_info": [vp, P(i32), P(i32), P(i32)],
@@ -567,6 +570,20 @@ class Server:
                 "t_submit": r.t_submit, "t_start": r.t_start, "t_done": r.t_done,
                 "estimate_bytes": r.estimate_bytes, "caps": list(r.cap_history[:n]),
                 "Ns": list(r.N_history[:n]), "message": r.message.decode(errors="replace")}
+
+    def profile(self, on: bool = True):
+        """Profile the slots' hot kernels from each slot's next request on."""
+        st = self.L.bem_server_profile_enable(self.h, int(on))
+        if st != BEM_OK:
+            raise BemError(st, "server profile enable failed")
+
+    def profile_read(self, kernel: int):
+        """(launches, ms, units) summed over the slots; the server must be idle."""
+        n, ms, u = C.c_int64(), C.c_double(), C.c_double()
+        st = self.L.bem_server_profile_read(self.h, int(kernel), C.byref(n), C.byref(ms), C.byref(u))
+        if st != BEM_OK:
+            raise BemError(st, "server profile read needs an idle server")
+        return int(n.value), float(ms.value), float(u.value)
 
     def stats(self):
         s = ServerStats()

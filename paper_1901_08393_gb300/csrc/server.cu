@@ -48,6 +48,8 @@ struct bem_server {
     int64_t in_flight_bytes = 0, peak_bytes = 0;
     int in_flight = 0, peak_in_flight = 0;
     bool stop = false;
+    int profile = 0;                 // slots profile their hot kernels (bem_profile_enable)
+    std::vector<bem_ctx *> ctxs;     // the slots' contexts, for the profile read
     std::chrono::steady_clock::time_point t0;
 
     double now() const
@@ -132,8 +134,14 @@ void worker_main(bem_server *srv)
     }
     bem_ctx *ctx = nullptr;
     if (bem_context_create(stream, 0, &ctx) != BEM_OK) ctx = nullptr;
+    if (ctx) {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->ctxs.push_back(ctx);
+    }
+    int prof_on = 0;
     for (;;) {
         Request *r = nullptr;
+        int want_prof = 0;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             for (;;) {
@@ -155,6 +163,11 @@ void worker_main(bem_server *srv)
             if (srv->in_flight_bytes > srv->peak_bytes) srv->peak_bytes = srv->in_flight_bytes;
             if (srv->in_flight > srv->peak_in_flight) srv->peak_in_flight = srv->in_flight;
             r->res.t_start = srv->now();
+            want_prof = srv->profile;
+        }
+        if (ctx && want_prof != prof_on) {  // this slot's context, on its own thread
+            bem_profile_enable(ctx, want_prof);
+            prof_on = want_prof;
         }
         run_request(srv, r, ctx);
         {
@@ -253,6 +266,37 @@ bem_status bem_server_stats(bem_server *s, bem_server_stats_t *out)
     out->peak_bytes = s->peak_bytes;
     out->budget = s->budget;
     out->clock = s->now();
+    return BEM_OK;
+}
+
+bem_status bem_server_profile_enable(bem_server *s, int32_t on)
+{
+    if (!s) return BEM_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->profile = on ? 1 : 0;
+    return BEM_OK;
+}
+
+bem_status bem_server_profile_read(bem_server *s, int32_t kernel, int64_t *launches, double *ms, double *units)
+{
+    if (!s || kernel < 0 || kernel >= bem::kProfKinds) return BEM_ERR_INVALID;
+    // the lock is held throughout, so that no slot starts a request on its context
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->in_flight != 0 || !s->queue.empty()) return BEM_ERR_INVALID;
+    int64_t n = 0;
+    double t = 0.0, u = 0.0;
+    for (bem_ctx *c : s->ctxs) {
+        int64_t cn = 0;
+        double cms = 0.0, cu = 0.0;
+        const bem_status st = bem_profile_read(c, kernel, &cn, &cms, &cu);
+        if (st) return st;
+        n += cn;
+        t += cms;
+        u += cu;
+    }
+    if (launches) *launches = n;
+    if (ms) *ms = t;
+    if (units) *units = u;
     return BEM_OK;
 }
 

@@ -93,3 +93,19 @@ def test_dual_basis_requests(cuda):
         assert r["status"] == 0, r["message"]
         recs, _ = bem.adaptive_run(bem.Mesh.upload(ctx, m.verts, m.tris), max_N=mx, max_levels=lv, tol=1e-10, **kw)
         assert [x["cap"] for x in recs] == r["caps"] and [x["N"] for x in recs] == r["Ns"]
+
+
+def test_server_profile_counts_the_slots_kernels(cuda):
+    """Profiling through the server sums every slot's hot kernels; results do not change."""
+    reqs = _requests()[:3]
+    srv = bem.Server(slots=2, hbm_budget_bytes=16 << 30, precision=bem.PREC_F32)
+    plain = [srv.wait(srv.submit(m.verts, m.tris, lv, mx)) for m, lv, mx in reqs]
+    srv.profile(True)
+    prof = [srv.wait(srv.submit(m.verts, m.tris, lv, mx)) for m, lv, mx in reqs]
+    far = srv.profile_read(bem.KERNEL_FAR)
+    mv = srv.profile_read(bem.KERNEL_MATVEC)
+    srv.close()
+    levels = sum(r["levels"] for r in prof)
+    assert far[0] >= len(reqs) and far[1] > 0.0 and far[2] > 0.0
+    assert mv[0] >= levels and mv[1] > 0.0 and mv[2] > 0.0  # a persistent solve per level at least
+    assert [r["caps"] for r in prof] == [r["caps"] for r in plain]
