@@ -790,21 +790,22 @@ def server_workload(args):
                     recs, _ = bem.adaptive_run(mh, theta=THETA, max_N=mx, max_levels=lv, precision=prec, tol=TOL,
                                                max_it=20000, precond=fpc)
                     mh.close()
-                    caps[i] = (recs[-1]["cap"], recs[-1]["N"])
+                    caps[i] = (recs[-1]["cap"], [r["N"] for r in recs])
                 torch.cuda.synchronize()
                 dt = time.perf_counter() - t0
                 # served Cap against the single-problem FP64-accurate run of the same request;
                 # the two runs take their own marking decisions, so near-ties of the
-                # estimator can give them different final meshes (and Caps that differ by
-                # the discretization error): the comparison is split by that
-                same = [i for i in sub if caps[i][1] == res[i]["N_final"]]
-                diff = [i for i in sub if caps[i][1] != res[i]["N_final"]]
+                # estimator can give them different meshes (and Caps that differ by the
+                # discretization error): the comparison is split by whether every level
+                # had the same size in both runs
+                same = [i for i in sub if caps[i][1] == list(res[i]["Ns"])]
+                diff = [i for i in sub if caps[i][1] != list(res[i]["Ns"])]
                 err = lambda ids: max((abs(res[i]["cap"] / caps[i][0] - 1.0) for i in ids), default=None)
                 cmp_[name] = {"requests": len(sub), "requests_per_s": len(sub) / dt,
                               "served_saturation_speedup": sat / (len(sub) / dt) if sat else None,
-                              "same_final_N": len(same),
-                              "served_vs_this_cap_rel_err_max_same_final_N": err(same),
-                              "served_vs_this_cap_rel_err_max_other_final_N": err(diff)}
+                              "same_level_sizes": len(same),
+                              "served_vs_this_cap_rel_err_max_same_level_sizes": err(same),
+                              "served_vs_this_cap_rel_err_max_other_level_sizes": err(diff)}
             line["single_problem_forms"] = cmp_
         ctx.close()
     if rank == 0:
