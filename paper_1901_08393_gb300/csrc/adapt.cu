@@ -141,7 +141,7 @@ __global__ void k_bitonic_global(unsigned long long *keys, int64_t n2, int64_t k
 {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n2 / 2) return;
-    const int64_t i = 2 * j * (t / j) + (t % j);
+    const int64_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // 2 j (t / j) + t % j, j a power of two
     cmp_swap(keys, i, i + j, (i & k) == 0);
 }
 
@@ -155,7 +155,7 @@ __global__ void k_bitonic_shared(unsigned long long *keys, int64_t n2, int64_t k
     __syncthreads();
     for (int64_t j = j0; j >= 1; j >>= 1) {
         const int t = threadIdx.x;
-        const int i = (int)(2 * j * (t / j) + (t % j));
+        const int i = (int)(((t & ~(j - 1)) << 1) | (t & (j - 1)));  // j a power of two
         const bool asc = ((base + i) & k) == 0;
         const unsigned long long a = sk[i], b = sk[i + j];
         if ((a > b) == asc) {
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kSortBlockThreads) k_bitonic_block(unsigned lo
     for (int k = 2; k <= n; k <<= 1)
         for (int j = k >> 1; j >= 1; j >>= 1) {
             for (int t = threadIdx.x; t < half; t += blockDim.x) {
-                const int i = 2 * j * (t / j) + (t % j);
+                const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // 2 j (t / j) + t % j
                 const bool asc = (i & k) == 0;
                 const unsigned long long a = sk[i], b = sk[i + j];
                 if ((a > b) == asc) {
