@@ -560,7 +560,7 @@ static bem_status operator_alloc(bem_mesh *mesh, const bem_assembly_opts *opts, 
 // entries of unrefined pairs from coarse.  sync: wait for the kernels (the public
 // entry points; the adaptive loop lets them run on).
 static bem_status assemble_impl(bem_mesh *mesh, const bem_assembly_opts *opts, const bem_operator *coarse, bool sync,
-                                bem_operator **out)
+                                bem_operator **out, bool upper_only = false)
 {
     bem_ctx *ctx = mesh->ctx;
     *out = nullptr;
@@ -582,7 +582,7 @@ static bem_status assemble_impl(bem_mesh *mesh, const bem_assembly_opts *opts, c
     bem_operator *op = nullptr;
     bem_status st = operator_alloc(mesh, use, &op);
     if (st) return st;
-    st = coarse ? assemble_update(op, coarse) : assemble_full(op);
+    st = coarse ? assemble_update(op, coarse, upper_only) : assemble_full(op, upper_only);
     if (!st && sync) {
         cudaError_t e = cudaStreamSynchronize(ctx->stream);
         if (e != cudaSuccess) st = cuda_error(ctx, e, coarse ? "incremental assembly" : "assembly");
@@ -687,6 +687,10 @@ bem_status bem_operator_read(const bem_operator *op, int64_t i0, int64_t ni, int
     CHECK_ARG(ctx, i0 >= 0 && j0 >= 0 && ni >= 0 && nj >= 0 && i0 + ni <= op->N && j0 + nj <= op->N,
               "block outside the operator");
     if (ni == 0 || nj == 0) return BEM_OK;
+    if (op->upper_only) {  // never the case for operators handed to callers; kept safe
+        bem_status sf = ensure_full(const_cast<bem_operator *>(op));
+        if (sf) return sf;
+    }
     if (op->precision == BEM_PREC_DF64) {
         Allocs tmp;
         double *blk = nullptr;
@@ -722,6 +726,7 @@ bem_status bem_operator_entries(const bem_operator *op, const int64_t *I, const 
     if ((st = dev_out_begin(ctx, out, sizeof(double) * K, dO))) return st;
     Allocs tmp;
     int32_t *bad = nullptr;
+    if (op->upper_only && (st = ensure_full(const_cast<bem_operator *>(op)))) return st;
     if ((st = dalloc(ctx, tmp, (void **)&bad, sizeof(int32_t), true))) return st;
     if (op->precision == BEM_PREC_DF64)
         { k_entries_df<<<nblk(K, 256), 256, 0, ctx->stream>>>((const float2 *)op->V, op->ld, op->N,
@@ -1006,9 +1011,9 @@ bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_l
         if (dual)
             st = dual_level_operator(cur, &opts->assembly, opts->incremental != 0, bary_prev, &op);
         else if (op_prev && opts->incremental && cur->parent)
-            st = assemble_impl(cur, &opts->assembly, op_prev, false, &op);
+            st = assemble_impl(cur, &opts->assembly, op_prev, false, &op, true);
         else
-            st = assemble_impl(cur, &opts->assembly, nullptr, false, &op);
+            st = assemble_impl(cur, &opts->assembly, nullptr, false, &op, true);
         if (op_prev) {
             bem_operator_destroy(op_prev);
             op_prev = nullptr;

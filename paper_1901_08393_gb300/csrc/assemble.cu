@@ -608,12 +608,25 @@ __global__ void k_near(const double *__restrict__ verts, const int32_t *__restri
 // V'[i][j] = Vc[parent[i]][parent[j]] for i, j < K (unrefined triangles).
 template <typename T>
 __global__ void k_gather_kept(const T *__restrict__ Vc, int64_t ldc, const int32_t *__restrict__ parent,
-                              int64_t K, T *__restrict__ V, int64_t ld)
+                              int64_t K, T *__restrict__ V, int64_t ld, int upper)
 {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= K) return;
     const int64_t pj = parent[j];
-    for (int64_t i = blockIdx.y; i < K; i += gridDim.y) V[i * ld + j] = Vc[(int64_t)parent[i] * ldc + pj];
+    // upper: entries i <= j only (the kept triangles keep their order, so these come
+    // from the coarse operator's upper triangle)
+    const int64_t iend = upper ? j + 1 : K;
+    for (int64_t i = blockIdx.y; i < iend; i += gridDim.y) V[i * ld + j] = Vc[(int64_t)parent[i] * ldc + pj];
+}
+
+// Mirror of the diagonal 64 x 64 blocks only: 32 x 32 tiles (2D, 2D), (2D+1, 2D),
+// (2D+1, 2D+1) of block D, item t = 3 D + (0, 1, 2).
+template <typename T>
+__global__ void k_mirror_diag(T *V, int64_t ld, int64_t N)
+{
+    const int64_t t = blockIdx.x, D = t / 3, r = t % 3;
+    const int64_t bi = 2 * D + (r > 0 ? 1 : 0), bj = 2 * D + (r == 2 ? 1 : 0);
+    mirror_tile<T>(V, ld, 0, N, 32 * bi, 32 * bj);
 }
 
 template <typename T>
@@ -792,7 +805,20 @@ __global__ void k_zero_padding(T *V, int64_t ld, int64_t N)
 }
 
 template <typename T>
-static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
+static bem_status launch_mirror_diag(bem_operator *op)
+{
+    bem_ctx *ctx = op->mesh->ctx;
+    const int64_t T32 = (op->N + 31) / 32, items = 3 * (T32 / 2) + (T32 % 2);
+    if (items > 0) {
+        k_mirror_diag<T><<<(unsigned)items, dim3(32, 8), 0, ctx->stream>>>((T *)op->V, op->ld, op->N); BEM_COUNT(ctx);
+        BEM_CK_LAUNCH(ctx);
+    }
+    return BEM_OK;
+}
+
+// upper: fill only the upper triangle and the diagonal blocks (op->upper_only)
+template <typename T>
+static bem_status assemble_t(bem_operator *op, const bem_operator *coarse, bool upper)
 {
     bem_mesh *m = op->mesh;
     bem_ctx *ctx = m->ctx;
@@ -807,7 +833,8 @@ static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
         if (K > 0) {
             dim3 grid(nblk(K, 256), (unsigned)(K < 65535 ? K : 65535));
             k_gather_kept<T><<<grid, 256, 0, ctx->stream>>>((const T *)coarse->V, coarse->ld, m->parent, K,
-                                                            (T *)op->V, op->ld); BEM_COUNT(ctx);
+                                                            (T *)op->V, op->ld,
+                                                            (upper || coarse->upper_only) ? 1 : 0); BEM_COUNT(ctx);
             BEM_CK_LAUNCH(ctx);
         }
     }
@@ -815,7 +842,14 @@ static bem_status assemble_t(bem_operator *op, const bem_operator *coarse)
     if ((st = far_variant<T>(op, K, N, &v))) return st;
     if (K > 0 && (st = launch_far<T>(op, v, 0, K, K, N))) return st;
     if ((st = launch_far<T>(op, v, K, N, K, N))) return st;
-    if ((st = launch_mirror<T>(op, K > 0 ? K : 0, N))) return st;
+    if (upper) {
+        if ((st = launch_mirror_diag<T>(op))) return st;
+    } else {
+        // a coarse operator with its upper triangle alone gave the kept block's upper half
+        const int64_t m0 = (coarse && coarse->upper_only) ? 0 : (K > 0 ? K : 0);
+        if ((st = launch_mirror<T>(op, m0, N))) return st;
+    }
+    op->upper_only = upper ? 1 : 0;
     if ((st = launch_near<T>(op, K))) return st;
     k_diag<T><<<nblk(N, 256), 256, 0, ctx->stream>>>((const T *)op->V, op->ld, N, op->diag); BEM_COUNT(ctx);
     BEM_CK_LAUNCH(ctx);
@@ -982,22 +1016,35 @@ bem_status gauss_legendre_upload(int n)
     return BEM_OK;
 }
 
-bem_status assemble_full(bem_operator *op)
+bem_status assemble_full(bem_operator *op, bool upper_only)
 {
     bem_status st = assembly_constants(op->mesh->ctx);
     if (st) return st;
-    if (op->precision == BEM_PREC_F64) return assemble_t<double>(op, nullptr);
-    if (op->precision == BEM_PREC_DF64) return assemble_t<float2>(op, nullptr);
-    return assemble_t<float>(op, nullptr);
+    if (op->precision == BEM_PREC_F64) return assemble_t<double>(op, nullptr, upper_only);
+    if (op->precision == BEM_PREC_DF64) return assemble_t<float2>(op, nullptr, upper_only);
+    return assemble_t<float>(op, nullptr, upper_only);
 }
 
-bem_status assemble_update(bem_operator *op, const bem_operator *coarse)
+bem_status assemble_update(bem_operator *op, const bem_operator *coarse, bool upper_only)
 {
     bem_status st = assembly_constants(op->mesh->ctx);
     if (st) return st;
-    if (op->precision == BEM_PREC_F64) return assemble_t<double>(op, coarse);
-    if (op->precision == BEM_PREC_DF64) return assemble_t<float2>(op, coarse);
-    return assemble_t<float>(op, coarse);
+    if (op->precision == BEM_PREC_F64) return assemble_t<double>(op, coarse, upper_only);
+    if (op->precision == BEM_PREC_DF64) return assemble_t<float2>(op, coarse, upper_only);
+    return assemble_t<float>(op, coarse, upper_only);
+}
+
+// The lower triangle of an upper-only operator, mirrored from the upper one (bit-
+// identical copies) before a reader of whole rows.
+bem_status ensure_full(bem_operator *op)
+{
+    if (!op || !op->upper_only) return BEM_OK;
+    bem_status st;
+    if (op->precision == BEM_PREC_F64) st = launch_mirror<double>(op, 0, op->N);
+    else if (op->precision == BEM_PREC_DF64) st = launch_mirror<float2>(op, 0, op->N);
+    else st = launch_mirror<float>(op, 0, op->N);
+    if (!st) op->upper_only = 0;
+    return st;
 }
 
 bem_status operator_diag(bem_operator *op)

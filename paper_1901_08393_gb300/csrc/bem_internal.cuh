@@ -121,6 +121,10 @@ struct bem_operator {
     void *V = nullptr;      // N x ld, row-major: double (F64), float2 hi/lo (DF64), float (F32)
     double *diag = nullptr; // N, FP64 diagonal
     int owns_mesh = 0;      // 1: mesh is a cells mesh freed with the operator
+    // 1: only the upper triangle (i <= j) and the diagonal 64 x 64 blocks hold entries
+    // (operators of the adaptive loop, read by the symmetric products alone);
+    // ensure_full mirrors the rest before any reader of whole rows
+    int upper_only = 0;
     // dual operators: the regularised hypersingular operator D^reg and the operator
     // preconditioner C = S D^reg S (both FP32, N x ld)
     float *cal_D = nullptr, *cal_C = nullptr;
@@ -180,12 +184,13 @@ bem_status mesh_bad_status(bem_ctx *ctx, const int64_t *bad3);
 
 // ----------------------------------------------------------------- assembly (assemble.cu)
 bem_status gauss_legendre_upload(int n);
-bem_status assemble_full(bem_operator *op);
+bem_status assemble_full(bem_operator *op, bool upper_only = false);
 // Operator handle with V (uninitialised) and diag allocated for mesh (api.cu).
 bem_status new_operator(bem_mesh *mesh, const bem_assembly_opts *opts, bem_operator **out);
 bem_status assembly_prepare(bem_ctx *ctx);  // constant tables on the device (once)
 bem_status far_tune(bem_operator *op);       // time the far-field tile variants for op's size class
-bem_status assemble_update(bem_operator *op, const bem_operator *coarse);
+bem_status assemble_update(bem_operator *op, const bem_operator *coarse, bool upper_only = false);
+bem_status ensure_full(bem_operator *op);
 bem_status operator_diag(bem_operator *op);
 
 // ----------------------------------------------------------------- batched assembly (assemble.cu)

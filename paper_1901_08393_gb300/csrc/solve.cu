@@ -1337,6 +1337,10 @@ static bem_status launch_mv(bem_operator *op, bool acc64, const double *x, doubl
     const double es = op->precision == BEM_PREC_F32 ? 4.0 : 8.0;
     const bool df = op->precision == BEM_PREC_DF64 || (op->precision == BEM_PREC_F32 && acc64);
     const bool sym = op->precision == BEM_PREC_DF64 && prow && pcol && tiles;
+    if (!sym && op->upper_only) {  // the row kernels read whole rows
+        const bem_status st = ensure_full(op);
+        if (st) return st;
+    }
     if (df) {
         k_to_df<<<nblk(op->ld, 256), 256, 0, ctx->stream>>>(x, op->N, op->ld, xdf); BEM_COUNT(ctx);
     }
