@@ -777,14 +777,18 @@ __device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int6
     }
     __syncthreads();
     const int ri = t >> 2, rc = t & 3;  // trailing update: row ri, columns rc + 4 m
+    __shared__ float dg[kBJ];
     for (int k = 0; k < kBJ; ++k) {
+        // every thread that scales column k takes the pivot itself (nothing writes A[k][k]
+        // during step k; the factor's diagonal is stored after the loop), so the step
+        // needs two barriers, not three
+        const float d = A[k][k];
+        const float dk = d > 0.f ? sqrtf(d) : 1.f;
         if (t == 0) {
-            const float d = A[k][k];
             if (!(d > 0.f)) s_fail = 1;
-            A[k][k] = d > 0.f ? sqrtf(d) : 1.f;
+            dg[k] = dk;
         }
-        __syncthreads();
-        if (t > k && t < kBJ) A[t][k] /= A[k][k];
+        if (t > k && t < kBJ) A[t][k] /= dk;
         __syncthreads();
         if (ri > k) {
             const float lik = A[ri][k];
@@ -792,6 +796,8 @@ __device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int6
         }
         __syncthreads();
     }
+    if (t < kBJ) A[t][t] = dg[t];
+    __syncthreads();
     double *out = binv + blk * kBJ * kBJ;
     if (s_fail) {  // diagonal block (Jacobi)
         for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
