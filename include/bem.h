@@ -297,9 +297,11 @@ typedef struct {
  * copied to the children starts each solve.  When every indicator
  * vanishes up to rounding (sum eta^2 <= 1e-20 sum h|T|phi^2/12, a symmetric mesh
  * with a constant solution) Eq. 2.6 holds for the empty set and the level is
- * refined uniformly instead.  records: caller array of max_levels entries;
- * n_levels receives the count; final_mesh (nullable) receives the last mesh
- * (caller destroys it). */
+ * refined uniformly instead.  The checks of each refined mesh (closed, no degenerate
+ * or duplicate triangle) are read with the sizes of the next refinement, or at the end
+ * for the last mesh, so a failed check (BEM_ERR_MESH) ends the loop one level later.
+ * records: caller array of max_levels entries; n_levels receives the count;
+ * final_mesh (nullable) receives the last mesh (caller destroys it). */
 bem_status bem_adaptive_run(bem_mesh *mesh, const bem_adaptive_opts *opts, bem_level_record *records,
                             int32_t *n_levels, bem_mesh **final_mesh);
 
