@@ -983,7 +983,9 @@ def main():
     adapt_ms = sum(r["ms_adapt"] for r in recs)
 
     # dominant kernel roofline
-    roof = roofline(PREC, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src)
+    # FP32 operators run the persistent solver too (every product from the packed copy)
+    mvk = "k_pcg_df (FP32 operator: packed-tile products, residual at convergence)" if PREC == bem.PREC_F32 else None
+    roof = roofline(PREC, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src, mv_kernel=mvk)
     roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / total_ms
 
     # end to end through the public API with host buffers
