@@ -47,9 +47,23 @@ ARITHMETIC = {
              "from a packed FP32 copy of the hi parts with double-float sums, residual replaced by the DF64 "
              "product b - Vx whenever ||r|| drops by 1e-4 and before convergence"),
     "f64": "native FP64 operator, products and sums",
-    "f32": "FP32 operator (near field FP64, rounded); CG products from its packed copy with double-float sums, "
-           "FP64-accurate residual at convergence",
+    "f32": "FP32 operator (near field FP64, rounded); CG products from working copies of its packed tiles "
+           "(iteration_products), FP64-accurate residuals from the exact FP32 product",
 }
+def products_label(prec_name, precond="block"):
+    """Source of the persistent solver's iteration products for this run (--products;
+    the library's default: the FP16 copy for FP32 operators under the block preconditioner)."""
+    mode = {0: ("fp16" if prec_name == "f32" and precond == "block" else "fp32"), 1: "fp32", 2: "fp16"}[PRODUCTS]
+    if prec_name == "f64":
+        return "FP64 operator rows (host-driven PCG)"
+    if mode == "fp16":
+        return ("FP16 working copy of the packed tiles (each tile over a power of two above its largest entry) "
+                "with FP32 sums; residual replaced by the operator's own product after every 10^2-fold drop of "
+                "||r|| and at convergence; the FP32 copy for the rest of the solve if a replacement finds too "
+                "little progress")
+    return "packed FP32 copy with double-float sums"
+
+
 PC_LABEL = {"block": "block-Jacobi preconditioner on Morton clusters of 64 triangles",
             "jacobi": "Jacobi preconditioner diag(V)"}
 MAX_N = 20000
@@ -65,6 +79,7 @@ PCG_TRAFFIC_RATIO = 18.072 / 18.294  # ncu DRAM bytes / algorithmic bytes of the
 PRECISIONS = {"df64": 2, "f64": 0, "f32": 1}
 PREC = 2
 PC = 1
+PRODUCTS = 0  # bem.PRODUCTS_DEFAULT
 
 
 def _peaks():
@@ -534,7 +549,7 @@ def batch_workload(args):
     meshes = [bem.Mesh.upload(ctx, m.verts, m.tris) for m in ms]
     pc = bem.PRECOND_BLOCK if args.precond == "block" else bem.PRECOND_JACOBI
     t_create = time.perf_counter()
-    b = bem.Batch(ctx, meshes, precision=bem.PREC_F32, precond=pc, tol=TOL, max_it=5000)
+    b = bem.Batch(ctx, meshes, precision=bem.PREC_F32, precond=pc, tol=TOL, max_it=5000, products=PRODUCTS)
     t_create = time.perf_counter() - t_create
     n_waves, arena, _ = b.waves()
     for _ in range(max(args.warmup, 1)):
@@ -561,7 +576,8 @@ def batch_workload(args):
     b.close()
     peaks, peak_src = _peaks()
     roof = roofline(bem.PREC_F32, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src,
-                    mv_kernel="k_pcg_batch (all problems of a wave in one cooperative launch, packed FP32 products)")
+                    mv_kernel="k_pcg_batch (one cooperative launch per group of similar sizes; products: "
+                              "config.iteration_products)")
     step_ms = 1e3 * sum(times) / len(times)
     roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / args.steps / step_ms
     roof["note"] = "CUDA events recorded inside the replayed wave graphs of the timed runs"
@@ -587,7 +603,8 @@ def batch_workload(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64-accurate residuals)", "data": "synthetic",
         "config": {"workload": f"batch: {len(ms)} uniform polycube meshes (g 3..10, p 0.3..0.7, log-uniform "
                                "500..30,000 triangles, seed 4), one assembly + solve each, FP32 V, PCG to 1e-10",
-                   "preconditioner": PC_LABEL[args.precond], "solver_ctas_max": info["ctas"],
+                   "preconditioner": PC_LABEL[args.precond], "iteration_products": products_label("f32", args.precond),
+                   "solver_ctas_max": info["ctas"],
                    "waves": n_waves, "arena_gb": arena / 1e9, "graph_replayed": bool(info["graph_used"]),
                    "sum_N2": float(sum(m.N * m.N for m in ms)), "create_s": t_create,
                    "l2": "V of the batch (tens of GB) exceeds L2"},
@@ -673,7 +690,8 @@ def server_workload(args):
                  f"triangles), one assembly + solve each, FP32 V + FP64 refinement to 1e-10, {args.slots} slots, "
                  f"HBM budget {budget >> 30} GiB")
     pc = bem.PRECOND_BLOCK if args.precond == "block" else bem.PRECOND_JACOBI
-    srv = bem.Server(slots=args.slots, hbm_budget_bytes=budget, precision=bem.PREC_F32, tol=TOL, precond=pc)
+    srv = bem.Server(slots=args.slots, hbm_budget_bytes=budget, precision=bem.PREC_F32, tol=TOL, precond=pc,
+                     products=PRODUCTS)
 
     def run_stream(realtime):
         ids = []
@@ -717,7 +735,7 @@ def server_workload(args):
     srv.profile(False)
     peaks, peak_src = _peaks()
     roof = roofline(1, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src,
-                    mv_kernel="k_pcg_df (FP32 operator: packed-tile products, residual at convergence)")
+                    mv_kernel="k_pcg_df (FP32 operator; products: config.iteration_products)")
     roof["note"] = ("CUDA events around each slot's launches over the timed requests; the requests run "
                     "concurrently, so a launch's time includes the kernels of other requests beside it")
     sat = None
@@ -736,7 +754,8 @@ def server_workload(args):
         "config": {"workload": label, "requests_per_step": len(jobs), "slots": args.slots,
                    "peak_in_flight": stats["peak_in_flight"], "peak_bytes": stats["peak_bytes"],
                    "failed": fails, "level_solves_per_step": solves // max(args.steps, 1),
-                   "preconditioner": PC_LABEL[args.precond]},
+                   "preconditioner": PC_LABEL[args.precond],
+                   "iteration_products": products_label("f32", args.precond)},
         "final_N": {"min": nf[0], "p10": _pct(nf, 0.1), "p50": _pct(nf, 0.5), "p90": _pct(nf, 0.9), "max": nf[-1]},
         "levels_hist": {str(k): sum(1 for r in res if r["levels"] == k) for k in range(1, 7)},
         "p50_latency_ms": _pct(lat, 0.5), "p99_latency_ms": _pct(lat, 0.99),
@@ -837,6 +856,8 @@ def main():
     ap.add_argument("--no-compare", action="store_true",
                     help="batch / serve: skip timing the single-problem forms on the same inputs")
     ap.add_argument("--slots", type=int, default=16, help="serve/batch: server slots")
+    ap.add_argument("--products", default="default", choices=["default", "fp32", "fp16"],
+                    help="source of the persistent solver's iteration products (bem_solve_opts.products)")
     ap.add_argument("--precond", default="auto", choices=["auto", "block", "jacobi", "calderon"],
                     help="PCG preconditioner (block: DF64 and FP32 operators, FP64 runs Jacobi); auto: "
                          "block, except jacobi on the graded cube (its V has indefinite diagonal blocks) and "
@@ -855,6 +876,8 @@ def main():
     ap.add_argument("--precision", default="df64", choices=sorted(PRECISIONS),
                     help="df64: FP64-accurate double-float on the FP32 pipe (default); f64: native FP64")
     args = ap.parse_args()
+    global PRODUCTS
+    PRODUCTS = {"default": 0, "fp32": 1, "fp16": 2}[args.products]
     if args.impl == "reference":
         return reference_arm(args)
     if args.precond == "auto":
@@ -921,7 +944,7 @@ def main():
         ev[0].record(stream)
         op = bem.Operator.assemble(msh, precision=bem.PREC_F32)
         ev[1].record(stream)
-        cap, _, info = bem.solve_capacity(op, tol=TOL, max_it=5000, precond=PC)
+        cap, _, info = bem.solve_capacity(op, tol=TOL, max_it=5000, precond=PC, products=PRODUCTS)
         ev[2].record(stream)
         op.close()
         torch.cuda.synchronize()
@@ -933,7 +956,7 @@ def main():
         if graded:
             return step_graded(mesh)
         recs, _ = bem.adaptive_run(mesh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC,
-                                   inexact_lambda=args.inexact, tile=args.far_tile)
+                                   inexact_lambda=args.inexact, tile=args.far_tile, products=PRODUCTS)
         return recs
 
     for _ in range(max(args.warmup, 0)):
@@ -984,7 +1007,7 @@ def main():
 
     # dominant kernel roofline
     # FP32 operators run the persistent solver too (every product from the packed copy)
-    mvk = "k_pcg_df (FP32 operator: packed-tile products, residual at convergence)" if PREC == bem.PREC_F32 else None
+    mvk = "k_pcg_df (FP32 operator; products: config.iteration_products)" if PREC == bem.PREC_F32 else None
     roof = roofline(PREC, far_n, far_ms, far_units, mv_n, mv_ms, mv_units, peaks, peak_src, mv_kernel=mvk)
     roof["share_of_step"] = (far_ms if roof["bound"] == "alu" else mv_ms) / total_ms
 
@@ -1003,7 +1026,7 @@ def main():
             r2 = step_graded(mh)
         else:
             r2, _ = bem.adaptive_run(mh, theta=THETA, max_N=args.max_n, tol=TOL, precision=PREC, precond=PC,
-                                     inexact_lambda=args.inexact, tile=args.far_tile)
+                                     inexact_lambda=args.inexact, tile=args.far_tile, products=PRODUCTS)
         cap_final = r2[-1]["cap"]
         mh.close()
         torch.cuda.synchronize()
@@ -1020,6 +1043,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
         "config": {"workload": WORKLOAD + (f" [inexact solves: lambda = {args.inexact}]" if args.inexact else ""),
                    "precision": args.precision, "arithmetic": ARITHMETIC[args.precision],
+                   "iteration_products": products_label(args.precision, pc_name),
                    "preconditioner": PC_LABEL[pc_name],
                    "final_N": recs[-1]["N"], "levels": len(recs),
                    "cap_final": recs[-1]["cap"], "parallelism": f"replicas x{ws}",

@@ -114,7 +114,21 @@ typedef struct {
                               such a stop counts as converged.  0: off (tol only) */
     int32_t h_mode;        /* ZZ weight of that estimator, as bem_zz_estimate (bem_adaptive_run
                               takes its own h_mode) */
+    int32_t products;      /* persistent solver, DF64 and FP32 operators: the source of the CG
+                              iteration's products.  BEM_PRODUCTS_DEFAULT (0): _FP16 for FP32
+                              operators under BEM_PRECOND_BLOCK, else _FP32.  _FP32: the packed FP32 copy with
+                              double-float sums (above).  _FP16: a further copy in
+                              FP16 (each 64 x 64 tile divided by a power of two above its largest
+                              entry; N^2 bytes) with FP32 sums, the residual replaced by the
+                              operator's own product (DF64, or the exact FP32 one) after every
+                              10^2-fold drop of ||r|| (or after 400 iterations without it), and
+                              the FP32 copy taken for the rest of the solve if a replaced residual
+                              has fallen by less than 10x since the previous one.  tol holds for
+                              the operator in every mode. */
 } bem_solve_opts;
+#define BEM_PRODUCTS_DEFAULT 0
+#define BEM_PRODUCTS_FP32 1
+#define BEM_PRODUCTS_FP16 2
 
 typedef struct {
     int32_t iterations;    /* CG iterations (summed over refinement sweeps) */

@@ -47,6 +47,7 @@ EXPORTS = [
     "bem_mesh_barycentric", "bem_operator_dual", "bem_zz_estimate_dual", "bem_operator_preconditioner",
     "bem_far_tiles", "bem_debug_barrier_fault", "bem_batch_waves",
 ]
+PRODUCTS_DEFAULT, PRODUCTS_FP32, PRODUCTS_FP16 = 0, 1, 2
 KERNEL_FAR = 0
 KERNEL_NEAR = 1
 KERNEL_MATVEC = 2
@@ -59,7 +60,7 @@ class AssemblyOpts(C.Structure):
 class SolveOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_it", C.c_int32), ("precond", C.c_int32),
                 ("max_outer", C.c_int32), ("inner_tol", C.c_double), ("reliable_delta", C.c_double),
-                ("inexact_lambda", C.c_double), ("h_mode", C.c_int32)]
+                ("inexact_lambda", C.c_double), ("h_mode", C.c_int32), ("products", C.c_int32)]
 
 
 class SolveInfo(C.Structure):
@@ -404,9 +405,9 @@ class Operator:
 
 def solve_capacity(op: Operator, tol=1e-10, max_it=10000, precond=PRECOND_JACOBI, x0=None,
                    max_outer=20, inner_tol=1e-5, phi_out=None, raise_not_converged=True, reliable_delta=0.0,
-                   inexact_lambda=0.0, h_mode=0):
+                   inexact_lambda=0.0, h_mode=0, products=0):
     """Cap and x with V x = |T| (Eq. 2.5, 2.8).  phi_out may be a CUDA tensor."""
-    o = SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode)
+    o = SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode, products)
     info = SolveInfo()
     cap = C.c_double()
     N = op.info()[0]
@@ -472,10 +473,11 @@ def mark_refine(mesh: Mesh, eta2, theta=0.5, bisec3=False):
 def adaptive_run(mesh: Mesh, theta=0.5, max_N=20000, max_levels=64, h_mode=0, precision=PREC_F64,
                  ss_order=4, tol=1e-12, max_it=20000, precond=PRECOND_JACOBI, incremental=True,
                  max_outer=20, inner_tol=1e-5, want_final=False, reliable_delta=0.0, inexact_lambda=0.0,
-                 basis=BASIS_P0, tile=0):
+                 basis=BASIS_P0, tile=0, products=0):
     """Alg. 1 in the library's native loop; returns (records, final Mesh or None)."""
     o = AdaptiveOpts(theta, max_N, max_levels, h_mode, AssemblyOpts(precision, ss_order, tile),
-                     SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode),
+                     SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, inexact_lambda, h_mode,
+                               products),
                      int(incremental), int(basis))
     recs = (LevelRecord * max_levels)()
     n = C.c_int32()
@@ -493,12 +495,13 @@ class Batch:
     graph once and replayed."""
 
     def __init__(self, ctx: Context, meshes, precision=PREC_DF64, ss_order=4, tol=1e-10, max_it=10000,
-                 precond=PRECOND_JACOBI, reliable_delta=0.0, use_graph=True, tile=0):
+                 precond=PRECOND_JACOBI, reliable_delta=0.0, use_graph=True, tile=0, products=0):
         self.ctx, self.meshes, self.h = ctx, list(meshes), None
         arr = (C.c_void_p * len(self.meshes))(*[m.h.value if hasattr(m.h, "value") else m.h for m in self.meshes])
         h = C.c_void_p()
         ctx.check(ctx.L.bem_batch_create(ctx.h, len(self.meshes), arr, C.byref(AssemblyOpts(precision, ss_order, tile)),
-                                         C.byref(SolveOpts(tol, max_it, precond, 20, 1e-5, reliable_delta)),
+                                         C.byref(SolveOpts(tol, max_it, precond, 20, 1e-5, reliable_delta, 0.0, 0,
+                                                           products)),
                                          int(bool(use_graph)), C.byref(h)))
         self.h = h
 
@@ -539,10 +542,10 @@ class Server:
 
     def __init__(self, slots=4, hbm_budget_bytes=64 << 30, theta=0.5, precision=PREC_F32, tol=1e-10,
                  max_it=20000, h_mode=0, ss_order=4, incremental=True, max_outer=20, inner_tol=1e-5,
-                 reliable_delta=0.0, precond=PRECOND_JACOBI, basis=BASIS_P0):
+                 reliable_delta=0.0, precond=PRECOND_JACOBI, basis=BASIS_P0, products=0):
         self.L = lib()
         o = AdaptiveOpts(theta, 0, 1, h_mode, AssemblyOpts(precision, ss_order),
-                         SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta),
+                         SolveOpts(tol, max_it, precond, max_outer, inner_tol, reliable_delta, 0.0, h_mode, products),
                          int(incremental), int(basis))
         h = C.c_void_p()
         st = self.L.bem_server_create(slots, int(hbm_budget_bytes), C.byref(o), C.byref(h))

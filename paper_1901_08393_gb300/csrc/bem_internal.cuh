@@ -239,7 +239,7 @@ bem_status matvec_f64(bem_operator *op, const double *x, double *y);
 // How the algorithmic bytes of a persistent solve are counted once its counts are read.
 struct PersistentRun {
     int prof = -1;  // profiler record of the launch
-    bool f32op = false, mixed = false, calpc = false;
+    bool f32op = false, mixed = false, calpc = false, h16 = false;
     double n2 = 0.0;  // N^2
 };
 // A solve whose results are still travelling to pinned host memory: solve_capacity
@@ -248,7 +248,8 @@ struct PersistentRun {
 // runs; other paths finish at once and leave pending false); after any later
 // synchronisation of the context's stream, solve_capacity_end reads them.
 struct SolveDeferred {
-    double *h = nullptr;  // pinned, 8 doubles: [0..4] solver out, [5] barrier error flag, [6] Cap
+    double *h = nullptr;  // pinned, 8 doubles: [0..4] solver out, [5] barrier error flag, [6] Cap,
+                          // [7] iterations with FP16 products
     bool pending = false;
     PersistentRun run;
     double tol = 0.0;

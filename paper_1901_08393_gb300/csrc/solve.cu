@@ -15,6 +15,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "bem_internal.cuh"
 #include "dfloat.cuh"
 #include "grid_sync.cuh"
@@ -264,6 +266,14 @@ __device__ __forceinline__ int symv_grab(unsigned long long *ctr, unsigned long 
 // pack (nullable): also write the FP32 hi parts of each staged tile, row-major
 // 64 x 64 at pack + 4096 k for tile k of the list (the packed upper triangle).
 constexpr int kTileF = kSB * kSB;
+// BEM_PRODUCTS_FP16: replaced residual after every 10^2-fold drop of ||r|| (r.r by
+// 10^4); fallback to the exact products when a replacement finds r.r above
+// kH16Progress times the previous replacement's (||r|| fallen by less than 10x)
+constexpr double kH16Delta2 = 1e-4;
+constexpr double kH16Progress = 1e-2;
+// a segment this long without reaching its drop also ends in a replaced residual (and
+// so in the progress test): the FP16 products can hold the recursion itself back
+constexpr int kH16SegMax = 400;
 
 __device__ void symv_tiles(const float2 *__restrict__ V, int64_t ld, int64_t N, const int2 *__restrict__ tiles,
                            int ntiles, const float2 *__restrict__ xdf, float2 *__restrict__ prow,
@@ -532,6 +542,113 @@ __device__ void symv_hi_tiles(const float *__restrict__ vp, const int2 *__restri
             const float2 s1 = par ? df_add(a1, cs[3]) : df_add(cs[1], a1);
             out = make_float4(s0.x, s0.y, s1.x, s1.y);
             reinterpret_cast<float4 *>(pcol + (int64_t)k * kSB)[2 * cg + par] = out;
+        }
+    }
+}
+
+// FP16 working copy of the packed tiles (BEM_PRODUCTS_FP16).  Each 64 x 64 tile is
+// stored as halves of its entries divided by a power of two s_k >= max |entry| of the
+// tile (exact in FP32, so only the FP16 rounding remains: 2^-11 of the tile's largest
+// entry).  One warp per tile: the maximum by a butterfly, then the halves.
+__device__ __forceinline__ void pack_h16_tiles(const float *__restrict__ vp, int ntiles, __half *__restrict__ vh,
+                                               float *__restrict__ vsc, int64_t w0, int64_t nw)
+{
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = w0; k < ntiles; k += nw) {
+        const float4 *T = reinterpret_cast<const float4 *>(vp + k * kTileF);
+        float mx = 0.f;
+        for (int f = lane; f < kTileF / 4; f += 32) {
+            const float4 v = __ldcg(T + f);
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        int ex = 0;
+        if (mx > 0.f) frexpf(mx, &ex);  // mx = m 2^ex, m in [0.5, 1): s = 2^ex > mx
+        const float inv = ldexpf(1.f, -ex);
+        if (lane == 0) vsc[k] = ldexpf(1.f, ex);
+        __half2 *H = reinterpret_cast<__half2 *>(vh + k * kTileF);
+        for (int f = lane; f < kTileF / 4; f += 32) {
+            const float4 v = __ldcg(T + f);
+            H[2 * f] = __floats2half2_rn(v.x * inv, v.y * inv);
+            H[2 * f + 1] = __floats2half2_rn(v.z * inv, v.w * inv);
+        }
+    }
+}
+
+__global__ void k_pack_h16(const float *__restrict__ vp, int ntiles, __half *__restrict__ vh, float *__restrict__ vsc)
+{
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    pack_h16_tiles(vp, ntiles, vh, vsc, w0, ((int64_t)gridDim.x * blockDim.x) >> 5);
+}
+
+// Product with the FP16 working copy: the layout and partials of symv_hi_tiles (lane
+// l: columns 4 (l % 16) .. +3, rows 32 (l / 16) + 8 c .. +7 in step c), 8 bytes per
+// lane and row, FP32 products of the half entries with the hi part of x and FP32
+// sums; the tile's scale multiplies its partials.  The iteration products of
+// BEM_PRODUCTS_FP16 only: the residuals that decide convergence use the exact form.
+__device__ void symv_h16_tiles(const __half *__restrict__ vh, const float *__restrict__ vsc,
+                               const int2 *__restrict__ tiles, int ntiles, const float2 *__restrict__ xdf,
+                               float2 *__restrict__ prow, float2 *__restrict__ pcol, float2 *xsw,
+                               unsigned long long *ctr, unsigned long long base, int static_k = -1)
+{
+    const int lane = threadIdx.x & 31, cg = lane & 15, par = lane >> 4;
+    const bool b1 = lane & 2, b2 = lane & 4, b3 = lane & 8;
+    for (int k = static_k >= 0 ? static_k : warp_grab(ctr, base); k < ntiles;
+         k = static_k >= 0 ? ntiles : warp_grab(ctr, base)) {
+        const int2 tj = tiles[k];
+        const float sk = vsc[k];
+        __syncwarp();
+        {
+            const float4 *src = reinterpret_cast<const float4 *>(xdf + (int64_t)(par ? tj.y : tj.x) * kSB) + 2 * cg;
+            float4 *dst = reinterpret_cast<float4 *>(xsw) + 2 * lane;
+            dst[0] = __ldcg(src);
+            dst[1] = __ldcg(src + 1);
+        }
+        __syncwarp();
+        float xc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xc[u] = xsw[kSB + 4 * cg + u].x;
+        const uint2 *T = reinterpret_cast<const uint2 *>(vh + (int64_t)k * kTileF);
+        float cs[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+        for (int ch = 0; ch < 4; ++ch) {
+            const int r0 = 32 * par + 8 * ch;
+            uint2 raw[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) raw[m] = __ldcs(T + (r0 + m) * 16 + cg);
+            float sr[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const float xr = xsw[r0 + m].x;
+                __half2 h01, h23;
+                memcpy(&h01, &raw[m].x, 4);
+                memcpy(&h23, &raw[m].y, 4);
+                const float2 a01 = __half22float2(h01), a23 = __half22float2(h23);
+                const float e[4] = {a01.x, a01.y, a23.x, a23.y};
+                float h = e[0] * xc[0];
+#pragma unroll
+                for (int u = 1; u < 4; ++u) h = __fmaf_rn(e[u], xc[u], h);
+                sr[m] = h;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) cs[u] = __fmaf_rn(e[u], xr, cs[u]);
+            }
+            // rows m: 8 -> 4 (xor 8) -> 2 (xor 4) -> 1 (xor 2), then xor 1
+            float t4[4], t2[2];
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                t4[j] = (b3 ? sr[j + 4] : sr[j]) + __shfl_xor_sync(0xffffffffu, b3 ? sr[j] : sr[j + 4], 8);
+#pragma unroll
+            for (int j = 0; j < 2; ++j)
+                t2[j] = (b2 ? t4[j + 2] : t4[j]) + __shfl_xor_sync(0xffffffffu, b2 ? t4[j] : t4[j + 2], 4);
+            float w = (b1 ? t2[1] : t2[0]) + __shfl_xor_sync(0xffffffffu, b1 ? t2[0] : t2[1], 2);
+            w += __shfl_xor_sync(0xffffffffu, w, 1);
+            if (!(lane & 1)) prow[(int64_t)k * kSB + r0 + ((lane >> 1) & 7)] = make_float2(w * sk, 0.f);
+        }
+        if (tj.x != tj.y) {  // lane keeps columns 4 (l % 16) + 2 (l / 16) + {0, 1}
+            const float a0 = __shfl_xor_sync(0xffffffffu, par ? cs[0] : cs[2], 16);
+            const float a1 = __shfl_xor_sync(0xffffffffu, par ? cs[1] : cs[3], 16);
+            const float s0 = (par ? cs[2] : cs[0]) + a0, s1 = (par ? cs[3] : cs[1]) + a1;
+            reinterpret_cast<float4 *>(pcol + (int64_t)k * kSB)[2 * cg + par] = make_float4(s0 * sk, 0.f, s1 * sk, 0.f);
         }
     }
 }
@@ -954,6 +1071,12 @@ struct PcgArgs {
     const float *dvp;
     long long bar_limit_ns;   // grid-barrier wait limit (ns)
     int absent_cta;           // failure-detection tests: this CTA leaves at its first barrier (-1: none)
+    // BEM_PRODUCTS_FP16: the FP16 working copy of the packed tiles and their scales
+    // (null: off).  FP32 operators: packed by the host before the launch; DF64: by
+    // the kernel from its packed hi parts after the first product.
+    __half *vh;
+    float *vsc;
+    double *n16_out;          // nullable: iterations that used the FP16 copy
 };
 
 // Per-CTA partial of one value per thread (fixed tree) into slot[cta].
@@ -1113,6 +1236,15 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     // r = b - V x0 (or b), z = M^-1 r, p = z
     const bool prod0 = a.has_x0 || mixed;
     if (prod0 && !df64_product(mixed)) return;
+    // FP16 iteration products (mixed mode): residuals replaced after every 10^2-fold
+    // drop of ||r||; back to the exact products for good if a replacement finds that
+    // the true residual fell by less than 10x since the previous one
+    bool use16 = mixed && a.vh != nullptr && !calpc;
+    if (use16 && !a.f32op) {  // the halves of the hi parts packed by the first product
+        pack_h16_tiles(a.vp, a.ntiles, a.vh, a.vsc, warp_g, nwarps);
+        if (!grid_barrier(gb, G)) return;
+    }
+    int n16 = 0, seg = 0;
     double rz_l = 0.0, rr_l = 0.0, bb_l = 0.0;
     for (int64_t i = i0; i < a.ld; i += stride) {
         if (i < a.N) {
@@ -1148,11 +1280,16 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
     const double bb = grid_total(pC, G);
     const double thr = a.tol * a.tol * (bb > 0.0 ? bb : 1.0);
     double rr_true = rr;  // r.r at the last residual formed with the DF64 product
+    double rr_true_prev = rr;
     int it = 0, ndf = prod0 ? 1 : 0, inexact_stop = 0;
     if (!grid_barrier(gb, G)) return;  // partial slots are reused below
     while (!(rr <= thr) && it < a.max_it) {
         double alpha, rz_new, rz_n = 0.0;
-        if (mixed) {
+        if (use16) {
+            symv_h16_tiles(a.vh, a.vsc, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, xsw, a.ctr, tbase, hi_static);
+            if (hi_static < 0) tbase += (unsigned long long)(a.ntiles + G * (kSymThreads / 32));
+            ++n16;
+        } else if (mixed) {
             hi_product(a.vp);
         } else {
             symv_tiles(a.V, a.ld, a.N, a.tiles, a.ntiles, a.pdf, a.prow, a.pcol, sm, cta, G, a.ctr, tbase);
@@ -1232,7 +1369,9 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
                 break;
             }
         }
-        if (mixed && (rr <= a.delta2 * rr_true || rr <= thr)) {
+        ++seg;
+        if (mixed && (rr <= (use16 ? kH16Delta2 : a.delta2) * rr_true || rr <= thr || (use16 && seg >= kH16SegMax))) {
+            seg = 0;
             // reliable update: replace the recursive residual by b - V x with the
             // DF64 product (the direction p is kept)
             if (!df64_product(false)) return;
@@ -1266,8 +1405,10 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
             cta_partial2(rz_n, rr_l, pB, pC, cta);
             if (!grid_barrier(gb, G)) return;
             grid_total2(pB, pC, G, rz_new, rr);
+            rr_true_prev = rr_true;
             rr_true = rr;
             ++ndf;
+            if (use16 && rr_true > kH16Progress * rr_true_prev) use16 = false;  // the same in every CTA
         }
         const double beta = rz_new / rz;
         if (a.lanczos && cta == 0 && threadIdx.x == 0 && it - 1 < a.lanczos_cap) {
@@ -1288,6 +1429,7 @@ __device__ __forceinline__ void pcg_body(const PcgArgs &a, const int G, const in
         a.out[2] = (double)it;
         a.out[3] = (double)ndf;
         a.out[4] = (double)inexact_stop;
+        if (a.n16_out) a.n16_out[0] = (double)n16;
     }
 }
 
@@ -1585,9 +1727,12 @@ static bem_status persistent_results(bem_ctx *ctx, const double *h, const Persis
     // 2); a mixed-mode iteration reads the packed FP32 upper triangle (4 x N^2 / 2),
     // written once by the first product (+ the packed FP32 C once per preconditioner
     // application)
+    // (FP16 working copy: N^2 bytes per iteration that used it, h[7] of them, and
+    // for DF64 its packing, 2 N^2 read and N^2 written once)
     const double n2 = r.n2;
-    const double bytes = (r.f32op  ? 2.0 * n2 * (h[2] + h[3])
-                          : r.mixed ? 4.0 * n2 * h[3] + 2.0 * n2 * (h[2] + 1.0)
+    const double i16 = r.h16 ? h[7] : 0.0, i32 = h[2] - i16;
+    const double bytes = (r.f32op  ? 2.0 * n2 * (i32 + h[3]) + n2 * i16
+                          : r.mixed ? 4.0 * n2 * h[3] + 2.0 * n2 * (i32 + 1.0) + n2 * i16 + (r.h16 ? 3.0 * n2 : 0.0)
                                     : 4.0 * n2 * (h[2] + h[3])) +
                          (r.calpc ? 2.0 * n2 * (h[2] + h[3]) : 0.0);
     prof_set_units(ctx, r.prof, bytes);
@@ -1597,7 +1742,8 @@ static bem_status persistent_results(bem_ctx *ctx, const double *h, const Persis
 static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, bool has_x0, double tol, int max_it,
                                  int precond, double delta, const int32_t *bperm, const double *binv, int nbj,
                                  double inexact_lambda, int h_mode, int *its_out, int *ndf_out, double *rel_out,
-                                 bool *ran, double *lmin, double *lmax, bool *inexact_out, SolveDeferred *def)
+                                 bool *ran, double *lmin, double *lmax, bool *inexact_out, SolveDeferred *def,
+                                 int products)
 {
     // FP32 operators: the products of the iteration and of the residuals read the
     // packed copy of the stored operator (the residual, formed from x with
@@ -1636,6 +1782,29 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     if (f32op) {
         k_pack_f32<<<(unsigned)std::min<int64_t>(((int64_t)nt_ * (kTileF / 4) + 255) / 256, 8 * ctx->sm_count), 256, 0,
                      ctx->stream>>>((const float *)op->V, op->ld, op->N, W.tiles, nt_, vp); BEM_COUNT(ctx);
+    }
+    // FP16 working copy for the iteration products (N^2 bytes and a scale per tile)
+    __half *vh = nullptr;
+    float *vsc = nullptr;
+    // default: FP16 for FP32 operators (whose stored entries are FP32 roundings already)
+    // under the block preconditioner (a condition number the FP16 copy's perturbation
+    // leaves room for; diag(V) on strongly graded meshes does not), else the packed
+    // FP32 hi parts
+    if (products == BEM_PRODUCTS_DEFAULT)
+        products = (f32op && precond == BEM_PRECOND_BLOCK) ? BEM_PRODUCTS_FP16 : BEM_PRODUCTS_FP32;
+    if (products == BEM_PRODUCTS_FP16 && vp && !calpc) {
+        const size_t hb = (size_t)nt_ * kTileF * sizeof(__half), sb = ((size_t)nt_ * sizeof(float) + 255) / 256 * 256;
+        if (ctx->budget <= 0 || ctx->in_use + (int64_t)(hb + sb) + (64 << 10) <= ctx->budget) {
+            if ((st = dalloc(ctx, tmp, (void **)&vh, hb + sb, false))) {
+                dfree_all(ctx, tmp);
+                return st;
+            }
+            vsc = reinterpret_cast<float *>(reinterpret_cast<char *>(vh) + hb);
+            if (f32op) {
+                k_pack_h16<<<(unsigned)std::min<int64_t>(((int64_t)nt_ * 32 + 255) / 256, 8 * ctx->sm_count), 256, 0,
+                             ctx->stream>>>(vp, nt_, vh, vsc); BEM_COUNT(ctx);
+            }
+        }
     }
     // Up to 3 CTAs per SM.  On small levels, CTAs that would only wait at the grid
     // barriers are left out: DF64 products take one tile per CTA, the mixed mode's
@@ -1706,6 +1875,9 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     a.precond = precond;
     a.has_x0 = has_x0 ? 1 : 0;
     a.dvp = dvp;
+    a.vh = vh;
+    a.vsc = vsc;
+    a.n16_out = out + 5;
     a.bar_limit_ns = ctx->bar_limit_ns;
     a.absent_cta = ctx->bar_absent_cta < G ? ctx->bar_absent_cta : -1;
     void *args[] = {&a};
@@ -1729,8 +1901,10 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
     run.mixed = vp != nullptr;
     run.calpc = calpc;
     run.n2 = (double)op->N * (double)op->N;
+    run.h16 = vh != nullptr;
     e = cudaMemcpyAsync(hres, out, 5 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(hres + 5, err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hres + 7, out + 5, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream);
     if (e == cudaSuccess && !def) e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) st = cuda_error(ctx, e, "persistent solve");
     if (!st && def) {
@@ -1738,7 +1912,7 @@ static bem_status pcg_persistent(bem_operator *op, Work &W, const double *rhs, b
         *ran = true;
         *lmin = *lmax = 0.0;  // no condition estimates for deferred solves
     } else if (!st) {
-        double h[6];
+        double h[8];
         memcpy(h, hres, sizeof(h));
         st = persistent_results(ctx, h, run, its_out, ndf_out, rel_out, inexact_out);
         if (!st) {
@@ -1878,7 +2052,7 @@ bem_status solve_capacity(bem_operator *op, const bem_solve_opts *o, const doubl
         if (op->precision != BEM_PREC_F64 && ctx->persistent_solver)
             st = pcg_persistent(op, W, W.b, d_x0 != nullptr, tol, max_it, precond, delta < 1.0 ? delta : 0.0, bperm,
                                 binv, nbj, o->inexact_lambda, o->h_mode, &its, &outer, &rel, &ran, &lam_min, &lam_max,
-                                &inexact, def);
+                                &inexact, def, o->products);
         if (!st && !ran && (precond == BEM_PRECOND_BLOCK || precond == BEM_PRECOND_CALDERON))
             st = set_error(ctx, BEM_ERR_CUDA, "this preconditioner needs the persistent solver, which could not be launched");
         if (st) goto out;
@@ -1982,6 +2156,8 @@ struct BatchSolveProb {
     double *part;
     int64_t part_n;  // doubles of part zeroed per run
     float *vp;       // packed FP32 upper triangle (FP32 operators: formed per run)
+    __half *vh;      // its FP16 working copy (BEM_PRODUCTS_FP16, FP32 operators), else null
+    float *vsc;      // and the tiles' scales
     const int2 *tiles;
     int64_t nt;
     const int32_t *perm;
@@ -2028,6 +2204,15 @@ __global__ void k_batch_pack(const BatchSolveProb *__restrict__ prob)
         if (row < pb->N) v = __ldcs(reinterpret_cast<const float4 *>(V + row * pb->ld + (int64_t)tj.y * kSB) + c4);
         reinterpret_cast<float4 *>(pb->vp)[f] = v;
     }
+}
+
+// FP16 working copies of the packed FP32 operators; grid (blocks, problems).
+__global__ void k_batch_pack_h16(const BatchSolveProb *__restrict__ prob)
+{
+    const BatchSolveProb *pb = prob + blockIdx.y;
+    if (!pb->vh) return;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    pack_h16_tiles(pb->vp, (int)pb->nt, pb->vh, pb->vsc, w0, ((int64_t)gridDim.x * blockDim.x) >> 5);
 }
 
 // Inverse cluster blocks of every problem; grid (largest cluster count, problems).
@@ -2099,6 +2284,7 @@ struct BatchWave {
 struct bem_batch {
     bem_ctx *ctx = nullptr;
     int P = 0, use_graph = 1, graph_used = 0, precond = BEM_PRECOND_JACOBI, precision = BEM_PREC_F32;
+    bool h16 = false;  // BEM_PRODUCTS_FP16: FP16 working copies for the iteration products
     double tol = 1e-10;
     void *arena = nullptr;
     size_t arena_bytes = 0;
@@ -2127,6 +2313,9 @@ static bem_status batch_enqueue(bem_batch *bt, BatchWave &w)
     BEM_COUNT(ctx);
     if (bt->precision == BEM_PREC_F32) {
         k_batch_pack<<<dim3(64, (unsigned)w.count), 256, 0, s>>>(w.d_sprob); BEM_COUNT(ctx);
+        if (bt->h16) {
+            k_batch_pack_h16<<<dim3(64, (unsigned)w.count), 256, 0, s>>>(w.d_sprob); BEM_COUNT(ctx);
+        }
     }
     if (bt->precond == BEM_PRECOND_BLOCK) {
         const dim3 gb((unsigned)w.max_nbj, (unsigned)w.count);
@@ -2163,7 +2352,7 @@ static bem_status batch_enqueue(bem_batch *bt, BatchWave &w)
 // Device bytes of one problem's block in the arena: V, diagonal, 7 solver vectors, the
 // double-float copy of the product's input, the tile partials of the product, the
 // packed FP32 upper triangle, the CTA partials and the inverse cluster blocks.
-static size_t batch_problem_bytes(int64_t N, int prec, bool packed, bool block, int G)
+static size_t batch_problem_bytes(int64_t N, int prec, bool packed, bool block, int G, bool h16)
 {
     auto al = [](size_t b) { return (b + 255) / 256 * 256; };
     const int64_t L = padded_ld(N), nb = L / kSB, nt = nb * (nb + 1) / 2;
@@ -2171,6 +2360,7 @@ static size_t batch_problem_bytes(int64_t N, int prec, bool packed, bool block, 
     size_t b = al(es * (size_t)N * (size_t)L) + al(8 * (size_t)N) + al(8 * 7 * (size_t)L) + al(8 * (size_t)L) +
                al(2 * (size_t)nt * kSB * 8) + al(sizeof(double) * (3 * (size_t)G + 8) + 64);
     if (packed) b += al((size_t)nt * kTileF * 4);
+    if (packed && h16) b += al((size_t)nt * kTileF * 2) + al((size_t)nt * 4);
     if (block) b += al(8 * (size_t)kBJ * kBJ * (size_t)((N + kBJ - 1) / kBJ));
     return b;
 }
@@ -2219,6 +2409,11 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
     const double delta = rd == 0.0 ? 1e-4 : (rd > 0.0 && rd < 1.0 ? rd : 0.0);
     const bool packed = prec == BEM_PREC_F32 || delta > 0.0;
     const bool block = precond == BEM_PRECOND_BLOCK;
+    {
+        const int pr = sopts ? sopts->products : BEM_PRODUCTS_DEFAULT;
+        bt->h16 = packed && (pr == BEM_PRODUCTS_FP16 ||
+                             (pr == BEM_PRODUCTS_DEFAULT && prec == BEM_PREC_F32 && precond == BEM_PRECOND_BLOCK));
+    }
     bt->prob.resize(count);
     bt->args.resize(count);
     auto fail = [&](bem_status code) {
@@ -2264,7 +2459,7 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
         int w = 0, n_in = 0;
         size_t wbytes = 0, maxw = 0;
         for (int p = 0; p < count; ++p) {
-            const size_t b = batch_problem_bytes(meshes[p]->N, prec, packed, block, Gmax);
+            const size_t b = batch_problem_bytes(meshes[p]->N, prec, packed, block, Gmax, bt->h16);
             if ((int64_t)b > avail) {
                 return fail(set_error(ctx, BEM_ERR_OOM,
                                       "problem %d (N = %lld) needs %zu bytes, more than the %lld available to a wave",
@@ -2408,9 +2603,17 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
             const size_t part_bytes = sizeof(double) * (3 * (size_t)g[k] + 8) + 64;
             cur += al(sizeof(double) * (3 * (size_t)Gmax + 8) + 64);
             float *vp = nullptr;
+            __half *vh = nullptr;
+            float *vsc = nullptr;
             if (packed) {
                 vp = reinterpret_cast<float *>(cur);
                 cur += al((size_t)pr.nt * kTileF * 4);
+                if (bt->h16) {
+                    vh = reinterpret_cast<__half *>(cur);
+                    cur += al((size_t)pr.nt * kTileF * 2);
+                    vsc = reinterpret_cast<float *>(cur);
+                    cur += al((size_t)pr.nt * 4);
+                }
             }
             double *binv = nullptr;
             if (block) {
@@ -2442,6 +2645,9 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
             a.out = bt->d_res + (size_t)kBatchRes * p;
             a.err = reinterpret_cast<int *>(bt->d_res + (size_t)kBatchRes * p + 6);
             a.vp = vp;
+            a.vh = vh;
+            a.vsc = vsc;
+            a.n16_out = bt->d_res + (size_t)kBatchRes * p + 7;
             a.bperm = pr.perm;
             a.binv = binv;
             a.nbj = pr.nbj;
@@ -2464,6 +2670,8 @@ bem_status bem_batch_create(bem_ctx *ctx, int32_t count, bem_mesh *const *meshes
             q.part = part;
             q.part_n = (int64_t)(part_bytes / 8);
             q.vp = prec == BEM_PREC_F32 ? vp : nullptr;
+            q.vh = prec == BEM_PREC_F32 ? vh : nullptr;
+            q.vsc = vsc;
             q.tiles = pr.tiles;
             q.nt = pr.nt;
             q.perm = pr.perm;
@@ -2631,7 +2839,12 @@ bem_status bem_batch_run(bem_batch *bt, bem_batch_result *results)
         for (int p = w.first; p < w.first + w.count; ++p) {
             const double *r = bt->h_res + (size_t)kBatchRes * p;
             const double n2 = (double)bt->prob[p].op->N * (double)bt->prob[p].op->N;
-            bytes += bt->precision == BEM_PREC_F32 ? 2.0 * n2 * (r[2] + r[3]) : 4.0 * n2 * r[3] + 2.0 * n2 * (r[2] + 1.0);
+            // iterations with the FP16 copy read N^2 bytes (r[7]); DF64 problems also
+            // pack it once from the hi parts (2 N^2 read, N^2 written)
+            const double i16 = bt->h16 ? r[7] : 0.0;
+            bytes += bt->precision == BEM_PREC_F32
+                         ? 2.0 * n2 * (r[2] - i16 + r[3]) + n2 * i16
+                         : 4.0 * n2 * r[3] + 2.0 * n2 * (r[2] - i16 + 1.0) + n2 * i16 + (bt->h16 ? 3.0 * n2 : 0.0);
             const int err = *reinterpret_cast<const int *>(r + 6);
             const double rel = std::sqrt(r[0] / (r[1] > 0.0 ? r[1] : 1.0));
             timeout |= err != 0;
