@@ -72,3 +72,21 @@ def test_adaptive_loop_with_fp16_products_matches_oracle(ctx):
     assert [r["N"] for r in recs] == [h["N"] for h in hist]
     for r, h in zip(recs, hist):
         assert abs(r["cap"] / h["cap"] - 1) < 1e-9
+
+
+@pytest.mark.parametrize("prec", [bem.PREC_DF64, bem.PREC_F32], ids=["df64", "f32"])
+def test_batch_with_fp16_products_matches_single_solves(ctx, prec):
+    """A batch takes the FP16 copy like a single solve (DF64 problems pack it inside the
+    cooperative launch, FP32 ones before it): every problem's Cap equals its single
+    solve's with the same products."""
+    ms = [inputs.cube_mesh(4), inputs.workload_polycube_adaptive(), inputs.fichera_mesh(2), inputs.icosphere_mesh(3)]
+    meshes = [bem.Mesh.upload(ctx, m.verts, m.tris) for m in ms]
+    b = bem.Batch(ctx, meshes, precision=prec, precond=bem.PRECOND_BLOCK, tol=1e-11, products=bem.PRODUCTS_FP16)
+    res = b.run()
+    for m, mesh, r in zip(ms, meshes, res):
+        op = bem.Operator.assemble(mesh, precision=prec)
+        cap, _, info = bem.solve_capacity(op, tol=1e-11, precond=bem.PRECOND_BLOCK, products=bem.PRODUCTS_FP16)
+        assert r["converged"] and r["relres"] <= 1e-11, (m.name, r)
+        assert abs(r["cap"] / cap - 1) < 1e-9, (m.name, r["cap"], cap)
+        op.close()
+    b.close()
