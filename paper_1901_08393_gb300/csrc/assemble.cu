@@ -77,9 +77,12 @@ static void gauss_legendre(int n, double *x, double *w)
     }
 }
 
+static bem_status far_df_attributes(bem_ctx *ctx);
+
 static bem_status assembly_constants(bem_ctx *ctx)
 {
     if (ctx->device < 64 && g_asm_ready[ctx->device]) return BEM_OK;
+    if (bem_status st = far_df_attributes(ctx)) return st;
     const double r15 = std::sqrt(15.0);
     const double wa = (155.0 - r15) / 1200.0, wb = (155.0 + r15) / 1200.0;
     const double w7[kQ] = {9.0 / 40.0, wa, wa, wa, wb, wb, wb};
@@ -266,20 +269,172 @@ __global__ void __launch_bounds__(C) k_far_f32(const float *__restrict__ q32,
 }
 
 // Double-float far field: see the file comment.
-// MB > 0: the column triangle's 21 offsets staged in shared memory as (hi, lo) pairs,
-// thread-major (conflict-free), instead of 42 registers, the point loops not unrolled,
-// and MB CTAs per SM requested (registers capped to fit) -- more resident warps for
-// the same work.  MB = 0: offsets in registers, loops unrolled.
+//
+// v rounded to the nearest multiple of q = 2^(e-23), for |v| < 2^(e-1) and big =
+// 1.5 * 2^e: v + big lies in [2^e, 2^(e+1)], whose spacing is q, and the subtraction
+// of big is exact (Sterbenz).
+__device__ __forceinline__ float grid_snap(float v, float big) { return __fsub_rn(__fadd_rn(v, big), big); }
+
+// s + e = a + b exactly for a, b >= 0 (Dekker's fast two-sum with the larger first).
+__device__ __forceinline__ void pos_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(fminf(a, b), __fsub_rn(s, fmaxf(a, b)));
+}
+
+// 1/|d| = y + yl for |d|^2 = Sh + Sl: the MUFU estimate y and one Newton step in
+// double-float, yl = y t / 2 with t = 1 - S y^2 and y^2 = y2 + y2e by a two-product.
+// The estimate's relative error is below 2^-22, so 1 - Sh y2 is below 2^-20 in size
+// and its single rounding in the FMA is below 2^-44; the other terms are of order
+// 2^-24 and enter by FMAs.
+__device__ __forceinline__ void df_rsqrt_newton(float Sh, float Sl, float &y, float &yl)
+{
+    y = rsqrtf(Sh);
+    float y2, y2e;
+    two_prod(y, y, y2, y2e);
+    float t = __fmaf_rn(-Sh, y2, 1.0f);
+    t = __fmaf_rn(-Sh, y2e, t);
+    t = __fmaf_rn(-Sl, y2, t);
+    yl = __fmul_rn(__fmul_rn(0.5f, y), t);
+}
+
+// sh + sl += w (y + yl) with the two-sum of the running sum (pos: sh and w y are not
+// negative, the larger added first)
+template <bool POS = false>
+__device__ __forceinline__ void df_acc_w(float2 w, float y, float yl, float &sh, float &sl)
+{
+    float ph, pe, u, ue;
+    two_prod(w.x, y, ph, pe);
+    pe = __fmaf_rn(w.x, yl, pe);
+    pe = __fmaf_rn(w.y, y, pe);
+    if (POS)
+        pos_two_sum(sh, ph, u, ue);
+    else
+        two_sum(sh, ph, u, ue);
+    sh = u;
+    sl = __fadd_rn(sl, __fadd_rn(pe, ue));
+}
+
+// Entry sum sum_a w_a sum_b w_b / |x_a - y_b| of a pair whose bounding balls are close
+// (|c_i - c_j| < 1.12 (R_i + R_j)): x_a - y_b = (D + o_a) - o_b in double-float by
+// two-sums, D = c_i - c_j, o the offsets from the centroids (o_b from the table).
+__device__ __forceinline__ void far_df_exact(const float *qi, const float *Dh, const float *Dl,
+                                             const float2 *__restrict__ oj, float &h_out, float &l_out)
+{
+    float acc_h = 0.0f, acc_l = 0.0f;
+#pragma unroll 1
+    for (int a = 0; a < kQ; ++a) {
+        float eh[3], el[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s, e;
+            two_sum(Dh[c], qi[2 * (3 * a + c)], s, e);
+            e = __fadd_rn(e, __fadd_rn(Dl[c], qi[2 * (3 * a + c) + 1]));
+            fast_two_sum(s, e, eh[c], el[c]);
+        }
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll 1
+        for (int b = 0; b < kQ; ++b) {
+            // d = e_a - o_b; |d|^2 = sum h^2 + 2 h l (two-product, two-sum)
+            float Sh = 0.0f, Sl = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float h, e;
+                const float2 o = oj[3 * b + c];
+                two_sum(eh[c], -o.x, h, e);
+                const float l = __fadd_rn(e, __fsub_rn(el[c], o.y));
+                float p, pe;
+                two_prod(h, h, p, pe);
+                pe = __fmaf_rn(__fmul_rn(2.0f, h), l, pe);
+                if (c == 0) {
+                    Sh = p;
+                    Sl = pe;
+                } else {
+                    float t, te;
+                    two_sum(Sh, p, t, te);
+                    Sh = t;
+                    Sl = __fadd_rn(Sl, __fadd_rn(pe, te));
+                }
+            }
+            float y, yl;
+            df_rsqrt_newton(Sh, Sl, y, yl);
+            df_acc_w(c_w7df[b], y, yl, sh, sl);
+        }
+        df_acc_w(c_w7df[a], sh, sl, acc_h, acc_l);
+    }
+    fast_two_sum(acc_h, acc_l, h_out, l_out);
+}
+
+// The same sum for a pair with |D| >= 1.12 (R_i + R_j) (R: the largest distance of a
+// triangle's points from its centroid): D, o_a and o_b are split on the pair's grid
+// q = 2^(e-23), 2^(e-1) > max(|D|_inf, r_i, r_j) (r: the largest |hi| of the offset
+// coordinates) with e odd -- hi parts multiples of q (exact), lo parts the rest -- so
+// that the hi part h of x_a - y_b is one exact subtraction and its lo part l one
+// rounded one; |d|^2 = h^2 + 2 h l + l^2 with h^2 by a two-product.  Every |x_a - y_b|
+// is at least 0.107 |D| and 2^e <= 8 |D|, so the lo parts' roundings (a few units of
+// 2^-24 q each) stay below 1e-11 of the entry.  sg: o_b on the grid, (hi, 2 lo),
+// stride C.
+template <int C, bool UNROLL>
+__device__ __forceinline__ void far_df_grid(const float *qi, const float *Dh, const float *Dl, float big,
+                                            const float2 *sg, float &h_out, float &l_out)
+{
+    float Dg[3], Dl2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Dg[c] = grid_snap(Dh[c], big);
+        Dl2[c] = __fmul_rn(2.0f, __fadd_rn(__fsub_rn(Dh[c], Dg[c]), Dl[c]));
+    }
+    float acc_h = 0.0f, acc_l = 0.0f;
+#pragma unroll(UNROLL ? kQ : 1)
+    for (int a = 0; a < kQ; ++a) {
+        float eh[3], el2[3];  // x_a - c_j: hi on the grid, twice the lo part
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float oh = qi[2 * (3 * a + c)], og = grid_snap(oh, big);
+            eh[c] = __fadd_rn(Dg[c], og);
+            el2[c] = __fmaf_rn(2.0f, __fadd_rn(__fsub_rn(oh, og), qi[2 * (3 * a + c) + 1]), Dl2[c]);
+        }
+        float sh = 0.0f, sl = 0.0f;
+#pragma unroll(UNROLL ? kQ : 1)
+        for (int b = 0; b < kQ; ++b) {
+            float p[3], pe[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 o = sg[(3 * b + c) * C];
+                const float dh = __fsub_rn(eh[c], o.x);  // exact
+                const float dl2 = __fsub_rn(el2[c], o.y);
+                p[c] = __fmul_rn(dh, dh);
+                pe[c] = __fmaf_rn(dh, dh, -p[c]);
+                pe[c] = __fmaf_rn(dl2, __fmaf_rn(0.25f, dl2, dh), pe[c]);  // 2 h l + l^2
+            }
+            float s1, e1, s2, e2, y, yl;
+            pos_two_sum(p[0], p[1], s1, e1);
+            pos_two_sum(s1, p[2], s2, e2);
+            df_rsqrt_newton(s2, __fadd_rn(__fadd_rn(pe[0], pe[1]), __fadd_rn(pe[2], __fadd_rn(e1, e2))), y, yl);
+            df_acc_w<true>(c_w7df[b], y, yl, sh, sl);
+        }
+        df_acc_w<true>(c_w7df[a], sh, sl, acc_h, acc_l);
+    }
+    fast_two_sum(acc_h, acc_l, h_out, l_out);
+}
+
+// MB > 0: MB CTAs per SM requested (registers capped to fit), the point loops rolled
+// unless UB.  The column triangle's offsets on the current pair's grid are kept in
+// dynamic shared memory (3 kQ x C pairs, thread-major: conflict-free), re-split only
+// when the grid changes from one row to the next.
+template <int C>
+constexpr size_t far_df_smem() { return sizeof(float2) * 3 * kQ * C; }
+
 template <int R, int C, int MB, bool UB = false>
 __device__ __forceinline__ void far_df_body(const float *__restrict__ qdf, float2 *__restrict__ V, int64_t ld,
                                             int64_t r1, int64_t c1, int64_t i0, int64_t cbase)
 {
-    constexpr bool S = MB > 0;
-    __shared__ float sq[R][53];
-    __shared__ float2 scol[S ? 3 * kQ * C : 1];
+    constexpr bool UNROLL = MB == 0 || UB;
+    __shared__ float sq[R][55];
+    extern __shared__ float2 far_dsm[];
     if (i0 > cbase + C - 1 || i0 >= r1) return;
-    for (int k = threadIdx.x; k < R * 53; k += C) {
-        const int r = k / 53, c = k % 53;
+    for (int k = threadIdx.x; k < R * 55; k += C) {
+        const int r = k / 55, c = k % 55;
         const int64_t i = i0 + r;
         sq[r][c] = (i < r1) ? qdf[i * kQdfStride + c] : 0.0f;
     }
@@ -287,25 +442,14 @@ __device__ __forceinline__ void far_df_body(const float *__restrict__ qdf, float
     const int64_t j = cbase + threadIdx.x;
     if (j >= c1) return;
     const float *qj = qdf + j * kQdfStride;
-    float oh[S ? 1 : 3 * kQ], ol[S ? 1 : 3 * kQ], cj[9];
-    if constexpr (S) {
-#pragma unroll
-        for (int k = 0; k < 3 * kQ; ++k)  // this thread's own column
-            scol[k * C + threadIdx.x] = make_float2(qj[2 * k], qj[2 * k + 1]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < 3 * kQ; ++k) {
-            oh[k] = qj[2 * k];
-            ol[k] = qj[2 * k + 1];
-        }
-    }
-    auto OF = [&](int k) -> float2 {
-        if constexpr (S) return scol[k * C + threadIdx.x];
-        else return make_float2(oh[k], ol[k]);
-    };
+    const float2 *oj = reinterpret_cast<const float2 *>(qj);
+    float2 *sg = far_dsm + threadIdx.x;
+    float cj[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) cj[k] = qj[42 + k];
+    const float rj = qj[53], Rj = qj[54];
     const float2 Aj = df_mul(make_float2(qj[51], qj[52]), c_inv4pi_df);
+    unsigned eg = 0u;  // exponent field of the grid bound sg holds (0: none)
     const int rows = (int)((r1 - i0) < R ? (r1 - i0) : R);
     for (int r = 0; r < rows; ++r) {
         const int64_t i = i0 + r;
@@ -323,70 +467,30 @@ __device__ __forceinline__ void far_df_body(const float *__restrict__ qdf, float
             l = __fadd_rn(l, __fadd_rn(__fadd_rn(e1, e2), s3));
             fast_two_sum(h, l, Dh[c], Dl[c]);
         }
-        float acc_h = 0.0f, acc_l = 0.0f;
-#pragma unroll(S ? 1 : kQ)
-        for (int a = 0; a < kQ; ++a) {
-            float eh[3], el[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                float s, e;
-                two_sum(Dh[c], qi[2 * (3 * a + c)], s, e);
-                e = __fadd_rn(e, __fadd_rn(Dl[c], qi[2 * (3 * a + c) + 1]));
-                fast_two_sum(s, e, eh[c], el[c]);
-            }
-            float sh = 0.0f, sl = 0.0f;
-#pragma unroll((S && !UB) ? 1 : kQ)
-            for (int b = 0; b < kQ; ++b) {
-                // d = e_a - o_b; |d|^2 = sum h^2 + 2 h l (two-product, two-sum)
-                float Sh = 0.0f, Sl = 0.0f;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float h, e;
-                    const float2 o = OF(3 * b + c);
-                    two_sum(eh[c], -o.x, h, e);
-                    const float l = __fadd_rn(e, __fsub_rn(el[c], o.y));
-                    float p, pe;
-                    two_prod(h, h, p, pe);
-                    pe = __fmaf_rn(__fmul_rn(2.0f, h), l, pe);
-                    if (c == 0) {
-                        Sh = p;
-                        Sl = pe;
-                    } else {
-                        float t, te;
-                        two_sum(Sh, p, t, te);
-                        Sh = t;
-                        Sl = __fadd_rn(Sl, __fadd_rn(pe, te));
-                    }
-                }
-                // 1/|d| = y + yl: MUFU estimate y, one Newton step in double-float
-                const float y = rsqrtf(Sh);
-                float y2, y2e, m, me;
-                two_prod(y, y, y2, y2e);
-                two_prod(Sh, y2, m, me);
-                float t = __fsub_rn(1.0f, m);
-                t = __fsub_rn(t, me);
-                t = __fmaf_rn(-Sh, y2e, t);
-                t = __fmaf_rn(-Sl, y2, t);
-                const float yl = __fmul_rn(__fmul_rn(0.5f, y), t);
-                // s += w_b (y + yl)
-                float ph, pe, u, ue;
-                two_prod(c_w7df[b].x, y, ph, pe);
-                pe = __fmaf_rn(c_w7df[b].x, yl, pe);
-                pe = __fmaf_rn(c_w7df[b].y, y, pe);
-                two_sum(sh, ph, u, ue);
-                sh = u;
-                sl = __fadd_rn(sl, __fadd_rn(pe, ue));
-            }
-            float ph, pe, u, ue;
-            two_prod(c_w7df[a].x, sh, ph, pe);
-            pe = __fmaf_rn(c_w7df[a].x, sl, pe);
-            pe = __fmaf_rn(c_w7df[a].y, sh, pe);
-            two_sum(acc_h, ph, u, ue);
-            acc_h = u;
-            acc_l = __fadd_rn(acc_l, __fadd_rn(pe, ue));
-        }
+        const float ri = qi[53], Rs = qi[54] + Rj;
+        const float bound = fmaxf(fmaxf(fabsf(Dh[0]), fabsf(Dh[1])), fmaxf(fmaxf(fabsf(Dh[2]), ri), rj));
+        // bound in [2^(eb-127), 2^(eb-126)); odd eb, so that the grid changes less often
+        // from one row to the next
+        const unsigned eb = (__float_as_uint(bound) >> 23) | 1u;
+        const float D2 = Dh[0] * Dh[0] + Dh[1] * Dh[1] + Dh[2] * Dh[2];
         float h, l;
-        fast_two_sum(acc_h, acc_l, h, l);
+        // the grid path where its bounds hold (and no product of it can leave the
+        // normal FP32 range); the two-sum path otherwise
+        if (D2 >= 1.26f * (Rs * Rs) && eb >= 93u && eb <= 185u) {
+            const float big = __uint_as_float(((eb + 2u) << 23) | 0x400000u);  // 1.5 * 2^(eb-125)
+            if (eb != eg) {
+#pragma unroll 1
+                for (int k = 0; k < 3 * kQ; ++k) {
+                    const float2 o = oj[k];
+                    const float g = grid_snap(o.x, big);
+                    sg[k * C] = make_float2(g, __fmul_rn(2.0f, __fadd_rn(__fsub_rn(o.x, g), o.y)));
+                }
+                eg = eb;
+            }
+            far_df_grid<C, UNROLL>(qi, Dh, Dl, big, sg, h, l);
+        } else {
+            far_df_exact(qi, Dh, Dl, oj, h, l);
+        }
         V[i * ld + j] = df_mul(df_mul(make_float2(qi[51], qi[52]), Aj), make_float2(h, l));
     }
 }
@@ -647,9 +751,10 @@ static void far_kernel(bem_operator *op, dim3 grid, int64_t r0, int64_t r1, int6
     else if (op->precision == BEM_PREC_DF64)
     {
         if constexpr (MB > 0)
-            k_far_df_s<R, C, MB, UB><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
+            k_far_df_s<R, C, MB, UB><<<grid, C, far_df_smem<C>(), s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1,
+                                                                       c0, c1);
         else
-            k_far_df<R, C><<<grid, C, 0, s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
+            k_far_df<R, C><<<grid, C, far_df_smem<C>(), s>>>(m->qdf, (float2 *)op->V, op->ld, r0, r1, c0, c1);
     }
     else
         k_far_f32<R, C><<<grid, C, 0, s>>>(m->q32, m->cent, (float *)op->V, op->ld, r0, r1, c0, c1);
@@ -945,7 +1050,22 @@ void batch_far_items(int v, int p, int64_t N, std::vector<int4> &items)
 template <typename T, int R, int C, int MB = 0, bool UB = false>
 static void far_batch_launch(const BatchAsm &b, cudaStream_t s)
 {
-    k_far_batch<T, R, C, MB, UB><<<(unsigned)b.n_far, C, 0, s>>>(b.prob, b.far_items);
+    const size_t smem = std::is_same<T, float2>::value ? far_df_smem<C>() : 0;
+    k_far_batch<T, R, C, MB, UB><<<(unsigned)b.n_far, C, smem, s>>>(b.prob, b.far_items);
+}
+
+// The DF64 tiles of 256 columns whose shared memory (row staging + the column
+// offsets on the pair grid) exceeds the default 48 KB per CTA.
+static bem_status far_df_attributes(bem_ctx *ctx)
+{
+    const int dyn = (int)far_df_smem<256>();
+    BEM_CK(ctx, cudaFuncSetAttribute(k_far_df<32, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    BEM_CK(ctx, cudaFuncSetAttribute(k_far_df<64, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    BEM_CK(ctx, cudaFuncSetAttribute(k_far_batch<float2, 32, 256, 0, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    BEM_CK(ctx, cudaFuncSetAttribute(k_far_batch<float2, 64, 256, 0, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    return BEM_OK;
 }
 
 // Event record that also fires when a captured graph replays (an external event node

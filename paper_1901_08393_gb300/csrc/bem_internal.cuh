@@ -17,7 +17,9 @@ constexpr int kQ64Stride = 24;     // doubles per triangle in the FP64 point tab
 constexpr int kQ32Stride = 24;     // floats per triangle in the FP32 offset table
 constexpr int kQdfStride = 56;     // floats per triangle in the double-float table:
                                    // [0,42) offsets hi/lo, [42,51) centroid as 3 floats
-                                   // per coordinate, [51,53) area hi/lo
+                                   // per coordinate, [51,53) area hi/lo, [53] the
+                                   // largest |hi| of the offsets, [54] the largest
+                                   // distance of a point from the centroid
 constexpr int kMaxSS = 16;         // largest Sauter-Schwab order accepted
 constexpr int kMaxValence = 96;    // triangles per vertex accepted by the pair builder
 constexpr double kInv4Pi = 0.079577471545947668;  // 1 / (4 pi)

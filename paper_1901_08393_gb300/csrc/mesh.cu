@@ -297,7 +297,23 @@ __global__ void k_geometry(const double *verts, const int32_t *tris, int64_t N, 
         }
     for (int c = 0; c < 3; ++c) split3(c3[c], f + 42 + 3 * c);
     split2(A, f + 51);
-    f[53] = f[54] = f[55] = 0.0f;
+    // the largest |hi part| of the 21 offset coordinates (the far field's grid bound)
+    // and the largest distance of a point from the centroid, rounded up
+    float rm = 0.0f;
+    for (int k = 0; k < 3 * kQ; ++k) rm = fmaxf(rm, fabsf(f[2 * k]));
+    double rd2 = 0.0;
+    for (int a = 0; a < kQ; ++a) {
+        double s2 = 0.0;
+        for (int c = 0; c < 3; ++c) {
+            const double off = c_radon_bary[a][0] * R[0][c] + c_radon_bary[a][1] * R[1][c] +
+                               c_radon_bary[a][2] * R[2][c];
+            s2 += off * off;
+        }
+        rd2 = rd2 > s2 ? rd2 : s2;
+    }
+    f[53] = rm;
+    f[54] = __double2float_ru(sqrt(rd2) * (1.0 + 1e-12));
+    f[55] = 0.0f;
     cent[4 * t + 0] = c3[0];
     cent[4 * t + 1] = c3[1];
     cent[4 * t + 2] = c3[2];
