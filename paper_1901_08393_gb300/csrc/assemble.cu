@@ -287,9 +287,13 @@ __device__ __forceinline__ void pos_two_sum(float a, float b, float &s, float &e
 // The estimate's relative error is below 2^-22, so 1 - Sh y2 is below 2^-20 in size
 // and its single rounding in the FMA is below 2^-44; the other terms are of order
 // 2^-24 and enter by FMAs.
+template <bool FTZ = false>
 __device__ __forceinline__ void df_rsqrt_newton(float Sh, float Sl, float &y, float &yl)
 {
-    y = rsqrtf(Sh);
+    if (FTZ)  // Sh known to be a normal number: the bare MUFU estimate
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(Sh));
+    else
+        y = rsqrtf(Sh);
     float y2, y2e;
     two_prod(y, y, y2, y2e);
     float t = __fmaf_rn(-Sh, y2, 1.0f);
@@ -395,8 +399,7 @@ __device__ __forceinline__ void far_df_grid(const float *qi, const float *Dh, co
             el2[c] = __fmaf_rn(2.0f, __fadd_rn(__fsub_rn(oh, og), qi[2 * (3 * a + c) + 1]), Dl2[c]);
         }
         float sh = 0.0f, sl = 0.0f;
-#pragma unroll(UNROLL ? kQ : 1)
-        for (int b = 0; b < kQ; ++b) {
+        auto point_pair = [&](int b) {
             float p[3], pe[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
@@ -410,8 +413,17 @@ __device__ __forceinline__ void far_df_grid(const float *qi, const float *Dh, co
             float s1, e1, s2, e2, y, yl;
             pos_two_sum(p[0], p[1], s1, e1);
             pos_two_sum(s1, p[2], s2, e2);
-            df_rsqrt_newton(s2, __fadd_rn(__fadd_rn(pe[0], pe[1]), __fadd_rn(pe[2], __fadd_rn(e1, e2))), y, yl);
+            df_rsqrt_newton<true>(s2, __fadd_rn(__fadd_rn(pe[0], pe[1]), __fadd_rn(pe[2], __fadd_rn(e1, e2))), y,
+                                  yl);
             df_acc_w<true>(c_w7df[b], y, yl, sh, sl);
+        };
+        if (UNROLL) {
+#pragma unroll
+            for (int b = 0; b < kQ; ++b) point_pair(b);
+        } else {  // two point pairs per trip: half the loop control
+            point_pair(0);
+#pragma unroll 2
+            for (int b = 1; b < kQ; ++b) point_pair(b);
         }
         df_acc_w<true>(c_w7df[a], sh, sl, acc_h, acc_l);
     }
