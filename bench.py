@@ -71,9 +71,12 @@ THETA = 0.5
 TOL = 1e-10
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (recipe table)
 FAR_FLOPS_PER_ENTRY = 49 * 11 + 16  # FP64 far field: per point pair 3 sub, 5 for r^2, rsqrt, 2 accumulate
-# Double-float far field: FP32 ALU operations per entry (49 x 74 per point pair, 7 x 45 per
-# row point, 92 per pair), against the FP32 issue peak 152 SMs x 128 lanes x 2.07 GHz.
-DF_FAR_OPS_PER_ENTRY = 49 * 74 + 7 * 45 + 92
+# Double-float far field: FP32 operations per entry of its grid form, which all but the
+# closest far pairs take (per point pair 44 FP32 arithmetic + 6 min/max + 1 MUFU; per row
+# point 31 for its split on the pair's grid and the outer sum; per entry 119 for the exact
+# centroid difference, the grid choice and the area products), against the FP32 issue
+# peak 152 SMs x 128 lanes x 2.07 GHz.
+DF_FAR_OPS_PER_ENTRY = 49 * 51 + 7 * 31 + 119
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 PCG_TRAFFIC_RATIO = 18.072 / 18.294  # ncu DRAM bytes / algorithmic bytes of the persistent solver
 PRECISIONS = {"df64": 2, "f64": 0, "f32": 1}

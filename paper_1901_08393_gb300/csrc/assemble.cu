@@ -12,9 +12,14 @@
 //      DF64 -- FP64-accurate double-float on the FP32 pipe: x_a - y_b is formed as
 //              (c_i - c_j) + (o_a - o_b) with the centroid difference taken exactly
 //              from three-float centroids and the offsets o from the centroid as
-//              hi/lo pairs; |r|^2 by two-product/two-sum; 1/|r| by the MUFU
-//              reciprocal square root and one Newton step in double-float (error
-//              ~1.5 e^2 ~ 1e-14); sums by two-sum.  V stored as hi/lo pairs.
+//              hi/lo pairs.  Pairs whose centroids are at least 1.12 (R_i + R_j)
+//              apart (R: the largest distance of a triangle's points from its
+//              centroid; almost all far pairs) split every term on one power-of-two
+//              grid chosen for the pair, so that the hi part of x_a - y_b is a single
+//              exact subtraction; closer pairs take it by two-sums.  |r|^2 by
+//              two-product/two-sum; 1/|r| by the MUFU reciprocal square root and one
+//              Newton step in double-float (error ~1.5 e^2 ~ 1e-14); sums by
+//              two-sum.  Entries within ~1e-12 of FP64.  V stored as hi/lo pairs.
 //      F64  -- native FP64 (GB300 issues FP64 at 1/64 of the FP32 rate).
 //      F32  -- centroid difference from hi + lo float centroids, offsets in FP32, MUFU rsqrt;
 //              no FP64 operation per pair (GB300 issues FP64 at 1/64 of the FP32 rate).
