@@ -715,14 +715,23 @@ __device__ __forceinline__ void near_entry(const double *__restrict__ verts, con
     if (i != j) V[j * ld + i] = e;
 }
 
+// All touching pairs of an assembly in one launch: the common-vertex pairs (the longest
+// work per thread) first, then the common-edge pairs, then the identical pairs of the
+// new triangles, so that the three lists overlap instead of running one after another.
 template <typename T>
 __global__ void k_near(const double *__restrict__ verts, const int32_t *__restrict__ tris,
-                       const double *__restrict__ area, const int32_t *__restrict__ pairs, int64_t npairs,
-                       int kind, int64_t K, int n, T *V, int64_t ld)
+                       const double *__restrict__ area, const int32_t *__restrict__ vert_pairs, int64_t n_vert,
+                       const int32_t *__restrict__ edge_pairs, int64_t n_edge, int64_t n_ident, int64_t K, int n,
+                       T *V, int64_t ld)
 {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= npairs) return;
-    near_entry<T>(verts, tris, area, pairs, idx, kind, K, n, V, ld);
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n_vert) {
+        near_entry<T>(verts, tris, area, vert_pairs, idx, 1, K, n, V, ld);
+    } else if ((idx -= n_vert) < n_edge) {
+        near_entry<T>(verts, tris, area, edge_pairs, idx, 2, K, n, V, ld);
+    } else if ((idx -= n_edge) < n_ident) {
+        near_entry<T>(verts, tris, area, nullptr, idx, 0, K, n, V, ld);
+    }
 }
 
 // ------------------------------------------------------------------ reuse and diagonal
@@ -903,15 +912,13 @@ static bem_status launch_near(bem_operator *op, int64_t K)
     bem_ctx *ctx = m->ctx;
     const int n = op->ss_order;
     const int prof = prof_start(ctx, BEM_KERNEL_NEAR, (double)(m->N - K + m->n_vert_pairs + m->n_edge_pairs));
-    if (m->N > K)
-        { k_near<T><<<nblk(m->N - K, 128), 128, 0, ctx->stream>>>(m->verts, m->tris, m->area, nullptr, m->N - K, 0,
-                                                                K, n, (T *)op->V, op->ld); BEM_COUNT(ctx); }
-    if (m->n_vert_pairs > 0)
-        { k_near<T><<<nblk(m->n_vert_pairs, 128), 128, 0, ctx->stream>>>(
-            m->verts, m->tris, m->area, m->vert_pairs, m->n_vert_pairs, 1, K, n, (T *)op->V, op->ld); BEM_COUNT(ctx); }
-    if (m->n_edge_pairs > 0)
-        { k_near<T><<<nblk(m->n_edge_pairs, 128), 128, 0, ctx->stream>>>(
-            m->verts, m->tris, m->area, m->edge_pairs, m->n_edge_pairs, 2, K, n, (T *)op->V, op->ld); BEM_COUNT(ctx); }
+    const int64_t n_ident = m->N > K ? m->N - K : 0, total = m->n_vert_pairs + m->n_edge_pairs + n_ident;
+    if (total > 0) {
+        k_near<T><<<nblk(total, 128), 128, 0, ctx->stream>>>(m->verts, m->tris, m->area, m->vert_pairs,
+                                                             m->n_vert_pairs, m->edge_pairs, m->n_edge_pairs, n_ident,
+                                                             K, n, (T *)op->V, op->ld);
+        BEM_COUNT(ctx);
+    }
     prof_stop(ctx, prof);
     BEM_CK_LAUNCH(ctx);
     return BEM_OK;
