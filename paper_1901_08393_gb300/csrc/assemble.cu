@@ -564,26 +564,31 @@ __device__ __forceinline__ double inv_norm3(double x, double y, double z)
     return rsqrt(x * x + y * y + z * z);
 }
 
+// The near-field quadratures below return one thread's share of the sum: thread sub of
+// a group of kNearGroup takes every kNearGroup-th index of the outermost loop, and the
+// group's shares are added in a fixed order before the constant factor is applied.
+constexpr int kNearGroup = 4;
+
 // Identical panels: (1/6) sum over the 6 hexagon sectors of int_0^1 1/|J w(eta)|.
-__device__ double ss_identical(const Tri &P, int n)
+__device__ double ss_identical(const Tri &P, int n, int sub)
 {
     const double *gx = c_glx[n], *gw = c_glw[n];
     const double J1[3] = {P.p[1][0] - P.p[0][0], P.p[1][1] - P.p[0][1], P.p[1][2] - P.p[0][2]};
     const double J2[3] = {P.p[2][0] - P.p[1][0], P.p[2][1] - P.p[1][1], P.p[2][2] - P.p[1][2]};
     const double H[7][2] = {{1, 0}, {1, 1}, {0, 1}, {-1, 0}, {-1, -1}, {0, -1}, {1, 0}};
     double s = 0.0;
-    for (int k = 0; k < 6; ++k) {
+    for (int k = sub; k < 6; k += kNearGroup) {
         const double px = H[k][0], py = H[k][1], qx = H[k + 1][0], qy = H[k + 1][1];
         for (int g = 0; g < n; ++g) {
             const double z1 = px + gx[g] * (qx - px), z2 = py + gx[g] * (qy - py);
             s += gw[g] * inv_norm3(z1 * J1[0] + z2 * J2[0], z1 * J1[1] + z2 * J2[1], z1 * J1[2] + z2 * J2[2]);
         }
     }
-    return s / 6.0;
+    return s;  // times 1/6
 }
 
 // Common edge: P = (A,B,C), Q = (A,B,D).  x - y = xi rho (+-a e + t1 fP - t2 fQ).
-__device__ double ss_edge(const Tri &P, const Tri &Q, int n)
+__device__ double ss_edge(const Tri &P, const Tri &Q, int n, int sub)
 {
     const double *gx = c_glx[n], *gw = c_glw[n];
     double e[3], fP[3], fQ[3];
@@ -593,7 +598,7 @@ __device__ double ss_edge(const Tri &P, const Tri &Q, int n)
         fQ[c] = Q.p[2][c] - Q.p[1][c];
     }
     double s = 0.0;
-    for (int iu = 0; iu < n; ++iu)
+    for (int iu = sub; iu < n; iu += kNearGroup)
         for (int iv = 0; iv < n; ++iv) {
             const double u = gx[iu], v = gx[iv], w = gw[iu] * gw[iv];
             // sub-region a: (own, a, other) = (1, u(1-v), uv), weight u
@@ -613,12 +618,12 @@ __device__ double ss_edge(const Tri &P, const Tri &Q, int n)
                            -ab * e[2] + hb * fP[2] - ob * fQ[2]);
             s += w * t;
         }
-    return s / 6.0;
+    return s;  // times 1/6
 }
 
 // Common vertex: P = (A,B,C), Q = (A,D,E).  Regions x = (1,e1), y = e2 (1,e3) and
 // x = e2 (1,e1), y = (1,e3), weight e2.
-__device__ double ss_vertex(const Tri &P, const Tri &Q, int n)
+__device__ double ss_vertex(const Tri &P, const Tri &Q, int n, int sub)
 {
     const double *gx = c_glx[n], *gw = c_glw[n];
     double a1[3], a2[3], b1[3], b2[3];
@@ -629,7 +634,7 @@ __device__ double ss_vertex(const Tri &P, const Tri &Q, int n)
         b2[c] = Q.p[2][c] - Q.p[1][c];
     }
     double s = 0.0;
-    for (int i1 = 0; i1 < n; ++i1) {
+    for (int i1 = sub; i1 < n; i1 += kNearGroup) {
         double xa[3];
         for (int c = 0; c < 3; ++c) xa[c] = a1[c] + gx[i1] * a2[c];
         for (int i3 = 0; i3 < n; ++i3) {
@@ -645,7 +650,7 @@ __device__ double ss_vertex(const Tri &P, const Tri &Q, int n)
             s += gw[i1] * gw[i3] * t;
         }
     }
-    return s / 3.0;
+    return s;  // times 1/3
 }
 
 __device__ __forceinline__ void load_tri(const double *verts, const int32_t *v, Tri &T)
@@ -655,82 +660,105 @@ __device__ __forceinline__ void load_tri(const double *verts, const int32_t *v, 
 }
 
 // kind 0: identical pairs i = j = K + idx; 1: common-vertex list; 2: common-edge list.
-// Pairs (i < j) with j < K are skipped (their entries are reused).
+// Pairs (i < j) with j < K are skipped (their entries are reused).  Called by every
+// thread of a warp (valid false for the padding): the kNearGroup threads of a pair each
+// integrate their share, the shares are summed in a fixed order ((s0 + s1) + (s2 + s3))
+// by shuffles, and the group's first thread writes the entry.
 template <typename T>
 __device__ __forceinline__ void near_entry(const double *__restrict__ verts, const int32_t *__restrict__ tris,
                                            const double *__restrict__ area, const int32_t *__restrict__ pairs,
-                                           int64_t idx, int kind, int64_t K, int n, T *V, int64_t ld)
+                                           int64_t idx, int kind, int64_t K, int n, T *V, int64_t ld, bool valid)
 {
-    int64_t i, j;
-    if (kind == 0) {
-        i = j = K + idx;
-    } else {
-        i = pairs[2 * idx];
-        j = pairs[2 * idx + 1];
-        if (j < K) return;
-    }
-    const int32_t *ti = tris + 3 * i, *tj = tris + 3 * j;
-    double I;
-    if (kind == 0) {
-        Tri P;
-        load_tri(verts, ti, P);
-        I = ss_identical(P, n);
-    } else if (kind == 2) {
-        // (u, v) = the shared vertices in the order they appear in triangle i
-        int32_t u = -1, v = -1, ci = -1, cj = -1;
-        for (int k = 0; k < 3; ++k) {
-            const bool in = (ti[k] == tj[0] || ti[k] == tj[1] || ti[k] == tj[2]);
-            if (in) {
-                if (u < 0) u = ti[k];
-                else v = ti[k];
-            } else {
-                ci = ti[k];
-            }
+    static_assert(kNearGroup == 4, "the group sum below adds four shares");
+    const int sub = (int)(threadIdx.x % kNearGroup);
+    int64_t i = 0, j = 0;
+    bool write = false;
+    double I = 0.0;
+    if (valid) {
+        if (kind == 0) {
+            i = j = K + idx;
+        } else {
+            i = pairs[2 * idx];
+            j = pairs[2 * idx + 1];
         }
-        for (int k = 0; k < 3; ++k)
-            if (tj[k] != u && tj[k] != v) cj = tj[k];
-        const int32_t pi[3] = {u, v, ci}, pj[3] = {u, v, cj};
-        Tri P, Q;
-        load_tri(verts, pi, P);
-        load_tri(verts, pj, Q);
-        I = ss_edge(P, Q, n);
-    } else {
-        int ki = 0, kj = 0;
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b)
-                if (ti[a] == tj[b]) {
-                    ki = a;
-                    kj = b;
-                }
-        const int32_t pi[3] = {ti[ki], ti[(ki + 1) % 3], ti[(ki + 2) % 3]};
-        const int32_t pj[3] = {tj[kj], tj[(kj + 1) % 3], tj[(kj + 2) % 3]};
-        Tri P, Q;
-        load_tri(verts, pi, P);
-        load_tri(verts, pj, Q);
-        I = ss_vertex(P, Q, n);
+        write = kind == 0 || j >= K;
     }
-    const double v = 4.0 * area[i] * area[j] * I * kInv4Pi;
-    const T e = Elem<T>::from_double(v);
-    V[i * ld + j] = e;
-    if (i != j) V[j * ld + i] = e;
+    if (write) {
+        const int32_t *ti = tris + 3 * i, *tj = tris + 3 * j;
+        if (kind == 0) {
+            Tri P;
+            load_tri(verts, ti, P);
+            I = ss_identical(P, n, sub);
+        } else if (kind == 2) {
+            // (u, v) = the shared vertices in the order they appear in triangle i
+            int32_t u = -1, v = -1, ci = -1, cj = -1;
+            for (int k = 0; k < 3; ++k) {
+                const bool in = (ti[k] == tj[0] || ti[k] == tj[1] || ti[k] == tj[2]);
+                if (in) {
+                    if (u < 0) u = ti[k];
+                    else v = ti[k];
+                } else {
+                    ci = ti[k];
+                }
+            }
+            for (int k = 0; k < 3; ++k)
+                if (tj[k] != u && tj[k] != v) cj = tj[k];
+            const int32_t pi[3] = {u, v, ci}, pj[3] = {u, v, cj};
+            Tri P, Q;
+            load_tri(verts, pi, P);
+            load_tri(verts, pj, Q);
+            I = ss_edge(P, Q, n, sub);
+        } else {
+            int ki = 0, kj = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b)
+                    if (ti[a] == tj[b]) {
+                        ki = a;
+                        kj = b;
+                    }
+            const int32_t pi[3] = {ti[ki], ti[(ki + 1) % 3], ti[(ki + 2) % 3]};
+            const int32_t pj[3] = {tj[kj], tj[(kj + 1) % 3], tj[(kj + 2) % 3]};
+            Tri P, Q;
+            load_tri(verts, pi, P);
+            load_tri(verts, pj, Q);
+            I = ss_vertex(P, Q, n, sub);
+        }
+    }
+    I += __shfl_xor_sync(0xffffffffu, I, 1);
+    I += __shfl_xor_sync(0xffffffffu, I, 2);
+    if (write && sub == 0) {
+        I = kind == 1 ? I / 3.0 : I / 6.0;
+        const double v = 4.0 * area[i] * area[j] * I * kInv4Pi;
+        const T e = Elem<T>::from_double(v);
+        V[i * ld + j] = e;
+        if (i != j) V[j * ld + i] = e;
+    }
 }
 
-// All touching pairs of an assembly in one launch: the common-vertex pairs (the longest
-// work per thread) first, then the common-edge pairs, then the identical pairs of the
-// new triangles, so that the three lists overlap instead of running one after another.
+// All touching pairs of an assembly in one launch, kNearGroup threads per pair: the
+// common-vertex pairs (the longest quadrature) first, then the common-edge pairs, then
+// the identical pairs of the new triangles, so that the three lists overlap instead of
+// running one after another.  Each list starts on a warp boundary (its pair count
+// rounded up to kNearPairsPerWarp), so that no warp runs two of the quadratures.
+constexpr int kNearPairsPerWarp = 32 / kNearGroup;
+inline int64_t near_pad(int64_t n) { return (n + kNearPairsPerWarp - 1) / kNearPairsPerWarp * kNearPairsPerWarp; }
+
 template <typename T>
 __global__ void k_near(const double *__restrict__ verts, const int32_t *__restrict__ tris,
                        const double *__restrict__ area, const int32_t *__restrict__ vert_pairs, int64_t n_vert,
                        const int32_t *__restrict__ edge_pairs, int64_t n_edge, int64_t n_ident, int64_t K, int n,
                        T *V, int64_t ld)
 {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx < n_vert) {
-        near_entry<T>(verts, tris, area, vert_pairs, idx, 1, K, n, V, ld);
-    } else if ((idx -= n_vert) < n_edge) {
-        near_entry<T>(verts, tris, area, edge_pairs, idx, 2, K, n, V, ld);
-    } else if ((idx -= n_edge) < n_ident) {
-        near_entry<T>(verts, tris, area, nullptr, idx, 0, K, n, V, ld);
+    const int64_t nvp = (n_vert + kNearPairsPerWarp - 1) / kNearPairsPerWarp * kNearPairsPerWarp;
+    const int64_t nep = (n_edge + kNearPairsPerWarp - 1) / kNearPairsPerWarp * kNearPairsPerWarp;
+    int64_t idx = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kNearGroup;
+    if (idx < nvp) {
+        near_entry<T>(verts, tris, area, vert_pairs, idx, 1, K, n, V, ld, idx < n_vert);
+    } else if ((idx -= nvp) < nep) {
+        near_entry<T>(verts, tris, area, edge_pairs, idx, 2, K, n, V, ld, idx < n_edge);
+    } else {
+        idx -= nep;
+        near_entry<T>(verts, tris, area, nullptr, idx, 0, K, n, V, ld, idx < n_ident);
     }
 }
 
@@ -912,9 +940,10 @@ static bem_status launch_near(bem_operator *op, int64_t K)
     bem_ctx *ctx = m->ctx;
     const int n = op->ss_order;
     const int prof = prof_start(ctx, BEM_KERNEL_NEAR, (double)(m->N - K + m->n_vert_pairs + m->n_edge_pairs));
-    const int64_t n_ident = m->N > K ? m->N - K : 0, total = m->n_vert_pairs + m->n_edge_pairs + n_ident;
+    const int64_t n_ident = m->N > K ? m->N - K : 0;
+    const int64_t total = near_pad(m->n_vert_pairs) + near_pad(m->n_edge_pairs) + n_ident;
     if (total > 0) {
-        k_near<T><<<nblk(total, 128), 128, 0, ctx->stream>>>(m->verts, m->tris, m->area, m->vert_pairs,
+        k_near<T><<<nblk(total * kNearGroup, 128), 128, 0, ctx->stream>>>(m->verts, m->tris, m->area, m->vert_pairs,
                                                              m->n_vert_pairs, m->edge_pairs, m->n_edge_pairs, n_ident,
                                                              K, n, (T *)op->V, op->ld);
         BEM_COUNT(ctx);
@@ -1040,23 +1069,24 @@ __global__ void k_mirror_batch(const BatchAsmProb *__restrict__ prob, const int6
 }
 
 // Item k of a problem: identical pairs [0, N), common-vertex pairs, common-edge pairs.
+// kNearGroup threads per item (every thread of a warp reaches near_entry's group sum).
 template <typename T>
 __global__ void k_near_batch(const BatchAsmProb *__restrict__ prob, const int64_t *__restrict__ pref, int P,
                              int64_t total, int n)
 {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= total) return;
-    const int p = batch_find(pref, P, k);
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kNearGroup;
+    const bool valid = k < total;
+    const int p = batch_find(pref, P, valid ? k : total - 1);
     const BatchAsmProb *pb = prob + p;
-    int64_t idx = k - pref[p];
+    int64_t idx = (valid ? k : total - 1) - pref[p];
     const int64_t N = pb->N;
     if (idx < N) {
-        near_entry<T>(pb->verts, pb->tris, pb->area, nullptr, idx, 0, 0, n, (T *)pb->V, pb->ld);
+        near_entry<T>(pb->verts, pb->tris, pb->area, nullptr, idx, 0, 0, n, (T *)pb->V, pb->ld, valid);
     } else if ((idx -= N) < pb->n_vert) {
-        near_entry<T>(pb->verts, pb->tris, pb->area, pb->vert_pairs, idx, 1, 0, n, (T *)pb->V, pb->ld);
+        near_entry<T>(pb->verts, pb->tris, pb->area, pb->vert_pairs, idx, 1, 0, n, (T *)pb->V, pb->ld, valid);
     } else {
         idx -= pb->n_vert;
-        near_entry<T>(pb->verts, pb->tris, pb->area, pb->edge_pairs, idx, 2, 0, n, (T *)pb->V, pb->ld);
+        near_entry<T>(pb->verts, pb->tris, pb->area, pb->edge_pairs, idx, 2, 0, n, (T *)pb->V, pb->ld, valid);
     }
 }
 
@@ -1137,7 +1167,8 @@ static bem_status batch_assemble_t(bem_ctx *ctx, const BatchAsm &b, cudaEvent_t 
     }
     if (ev && (st = record_timing_event(ctx, ev[2]))) return st;
     if (b.n_near > 0) {
-        k_near_batch<T><<<nblk(b.n_near, 128), 128, 0, s>>>(b.prob, b.near_pref, b.P, b.n_near, b.ss_order);
+        k_near_batch<T><<<nblk(b.n_near * kNearGroup, 128), 128, 0, s>>>(b.prob, b.near_pref, b.P, b.n_near,
+                                                                          b.ss_order);
         BEM_COUNT(ctx);
         BEM_CK_LAUNCH(ctx);
     }
