@@ -763,18 +763,31 @@ __global__ void k_near(const double *__restrict__ verts, const int32_t *__restri
 }
 
 // ------------------------------------------------------------------ reuse and diagonal
-// V'[i][j] = Vc[parent[i]][parent[j]] for i, j < K (unrefined triangles).
+// V'[i][j] = Vc[parent[i]][parent[j]] for i, j < K (unrefined triangles), by 64 x 64
+// tiles: CTA (bx, by) copies rows 64 by.. and columns 64 bx.., thread t column t % 64 and
+// the 16 rows 16 (t / 64).. of the tile (16 independent loads in flight; a warp reads
+// 32 nearly consecutive entries of a coarse row, the kept triangles keeping their
+// order).  upper: entries i <= j only (tiles below the diagonal return at once; the
+// kept triangles keep their order, so these come from the coarse operator's upper
+// triangle).
 template <typename T>
-__global__ void k_gather_kept(const T *__restrict__ Vc, int64_t ldc, const int32_t *__restrict__ parent,
-                              int64_t K, T *__restrict__ V, int64_t ld, int upper)
+__global__ void __launch_bounds__(256) k_gather_kept(const T *__restrict__ Vc, int64_t ldc,
+                                                     const int32_t *__restrict__ parent, int64_t K,
+                                                     T *__restrict__ V, int64_t ld, int upper)
 {
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (upper && blockIdx.y > blockIdx.x) return;
+    const int64_t j = (int64_t)blockIdx.x * 64 + (threadIdx.x & 63);
+    const int64_t i0 = (int64_t)blockIdx.y * 64 + 16 * (threadIdx.x >> 6);
     if (j >= K) return;
     const int64_t pj = parent[j];
-    // upper: entries i <= j only (the kept triangles keep their order, so these come
-    // from the coarse operator's upper triangle)
-    const int64_t iend = upper ? j + 1 : K;
-    for (int64_t i = blockIdx.y; i < iend; i += gridDim.y) V[i * ld + j] = Vc[(int64_t)parent[i] * ldc + pj];
+    const int64_t iend = upper ? (j + 1 < K ? j + 1 : K) : K;
+    T v[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+        if (i0 + r < iend) v[r] = Vc[(int64_t)parent[i0 + r] * ldc + pj];
+#pragma unroll
+    for (int r = 0; r < 16; ++r)
+        if (i0 + r < iend) V[(i0 + r) * ld + j] = v[r];
 }
 
 // Mirror of the diagonal 64 x 64 blocks only: 32 x 32 tiles (2D, 2D), (2D+1, 2D),
@@ -989,7 +1002,7 @@ static bem_status assemble_t(bem_operator *op, const bem_operator *coarse, bool 
     if (coarse) {
         K = m->n_kept;
         if (K > 0) {
-            dim3 grid(nblk(K, 256), (unsigned)(K < 65535 ? K : 65535));
+            dim3 grid(nblk(K, 64), nblk(K, 64));
             k_gather_kept<T><<<grid, 256, 0, ctx->stream>>>((const T *)coarse->V, coarse->ld, m->parent, K,
                                                             (T *)op->V, op->ld,
                                                             (upper || coarse->upper_only) ? 1 : 0); BEM_COUNT(ctx);
