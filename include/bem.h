@@ -71,10 +71,9 @@ typedef struct {
                           context times every variant on its own far-field block and the
                           context keeps the fastest; k = 1..BEM_FAR_TILE_VARIANTS: variant k,
                           rows x columns per CTA 32x256, 16x256, 64x256, 8x128, 16x128, 32x128,
-                          and (DF64: column points in shared memory instead of registers, at
-                          least m CTAs per SM) 8x128 m8, 16x128 m8, 32x128 m8, 8x128 m9,
-                          8x64 m16, 8x64 m18, and with the point loop unrolled 8x128 m6,
-                          32x128 m6 */
+                          and (DF64: point loops rolled, at least m CTAs per SM) 8x128 m8,
+                          16x128 m8, 32x128 m8, 8x128 m9, 8x64 m16, 8x64 m18, and with the
+                          point loops unrolled 8x128 m6, 32x128 m6 */
 } bem_assembly_opts;
 #define BEM_FAR_TILE_VARIANTS 14
 

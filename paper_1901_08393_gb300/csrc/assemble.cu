@@ -3,9 +3,10 @@
 //
 //  * Far field (no common vertex): 7 x 7 product of Radon's degree-5 rule,
 //      V_ij = |Ti||Tj|/(4pi) sum_a w_a sum_b w_b / |x_a - y_b|.
-//    One thread per column j holds its 7 points in registers; the CTA stages R
-//    row triangles in shared memory and walks them (broadcast reads; R x C tile
-//    variants, chosen per size class by timing them).  Only
+//    One thread per column j holds its 7 points (FP64, FP32: in registers; DF64: on
+//    the current pair's grid in shared memory); the CTA stages R row triangles in
+//    shared memory and walks them (broadcast reads; R x C tile variants, chosen per
+//    size class by timing them).  Only
 //    entries with i <= j are computed; the strict lower triangle is mirrored, so
 //    V is exactly symmetric and an incremental re-assembly reproduces the full
 //    one bit for bit.  Three arithmetic variants:
@@ -137,8 +138,8 @@ template <> struct Elem<float2> {
 // more, smaller CTAs) and on the arithmetic, and is chosen by timing (autotune).
 struct FarTileS {
     int rows, cols;
-    int min_ctas;  // DF64: > 0 -- column offsets in shared memory, this many CTAs per SM
-                   // requested (the other arithmetics use their register form)
+    int min_ctas;  // DF64: > 0 -- point loops rolled, this many CTAs per SM requested
+                   // (the other arithmetics use their unrolled register form)
 };
 constexpr FarTileS kFarTiles[kFarTileVariants] = {
     {32, 256, 0}, {16, 256, 0}, {64, 256, 0}, {8, 128, 0}, {16, 128, 0}, {32, 128, 0}, {8, 128, 8},
