@@ -870,10 +870,11 @@ __device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int6
     __shared__ float A[kBJ][kBJ + 1];
     __shared__ float B[kBJ][kBJ + 1];
     __shared__ double sc[kBJ], d0[kBJ];
+    __shared__ int32_t pk[kBJ];  // the cluster's rows, read once
     __shared__ int s_fail;
     const int t = threadIdx.x;
-    const int32_t *pk = perm + blk * kBJ;
     if (t == 0) s_fail = 0;
+    if (t < kBJ) pk[t] = perm[blk * kBJ + t];
     __syncthreads();
     if (t < kBJ) {
         const int32_t g = pk[t];
@@ -883,14 +884,22 @@ __device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int6
         sc[t] = d > 0.0 ? 1.0 / sqrt(d) : 1.0;
     }
     __syncthreads();
-    for (int idx = t; idx < kBJ * kBJ; idx += blockDim.x) {
-        const int i = idx / kBJ, j = idx % kBJ;
+    // 16 entries per thread (blockDim.x = 256), their scattered reads issued together
+    constexpr int kPer = kBJ * kBJ / 256;
+    double av[kPer];
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) {
+        const int idx = t + 256 * m, i = idx / kBJ, j = idx % kBJ;
         const int32_t gi = pk[i], gj = pk[j];
         // upper-triangle read: V (i, j) for i <= j (batch operators mirror only their
         // diagonal blocks; mirrored entries are bit-identical copies)
         const int64_t lo = gi < gj ? gi : gj, hi = gi < gj ? gj : gi;
-        const double a = (gi >= 0 && gj >= 0) ? elem_f64(V, lo * ld + hi) : (i == j ? 1.0 : 0.0);
-        A[i][j] = (float)(a * sc[i] * sc[j]);
+        av[m] = (gi >= 0 && gj >= 0) ? elem_f64(V, lo * ld + hi) : (i == j ? 1.0 : 0.0);
+    }
+#pragma unroll
+    for (int m = 0; m < kPer; ++m) {
+        const int idx = t + 256 * m, i = idx / kBJ, j = idx % kBJ;
+        A[i][j] = (float)(av[m] * sc[i] * sc[j]);
     }
     __syncthreads();
     const int ri = t >> 2, rc = t & 3;  // trailing update: row ri, columns rc + 4 m
@@ -899,17 +908,34 @@ __device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int6
         // every thread that scales column k takes the pivot itself (nothing writes A[k][k]
         // during step k; the factor's diagonal is stored after the loop), so the step
         // needs two barriers, not three
+        // the pivot's reciprocal square root scales the column (a multiplication instead
+        // of a division per entry); the factor's diagonal is d times it
         const float d = A[k][k];
-        const float dk = d > 0.f ? sqrtf(d) : 1.f;
+        const float rk = d > 0.f ? rsqrtf(d) : 1.f;
         if (t == 0) {
             if (!(d > 0.f)) s_fail = 1;
-            dg[k] = dk;
+            dg[k] = d > 0.f ? d * rk : 1.f;
         }
-        if (t > k && t < kBJ) A[t][k] /= dk;
+        if (t > k && t < kBJ) A[t][k] *= rk;
         __syncthreads();
         if (ri > k) {
+            // the row's entries and the column's, read before any is written (no shared
+            // load waits on a store of this thread)
             const float lik = A[ri][k];
-            for (int j = k + 1 + rc; j <= ri; j += 4) A[ri][j] -= lik * A[j][k];
+            float aj[kBJ / 4], cj[kBJ / 4];
+#pragma unroll
+            for (int m = 0; m < kBJ / 4; ++m) {
+                const int j = k + 1 + rc + 4 * m;
+                if (j <= ri) {
+                    aj[m] = A[j][k];
+                    cj[m] = A[ri][j];
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < kBJ / 4; ++m) {
+                const int j = k + 1 + rc + 4 * m;
+                if (j <= ri) A[ri][j] = cj[m] - lik * aj[m];
+            }
         }
         __syncthreads();
     }
@@ -924,13 +950,24 @@ __device__ __forceinline__ void block_inverse_body(const T *__restrict__ V, int6
         return;
     }
     if (t < kBJ) {  // column t of L^-1 (lower), forward substitution
+        // four partial sums over k (c + 4 q + r), so that four shared loads and FMAs are
+        // in flight instead of one dependent chain; (s0 + s1) + (s2 + s3) at the end
         const int c = t;
         for (int i = 0; i < kBJ; ++i) {
             float v = 0.f;
             if (i >= c) {
-                v = i == c ? 1.f : 0.f;
-                for (int k = c; k < i; ++k) v = __fmaf_rn(-A[i][k], B[k][c], v);
-                v /= A[i][i];
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                int k = c;
+                for (; k + 4 <= i; k += 4) {
+                    s0 = __fmaf_rn(A[i][k], B[k][c], s0);
+                    s1 = __fmaf_rn(A[i][k + 1], B[k + 1][c], s1);
+                    s2 = __fmaf_rn(A[i][k + 2], B[k + 2][c], s2);
+                    s3 = __fmaf_rn(A[i][k + 3], B[k + 3][c], s3);
+                }
+                if (k < i) s0 = __fmaf_rn(A[i][k], B[k][c], s0);
+                if (k + 1 < i) s1 = __fmaf_rn(A[i][k + 1], B[k + 1][c], s1);
+                if (k + 2 < i) s2 = __fmaf_rn(A[i][k + 2], B[k + 2][c], s2);
+                v = ((i == c ? 1.f : 0.f) - ((s0 + s1) + (s2 + s3))) / A[i][i];
             }
             B[i][c] = v;
         }
